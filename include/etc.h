@@ -1,0 +1,179 @@
+/*
+ * libetc -- effective thermal conductivity of a voxel RVE on one B300 GPU.
+ *
+ * C ABI of the hot path of Ye, Fu & Chung, "A fast cosine transformation
+ * accelerated method for predicting effective thermal conductivity"
+ * (arXiv 2404.02433):
+ *   - the problem (Sec. 2.1): -div(K grad p) = 0 on an Lx x Ly x Lz box with an
+ *     orthotropic diagonal K = diag(kx, ky, kz) > 0 per voxel, p = p_in on one
+ *     face, p = p_out on the opposite face, zero flux on the other four;
+ *   - its TPFA discretisation (Sec. 2.2, Eq. scaled bilinear forms): one unknown
+ *     per voxel, harmonic-mean face conductances, half-cell Dirichlet faces;
+ *   - PCG (Algorithm 1) preconditioned by the homogeneous reference operator
+ *     (Eq. refer bilinear forms), whose parameters come from the linear
+ *     programme of Algorithm 2 and which is inverted by 2-D cosine transforms
+ *     plus tridiagonal solves (Algorithm 3);
+ *   - the effective conductivity from the outflow (Eq. effective formula dis).
+ *
+ * Conventions common to every entry point:
+ *   - Voxel arrays are dense float64 in C order [nz][ny][nx] (x fastest), the
+ *     index set I_h of Sec. 2.2.  Pointers may be device, pinned-host or
+ *     pageable-host memory (the library copies with cudaMemcpyDefault).
+ *   - dir is the loading direction: 0 = x, 1 = y, 2 = z.  Internally the medium
+ *     is permuted so that the loading axis is the slowest ("loading frame"):
+ *     dir z keeps (x, y, z); dir y uses (x, z, y); dir x uses (y, z, x), listed
+ *     fastest to slowest.  Component entry points marked "loading frame" take
+ *     and return arrays in that permuted layout, [n2][n1][n0].
+ *   - Every function returns an etc_status, never throws and never exits.
+ *     Arguments are validated on the host before any GPU work; a rejected call
+ *     returns ETC_EINVAL and changes nothing.  After ETC_ECUDA the handle should
+ *     be destroyed.  etc_last_error() gives a one-line reason.
+ *   - A handle is used from one host thread at a time.  All its GPU work is
+ *     ordered on the stream given to etc_create_rve; calls that return numbers
+ *     to the host synchronise that stream before returning.
+ */
+#ifndef ETC_H
+#define ETC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etc_rve etc_rve;
+typedef int etc_status;
+
+enum {
+  ETC_OK = 0,
+  ETC_EINVAL = 1,      /* bad argument (size, length, kappa, p_in == p_out, dir) */
+  ETC_ENOMEM = 2,      /* device or pinned-host allocation failed */
+  ETC_ECUDA = 3,       /* a CUDA runtime call failed */
+  ETC_ENOCONV = 4,     /* maxit reached; results hold the last iterate */
+  ETC_EBREAKDOWN = 5,  /* non-finite or non-positive PCG scalar */
+  ETC_ESTATE = 6       /* call out of order (e.g. solution of an unsolved dir) */
+};
+
+/* Arithmetic of the preconditioner apply. */
+enum {
+  ETC_PREC_FP64 = 0,   /* everything in FP64: plain PCG (Algorithm 1) */
+  ETC_PREC_MIXED = 1   /* Algorithm 3 in FP32, the rest FP64, flexible PCG */
+};
+
+/* How the five reference parameters of Eq. (refer bilinear forms) are chosen. */
+enum {
+  ETC_REF_LP = 0,      /* optimum of the LP of Algorithm 2 (centred optimal point) */
+  ETC_REF_ONES = 1,    /* all equal to 1 (the paper's "one" setting, Sec. 4.4) */
+  ETC_REF_USER = 2     /* values given to etc_set_reference_params */
+};
+
+typedef struct {
+  double rtol;         /* exit when ||r||_2 <= rtol ||b||_2 (Eq. exit); default 1e-8 */
+  int maxit;           /* iteration cap; default 5000 */
+  int precision;       /* ETC_PREC_*; default ETC_PREC_FP64 */
+  int true_residual;   /* 1: also compute ||b - A p|| / ||b|| at exit; default 1 */
+} etc_opts;
+
+typedef struct {
+  int iters;           /* PCG iterations (products with A after the initial residual) */
+  int status;          /* ETC_OK, ETC_ENOCONV or ETC_EBREAKDOWN */
+  double relres;       /* ||r|| / ||b|| of the recursively updated residual */
+  double true_relres;  /* ||b - A p|| / ||b||, or -1 if not computed */
+  double kref[5];      /* reference parameters used: x, y, z, in, out of the
+                          loading frame, in units of kappa / h^2 (Sec. 2.2) */
+  double cond_bound;   /* Lambda''/Lambda' of Lemma 3.1 for kref */
+  double kappa_in;     /* effective conductivity from the inflow face */
+  double column[3];    /* K[:, dir] in physical axes x, y, z (see etc_effective_tensor) */
+  double t_setup_ms;   /* faces, LP, pivot tables */
+  double t_solve_ms;   /* PCG loop and post-processing */
+} etc_info;
+
+/* Fill *opts with the defaults listed in etc_opts. */
+etc_status etc_default_opts(etc_opts* opts);
+
+/*
+ * Create an RVE handle: copies the voxel conductivities (Sec. 2.2, arrays
+ * kappa^x, kappa^y, kappa^z on I_h) and allocates every device buffer the
+ * solve needs (about 14 doubles per voxel).
+ *   nx, ny, nz  >= 1 voxels per axis; lx, ly, lz > 0 box lengths (h = L / N).
+ *   kx          nx*ny*nz doubles; ky, kz the same, or NULL / equal to kx for an
+ *               isotropic medium (one array is then stored).  Every value must
+ *               be finite and > 0 (Sec. 2.1), else ETC_EINVAL.  The caller keeps
+ *               ownership; the arrays may be freed once this call returns.
+ *   stream      cudaStream_t to order all work of the handle (NULL = legacy).
+ *   out         receives the handle; unchanged on error.
+ */
+etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double lz,
+                          const double* kx, const double* ky, const double* kz,
+                          void* stream, etc_rve** out);
+
+/* Release every resource of the handle (NULL is accepted). */
+etc_status etc_destroy_rve(etc_rve* rve);
+
+/*
+ * Choose how kappa_ref is set for loading direction dir (Algorithm 2).
+ *   mode     ETC_REF_LP (default), ETC_REF_ONES or ETC_REF_USER.
+ *   kref_in  5 positive values (x, y, z, in, out of the loading frame, units of
+ *            kappa / h^2), read for ETC_REF_USER only.
+ *   kref_out if not NULL, receives the parameters that the next solve of dir
+ *            will use (this runs the face assembly of dir on the GPU).
+ */
+etc_status etc_set_reference_params(etc_rve* rve, int dir, int mode, const double* kref_in,
+                                    double* kref_out);
+
+/*
+ * Solve the TPFA system for loading direction dir with p = p_in on the low face
+ * and p_out on the high face of that axis (Sec. 2.1), by PCG with initial guess
+ * 0, and return the effective conductivity kappa_eff (Eq. effective formula dis,
+ * outflow side).  opts may be NULL (defaults).  info may be NULL.
+ * p_in == p_out is rejected (Sec. 2.1).  ETC_ENOCONV still fills kappa_eff and
+ * info from the last iterate.
+ */
+etc_status etc_solve_direction(etc_rve* rve, int dir, double p_in, double p_out,
+                               const etc_opts* opts, double* kappa_eff, etc_info* info);
+
+/* Copy the solution p of the last solve of dir into dst (nx*ny*nz doubles, the
+ * ORIGINAL [nz][ny][nx] layout, device or host memory).  ETC_ESTATE if dir has
+ * not been solved. */
+etc_status etc_get_solution(etc_rve* rve, int dir, double* dst);
+
+/*
+ * Three solves (dir = x, y, z, p_in = 1, p_out = 0) giving the 3x3 tensor
+ * K[a*3 + b] = L^b <v_a> / (p_in - p_out) under load b, where <v_a> is the
+ * volume average of the cell-averaged a-face fluxes of Eq. (flux) (Neumann faces
+ * carry zero flux).  The diagonal is the outflow formula of Eq. (effective
+ * formula dis).  The off-diagonal entries are this library's definition: the
+ * paper defers the full tensor to a citation (Sec. 2.1).  info may be NULL,
+ * else receives 3 records.
+ */
+etc_status etc_effective_tensor(etc_rve* rve, const etc_opts* opts, double* K,
+                                etc_info* info);
+
+/* Loading-frame sizes (n0, n1, n2) of direction dir. */
+etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);
+
+/*
+ * Component entry points (loading frame of dir, device pointers, n0*n1*n2
+ * doubles each, in/out must not overlap).  They run the same kernels as the
+ * solve and exist so that each kernel can be checked on its own.
+ */
+
+/* q = A w: the TPFA operator of Eq. (scaled bilinear forms) for direction dir. */
+etc_status etc_apply_operator(etc_rve* rve, int dir, const double* w, double* q);
+
+/* z = A_ref^{-1} r by Algorithm 3 with the kref that the next solve of dir uses;
+ * precision = ETC_PREC_FP64 or ETC_PREC_MIXED (FP32 transforms and solves). */
+etc_status etc_apply_preconditioner(etc_rve* rve, int dir, int precision, const double* r,
+                                    double* z);
+
+/* Per plane k, the 2-D transform over axes 0 and 1 of the loading frame:
+ * inverse == 0 applies Eq. (forward DCT) along both axes, inverse == 1 applies
+ * Eq. (backward DCT) along both axes (FP64). */
+etc_status etc_dct_planes(etc_rve* rve, int dir, int inverse, const double* in, double* out);
+
+const char* etc_status_string(etc_status status);
+const char* etc_last_error(const etc_rve* rve);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETC_H */

@@ -1,0 +1,775 @@
+// Host side of libetc: the C ABI declared in include/etc.h.
+//
+// A handle owns the voxel conductivities, the per-direction face arrays, the
+// PCG vectors, the cosine-transform tables and a small device state block.  A
+// solve (Sec. 2.2 "complete routine") is: permute to the loading frame, face
+// assembly with group extrema (K-setup), reference parameters on the host
+// (Algorithm 2), pivot tables of the tridiagonal systems, then PCG
+// (Algorithm 1 with Algorithm 3) on the handle's stream, then the outflow
+// formula (Eq. effective formula dis).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/etc.h"
+#include "dct_device.cuh"
+#include "etc_internal.cuh"
+#include "launchers.h"
+
+using namespace etc;
+
+namespace {
+
+struct PlanStore {
+  DctPlan<double> p64;
+  DctPlan<float> p32;
+  double* lam = nullptr;   // device, n: 4 sin^2(pi k / 2n)
+  void* mem64 = nullptr;   // device table blocks
+  void* mem32 = nullptr;
+};
+
+}  // namespace
+
+struct etc_rve {
+  int nx = 0, ny = 0, nz = 0;
+  double L[3] = {1, 1, 1};
+  long long n = 0;
+  long long plane_max = 0;
+  cudaStream_t stream = nullptr;
+  bool iso = true;
+  double* kap[3] = {nullptr, nullptr, nullptr};
+  // working set (loading frame of the current direction)
+  double *T0 = nullptr, *T1 = nullptr, *T2 = nullptr, *D = nullptr;
+  double *Bin = nullptr, *Bout = nullptr;
+  double *r = nullptr, *q = nullptr, *w[2] = {nullptr, nullptr}, *t64 = nullptr, *h64 = nullptr;
+  double* z64 = nullptr;
+  float *t32 = nullptr, *h32 = nullptr, *z32 = nullptr;
+  double* kperm[3] = {nullptr, nullptr, nullptr};  // views into scratch during setup
+  double* xsol[3] = {nullptr, nullptr, nullptr};
+  double* partials = nullptr;
+  size_t npartials = 0;
+  PcgState* st = nullptr;        // device
+  PcgState* st_host = nullptr;   // pinned, 3 slots: [0] upload, [1], [2] readback
+  std::map<int, PlanStore> plans;
+  int setup_dir = -1;            // direction whose faces are in T0..Bout
+  bool have_ext = false;
+  double ext[10];
+  int ref_mode[3] = {ETC_REF_LP, ETC_REF_LP, ETC_REF_LP};
+  double kref_user[3][5];
+  int pivots_for = -1;           // direction whose pivot tables are built
+  int pivots_prec = -1;
+  double pivots_kref[5];
+  bool solved[3] = {false, false, false};
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ errors
+etc_status fail(etc_rve* h, etc_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? ETC_ENOMEM : ETC_ECUDA,           \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+// Allocation-failure injection for tests: ETC_FAIL_ALLOC_AFTER=k makes the
+// (k+1)-th device allocation of a handle report out-of-memory.
+int alloc_budget() {
+  const char* s = std::getenv("ETC_FAIL_ALLOC_AFTER");
+  return s ? std::atoi(s) : -1;
+}
+
+cudaError_t dev_alloc(etc_rve* h, void** p, size_t bytes) {
+  static thread_local int count = 0;
+  const int budget = alloc_budget();
+  if (budget >= 0) {
+    if ((int)h->allocs.size() >= budget) return cudaErrorMemoryAllocation;
+  }
+  (void)count;
+  cudaError_t e = cudaMalloc(p, bytes == 0 ? 16 : bytes);
+  if (e == cudaSuccess) h->allocs.push_back(*p);
+  return e;
+}
+
+template <typename T>
+cudaError_t dalloc(etc_rve* h, T** p, size_t count) {
+  return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void release(etc_rve* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->st_host) cudaFreeHost(h->st_host);
+  h->st_host = nullptr;
+}
+
+// ------------------------------------------------------------------ plans
+// Radices of the Stockham FFT of length m (8 first, 3 and 5 last); false if m
+// has a prime factor above 5.
+bool factor(int m, int* rad, int* nst) {
+  int e2 = 0, e3 = 0, e5 = 0, v = m;
+  while (v % 2 == 0) { v /= 2; ++e2; }
+  while (v % 3 == 0) { v /= 3; ++e3; }
+  while (v % 5 == 0) { v /= 5; ++e5; }
+  if (v != 1) return false;
+  std::vector<int> r;
+  while (e2 >= 3) { r.push_back(8); e2 -= 3; }
+  if (e2 == 2) r.push_back(4);
+  if (e2 == 1) {
+    if (!r.empty() && r.back() == 8) { r.back() = 4; r.push_back(4); }
+    else r.push_back(2);
+  }
+  for (int i = 0; i < e3; ++i) r.push_back(3);
+  for (int i = 0; i < e5; ++i) r.push_back(5);
+  if ((int)r.size() > kMaxStages) return false;
+  *nst = (int)r.size();
+  for (int i = 0; i < *nst; ++i) rad[i] = r[i];
+  return true;
+}
+
+// Host tables in long double, rounded once to the device type.
+template <typename R>
+cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** mem) {
+  const int n = s.n, m = s.m;
+  const size_t ntw = s.fft ? 2 * (size_t)m : 0;
+  const size_t npost = s.fft ? 4 * (size_t)(m + 1) : 0;
+  const size_t ncos = 4 * (size_t)n;
+  std::vector<R> buf(ntw + 2 * npost + ncos);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  R* tw = buf.data();
+  R* fp = tw + ntw;
+  R* ip = fp + npost;
+  R* cq = ip + npost;
+  for (int j = 0; j < (int)(ntw / 2); ++j) {
+    const long double a = -2.0L * pi * j / m;
+    tw[2 * j] = (R)cosl(a);
+    tw[2 * j + 1] = (R)sinl(a);
+  }
+  if (s.fft)
+    for (int k = 0; k <= m; ++k) {
+      const long double th = pi * k / (2.0L * n);
+      fp[4 * k + 0] = (R)(cosl(th) / 2);
+      fp[4 * k + 1] = (R)(sinl(th) / 2);
+      fp[4 * k + 2] = (R)(cosl(5 * th) / 2);
+      fp[4 * k + 3] = (R)(sinl(5 * th) / 2);
+      ip[4 * k + 0] = (R)(cosl(th) / (2.0L * m));
+      ip[4 * k + 1] = (R)(sinl(th) / (2.0L * m));
+      ip[4 * k + 2] = (R)cosl(4 * th);
+      ip[4 * k + 3] = (R)sinl(4 * th);
+    }
+  for (int q = 0; q < 4 * n; ++q) cq[q] = (R)cosl(pi * q / (2.0L * n));
+  R* d = nullptr;
+  cudaError_t e = dalloc(h, &d, buf.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(d, buf.data(), buf.size() * sizeof(R), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  t->tw = d;
+  t->fpost = d + ntw;
+  t->ipre = d + ntw + npost;
+  t->cosq = d + ntw + 2 * npost;
+  *mem = d;
+  return cudaSuccess;
+}
+
+etc_status make_plan(etc_rve* h, int n) {
+  if (h->plans.count(n)) return ETC_OK;
+  PlanStore ps;
+  DctShape s;
+  std::memset(&s, 0, sizeof(s));
+  s.n = n;
+  s.m = n / 2;
+  s.fft = (n % 2 == 0) && factor(s.m, s.radix, &s.nst);
+  if (!s.fft) { s.nst = 0; s.m = n / 2; }
+  ps.p64.s = s;
+  ps.p32.s = s;
+  CK(build_tables<double>(h, s, &ps.p64.t, &ps.mem64));
+  CK(build_tables<float>(h, s, &ps.p32.t, &ps.mem32));
+  std::vector<double> lam(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int k = 0; k < n; ++k) {
+    const long double sv = sinl(pi * k / (2.0L * n));
+    lam[k] = (double)(4.0L * sv * sv);
+  }
+  CK(dalloc(h, &ps.lam, (size_t)n));
+  CK(cudaMemcpy(ps.lam, lam.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  h->plans[n] = ps;
+  return ETC_OK;
+}
+
+// ------------------------------------------------------------------ frames
+// Physical axes (x=0,y=1,z=2) of the loading frame, fastest to slowest.
+void frame_of(int dir, int f[3]) {
+  if (dir == 2) { f[0] = 0; f[1] = 1; f[2] = 2; }
+  else if (dir == 1) { f[0] = 0; f[1] = 2; f[2] = 1; }
+  else { f[0] = 1; f[1] = 2; f[2] = 0; }
+}
+
+Geometry geom_of(const etc_rve* h, int dir) {
+  int f[3];
+  frame_of(dir, f);
+  const int N[3] = {h->nx, h->ny, h->nz};
+  Geometry g;
+  g.n0 = N[f[0]];
+  g.n1 = N[f[1]];
+  g.n2 = N[f[2]];
+  g.plane = (long long)g.n0 * g.n1;
+  g.n = g.plane * g.n2;
+  return g;
+}
+
+// Original-layout strides of physical axis a.
+long long phys_stride(const etc_rve* h, int a) {
+  return a == 0 ? 1 : (a == 1 ? (long long)h->nx : (long long)h->nx * h->ny);
+}
+
+cudaError_t to_frame(etc_rve* h, int dir, const double* in, double* out) {
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  return launch_permute(in, out, g.n0, g.n1, g.n2, phys_stride(h, f[0]), phys_stride(h, f[1]),
+                        phys_stride(h, f[2]), h->stream);
+}
+
+cudaError_t from_frame(etc_rve* h, int dir, const double* in, double* out) {
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  long long sf[3] = {1, g.n0, g.plane};  // frame strides of frame axes 0,1,2
+  long long s[3];
+  for (int a = 0; a < 3; ++a)
+    for (int l = 0; l < 3; ++l)
+      if (f[l] == a) s[a] = sf[l];
+  return launch_permute(in, out, h->nx, h->ny, h->nz, s[0], s[1], s[2], h->stream);
+}
+
+// ------------------------------------------------------------------ setup of a direction
+etc_status read_state(etc_rve* h, int slot) {
+  CK(cudaMemcpyAsync(&h->st_host[slot], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+etc_status setup_faces(etc_rve* h, int dir) {
+  if (h->setup_dir == dir) return ETC_OK;
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  const int N[3] = {h->nx, h->ny, h->nz};
+  double* comp[3];
+  // loading-frame component along frame axis l is kappa^{f[l]}
+  double* scratch[3] = {h->t64, h->z64, h->q};
+  for (int l = 0; l < 3; ++l) {
+    const double* src = h->kap[f[l]];
+    bool reuse = false;
+    for (int p = 0; p < l; ++p)
+      if (h->kap[f[p]] == src) { comp[l] = comp[p]; reuse = true; }
+    if (reuse) continue;
+    if (dir == 2) comp[l] = const_cast<double*>(src);
+    else {
+      CK(to_frame(h, dir, src, scratch[l]));
+      comp[l] = scratch[l];
+    }
+  }
+  const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
+  CK(launch_faces(g, 1.0 / (hh[0] * hh[0]), 1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), comp[0],
+                  comp[1], comp[2], h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, h->partials,
+                  h->st, h->stream));
+  etc_status s = read_state(h, 1);
+  if (s != ETC_OK) return s;
+  std::memcpy(h->ext, h->st_host[1].ext, sizeof(h->ext));
+  h->setup_dir = dir;
+  h->pivots_for = -1;
+  return ETC_OK;
+}
+
+// Algorithm 2: centred optimum of the LP, kappa_ref^g = sqrt(min_g max_g);
+// a group without faces gets 1.
+void lp_reference(const double* ext, double* kref) {
+  for (int gi = 0; gi < 5; ++gi) {
+    const double lo = ext[2 * gi], hi = ext[2 * gi + 1];
+    kref[gi] = (std::isfinite(lo) && std::isfinite(hi) && lo > 0) ? std::sqrt(lo * hi) : 1.0;
+  }
+}
+
+double cond_bound_of(const double* ext, const double* kref) {
+  double lo = INFINITY, hi = 0.0;
+  for (int gi = 0; gi < 5; ++gi) {
+    if (!std::isfinite(ext[2 * gi]) || !(ext[2 * gi] > 0)) continue;
+    lo = std::fmin(lo, ext[2 * gi] / kref[gi]);
+    hi = std::fmax(hi, ext[2 * gi + 1] / kref[gi]);
+  }
+  return hi / lo;
+}
+
+void reference_for(etc_rve* h, int dir, double* kref) {
+  if (h->ref_mode[dir] == ETC_REF_USER) std::memcpy(kref, h->kref_user[dir], 5 * sizeof(double));
+  else if (h->ref_mode[dir] == ETC_REF_ONES) for (int i = 0; i < 5; ++i) kref[i] = 1.0;
+  else lp_reference(h->ext, kref);
+}
+
+etc_status setup_pivots(etc_rve* h, int dir, int prec, const double* kref) {
+  if (h->pivots_for == dir && h->pivots_prec == prec &&
+      std::memcmp(h->pivots_kref, kref, sizeof(h->pivots_kref)) == 0)
+    return ETC_OK;
+  const Geometry g = geom_of(h, dir);
+  const PlanStore& p0 = h->plans[g.n0];
+  const PlanStore& p1 = h->plans[g.n1];
+  if (prec == ETC_PREC_FP64) CK(launch_pivots<double>(g, p0.lam, p1.lam, kref, h->h64, h->stream));
+  else CK(launch_pivots<float>(g, p0.lam, p1.lam, kref, h->h32, h->stream));
+  h->pivots_for = dir;
+  h->pivots_prec = prec;
+  std::memcpy(h->pivots_kref, kref, sizeof(h->pivots_kref));
+  return ETC_OK;
+}
+
+// ------------------------------------------------------------------ preconditioner chain
+// t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal,
+// inverse y, inverse x into z.
+template <typename R, typename TZ>
+etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
+                        const DctPlan<R>& p1, R* t, const R* hp, TZ* z, double kz, int mode,
+                        int par, int flex) {
+  const int check = (mode == 1);
+  CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream));
+  const double wscale = 4.0 / ((double)g.n0 * g.n1 * kz);
+  CK(launch_tridiag<R>(g, h->st, t, hp, wscale, h->partials, mode, h->stream));
+  CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream));
+  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, z, h->q, 1.0 / kz, par, check, flex, h->partials,
+                          h->stream)));
+  return ETC_OK;
+}
+
+etc_status validate_opts(etc_rve* h, const etc_opts* o) {
+  if (!(o->rtol > 0.0) || !std::isfinite(o->rtol))
+    return fail(h, ETC_EINVAL, "rtol must be finite and > 0");
+  if (o->maxit < 1) return fail(h, ETC_EINVAL, "maxit must be >= 1");
+  if (o->precision != ETC_PREC_FP64 && o->precision != ETC_PREC_MIXED)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  return ETC_OK;
+}
+
+// One PCG iteration (par = parity of the iteration index).
+etc_status launch_iteration(etc_rve* h, const Geometry& g, int dir, int prec, double kz,
+                            int par) {
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  double* x = h->xsol[dir];
+  if (prec == ETC_PREC_FP64) {
+    CK(launch_matvec<double>(g, h->st, h->z64, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
+                             h->T2, h->D, h->partials, par, 1, h->stream));
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[par], h->q, h->r, nullptr, h->t64,
+                            h->partials, par, 0.0, 1, h->stream));
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, par,
+                                        0);
+  }
+  CK(launch_matvec<float>(g, h->st, h->z32, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1, h->T2,
+                          h->D, h->partials, par, 1, h->stream));
+  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[par], h->q, h->r, nullptr, h->t32,
+                         h->partials, par, 0.0, 1, h->stream));
+  return precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, par, 1);
+}
+
+etc_status check_dir(etc_rve* h, int dir) {
+  if (dir < 0 || dir > 2) return fail(h, ETC_EINVAL, "dir must be 0, 1 or 2");
+  return ETC_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+etc_status etc_default_opts(etc_opts* o) {
+  if (!o) return ETC_EINVAL;
+  o->rtol = 1e-8;
+  o->maxit = 5000;
+  o->precision = ETC_PREC_FP64;
+  o->true_residual = 1;
+  return ETC_OK;
+}
+
+const char* etc_status_string(etc_status s) {
+  switch (s) {
+    case ETC_OK: return "ok";
+    case ETC_EINVAL: return "invalid argument";
+    case ETC_ENOMEM: return "out of memory";
+    case ETC_ECUDA: return "CUDA error";
+    case ETC_ENOCONV: return "no convergence within maxit";
+    case ETC_EBREAKDOWN: return "PCG breakdown (non-finite or non-positive scalar)";
+    case ETC_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* etc_last_error(const etc_rve* h) { return h ? h->err.c_str() : ""; }
+
+etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double lz,
+                          const double* kx, const double* ky, const double* kz, void* stream,
+                          etc_rve** out) {
+  etc_rve* h = nullptr;
+  if (!out) return ETC_EINVAL;
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 8192 || ny > 8192 || nz > 8192) return ETC_EINVAL;
+  if (!(lx > 0) || !(ly > 0) || !(lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) ||
+      !std::isfinite(lz))
+    return ETC_EINVAL;
+  if (!kx) return ETC_EINVAL;
+  const long long n = (long long)nx * ny * nz;
+  if (n > (1LL << 34)) return ETC_EINVAL;
+  h = new etc_rve();
+  h->nx = nx; h->ny = ny; h->nz = nz;
+  h->L[0] = lx; h->L[1] = ly; h->L[2] = lz;
+  h->n = n;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  h->iso = (ky == nullptr || ky == kx) && (kz == nullptr || kz == kx);
+  h->plane_max = std::max((long long)nx * ny, std::max((long long)ny * nz, (long long)nx * nz));
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < 5; ++i) h->kref_user[d][i] = 1.0;
+  auto bail = [&](etc_status s) { release(h); delete h; return s; };
+  etc_status s = ETC_OK;
+#define CKC(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(e_ == cudaErrorMemoryAllocation ? ETC_ENOMEM : ETC_ECUDA);               \
+  } while (0)
+  // conductivities
+  const double* src[3] = {kx, ky ? ky : kx, kz ? kz : kx};
+  const int ncomp = h->iso ? 1 : 3;
+  for (int c = 0; c < ncomp; ++c) {
+    CKC(dalloc(h, &h->kap[c], (size_t)n));
+    CKC(cudaMemcpyAsync(h->kap[c], src[c], n * sizeof(double), cudaMemcpyDefault, h->stream));
+  }
+  if (h->iso) h->kap[1] = h->kap[2] = h->kap[0];
+  // working set; face arrays carry one extra zero plane for the matvec halo
+  const size_t nt = (size_t)n + (size_t)h->plane_max + 64;
+  CKC(dalloc(h, &h->T0, nt)); CKC(dalloc(h, &h->T1, nt)); CKC(dalloc(h, &h->T2, nt));
+  CKC(dalloc(h, &h->D, (size_t)n));
+  CKC(cudaMemsetAsync(h->T0, 0, nt * sizeof(double), h->stream));
+  CKC(cudaMemsetAsync(h->T1, 0, nt * sizeof(double), h->stream));
+  CKC(cudaMemsetAsync(h->T2, 0, nt * sizeof(double), h->stream));
+  CKC(dalloc(h, &h->Bin, (size_t)h->plane_max)); CKC(dalloc(h, &h->Bout, (size_t)h->plane_max));
+  CKC(dalloc(h, &h->r, (size_t)n)); CKC(dalloc(h, &h->q, (size_t)n));
+  CKC(dalloc(h, &h->w[0], (size_t)n)); CKC(dalloc(h, &h->w[1], (size_t)n));
+  CKC(dalloc(h, &h->t64, (size_t)n)); CKC(dalloc(h, &h->h64, (size_t)n));
+  CKC(dalloc(h, &h->z64, (size_t)n));
+  // FP32 buffers of the mixed path alias nothing: they are small next to FP64
+  CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
+  CKC(dalloc(h, &h->z32, (size_t)n));
+  // partials: the largest reduction grid over the three directions
+  size_t np = 1024;
+  for (int d = 0; d < 3; ++d) {
+    const Geometry g = geom_of(h, d);
+    np = std::max<size_t>(np, matvec_blocks(g));
+    np = std::max<size_t>(np, fwd_x_blocks(g, 4));
+    np = std::max<size_t>(np, fwd_x_blocks(g, 8));
+    np = std::max<size_t>(np, tridiag_blocks(g));
+  }
+  np = std::max<size_t>(np, 148 * 32);
+  h->npartials = np * 10;
+  CKC(dalloc(h, &h->partials, h->npartials));
+  CKC(dalloc(h, &h->st, 1));
+  CKC(cudaMemsetAsync(h->st, 0, sizeof(PcgState), h->stream));
+  {
+    cudaError_t e = cudaMallocHost(&h->st_host, 3 * sizeof(PcgState));
+    if (e != cudaSuccess) { h->st_host = nullptr; return bail(ETC_ENOMEM); }
+  }
+  CKC(set_smem_attrs<double>());
+  CKC(set_smem_attrs<float>());
+  for (int ax : {nx, ny, nz}) {
+    s = make_plan(h, ax);
+    if (s != ETC_OK) return bail(s);
+  }
+  // validation of the conductivities (Sec. 2.1: bounded between positive constants)
+  for (int c = 0; c < ncomp; ++c) CKC(launch_kappa_stats(h->kap[c], n, h->partials, h->st, c, h->stream));
+  CKC(cudaMemcpyAsync(&h->st_host[1], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost, h->stream));
+  CKC(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < ncomp; ++c)
+    if (h->st_host[1].ext[3 * c + 2] != 0.0) {
+      release(h); delete h;
+      return ETC_EINVAL;
+    }
+#undef CKC
+  *out = h;
+  return ETC_OK;
+}
+
+etc_status etc_destroy_rve(etc_rve* h) {
+  if (!h) return ETC_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  release(h);
+  delete h;
+  return ETC_OK;
+}
+
+etc_status etc_loading_dims(const etc_rve* h, int dir, int* dims) {
+  if (!h || !dims || dir < 0 || dir > 2) return ETC_EINVAL;
+  const Geometry g = geom_of(h, dir);
+  dims[0] = g.n0; dims[1] = g.n1; dims[2] = g.n2;
+  return ETC_OK;
+}
+
+etc_status etc_set_reference_params(etc_rve* h, int dir, int mode, const double* kin,
+                                    double* kout) {
+  if (!h) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (mode != ETC_REF_LP && mode != ETC_REF_ONES && mode != ETC_REF_USER)
+    return fail(h, ETC_EINVAL, "unknown reference-parameter mode");
+  if (mode == ETC_REF_USER) {
+    if (!kin) return fail(h, ETC_EINVAL, "kref_in is NULL");
+    for (int i = 0; i < 5; ++i)
+      if (!(kin[i] > 0) || !std::isfinite(kin[i]))
+        return fail(h, ETC_EINVAL, "kref_in values must be finite and > 0");
+    std::memcpy(h->kref_user[dir], kin, 5 * sizeof(double));
+  }
+  h->ref_mode[dir] = mode;
+  if (kout) {
+    s = setup_faces(h, dir);
+    if (s != ETC_OK) return s;
+    reference_for(h, dir, kout);
+  }
+  return ETC_OK;
+}
+
+etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
+                               const etc_opts* opts_in, double* kappa_eff, etc_info* info) {
+  if (!h) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (!std::isfinite(p_in) || !std::isfinite(p_out) || p_in == p_out)
+    return fail(h, ETC_EINVAL, "p_in and p_out must be finite and different (Sec. 2.1)");
+  etc_opts o;
+  etc_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  s = validate_opts(h, &o);
+  if (s != ETC_OK) return s;
+  const int prec = o.precision;
+  const Geometry g = geom_of(h, dir);
+  int f[3];
+  frame_of(dir, f);
+  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  double* x = h->xsol[dir];
+
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1)); CK(cudaEventCreate(&e2));
+  CK(cudaEventRecord(e0, h->stream));
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  double kref[5];
+  reference_for(h, dir, kref);
+  s = setup_pivots(h, dir, prec, kref);
+  if (s != ETC_OK) return s;
+  CK(cudaEventRecord(e1, h->stream));
+
+  // initial state
+  PcgState& up = h->st_host[0];
+  std::memset(&up, 0, sizeof(PcgState));
+  up.maxit = o.maxit;
+  up.flexible = (prec == ETC_PREC_MIXED);
+  CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_init(g, h->Bin, h->Bout, p_in, p_out, h->r, x, h->w[1], h->stream));
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  const double kz = kref[2];
+  if (prec == ETC_PREC_FP64) {
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
+                            h->partials, 0, o.rtol * o.rtol, 0, h->stream));
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, 1, 0);
+  } else {
+    CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
+                           h->partials, 0, o.rtol * o.rtol, 0, h->stream));
+    s = precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, 1, 0);
+  }
+  if (s != ETC_OK) return s;
+
+  // PCG loop: chunks of iterations run ahead; the host reads the device state
+  // of the previous chunk while the next one executes.
+  int launched = 0;
+  int slot = 1;
+  bool have_prev = false;
+  int prev_slot = 2;
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+  int chunk = 2;
+  const long long hard_cap = (long long)o.maxit + 64;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      s = launch_iteration(h, g, dir, prec, kz, launched & 1);
+      if (s != ETC_OK) return s;
+      ++launched;
+    }
+    CK(cudaMemcpyAsync(&h->st_host[slot], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaEventRecord(ev[slot], h->stream));
+    if (have_prev) {
+      CK(cudaEventSynchronize(ev[prev_slot]));
+      if (h->st_host[prev_slot].done) break;
+    }
+    have_prev = true;
+    prev_slot = slot;
+    slot = (slot == 1) ? 2 : 1;
+    if (chunk < 16) chunk *= 2;
+    if (launched > hard_cap) {
+      CK(cudaEventSynchronize(ev[prev_slot]));
+      if (h->st_host[prev_slot].done) break;
+      return fail(h, ETC_ECUDA, "PCG did not report completion within maxit iterations");
+    }
+  }
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+
+  // post-processing
+  CK(launch_flux(g, x, h->T0, h->T1, h->T2, h->Bin, h->Bout, p_in, p_out, h->partials, h->st,
+                 h->stream));
+  if (o.true_residual)
+    CK(launch_true_residual(g, x, h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, p_in, p_out,
+                            h->partials, h->st, h->stream));
+  CK(cudaEventRecord(e2, h->stream));
+  s = read_state(h, 1);
+  if (s != ETC_OK) return s;
+  const PcgState& st = h->st_host[1];
+  float ms_setup = 0, ms_solve = 0;
+  cudaEventElapsedTime(&ms_setup, e0, e1);
+  cudaEventElapsedTime(&ms_solve, e1, e2);
+  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+
+  const int N[3] = {h->nx, h->ny, h->nz};
+  const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
+  const double dp = p_in - p_out;
+  const double L2 = h->L[f[2]];
+  const double keff = L2 * hh[2] * st.res[3] / ((double)g.plane * dp);
+  const double kin_v = L2 * hh[2] * st.res[4] / ((double)g.plane * dp);
+  double vbar[3];
+  vbar[0] = hh[0] * st.res[0] / (double)g.n;
+  vbar[1] = hh[1] * st.res[1] / (double)g.n;
+  vbar[2] = hh[2] * (st.res[2] + 0.5 * st.res[3] + 0.5 * st.res[4]) / (double)g.n;
+  if (kappa_eff) *kappa_eff = keff;
+  if (info) {
+    info->iters = st.iter;
+    info->status = st.status;
+    info->relres = std::sqrt(st.rr / st.bb);
+    info->true_relres = o.true_residual ? std::sqrt(st.res[5] / st.bb) : -1.0;
+    std::memcpy(info->kref, kref, sizeof(kref));
+    info->cond_bound = cond_bound_of(h->ext, kref);
+    info->kappa_in = kin_v;
+    for (int l = 0; l < 3; ++l) info->column[f[l]] = h->L[dir] * vbar[l] / dp;
+    info->t_setup_ms = ms_setup;
+    info->t_solve_ms = ms_solve;
+  }
+  h->solved[dir] = true;
+  if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
+  if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
+  return ETC_OK;
+}
+
+etc_status etc_get_solution(etc_rve* h, int dir, double* dst) {
+  if (!h || !dst) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (!h->solved[dir]) return fail(h, ETC_ESTATE, "direction not solved");
+  if (dir == 2) {
+    CK(cudaMemcpyAsync(dst, h->xsol[dir], h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+  } else {
+    // un-permute into scratch, then copy to the caller (device or host)
+    CK(from_frame(h, dir, h->xsol[dir], h->t64));
+    CK(cudaMemcpyAsync(dst, h->t64, h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+etc_status etc_effective_tensor(etc_rve* h, const etc_opts* opts, double* K, etc_info* info) {
+  if (!h || !K) return ETC_EINVAL;
+  etc_status worst = ETC_OK;
+  for (int b = 0; b < 3; ++b) {
+    double keff = 0;
+    etc_info inf;
+    etc_status s = etc_solve_direction(h, b, 1.0, 0.0, opts, &keff, &inf);
+    if (s != ETC_OK && s != ETC_ENOCONV && s != ETC_EBREAKDOWN) return s;
+    if (s != ETC_OK) worst = s;
+    for (int a = 0; a < 3; ++a) K[3 * a + b] = inf.column[a];
+    K[3 * b + b] = keff;
+    if (info) info[b] = inf;
+  }
+  return worst;
+}
+
+etc_status etc_apply_operator(etc_rve* h, int dir, const double* w, double* q) {
+  if (!h || !w || !q) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  const Geometry g = geom_of(h, dir);
+  CK(launch_matvec<double>(g, h->st, w, nullptr, nullptr, q, h->T0, h->T1, h->T2, h->D,
+                           h->partials, 0, 0, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double* r, double* z) {
+  if (!h || !r || !z) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  double kref[5];
+  reference_for(h, dir, kref);
+  s = setup_pivots(h, dir, prec, kref);
+  if (s != ETC_OK) return s;
+  const Geometry g = geom_of(h, dir);
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  if (prec == ETC_PREC_FP64) {
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t64,
+                            h->partials, 0, 0.0, 2, h->stream));
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, kref[2], 0, 0, 0);
+  } else {
+    CK(launch_fwd_x<float>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t32,
+                           h->partials, 0, 0.0, 2, h->stream));
+    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, kref[2], 0, 0, 0);
+  }
+  if (s != ETC_OK) return s;
+  CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, double* out) {
+  if (!h || !in || !out) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  const Geometry g = geom_of(h, dir);
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  if (!inverse) {
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, in, h->t64,
+                            h->partials, 0, 0.0, 2, h->stream));
+    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 0, h->stream));
+    CK(cudaMemcpyAsync(out, h->t64, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(h->t64, in, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 0, h->stream));
+    CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, nullptr, 1.0, 0, 0, 0,
+                                     h->partials, h->stream)));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+}  // extern "C"

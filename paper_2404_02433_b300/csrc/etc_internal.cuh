@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of libetc.
+//
+// Layout convention (all kernels): a voxel field is a dense array in the
+// LOADING frame, index c = (k * N1 + j) * N0 + i, with i (axis 0) fastest and
+// k (axis 2) the loading axis that carries the Dirichlet faces (the paper puts
+// Gamma_in / Gamma_out at the two z faces, Sec. 2.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etc {
+
+constexpr int kMaxStages = 12;
+
+// Cosine-transform plan for one axis length n (Sec. 3.2, Definition "1D DCT").
+// fft == 1: even n, complex FFT of length m = n/2 by Stockham stages with the
+// listed radices; fft == 0: direct O(n^2) summation with the cos table.
+template <typename R>
+struct DctTables {
+  const R* tw;     // m complex: exp(-2 pi i j / m)
+  const R* fpost;  // (m+1) x 4: cos(t)/2, sin(t)/2, cos(5t)/2, sin(5t)/2, t = pi k / (2n)
+  const R* ipre;   // (m+1) x 4: cos(t)/(2m), sin(t)/(2m), cos(4t), sin(4t)
+  const R* cosq;   // 4n: cos(pi q / (2n))
+};
+
+struct DctShape {
+  int n, m, fft, nst;
+  int radix[kMaxStages];
+};
+
+template <typename R>
+struct DctPlan {
+  DctShape s;
+  DctTables<R> t;
+};
+
+// Device-resident PCG scalars (Algorithm 1).  Written by the last block of the
+// kernel that finishes each reduction; read by the kernels that follow.
+struct PcgState {
+  double rho;        // r . z of the current residual
+  double beta;       // rho_new / rho (0 before the first search direction)
+  double alpha[2];   // step length, by parity of the iteration
+  double rr;         // ||r||^2
+  double bb;         // ||b||^2
+  double thresh2;    // rtol^2 ||b||^2
+  double dq;         // w . A w of the current iteration
+  double zq;         // flexible PCG: z_new . q_old
+  double res[8];     // post-processing sums
+  double ext[10];    // group extrema of the face assembly
+  int iter;          // completed iterations (products with A)
+  int maxit;
+  int done;          // 1 once converged / stopped; kernels then return at entry
+  int status;        // ETC_OK / ETC_ENOCONV / ETC_EBREAKDOWN
+  int phase;         // 0 = initial preconditioner apply, 1 = iterating
+  int flexible;      // 1 = Polak-Ribiere beta (mixed precision path)
+  unsigned int cnt[8];  // arrival counters of the last-block reductions
+};
+
+enum CounterSlot { kCntDot = 0, kCntRes = 1, kCntRho = 2, kCntAux = 3, kCntFlux = 4,
+                   kCntExt = 5, kCntZq = 6 };
+
+// Status values mirrored from include/etc.h.
+enum { kOK = 0, kEINVAL = 1, kENOMEM = 2, kECUDA = 3, kENOCONV = 4, kEBREAKDOWN = 5,
+       kESTATE = 6 };
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += sh[w];
+  return t;
+}
+
+// Publish one partial per block; returns true in the block that arrives last.
+// That block may then read every partial (with __ldcg) in index order, which
+// makes the reduction deterministic.  The counter is reset for the next use.
+__device__ __forceinline__ bool publish_partial(double* partials, int nparts, double value,
+                                                int slot_stride, unsigned int* counter,
+                                                int* is_last_sh) {
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  (void)nparts;
+  if (threadIdx.x == 0) {
+    partials[(size_t)bid * slot_stride] = value;
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *is_last_sh = (prev == nb - 1);
+  }
+  __syncthreads();
+  const bool last = *is_last_sh != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Fixed-order sum of nb partials by one block (deterministic).
+__device__ __forceinline__ double sum_partials(const double* partials, int nb, int stride,
+                                               double* sh) {
+  double v = 0.0;
+  // each thread sums a contiguous chunk, then the chunks are added in order
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  for (int b = b0; b < b0 + per && b < nb; ++b) v += __ldcg(partials + (size_t)b * stride);
+  // ordered combination of the per-thread chunks
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  // warp-level ordered tree is deterministic for a fixed blockDim
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += sh[w];
+  return t;
+}
+
+// ---------------------------------------------------------------- host launchers
+struct Geometry {
+  int n0, n1, n2;     // loading-frame sizes
+  long long n;        // n0 * n1 * n2
+  long long plane;    // n0 * n1
+};
+
+}  // namespace etc

@@ -1,0 +1,876 @@
+// CUDA kernels of the TPFA + PCG hot path and their host launchers.
+//
+// Per PCG iteration (Algorithm 1) the solver launches, in stream order:
+//   matvec   w <- z + beta w_old ; q <- A w ; partial w.q   -> alpha  (last block)
+//   fwd_x    x <- x + alpha w ; r <- r - alpha q ; ||r||^2 -> convergence (last block);
+//            forward DCT of r along axis 0
+//   fwd_y    forward DCT along axis 1                                  (Algorithm 3, step 1)
+//   tridiag  T_{i'j'} z^ = r^ along axis 2 ; r.z in the transform domain -> beta
+//                                                                       (Algorithm 3, step 2)
+//   inv_y    backward DCT along axis 1                                 (Algorithm 3, step 3)
+//   inv_x    backward DCT along axis 0 -> z (flexible PCG: z.q -> beta)
+// Every kernel returns at entry once the device flag `done` is set, so the host
+// may launch iterations ahead of the convergence test.
+#include <cstdio>
+
+#include "dct_device.cuh"
+#include "etc_internal.cuh"
+#include "launchers.h"
+
+namespace etc {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long gidx() {
+  return (long long)blockIdx.x * blockDim.x + threadIdx.x;
+}
+
+// Each block writes nv values, the last block to arrive gets true.
+__device__ __forceinline__ bool publish_values(double* partials, int stride, const double* vals,
+                                               int nv, unsigned int* counter, int* flag) {
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  if (threadIdx.x == 0) {
+    for (int v = 0; v < nv; ++v) partials[(size_t)bid * stride + v] = vals[v];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *flag = (prev == nb - 1);
+  }
+  __syncthreads();
+  const bool last = *flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// ------------------------------------------------------------------ setup: checks
+// min, max and count of non-finite or non-positive values of one input array.
+__global__ void k_kappa_stats(const double* __restrict__ a, long long n, double* partials,
+                              PcgState* st, int slot) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  double lo = INFINITY, hi = -INFINITY, bad = 0.0;
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double v = a[c];
+    if (!(v > 0.0) || !isfinite(v)) bad += 1.0;
+    else { lo = fmin(lo, v); hi = fmax(hi, v); }
+  }
+  // block min / max / sum
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    bad += __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  __shared__ double wl[32], wh[32], wb[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) { wl[wid] = lo; wh[wid] = hi; wb[wid] = bad; }
+  __syncthreads();
+  double vals[3] = {INFINITY, -INFINITY, 0.0};
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) {
+      vals[0] = fmin(vals[0], wl[w]); vals[1] = fmax(vals[1], wh[w]); vals[2] += wb[w];
+    }
+  (void)sh;
+  if (publish_values(partials, 3, vals, 3, &st->cnt[kCntExt], &flag)) {
+    if (threadIdx.x == 0) {
+      double l2 = INFINITY, h2 = -INFINITY, b2 = 0.0;
+      const unsigned int nb = nblocks();
+      for (unsigned int b = 0; b < nb; ++b) {
+        l2 = fmin(l2, __ldcg(partials + 3 * b));
+        h2 = fmax(h2, __ldcg(partials + 3 * b + 1));
+        b2 += __ldcg(partials + 3 * b + 2);
+      }
+      st->ext[3 * slot] = l2; st->ext[3 * slot + 1] = h2; st->ext[3 * slot + 2] = b2;
+      st->cnt[kCntExt] = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ setup: permutation
+// out[o2][o1][o0] = in[o0*s0 + o1*s1 + o2*s2] (in dense, out dense).  When the
+// input-contiguous axis is not o0 it is axis f (1 or 2) and a 32x32 shared
+// tile makes both sides coalesced.
+__global__ void k_permute_direct(const double* __restrict__ in, double* __restrict__ out, int d0,
+                                 int d1, int d2, long long s1, long long s2) {
+  const long long n = (long long)d0 * d1 * d2;
+  for (long long o = gidx(); o < n; o += (long long)gridDim.x * blockDim.x) {
+    const long long o0 = o % d0, r = o / d0, o1 = r % d1, o2 = r / d1;
+    out[o] = in[o0 + o1 * s1 + o2 * s2];
+  }
+}
+
+__global__ void k_permute_tile(const double* __restrict__ in, double* __restrict__ out, int d0,
+                               int d1, int d2, long long s0, long long so, int f) {
+  __shared__ double tile[32][33];
+  const int df = (f == 1) ? d1 : d2;
+  const int o0b = blockIdx.x * 32, ofb = blockIdx.y * 32, oo = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int o0 = o0b + rr, of = ofb + tx;
+    if (o0 < d0 && of < df) tile[rr][tx] = in[(long long)o0 * s0 + of + (long long)oo * so];
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int o0 = o0b + tx, of = ofb + rr;
+    if (o0 < d0 && of < df) {
+      const long long o1 = (f == 1) ? of : oo, o2 = (f == 1) ? oo : of;
+      out[o0 + (long long)d0 * (o1 + (long long)d1 * o2)] = tile[tx][rr];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ setup: faces
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * (a * b) / (a + b); }
+
+// Face conductances of Eq. (scaled bilinear forms) in the loading frame, the
+// diagonal D of A, the Dirichlet planes and the group extrema of
+// Eq. (parameters for linear programming): res[0..9] = (min, max) of the x, y,
+// z internal faces, kappa~^z on plane 0 and on plane n2-1.
+__global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
+                        const double* __restrict__ k0, const double* __restrict__ k1,
+                        const double* __restrict__ k2, double* __restrict__ T0,
+                        double* __restrict__ T1, double* __restrict__ T2, double* __restrict__ D,
+                        double* __restrict__ Bin, double* __restrict__ Bout, double* partials,
+                        PcgState* st) {
+  __shared__ int flag;
+  double ext[10];
+  for (int e = 0; e < 10; e += 2) { ext[e] = INFINITY; ext[e + 1] = -INFINITY; }
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n0);
+    const long long rem = c / g.n0;
+    const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
+    const double s0 = k0[c] * ih0, s1 = k1[c] * ih1, s2 = k2[c] * ih2;
+    const double t0 = (i > 0) ? harmonic(k0[c - 1] * ih0, s0) : 0.0;
+    const double t1 = (j > 0) ? harmonic(k1[c - g.n0] * ih1, s1) : 0.0;
+    const double t2 = (k > 0) ? harmonic(k2[c - g.plane] * ih2, s2) : 0.0;
+    const double p0 = (i < g.n0 - 1) ? harmonic(s0, k0[c + 1] * ih0) : 0.0;
+    const double p1 = (j < g.n1 - 1) ? harmonic(s1, k1[c + g.n0] * ih1) : 0.0;
+    const double p2 = (k < g.n2 - 1) ? harmonic(s2, k2[c + g.plane] * ih2) : 0.0;
+    double d = t0 + p0 + t1 + p1 + t2 + p2;
+    if (k == 0) { d += 2.0 * s2; Bin[c] = 2.0 * s2; ext[6] = fmin(ext[6], s2); ext[7] = fmax(ext[7], s2); }
+    if (k == g.n2 - 1) {
+      d += 2.0 * s2; Bout[c - (long long)k * g.plane] = 2.0 * s2;
+      ext[8] = fmin(ext[8], s2); ext[9] = fmax(ext[9], s2);
+    }
+    T0[c] = t0; T1[c] = t1; T2[c] = t2; D[c] = d;
+    if (i > 0) { ext[0] = fmin(ext[0], t0); ext[1] = fmax(ext[1], t0); }
+    if (j > 0) { ext[2] = fmin(ext[2], t1); ext[3] = fmax(ext[3], t1); }
+    if (k > 0) { ext[4] = fmin(ext[4], t2); ext[5] = fmax(ext[5], t2); }
+  }
+  __shared__ double we[32][10];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int e = 0; e < 10; e += 2) {
+      ext[e] = fmin(ext[e], __shfl_down_sync(0xffffffffu, ext[e], o));
+      ext[e + 1] = fmax(ext[e + 1], __shfl_down_sync(0xffffffffu, ext[e + 1], o));
+    }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0)
+    for (int e = 0; e < 10; ++e) we[wid][e] = ext[e];
+  __syncthreads();
+  double vals[10];
+  if (threadIdx.x == 0) {
+    for (int e = 0; e < 10; e += 2) { vals[e] = INFINITY; vals[e + 1] = -INFINITY; }
+    for (int w = 0; w < nw; ++w)
+      for (int e = 0; e < 10; e += 2) {
+        vals[e] = fmin(vals[e], we[w][e]);
+        vals[e + 1] = fmax(vals[e + 1], we[w][e + 1]);
+      }
+  }
+  if (publish_values(partials, 10, vals, 10, &st->cnt[kCntExt], &flag)) {
+    if (threadIdx.x == 0) {
+      double r[10];
+      for (int e = 0; e < 10; e += 2) { r[e] = INFINITY; r[e + 1] = -INFINITY; }
+      const unsigned int nb = nblocks();
+      for (unsigned int b = 0; b < nb; ++b)
+        for (int e = 0; e < 10; e += 2) {
+          r[e] = fmin(r[e], __ldcg(partials + 10 * (size_t)b + e));
+          r[e + 1] = fmax(r[e + 1], __ldcg(partials + 10 * (size_t)b + e + 1));
+        }
+      for (int e = 0; e < 10; ++e) st->ext[e] = r[e];
+      st->cnt[kCntExt] = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ setup: pivots
+// For every (i', j'): the LDL^T pivots of T_{i'j'} / kappa_ref^z (Sec. 3.2),
+// stored as h_k = 1 / pivot_k in the layout of the transformed field.
+template <typename R>
+__global__ void k_pivots(Geometry g, const double* __restrict__ lam0,
+                         const double* __restrict__ lam1, double kx, double ky, double kz,
+                         double kin, double kout, R* __restrict__ h) {
+  const long long s = gidx();
+  if (s >= g.plane) return;
+  const int i = (int)(s % g.n0), j = (int)(s / g.n0);
+  const double sv = (lam0[i] * kx + lam1[j] * ky) / kz;
+  const double a_in = 2.0 * kin / kz, a_out = 2.0 * kout / kz;
+  if (g.n2 == 1) {
+    h[s] = (R)(1.0 / (sv + a_in + a_out));
+    return;
+  }
+  double hp = 1.0 / (sv + 1.0 + a_in);
+  h[s] = (R)hp;
+  for (int k = 1; k < g.n2; ++k) {
+    const double dk = (k == g.n2 - 1) ? (sv + 1.0 + a_out) : (sv + 2.0);
+    hp = 1.0 / (dk - hp);
+    h[(long long)k * g.plane + s] = (R)hp;
+  }
+}
+
+// ------------------------------------------------------------------ init
+// r = b (Eq. flux: b_in p_in on plane 0, b_out p_out on plane n2-1), x = 0,
+// w_old = 0.
+__global__ void k_init(Geometry g, const double* __restrict__ Bin, const double* __restrict__ Bout,
+                       double pin, double pout, double* __restrict__ r, double* __restrict__ x,
+                       double* __restrict__ w0) {
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const long long k = c / g.plane, s = c - k * g.plane;
+    double b = 0.0;
+    if (k == 0) b += Bin[s] * pin;
+    if (k == g.n2 - 1) b += Bout[s] * pout;
+    r[c] = b;
+    x[c] = 0.0;
+    w0[c] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ matvec
+// 2.5-D blocking: a 32 x 8 tile of (i, j) marches along k; w of the tile (plus
+// a one-cell halo in i and j) sits in shared memory, the k-neighbours in
+// registers.  q_c = D_c w_c - sum_f T_f w_nb (Eq. scaled bilinear forms).
+// MODE 0: q = A z only.  MODE 1: PCG step, w_new = z + beta w_old, dot -> alpha.
+template <typename TZ, int MODE>
+__global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
+                                               const TZ* __restrict__ z,
+                                               const double* __restrict__ wold,
+                                               double* __restrict__ wnew, double* __restrict__ q,
+                                               const double* __restrict__ T0,
+                                               const double* __restrict__ T1,
+                                               const double* __restrict__ T2,
+                                               const double* __restrict__ D, double* partials,
+                                               int chunk, int par) {
+  __shared__ double s[10][34];
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE == 1 && st->done) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
+  const int k0 = blockIdx.z * chunk;
+  const int k1 = min(k0 + chunk, g.n2);
+  const bool in = (i < g.n0) && (j < g.n1);
+  const double beta = (MODE == 1) ? st->beta : 0.0;
+  auto wn = [&](long long c) -> double {
+    return (MODE == 1) ? fma(beta, wold[c], (double)z[c]) : (double)z[c];
+  };
+  const long long col = (long long)j * g.n0 + i;
+  double wm = 0.0, wc = 0.0, wp = 0.0;
+  if (in && k0 > 0) wm = wn((long long)(k0 - 1) * g.plane + col);
+  if (in) wc = wn((long long)k0 * g.plane + col);
+  double t2c = in ? T2[(long long)k0 * g.plane + col] : 0.0;
+  double dot = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const long long c = (long long)k * g.plane + col;
+    wp = (in && k + 1 < g.n2) ? wn(c + g.plane) : 0.0;
+    s[ty + 1][tx + 1] = wc;
+    if (tx == 0) s[ty + 1][0] = (j < g.n1 && i > 0 && i - 1 < g.n0) ? wn(c - 1) : 0.0;
+    if (tx == 31) s[ty + 1][33] = (j < g.n1 && i + 1 < g.n0) ? wn(c + 1) : 0.0;
+    if (ty == 0) s[0][tx + 1] = (i < g.n0 && j > 0 && j - 1 < g.n1) ? wn(c - g.n0) : 0.0;
+    if (ty == 7) s[9][tx + 1] = (i < g.n0 && j + 1 < g.n1) ? wn(c + g.n0) : 0.0;
+    __syncthreads();
+    if (in) {
+      const double t2n = T2[c + g.plane];  // zero padding beyond the last plane
+      double qv = D[c] * wc;
+      qv = fma(-T0[c], s[ty + 1][tx], qv);
+      qv = fma(-T0[c + 1], s[ty + 1][tx + 2], qv);
+      qv = fma(-T1[c], s[ty][tx + 1], qv);
+      qv = fma(-T1[c + g.n0], s[ty + 2][tx + 1], qv);
+      qv = fma(-t2c, wm, qv);
+      qv = fma(-t2n, wp, qv);
+      q[c] = qv;
+      if (MODE == 1) {
+        wnew[c] = wc;
+        dot = fma(wc, qv, dot);
+      }
+      t2c = t2n;
+    }
+    __syncthreads();
+    wm = wc;
+    wc = wp;
+  }
+  if (MODE == 1) {
+    const double bs = block_sum(dot, sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag)) {
+      const double dq = sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        const double alpha = st->rho / dq;
+        st->dq = dq;
+        st->alpha[par] = alpha;
+        if (!(dq > 0.0) || !isfinite(alpha)) { st->status = kEBREAKDOWN; st->done = 1; }
+        st->cnt[kCntDot] = 0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ forward DCT along axis 0
+// MODE 0: initial residual (r = b already): ||r||^2 -> ||b||^2.
+// MODE 1: PCG update x += alpha w, r -= alpha q, ||r||^2 -> convergence test.
+// MODE 2: transform only (component entry point), no state.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgState* st,
+                                              double* __restrict__ x,
+                                              const double* __restrict__ w,
+                                              const double* __restrict__ q,
+                                              double* __restrict__ r, const double* __restrict__ rin,
+                                              R* __restrict__ t, double* partials, int L, int par,
+                                              double rtol2) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE != 2 && st->done) return;
+  const Lay y = make_lay(L, g.n0, false);
+  c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
+  c2<R>* b = a + L * dct_half_alloc(g.n0);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)blockIdx.x * L;
+  const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  double acc = 0.0;
+  const int tot = L * g.n0;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e / g.n0, i = e - l * g.n0;
+    const long long row = row0 + l;
+    R u = (R)0;
+    if (row < nrows) {
+      const long long c = row * g.n0 + i;
+      double rv;
+      if (MODE == 2) {
+        rv = rin[c];
+      } else {
+        rv = r[c];
+        if (MODE == 1) {
+          x[c] = fma(alpha, w[c], x[c]);
+          rv = fma(-alpha, q[c], rv);
+          r[c] = rv;
+        }
+        acc = fma(rv, rv, acc);
+      }
+      u = (R)rv;
+    }
+    dct2_put<R>(p.s, y, a, l, i, u);
+  }
+  __syncthreads();
+  dct2_run<R>(p, y, a, b, [&](int l, int k, R v) {
+    const long long row = row0 + l;
+    if (row < nrows) t[row * g.n0 + k] = v;
+  });
+  if (MODE != 2) {
+    const double bs = block_sum(acc, sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], &flag)) {
+      const double rr = sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        st->rr = rr;
+        if (MODE == 0) {
+          st->bb = rr;
+          st->thresh2 = rtol2 * rr;
+          if (!(rr > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+        } else {
+          st->iter += 1;
+          if (!isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+          else if (rr <= st->thresh2) { st->status = kOK; st->done = 1; }
+          else if (st->iter >= st->maxit) { st->status = kENOCONV; st->done = 1; }
+        }
+        st->cnt[kCntRes] = 0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ DCT along axis 1 (in place)
+template <typename R, int INVERSE>
+__global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const PcgState* st,
+                                              R* __restrict__ t, int TI, int check) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (check && st->done) return;
+  const Lay y = make_lay(TI, g.n1, true);
+  c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
+  c2<R>* b = a + TI * dct_half_alloc(g.n1);
+  const long long k = blockIdx.y;
+  const int i0 = blockIdx.x * TI;
+  R* base = t + k * g.plane + i0;
+  const int tot = TI * g.n1;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e % TI, jj = e / TI;
+    const R v = (i0 + l < g.n0) ? base[(long long)jj * g.n0 + l] : (R)0;
+    if (INVERSE) dct3_put<R>(y, b, l, jj, v);
+    else dct2_put<R>(p.s, y, a, l, jj, v);
+  }
+  __syncthreads();
+  auto store = [&](int l, int kk, R v) {
+    if (i0 + l < g.n0) base[(long long)kk * g.n0 + l] = v;
+  };
+  if (INVERSE) dct3_run<R>(p, y, a, b, (R)1, store);
+  else dct2_run<R>(p, y, a, b, store);
+}
+
+// ------------------------------------------------------------------ tridiagonal along axis 2
+// Forward sweep y_k = r^_k + h_{k-1} y_{k-1}, backward z_k = h_k (y_k + z_{k+1})
+// solves (T_{i'j'}/kappa_ref^z) z = r^.  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
+// so rho = r.z follows from Parseval for the DCT pair of Sec. 3.2.
+// MODE 0: solve only.  MODE 1: PCG, rho_new -> beta (plain PCG) or stored
+// for the flexible update.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __restrict__ t,
+                                                const R* __restrict__ h, double wscale,
+                                                double* partials) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE == 1 && st->done) return;
+  const long long s = gidx();
+  double acc = 0.0;
+  if (s < g.plane) {
+    R yv = (R)0, hp = (R)0;
+    R part = (R)0;
+    for (int k = 0; k < g.n2; ++k) {
+      const long long c = (long long)k * g.plane + s;
+      const R hk = h[c];
+      yv = fma(hp, yv, t[c]);
+      t[c] = yv;
+      part = fma(hk * yv, yv, part);
+      hp = hk;
+    }
+    R zn = (R)0;
+    for (int k = g.n2 - 1; k >= 0; --k) {
+      const long long c = (long long)k * g.plane + s;
+      zn = h[c] * (t[c] + zn);
+      t[c] = zn;
+    }
+    const int i = (int)(s % g.n0), j = (int)(s / g.n0);
+    const double wgt = (i == 0 ? 0.5 : 1.0) * (j == 0 ? 0.5 : 1.0);
+    acc = wgt * (double)part;
+  }
+  if (MODE == 1) {
+    const double bs = block_sum(acc, sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntRho], &flag)) {
+      const double rho_new = wscale * sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+          if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
+        }
+        if (st->phase == 0) {
+          st->rho = rho_new;
+          st->beta = 0.0;
+          st->phase = 1;
+        } else if (!st->flexible) {
+          st->beta = rho_new / st->rho;
+          st->rho = rho_new;
+        } else {
+          st->res[7] = rho_new;  // consumed by k_inv_x (flexible beta)
+        }
+        st->cnt[kCntRho] = 0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ backward DCT along axis 0
+// z = scale * (backward DCT of t along axis 0).  FLEX: accumulate z . q for
+// the flexible (Polak-Ribiere) beta = -alpha z.q / rho.
+template <typename R, typename TZ, int FLEX>
+__global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgState* st,
+                                              const R* __restrict__ t, TZ* __restrict__ z,
+                                              const double* __restrict__ q, R scale, int L,
+                                              int par, int check, double* partials) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (check && st->done) return;
+  const Lay y = make_lay(L, g.n0, false);
+  c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
+  c2<R>* b = a + L * dct_half_alloc(g.n0);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)blockIdx.x * L;
+  const int tot = L * g.n0;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int l = e / g.n0, k = e - l * g.n0;
+    const long long row = row0 + l;
+    dct3_put<R>(y, b, l, k, row < nrows ? t[row * g.n0 + k] : (R)0);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  dct3_run<R>(p, y, a, b, scale, [&](int l, int i, R v) {
+    const long long row = row0 + l;
+    if (row < nrows) {
+      const long long c = row * g.n0 + i;
+      z[c] = (TZ)v;
+      if (FLEX) acc = fma((double)v, q[c], acc);
+    }
+  });
+  if (FLEX) {
+    const double bs = block_sum(acc, sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntZq], &flag)) {
+      const double zq = sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        st->zq = zq;
+        const double rho_new = st->res[7];
+        if (st->iter > 0) {
+          // beta = z_new.(r_new - r_old) / rho_old with r_new - r_old = -alpha q
+          st->beta = -st->alpha[par] * zq / st->rho;
+        } else {
+          st->beta = 0.0;
+        }
+        st->rho = rho_new;
+        if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
+        st->cnt[kCntZq] = 0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ post-processing
+// Sums for Eq. (flux) / Eq. (effective formula dis) in the loading frame:
+// res[0..2] internal-face flux sums T (p_minus - p_plus) per axis (times h later),
+// res[3] = sum b_out (p_{n2-1} - p_out), res[4] = sum b_in (p_in - p_0).
+__global__ void k_flux(Geometry g, const double* __restrict__ x, const double* __restrict__ T0,
+                       const double* __restrict__ T1, const double* __restrict__ T2,
+                       const double* __restrict__ Bin, const double* __restrict__ Bout,
+                       double pin, double pout, double* partials, PcgState* st) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  double a[5] = {0, 0, 0, 0, 0};
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n0);
+    const long long rem = c / g.n0;
+    const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
+    const double xc = x[c];
+    if (i > 0) a[0] = fma(T0[c], x[c - 1] - xc, a[0]);
+    if (j > 0) a[1] = fma(T1[c], x[c - g.n0] - xc, a[1]);
+    if (k > 0) a[2] = fma(T2[c], x[c - g.plane] - xc, a[2]);
+    const long long s = c - (long long)k * g.plane;
+    if (k == g.n2 - 1) a[3] = fma(Bout[s], xc - pout, a[3]);
+    if (k == 0) a[4] = fma(Bin[s], pin - xc, a[4]);
+  }
+  double vals[5];
+  for (int e = 0; e < 5; ++e) vals[e] = block_sum(a[e], sh);
+  if (publish_values(partials, 5, vals, 5, &st->cnt[kCntFlux], &flag)) {
+    if (threadIdx.x == 0) {
+      const unsigned int nb = nblocks();
+      for (int e = 0; e < 5; ++e) {
+        double v = 0.0;
+        for (unsigned int b = 0; b < nb; ++b) v += __ldcg(partials + 5 * (size_t)b + e);
+        st->res[e] = v;
+      }
+      st->cnt[kCntFlux] = 0;
+    }
+  }
+}
+
+// ||b - A x||^2 -> res[5] (true residual at exit).
+__global__ void k_true_residual(Geometry g, const double* __restrict__ x,
+                                const double* __restrict__ T0, const double* __restrict__ T1,
+                                const double* __restrict__ T2, const double* __restrict__ D,
+                                const double* __restrict__ Bin, const double* __restrict__ Bout,
+                                double pin, double pout, double* partials, PcgState* st) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  double acc = 0.0;
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n0);
+    const long long rem = c / g.n0;
+    const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
+    const long long s = c - (long long)k * g.plane;
+    double b = 0.0;
+    if (k == 0) b += Bin[s] * pin;
+    if (k == g.n2 - 1) b += Bout[s] * pout;
+    double ax = D[c] * x[c];
+    if (i > 0) ax -= T0[c] * x[c - 1];
+    if (i < g.n0 - 1) ax -= T0[c + 1] * x[c + 1];
+    if (j > 0) ax -= T1[c] * x[c - g.n0];
+    if (j < g.n1 - 1) ax -= T1[c + g.n0] * x[c + g.n0];
+    if (k > 0) ax -= T2[c] * x[c - g.plane];
+    if (k < g.n2 - 1) ax -= T2[c + g.plane] * x[c + g.plane];
+    const double d = b - ax;
+    acc = fma(d, d, acc);
+  }
+  const double bs = block_sum(acc, sh);
+  double v[1] = {bs};
+  if (publish_values(partials, 1, v, 1, &st->cnt[kCntAux], &flag)) {
+    const double tot = sum_partials(partials, (int)nblocks(), 1, sh);
+    if (threadIdx.x == 0) {
+      st->res[5] = tot;
+      st->cnt[kCntAux] = 0;
+    }
+  }
+}
+
+// Element-wise FP32 -> FP64 copy (component entry points of the mixed path).
+__global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) b[c] = (double)a[c];
+}
+
+// ================================================================== launchers
+static inline unsigned int grid_for(long long n, int bs, int cap = 148 * 32) {
+  long long gb = (n + bs - 1) / bs;
+  if (gb > cap) gb = cap;
+  if (gb < 1) gb = 1;
+  return (unsigned int)gb;
+}
+
+cudaError_t launch_kappa_stats(const double* a, long long n, double* partials, PcgState* st,
+                               int slot, cudaStream_t s) {
+  k_kappa_stats<<<grid_for(n, 256, 148 * 8), 256, 0, s>>>(a, n, partials, st, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const double* in, double* out, int d0, int d1, int d2, long long s0,
+                           long long s1, long long s2, cudaStream_t s) {
+  const long long n = (long long)d0 * d1 * d2;
+  if (s0 == 1) {
+    k_permute_direct<<<grid_for(n, 256), 256, 0, s>>>(in, out, d0, d1, d2, s1, s2);
+  } else {
+    const int f = (s1 == 1) ? 1 : 2;
+    const int df = (f == 1) ? d1 : d2;
+    const int dother = (f == 1) ? d2 : d1;
+    const long long so = (f == 1) ? s2 : s1;
+    dim3 grid((d0 + 31) / 32, (df + 31) / 32, dother);
+    k_permute_tile<<<grid, 256, 0, s>>>(in, out, d0, d1, d2, s0, so, f);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, const double* k0,
+                         const double* k1, const double* k2, double* T0, double* T1, double* T2,
+                         double* D, double* Bin, double* Bout, double* partials, PcgState* st,
+                         cudaStream_t s) {
+  k_faces<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, ih0, ih1, ih2, k0, k1, k2, T0, T1, T2, D,
+                                                     Bin, Bout, partials, st);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* lam1,
+                          const double* kref, R* h, cudaStream_t s) {
+  k_pivots<R><<<grid_for(g.plane, 128, 1 << 30), 128, 0, s>>>(g, lam0, lam1, kref[0], kref[1],
+                                                             kref[2], kref[3], kref[4], h);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pivots<double>(const Geometry&, const double*, const double*,
+                                           const double*, double*, cudaStream_t);
+template cudaError_t launch_pivots<float>(const Geometry&, const double*, const double*,
+                                          const double*, float*, cudaStream_t);
+
+cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
+                        double pout, double* r, double* x, double* w0, cudaStream_t s) {
+  k_init<<<grid_for(g.n, 256), 256, 0, s>>>(g, Bin, Bout, pin, pout, r, x, w0);
+  return cudaGetLastError();
+}
+
+static inline unsigned int matvec_chunk(const Geometry& g, dim3* grid) {
+  const int tx = (g.n0 + 31) / 32, ty = (g.n1 + 7) / 8;
+  const long long tiles = (long long)tx * ty;
+  long long want = (4 * 148 + tiles - 1) / tiles;
+  long long maxc = (g.n2 + 7) / 8;
+  if (want > maxc) want = maxc;
+  if (want < 1) want = 1;
+  const int chunk = (int)((g.n2 + want - 1) / want);
+  *grid = dim3(tx, ty, (g.n2 + chunk - 1) / chunk);
+  return chunk;
+}
+
+unsigned int matvec_blocks(const Geometry& g) {
+  dim3 grid;
+  matvec_chunk(g, &grid);
+  return grid.x * grid.y * grid.z;
+}
+
+template <typename TZ>
+cudaError_t launch_matvec(const Geometry& g, PcgState* st, const TZ* z, const double* wold,
+                          double* wnew, double* q, const double* T0, const double* T1,
+                          const double* T2, const double* D, double* partials, int par, int mode,
+                          cudaStream_t s) {
+  dim3 grid;
+  const int chunk = matvec_chunk(g, &grid);
+  if (mode == 0)
+    k_matvec<TZ, 0><<<grid, 256, 0, s>>>(g, st, z, wold, wnew, q, T0, T1, T2, D, partials, chunk,
+                                         par);
+  else
+    k_matvec<TZ, 1><<<grid, 256, 0, s>>>(g, st, z, wold, wnew, q, T0, T1, T2, D, partials, chunk,
+                                         par);
+  return cudaGetLastError();
+}
+template cudaError_t launch_matvec<double>(const Geometry&, PcgState*, const double*,
+                                           const double*, double*, double*, const double*,
+                                           const double*, const double*, const double*, double*,
+                                           int, int, cudaStream_t);
+template cudaError_t launch_matvec<float>(const Geometry&, PcgState*, const float*, const double*,
+                                          double*, double*, const double*, const double*,
+                                          const double*, const double*, double*, int, int,
+                                          cudaStream_t);
+
+// rows per block of the axis-0 transforms and their shared memory
+template <typename R>
+int rows_per_block(int n0) {
+  int L = 2048 / (n0 > 0 ? n0 : 1);
+  if (L < 1) L = 1;
+  if (L > 64) L = 64;
+  return L;
+}
+template <typename R>
+size_t smem_x(int n0, int L) {
+  return 2ull * L * dct_half_alloc(n0) * sizeof(c2<R>);
+}
+template <typename R>
+int cols_per_block(int n1) {
+  int TI = (sizeof(R) == 8 ? 4096 : 8192) / (n1 > 0 ? n1 : 1);
+  if (TI < 1) TI = 1;
+  if (TI > 32) TI = 32;
+  return TI;
+}
+template <typename R>
+size_t smem_y(int n1, int TI) {
+  return 2ull * TI * dct_half_alloc(n1) * sizeof(c2<R>);
+}
+
+unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes) {
+  const int L = (elem_bytes == 8) ? rows_per_block<double>(g.n0) : rows_per_block<float>(g.n0);
+  const long long nrows = (long long)g.n1 * g.n2;
+  return (unsigned int)((nrows + L - 1) / L);
+}
+
+static const size_t kMaxDyn = 200 * 1024;
+
+template <typename R>
+cudaError_t set_smem_attrs() {
+  cudaError_t e = cudaSuccess;
+#define SETA(fn)                                                                           \
+  if (e == cudaSuccess)                                                                    \
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDyn);
+  SETA((k_fwd_x<R, 0>));
+  SETA((k_fwd_x<R, 1>));
+  SETA((k_fwd_x<R, 2>));
+  SETA((k_dct_y<R, 0>));
+  SETA((k_dct_y<R, 1>));
+  SETA((k_inv_x<R, double, 0>));
+  SETA((k_inv_x<R, float, 0>));
+  SETA((k_inv_x<R, double, 1>));
+  SETA((k_inv_x<R, float, 1>));
+#undef SETA
+  return e;
+}
+template cudaError_t set_smem_attrs<double>();
+template cudaError_t set_smem_attrs<float>();
+
+template <typename R>
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
+                         const double* w, const double* q, double* r, const double* rin, R* t,
+                         double* partials, int par, double rtol2, int mode, cudaStream_t s) {
+  const int L = rows_per_block<R>(g.n0);
+  const size_t sm = smem_x<R>(g.n0, L);
+  if (sm > kMaxDyn) return cudaErrorInvalidValue;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  if (mode == 0)
+    k_fwd_x<R, 0><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+  else if (mode == 1)
+    k_fwd_x<R, 1><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+  else
+    k_fwd_x<R, 2><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+  return cudaGetLastError();
+}
+template cudaError_t launch_fwd_x<double>(const Geometry&, const DctPlan<double>&, PcgState*,
+                                          double*, const double*, const double*, double*,
+                                          const double*, double*, double*, int, double, int,
+                                          cudaStream_t);
+template cudaError_t launch_fwd_x<float>(const Geometry&, const DctPlan<float>&, PcgState*,
+                                         double*, const double*, const double*, double*,
+                                         const double*, float*, double*, int, double, int,
+                                         cudaStream_t);
+
+template <typename R>
+cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
+                         int inverse, int check, cudaStream_t s) {
+  if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
+  const int TI = cols_per_block<R>(g.n1);
+  const size_t sm = smem_y<R>(g.n1, TI);
+  if (sm > kMaxDyn) return cudaErrorInvalidValue;
+  dim3 grid((g.n0 + TI - 1) / TI, g.n2);
+  if (inverse) k_dct_y<R, 1><<<grid, 256, sm, s>>>(g, p, st, t, TI, check);
+  else k_dct_y<R, 0><<<grid, 256, sm, s>>>(g, p, st, t, TI, check);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dct_y<double>(const Geometry&, const DctPlan<double>&,
+                                          const PcgState*, double*, int, int, cudaStream_t);
+template cudaError_t launch_dct_y<float>(const Geometry&, const DctPlan<float>&, const PcgState*,
+                                         float*, int, int, cudaStream_t);
+
+unsigned int tridiag_blocks(const Geometry& g) {
+  return (unsigned int)((g.plane + 127) / 128);
+}
+
+template <typename R>
+cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
+                           double* partials, int mode, cudaStream_t s) {
+  const unsigned int nb = tridiag_blocks(g);
+  if (mode == 0) k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
+  else k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
+  return cudaGetLastError();
+}
+template cudaError_t launch_tridiag<double>(const Geometry&, PcgState*, double*, const double*,
+                                            double, double*, int, cudaStream_t);
+template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, const float*,
+                                           double, double*, int, cudaStream_t);
+
+template <typename R, typename TZ>
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
+                         const double* q, double scale, int par, int check, int flex,
+                         double* partials, cudaStream_t s) {
+  const int L = rows_per_block<R>(g.n0);
+  const size_t sm = smem_x<R>(g.n0, L);
+  if (sm > kMaxDyn) return cudaErrorInvalidValue;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  if (flex)
+    k_inv_x<R, TZ, 1><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
+  else
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
+  return cudaGetLastError();
+}
+template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
+                                                  PcgState*, const double*, double*,
+                                                  const double*, double, int, int, int, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_inv_x<float, float>(const Geometry&, const DctPlan<float>&, PcgState*,
+                                                const float*, float*, const double*, double, int,
+                                                int, int, double*, cudaStream_t);
+template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
+                                                 PcgState*, const float*, double*, const double*,
+                                                 double, int, int, int, double*, cudaStream_t);
+
+cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
+                        const double* T2, const double* Bin, const double* Bout, double pin,
+                        double pout, double* partials, PcgState* st, cudaStream_t s) {
+  k_flux<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, Bin, Bout, pin, pout,
+                                                     partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_true_residual(const Geometry& g, const double* x, const double* T0,
+                                 const double* T1, const double* T2, const double* D,
+                                 const double* Bin, const double* Bout, double pin, double pout,
+                                 double* partials, PcgState* st, cudaStream_t s) {
+  k_true_residual<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, D, Bin, Bout, pin,
+                                                              pout, partials, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s) {
+  k_widen<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+}  // namespace etc

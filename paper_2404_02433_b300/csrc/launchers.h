@@ -1,0 +1,58 @@
+// Host-side launchers of the kernels in kernels.cu (internal to libetc).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "etc_internal.cuh"
+
+namespace etc {
+
+cudaError_t launch_kappa_stats(const double* a, long long n, double* partials, PcgState* st,
+                               int slot, cudaStream_t s);
+cudaError_t launch_permute(const double* in, double* out, int d0, int d1, int d2, long long s0,
+                           long long s1, long long s2, cudaStream_t s);
+cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, const double* k0,
+                         const double* k1, const double* k2, double* T0, double* T1, double* T2,
+                         double* D, double* Bin, double* Bout, double* partials, PcgState* st,
+                         cudaStream_t s);
+template <typename R>
+cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* lam1,
+                          const double* kref, R* h, cudaStream_t s);
+cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
+                        double pout, double* r, double* x, double* w0, cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_matvec(const Geometry& g, PcgState* st, const TZ* z, const double* wold,
+                          double* wnew, double* q, const double* T0, const double* T1,
+                          const double* T2, const double* D, double* partials, int par, int mode,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
+                         const double* w, const double* q, double* r, const double* rin, R* t,
+                         double* partials, int par, double rtol2, int mode, cudaStream_t s);
+template <typename R>
+cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
+                         int inverse, int check, cudaStream_t s);
+template <typename R>
+cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
+                           double* partials, int mode, cudaStream_t s);
+template <typename R, typename TZ>
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
+                         const double* q, double scale, int par, int check, int flex,
+                         double* partials, cudaStream_t s);
+cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
+                        const double* T2, const double* Bin, const double* Bout, double pin,
+                        double pout, double* partials, PcgState* st, cudaStream_t s);
+cudaError_t launch_true_residual(const Geometry& g, const double* x, const double* T0,
+                                 const double* T1, const double* T2, const double* D,
+                                 const double* Bin, const double* Bout, double pin, double pout,
+                                 double* partials, PcgState* st, cudaStream_t s);
+cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s);
+template <typename R>
+cudaError_t set_smem_attrs();
+
+// Grid sizes of the reduction kernels (to size the partials buffer).
+unsigned int matvec_blocks(const Geometry& g);
+unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes);
+unsigned int tridiag_blocks(const Geometry& g);
+
+}  // namespace etc

@@ -1,0 +1,235 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Kernel by kernel (operator, 2-D cosine transforms, preconditioner) and end to
+end (kappa_eff, the solution field, the 3x3 tensor), on seeded inputs whose
+sizes span several tiles, ragged tails, odd and mixed-radix lengths, and the
+degenerate one-voxel axes.  Tolerances: 1e-12 relative (max norm) for FP64
+kernels, 2e-5 for the FP32 preconditioner, 1e-9 relative on kappa_eff at
+rtol 1e-10 (the FP64 bar), 1e-6 for the mixed path at rtol 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import etc_oracle as O
+from paper_2404_02433_b300 import binding as B
+from paper_2404_02433_b300 import microstructure as M
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def make(kx, ky=None, kz=None, lengths=(1.0, 1.0, 1.0)):
+    return B.RVE(dev(kx), None if ky is None else dev(ky), None if kz is None else dev(kz),
+                 lengths=lengths)
+
+
+SHAPES = [(18, 20, 24), (11, 13, 17), (36, 48, 40), (5, 7, 1), (9, 1, 33), (1, 6, 4),
+          (16, 16, 16), (12, 10, 30)]
+
+
+def oracle_faces(kx, ky, kz, lengths, direction):
+    (k0, k1, k2), lens = O.permute_medium(kx, ky, kz, lengths, direction)
+    return O.face_conductances(k0, k1, k2, lens), (k0.shape)
+
+
+# ------------------------------------------------------------------ kernels
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_operator_matches_oracle(shape, direction):
+    rng = np.random.default_rng(hash((shape, direction)) % 2**32)
+    kx, ky, kz = (rng.uniform(0.1, 10.0, shape) for _ in range(3))
+    lengths = (1.0, 1.3, 0.7)
+    rve = make(kx, ky, kz, lengths)
+    f, fshape = oracle_faces(kx, ky, kz, lengths, direction)
+    assert rve.loading_dims(direction) == tuple(reversed(fshape))
+    w = rng.standard_normal(fshape)
+    q = torch.empty(fshape, dtype=torch.float64, device="cuda")
+    B.etc_apply_operator(rve.h, direction, dev(w), q)
+    assert relmax(host(q), O.apply_operator(f, w)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(8, 64, 96), (4, 160, 192), (3, 200, 50)])
+def test_dct_planes_match_oracle(shape):
+    rng = np.random.default_rng(sum(shape))
+    k = rng.uniform(1.0, 2.0, shape)
+    rve = make(k)
+    u = rng.standard_normal(shape)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
+    ref = O.dct_forward(O.dct_forward(u, 2), 1)
+    assert relmax(host(out), ref) < 1e-12
+    back = torch.empty_like(out)
+    B.etc_dct_planes(rve.h, 2, 1, dev(ref), back)
+    assert relmax(host(back), u) < 1e-12
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("direction", [0, 2])
+def test_preconditioner_matches_oracle(shape, direction):
+    rng = np.random.default_rng(7 + sum(shape) + direction)
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    f, fshape = oracle_faces(kx, ky, kz, (1.0, 1.0, 1.0), direction)
+    kref_o = O.reference_parameters(O.group_extrema(f))
+    kref_g = rve.set_reference(direction, B.ETC_REF_LP)
+    np.testing.assert_allclose(kref_g, kref_o, rtol=1e-13)
+    r = rng.standard_normal(fshape)
+    z = torch.empty(fshape, dtype=torch.float64, device="cuda")
+    B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_FP64, dev(r), z)
+    zo = O.apply_reference_inverse(r, kref_o)
+    assert relmax(host(z), zo) < 1e-11
+    # user-set parameters chosen by the test
+    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
+    rve.set_reference(direction, B.ETC_REF_USER, ku)
+    B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_FP64, dev(r), z)
+    assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 1e-11
+    # FP32 transforms and solves (mixed path)
+    B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_MIXED, dev(r), z)
+    assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 2e-5
+
+
+# ------------------------------------------------------------------ end to end
+def test_config_32_spheres_direction_x():
+    # 32^3 two-phase random spheres (radius 3-5, fraction 0.3, 1:10), rtol 1e-10, load x
+    k, info = M.random_spheres((32, 32, 32), (3, 5), 0.3, 1001, 1.0, 10.0)
+    ref = O.solve_direction(k, k, k, 0, rtol=1e-10)
+    rve = make(k)
+    kap, inf = rve.solve(0, rtol=1e-10)
+    assert abs(kap - ref.kappa_eff) <= 1e-9 * ref.kappa_eff
+    assert abs(inf["iters"] - ref.iters) <= 1
+    assert inf["status"] == B.ETC_OK and inf["relres"] <= 1e-10
+    assert inf["true_relres"] < 1e-9
+    np.testing.assert_allclose(inf["kref"], ref.kref, rtol=1e-13)
+    p = host(rve.solution(0))
+    assert relmax(p, ref.p) < 1e-8
+
+
+@pytest.mark.parametrize("shape", [(18, 20, 24), (11, 13, 17), (1, 6, 4), (7, 1, 9), (1, 1, 5),
+                                   (6, 1, 1), (1, 1, 1)])
+def test_tensor_matches_oracle(shape):
+    rng = np.random.default_rng(sum(shape) * 3 + 1)
+    kx = M.two_phase_random(shape, seed=sum(shape), fraction=0.35, kappa_inclusion=20.0)
+    ky, kz = kx * rng.uniform(0.5, 2.0, shape), kx * rng.uniform(0.5, 2.0, shape)
+    lengths = (1.0, 0.8, 1.5)
+    K_o, res_o = O.effective_tensor(kx, ky, kz, lengths, rtol=1e-10)
+    rve = make(kx, ky, kz, lengths)
+    K, infos, st = rve.tensor(rtol=1e-10)
+    K = np.array(K).reshape(3, 3)
+    assert st == B.ETC_OK
+    np.testing.assert_allclose(np.diag(K), np.diag(K_o), rtol=1e-9)
+    assert np.abs(K - K_o).max() <= 1e-9 * np.abs(K_o).max()
+    for d in range(3):
+        assert abs(infos[d]["iters"] - res_o[d].iters) <= 1
+        assert abs(infos[d]["kappa_in"] - res_o[d].kappa_eff) <= 1e-8 * res_o[d].kappa_eff
+
+
+def test_homogeneous_one_iteration_exact():
+    shape = (10, 12, 14)
+    comps = (np.full(shape, 2.0), np.full(shape, 3.5), np.full(shape, 0.7))
+    rve = make(*comps)
+    for d in range(3):
+        kap, inf = rve.solve(d, p_in=2.0, p_out=-1.0, rtol=1e-12)
+        assert inf["iters"] == 1
+        assert kap == pytest.approx(comps[d][0, 0, 0], rel=1e-12)
+
+
+def test_series_laminate_harmonic_mean():
+    vals = [1.0, 10.0, 3.0, 0.2, 7.0]
+    k = M.series_laminate((20, 12, 11), vals, 2)
+    rve = make(k)
+    kap, inf = rve.solve(2, rtol=1e-12)
+    layer = [vals[l % len(vals)] for l in range(20)]
+    assert kap == pytest.approx(20 / sum(1 / v for v in layer), rel=1e-10)
+
+
+def test_mixed_precision_matches_fp64_oracle():
+    k, _ = M.random_spheres((40, 36, 48), (3, 6), 0.3, 77, 1.0, 100.0)
+    ref = O.solve_direction(k, k, k, 2, rtol=1e-10)
+    rve = make(k)
+    kap, inf = rve.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
+    assert inf["status"] == B.ETC_OK
+    assert abs(kap - ref.kappa_eff) <= 1e-6 * ref.kappa_eff
+    assert inf["true_relres"] < 1e-7
+
+
+def test_solution_unpermuted_each_direction():
+    shape = (9, 10, 11)
+    rng = np.random.default_rng(5)
+    kx, ky, kz = (rng.uniform(0.5, 4.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    for d in range(3):
+        rve.solve(d, rtol=1e-11)
+        ref = O.solve_direction(kx, ky, kz, d, rtol=1e-11)
+        assert relmax(host(rve.solution(d)), ref.p) < 1e-8
+        host_out = np.empty(shape)
+        B.etc_get_solution(rve.h, d, host_out)
+        assert relmax(host_out, ref.p) < 1e-8
+
+
+# ------------------------------------------------------------------ errors & limits
+def test_invalid_arguments():
+    k = np.ones((4, 4, 4))
+    rve = make(k)
+    with pytest.raises(B.EtcError) as e:
+        rve.solve(2, p_in=1.0, p_out=1.0)
+    assert e.value.status == B.ETC_EINVAL
+    with pytest.raises(B.EtcError):
+        rve.solve(3)
+    with pytest.raises(B.EtcError):
+        rve.solve(0, rtol=-1.0)
+    bad = k.copy(); bad[1, 2, 3] = 0.0
+    with pytest.raises(B.EtcError) as e:
+        make(bad)
+    assert e.value.status == B.ETC_EINVAL
+    bad[1, 2, 3] = np.nan
+    with pytest.raises(B.EtcError):
+        make(bad)
+    with pytest.raises(B.EtcError) as e:
+        B.etc_get_solution(rve.h, 1, torch.empty((4, 4, 4), dtype=torch.float64, device="cuda"))
+    assert e.value.status == B.ETC_ESTATE
+
+
+def test_maxit_reports_noconv_with_info():
+    k, _ = M.random_spheres((24, 24, 24), (3, 5), 0.3, 9, 1.0, 1000.0)
+    rve = make(k)
+    opts = B.make_opts(rtol=1e-12, maxit=3)
+    st, kap, info = B.etc_solve_direction(rve.h, 2, 1.0, 0.0, opts)
+    assert st == B.ETC_ENOCONV
+    assert info.iters == 3 and info.status == B.ETC_ENOCONV
+    assert np.isfinite(kap) and kap > 0 and info.relres > 1e-12
+
+
+def test_deterministic_bitwise():
+    k, _ = M.random_spheres((32, 32, 32), (3, 5), 0.3, 1001, 1.0, 10.0)
+    rve = make(k)
+    a, ia = rve.solve(1, rtol=1e-10)
+    pa = host(rve.solution(1)).copy()
+    b, ib = rve.solve(1, rtol=1e-10)
+    pb = host(rve.solution(1))
+    assert a == b and ia["iters"] == ib["iters"]
+    assert np.array_equal(pa, pb)
+
+
+def test_host_pointer_input_equals_device_input():
+    k, _ = M.random_spheres((20, 22, 24), (3, 5), 0.3, 3, 1.0, 10.0)
+    h = B.etc_create_rve(24, 22, 20, 1.0, 1.0, 1.0, np.ascontiguousarray(k),
+                         stream=torch.cuda.current_stream().cuda_stream)
+    try:
+        st, kap_h, _ = B.etc_solve_direction(h, 2, 1.0, 0.0, B.make_opts(rtol=1e-10))
+    finally:
+        B.etc_destroy_rve(h)
+    kap_d, _ = make(k).solve(2, rtol=1e-10)
+    assert kap_h == kap_d
