@@ -1,0 +1,473 @@
+#!/usr/bin/env python3
+"""Benchmark of the ETC hot path on B300: DOF*iterations/s at 512^3.
+
+Workload: 512^3 voxel RVE, two-phase random non-overlapping spheres (radius
+8-20 voxels, volume fraction 0.25, seed 2001), matrix 1 and inclusions 100 and
+1000 (two RVEs of the same geometry), full 3x3 ETC tensor (three loading
+directions each), PCG to relative residual 1e-8.  One step = both tensors
+(six solves), each solve including its preparation (face assembly, LP,
+pivot tables) -- the inputs are resident in HBM before the timed region.
+
+value     = sum over the step of (voxels x PCG iterations) / time, FP64 PCG.
+mixed     = the same with the FP32 preconditioner (flexible PCG).
+e2e       = FP64 through the C ABI from pinned host buffers: create handle
+            (H2D of kappa), tensor, K back to the host, destroy -- per step.
+roofline  = dominant kernel of the FP64 iteration (CUDA events on the
+            library's stream), against the FP64 nominal peak.
+cpu_baseline / --impl reference = the CPU oracle on a bounded slab sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own copy (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution and DOF·iters/s at 512^3, FP64 vs mixed PCG, relres 1e-8"
+UNIT = "DOF*iter/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25      # dense FP64 of B300 (nominal table of the profiling recipe)
+HBM_FALLBACK_GBS = 6400.0
+SEED = 2001
+RADII = (8.0, 20.0)
+PHI = 0.25
+CONTRASTS = (100.0, 1000.0)
+RTOL = 1e-8
+KERNELS = ["matvec", "fwd_x", "fwd_y", "tridiag", "inv_y", "inv_x"]
+
+
+# ------------------------------------------------------------------ arithmetic per DOF
+def _radices(m):
+    e2 = e3 = e5 = 0
+    v = m
+    while v % 2 == 0:
+        v //= 2; e2 += 1
+    while v % 3 == 0:
+        v //= 3; e3 += 1
+    while v % 5 == 0:
+        v //= 5; e5 += 1
+    if v != 1:
+        return None
+    r = []
+    while e2 >= 3:
+        r.append(8); e2 -= 3
+    if e2 == 2:
+        r.append(4)
+    if e2 == 1:
+        if r and r[-1] == 8:
+            r[-1] = 4; r.append(4)
+        else:
+            r.append(2)
+    return r + [3] * e3 + [5] * e5
+
+
+# flops per complex point of one Stockham pass: (no twiddle, with twiddles)
+_BFLY = {2: 2.0, 3: 16.0 / 3, 4: 4.0, 5: 9.6, 8: 7.0}
+
+
+def dct_flops_per_point(n, inverse):
+    """FP64 flops (FMA = 2) per real point of one 1-D pass, as the kernels do them."""
+    rad = _radices(n // 2) if n % 2 == 0 else None
+    if rad is None:
+        return 2.0 * n
+    fft = sum(_BFLY[r] + (6.0 * (r - 1) / r if s > 0 else 0.0) for s, r in enumerate(rad))
+    return fft / 2.0 + (9.0 if inverse else 8.0)
+
+
+def kernel_model(n0, n1, mixed=False):
+    """(flops, bytes) per DOF of each kernel of one PCG iteration."""
+    fx, fy = dct_flops_per_point(n0, False), dct_flops_per_point(n1, False)
+    ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
+    if not mixed:
+        return {"matvec": (17.0, 64.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
+                "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix, 16.0)}
+    # FP32 transforms: their flops run on the FP32 pipes; FP64 work listed only
+    return {"matvec": (17.0, 60.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
+            "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 16.0)}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def sphere_mask(n):
+    from paper_2404_02433_b300 import microstructure as M
+    mask, info = M.random_spheres((n, n, n), RADII, PHI, SEED, kappa_matrix=0.0,
+                                  kappa_inclusion=1.0)
+    return mask, info
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock and throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").splitlines():
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 7:
+                continue
+            try:
+                sm.append(float(v[0])); mx.append(float(v[1]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, v[3:7]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts):
+            return parts[local_rank].strip()
+    return str(local_rank)
+
+
+def src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2404_02433_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode()); h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, mixed):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since that capture; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_512.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    meta = dict(l.split(":", 1) for l in lines if ":" in l and not l.startswith("#"))
+    if meta.get("source_hash", "").strip() != src_hash():
+        return None
+    key = ("mixed_" if mixed else "fp64_") + kernel
+    try:
+        return float(meta[key].split()[0])
+    except (KeyError, ValueError, IndexError):
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(mask, iters, warmup=0):
+    """Oracle PCG iterations (Algorithm 1) on the first 32 z-planes of the
+    kappa_inc = 1000 RVE loaded along z.  Returns (seconds per iteration, DOF, threads)."""
+    from oracle import etc_oracle as O
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([p.get("num_threads", 1) for p in threadpool_info()] or [1])
+    except Exception:
+        threads = os.cpu_count()
+    slab = np.ascontiguousarray(1.0 + (CONTRASTS[-1] - 1.0) * mask[:32])
+    nz = slab.shape[0]
+    lens = (1.0, 1.0, nz / mask.shape[0])
+    f = O.face_conductances(slab, slab, slab, lens)
+    kref = O.reference_parameters(O.group_extrema(f))
+    b = O.right_hand_side(f, 1.0, 0.0)
+    p = np.zeros_like(b)
+    r = b.copy()
+    z = O.apply_reference_inverse(r, kref)
+    w = z.copy()
+    rho = float(np.vdot(r, z))
+    times = []
+    for it in range(warmup + iters):
+        t0 = time.perf_counter()
+        q = O.apply_operator(f, w)
+        alpha = rho / float(np.vdot(q, w))
+        p = p + alpha * w
+        r = r - alpha * q
+        z = O.apply_reference_inverse(r, kref)
+        rho_new = float(np.vdot(r, z))
+        w = z + (rho_new / rho) * w
+        rho = rho_new
+        if it >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times, slab.size, threads
+
+
+# ------------------------------------------------------------------ main arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2404_02433_b300 import binding as B
+    from paper_2404_02433_b300 import build as BUILD
+
+    BUILD.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = args.n
+    mask, ginfo = sphere_mask(n)
+    kap_host = [np.ascontiguousarray(1.0 + (c - 1.0) * mask) for c in CONTRASTS]
+    stream = torch.cuda.current_stream(dev)
+    kap_dev = [torch.from_numpy(k).to(dev) for k in kap_host]
+    rves = [B.RVE(k, lengths=(1.0, 1.0, 1.0), stream=stream) for k in kap_dev]
+    del kap_dev
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def maxr(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sumr(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def step(precision):
+        Ks, iters = [], 0
+        for rv in rves:
+            K, infos, st = rv.tensor(rtol=RTOL, precision=precision)
+            if st != B.ETC_OK:
+                raise RuntimeError(f"solve status {st}")
+            Ks.append(K)
+            iters += sum(i["iters"] for i in infos)
+        return Ks, iters
+
+    def timed(precision, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            step(precision)
+        barrier(); torch.cuda.synchronize()
+        l0 = B.etc_kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(gpu_index(local_rank)) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        e0.record(stream)
+        tw = time.perf_counter()
+        iters, Ks = 0, None
+        for _ in range(steps):
+            Ks, it = step(precision)
+            iters += it
+        e1.record(stream)
+        torch.cuda.synchronize(); barrier()
+        wall = time.perf_counter() - tw
+        if sampler:
+            sampler.__exit__()
+        ms = e0.elapsed_time(e1)
+        launches = B.etc_kernel_launches() - l0
+        return ms, wall, iters, Ks, launches, (sampler.summary() if sampler else None)
+
+    # ---- FP64 (the plain method)
+    ms64, wall64, it64, K64, launches, clk = timed(B.ETC_PREC_FP64, args.steps, args.warmup, True)
+    tmax = maxr(ms64 / 1e3)
+    dof_iters = float(n) ** 3 * it64
+    value = sumr(dof_iters) / tmax
+    # ---- mixed precision (FP32 preconditioner, flexible PCG)
+    msm, wallm, itm, Km, _, _ = timed(B.ETC_PREC_MIXED, args.steps, 1)
+    tmaxm = maxr(msm / 1e3)
+    value_m = sumr(float(n) ** 3 * itm) / tmaxm
+    etc_err = max(abs(a - b) / abs(b) for K1, K2 in zip(Km, K64) for a, b in
+                  ((K1[3 * d + d], K2[3 * d + d]) for d in range(3)))
+
+    # ---- per-kernel timing of the dominant kernel (FP64 and mixed, load z, contrast 1000)
+    hbm, hbm_src = peaks()
+    prof = {}
+    for label, prec in (("fp64", B.ETC_PREC_FP64), ("mixed", B.ETC_PREC_MIXED)):
+        ms = B.etc_profile_iteration(rves[-1].h, 2, prec, 4)
+        prof[label] = dict(zip(KERNELS, ms))
+
+    def roofline(label, mixed):
+        model = kernel_model(n, n, mixed)
+        ms = prof[label]
+        k = max(ms, key=ms.get)
+        flops, byts = model[k]
+        dof = float(n) ** 3
+        t_alu = flops * dof / (FP64_NOMINAL_TFLOPS * 1e12)
+        t_hbm = byts * dof / (hbm * 1e9)
+        sec = ms[k] / 1e3
+        traffic = recorded_traffic(k, mixed)
+        if t_alu >= t_hbm:
+            ach = flops * dof / sec / 1e12
+            return {"kernel": k, "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS,
+                    "traffic": traffic, "peak_source": "FP64 nominal (recipe table)",
+                    "ms_per_launch": ms[k], "share": ms[k] / sum(ms.values())}
+        ach = byts * dof / sec / 1e9
+        return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": traffic, "peak_source": hbm_src,
+                "ms_per_launch": ms[k], "share": ms[k] / sum(ms.values())}
+
+    roof = roofline("fp64", False)
+    roof_m = roofline("mixed", True)
+
+    # ---- end to end through the C ABI from pinned host memory
+    pinned = [torch.from_numpy(k).pin_memory() for k in kap_host]
+    opts = B.make_opts(rtol=RTOL)
+
+    def e2e_step():
+        iters = 0
+        for kp in pinned:
+            h = B.etc_create_rve(n, n, n, 1.0, 1.0, 1.0, kp, stream=stream.cuda_stream)
+            try:
+                st, K, infos = B.etc_effective_tensor(h, opts)
+                iters += sum(i.iters for i in infos)
+            finally:
+                B.etc_destroy_rve(h)
+        return iters
+
+    # free the resident handles first so both fit comfortably
+    for rv in rves:
+        rv.close()
+    e2e_step()
+    barrier(); torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_e = 0
+    for _ in range(args.e2e_steps):
+        it_e += e2e_step()
+    torch.cuda.synchronize(); barrier()
+    te = maxr(time.perf_counter() - t0)
+    e2e_value = sumr(float(n) ** 3 * it_e) / te
+    h2d = 2 * 8 * n ** 3
+    d2h = 2 * (9 * 8 + 3 * 112)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{n}^3 random spheres r8-20 phi0.25 seed{SEED}, contrasts "
+                               f"1:100 and 1:1000, 3 directions each (full 3x3 tensor), "
+                               f"PCG rtol {RTOL:g}, FP64",
+                   "n": n, "achieved_fraction": ginfo["fraction"], "spheres": ginfo["spheres"],
+                   "solves_per_step": 6, "pcg_iters_per_step": it64 / args.steps,
+                   "time_to_solution_s_per_tensor": ms64 / args.steps / 2e3,
+                   "l2": "inputs larger than L2 (1 GiB per vector)",
+                   "parallelism": f"replicas x{world}"},
+        "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": msm / args.steps,
+                  "pcg_iters_per_step": itm / args.steps, "dtype": "f64 outer, f32 preconditioner",
+                  "max_rel_diff_kappa_eff_vs_fp64": etc_err,
+                  "time_to_solution_s_per_tensor": msm / args.steps / 2e3,
+                  "roofline": roof_m, "kernel_ms": prof["mixed"]},
+        "roofline": roof,
+        "kernel_ms": prof["fp64"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                "note": "create_rve from pinned host kappa + effective_tensor + K to host + "
+                        "destroy, per RVE"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        times, dof, threads = oracle_sample(mask, args.cpu_iters, warmup=0)
+        out["cpu_baseline"] = {
+            "value": dof * len(times) / sum(times), "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{len(times)} oracle PCG iterations (Algorithm 1, direct-sum DCT) on the "
+                      f"first 32 z-planes (512x512x32) of the 1:1000 RVE, load z; setup untimed"}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n = args.n
+    mask, _ = sphere_mask(n)
+    times, dof, threads = oracle_sample(mask, args.steps, warmup=args.warmup)
+    value = dof * len(times) / sum(times)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(args.gpus),
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"{n}^3 random spheres r8-20 phi0.25 seed{SEED}, 1:1000, "
+                                  f"oracle PCG iterations on a 512x512x32 slab, load z"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": "one oracle PCG iteration per step on the first 32 "
+                                      "z-planes of the 1:1000 RVE"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help=argparse.SUPPRESS)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-iters", type=int, default=4)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

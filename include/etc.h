@@ -169,6 +169,19 @@ etc_status etc_apply_preconditioner(etc_rve* rve, int dir, int precision, const 
  * Eq. (backward DCT) along both axes (FP64). */
 etc_status etc_dct_planes(etc_rve* rve, int dir, int inverse, const double* in, double* out);
 
+/*
+ * Measurement support.  etc_profile_iteration runs the initial preconditioner
+ * apply of dir and then `iters` PCG iterations with a CUDA event between
+ * consecutive kernels on the handle's stream, and writes the mean time in ms
+ * of each kernel of the iteration to ms[0..5]: matvec, forward DCT axis 0 (with
+ * the x/r update), forward DCT axis 1, tridiagonal solves, backward DCT axis 1,
+ * backward DCT axis 0.  It leaves dir marked unsolved.
+ */
+etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters, double* ms);
+
+/* Kernels launched by this library since the process started (all handles). */
+unsigned long long etc_kernel_launches(void);
+
 const char* etc_status_string(etc_status status);
 const char* etc_last_error(const etc_rve* rve);
 

@@ -23,7 +23,7 @@ EXPORTED = (
     "etc_default_opts", "etc_create_rve", "etc_destroy_rve", "etc_set_reference_params",
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
-    "etc_last_error",
+    "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
 )
 
 
@@ -81,6 +81,8 @@ def load_library(path: str | None = None):
         "etc_dct_planes": ([vp, c_int, c_int, vp, vp], c_int),
         "etc_status_string": ([c_int], ctypes.c_char_p),
         "etc_last_error": ([vp], ctypes.c_char_p),
+        "etc_profile_iteration": ([vp, c_int, c_int, c_int, dp], c_int),
+        "etc_kernel_launches": ([], ctypes.c_ulonglong),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +185,16 @@ def etc_apply_preconditioner(h, direction, precision, r, z):
 
 def etc_dct_planes(h, direction, inverse, x, y):
     return _check(load_library().etc_dct_planes(h, direction, int(inverse), _ptr(x), _ptr(y)), h)
+
+
+def etc_profile_iteration(h, direction, precision, iters):
+    ms = (c_double * 6)()
+    _check(load_library().etc_profile_iteration(h, direction, precision, iters, ms), h)
+    return [ms[i] for i in range(6)]
+
+
+def etc_kernel_launches():
+    return int(load_library().etc_kernel_launches())
 
 
 # -------------------------------------------------------------- tensor wrapper

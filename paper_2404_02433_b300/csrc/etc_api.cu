@@ -93,12 +93,10 @@ int alloc_budget() {
 }
 
 cudaError_t dev_alloc(etc_rve* h, void** p, size_t bytes) {
-  static thread_local int count = 0;
   const int budget = alloc_budget();
   if (budget >= 0) {
     if ((int)h->allocs.size() >= budget) return cudaErrorMemoryAllocation;
   }
-  (void)count;
   cudaError_t e = cudaMalloc(p, bytes == 0 ? 16 : bytes);
   if (e == cudaSuccess) h->allocs.push_back(*p);
   return e;
@@ -769,6 +767,99 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
                                      h->partials, h->stream)));
   }
   CK(cudaStreamSynchronize(h->stream));
+  return ETC_OK;
+}
+
+unsigned long long etc_kernel_launches(void) { return launch_count(); }
+
+etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, double* ms) {
+  if (!h || !ms || iters < 1) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  double kref[5];
+  reference_for(h, dir, kref);
+  s = setup_pivots(h, dir, prec, kref);
+  if (s != ETC_OK) return s;
+  const Geometry g = geom_of(h, dir);
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  const double kz = kref[2];
+  double* x = h->xsol[dir];
+  PcgState& up = h->st_host[0];
+  std::memset(&up, 0, sizeof(PcgState));
+  up.maxit = iters + 1;
+  up.flexible = (prec == ETC_PREC_MIXED);
+  CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_init(g, h->Bin, h->Bout, 1.0, 0.0, h->r, x, h->w[1], h->stream));
+  // rtol = 0: the timed iterations never take the convergence exit
+  if (prec == ETC_PREC_FP64) {
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
+                            h->partials, 0, 0.0, 0, h->stream));
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, 1, 0);
+  } else {
+    CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
+                           h->partials, 0, 0.0, 0, h->stream));
+    s = precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, 1, 0);
+  }
+  if (s != ETC_OK) return s;
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double wscale = 4.0 / ((double)g.n0 * g.n1 * kz);
+  for (int it = 0; it < iters; ++it) {
+    const int par = it & 1;
+    CK(cudaEventRecord(ev[0], h->stream));
+    if (prec == ETC_PREC_FP64) {
+      CK(launch_matvec<double>(g, h->st, h->z64, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
+                               h->T2, h->D, h->partials, par, 1, h->stream));
+      CK(cudaEventRecord(ev[1], h->stream));
+      CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[par], h->q, h->r, nullptr, h->t64,
+                              h->partials, par, 0.0, 1, h->stream));
+      CK(cudaEventRecord(ev[2], h->stream));
+      CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 1, h->stream));
+      CK(cudaEventRecord(ev[3], h->stream));
+      CK(launch_tridiag<double>(g, h->st, h->t64, h->h64, wscale, h->partials, 1, h->stream));
+      CK(cudaEventRecord(ev[4], h->stream));
+      CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 1, h->stream));
+      CK(cudaEventRecord(ev[5], h->stream));
+      CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, h->z64, h->q, 1.0 / kz, par, 1,
+                                       0, h->partials, h->stream)));
+    } else {
+      CK(launch_matvec<float>(g, h->st, h->z32, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
+                              h->T2, h->D, h->partials, par, 1, h->stream));
+      CK(cudaEventRecord(ev[1], h->stream));
+      CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[par], h->q, h->r, nullptr, h->t32,
+                             h->partials, par, 0.0, 1, h->stream));
+      CK(cudaEventRecord(ev[2], h->stream));
+      CK(launch_dct_y<float>(g, P1.p32, h->st, h->t32, 0, 1, h->stream));
+      CK(cudaEventRecord(ev[3], h->stream));
+      CK(launch_tridiag<float>(g, h->st, h->t32, h->h32, wscale, h->partials, 1, h->stream));
+      CK(cudaEventRecord(ev[4], h->stream));
+      CK(launch_dct_y<float>(g, P1.p32, h->st, h->t32, 1, 1, h->stream));
+      CK(cudaEventRecord(ev[5], h->stream));
+      CK((launch_inv_x<float, float>(g, P0.p32, h->st, h->t32, h->z32, h->q, 1.0 / kz, par, 1, 1,
+                                     h->partials, h->stream)));
+    }
+    CK(cudaEventRecord(ev[6], h->stream));
+    CK(cudaEventSynchronize(ev[6]));
+    for (int k = 0; k < 6; ++k) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      acc[k] += t;
+    }
+  }
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  s = read_state(h, 1);
+  if (s != ETC_OK) return s;
+  if (h->st_host[1].done && h->st_host[1].status == ETC_EBREAKDOWN)
+    return fail(h, ETC_EBREAKDOWN, "breakdown during profiling iterations");
+  for (int k = 0; k < 6; ++k) ms[k] = acc[k] / iters;
+  h->solved[dir] = false;
   return ETC_OK;
 }
 

@@ -49,7 +49,6 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // min, max and count of non-finite or non-positive values of one input array.
 __global__ void k_kappa_stats(const double* __restrict__ a, long long n, double* partials,
                               PcgState* st, int slot) {
-  __shared__ double sh[32];
   __shared__ int flag;
   double lo = INFINITY, hi = -INFINITY, bad = 0.0;
   for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
@@ -72,7 +71,6 @@ __global__ void k_kappa_stats(const double* __restrict__ a, long long n, double*
     for (int w = 0; w < nw; ++w) {
       vals[0] = fmin(vals[0], wl[w]); vals[1] = fmax(vals[1], wh[w]); vals[2] += wb[w];
     }
-  (void)sh;
   if (publish_values(partials, 3, vals, 3, &st->cnt[kCntExt], &flag)) {
     if (threadIdx.x == 0) {
       double l2 = INFINITY, h2 = -INFINITY, b2 = 0.0;
@@ -614,6 +612,10 @@ __global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, lon
 }
 
 // ================================================================== launchers
+static unsigned long long g_launches = 0;  // kernels launched by this library
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+static inline void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
 static inline unsigned int grid_for(long long n, int bs, int cap = 148 * 32) {
   long long gb = (n + bs - 1) / bs;
   if (gb > cap) gb = cap;
@@ -624,6 +626,7 @@ static inline unsigned int grid_for(long long n, int bs, int cap = 148 * 32) {
 cudaError_t launch_kappa_stats(const double* a, long long n, double* partials, PcgState* st,
                                int slot, cudaStream_t s) {
   k_kappa_stats<<<grid_for(n, 256, 148 * 8), 256, 0, s>>>(a, n, partials, st, slot);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -640,6 +643,7 @@ cudaError_t launch_permute(const double* in, double* out, int d0, int d1, int d2
     dim3 grid((d0 + 31) / 32, (df + 31) / 32, dother);
     k_permute_tile<<<grid, 256, 0, s>>>(in, out, d0, d1, d2, s0, so, f);
   }
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -649,6 +653,7 @@ cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, 
                          cudaStream_t s) {
   k_faces<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, ih0, ih1, ih2, k0, k1, k2, T0, T1, T2, D,
                                                      Bin, Bout, partials, st);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -657,6 +662,7 @@ cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* l
                           const double* kref, R* h, cudaStream_t s) {
   k_pivots<R><<<grid_for(g.plane, 128, 1 << 30), 128, 0, s>>>(g, lam0, lam1, kref[0], kref[1],
                                                              kref[2], kref[3], kref[4], h);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_pivots<double>(const Geometry&, const double*, const double*,
@@ -667,6 +673,7 @@ template cudaError_t launch_pivots<float>(const Geometry&, const double*, const 
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
                         double pout, double* r, double* x, double* w0, cudaStream_t s) {
   k_init<<<grid_for(g.n, 256), 256, 0, s>>>(g, Bin, Bout, pin, pout, r, x, w0);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -701,6 +708,7 @@ cudaError_t launch_matvec(const Geometry& g, PcgState* st, const TZ* z, const do
   else
     k_matvec<TZ, 1><<<grid, 256, 0, s>>>(g, st, z, wold, wnew, q, T0, T1, T2, D, partials, chunk,
                                          par);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_matvec<double>(const Geometry&, PcgState*, const double*,
@@ -780,6 +788,7 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, d
     k_fwd_x<R, 1><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
   else
     k_fwd_x<R, 2><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_fwd_x<double>(const Geometry&, const DctPlan<double>&, PcgState*,
@@ -801,6 +810,7 @@ cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState*
   dim3 grid((g.n0 + TI - 1) / TI, g.n2);
   if (inverse) k_dct_y<R, 1><<<grid, 256, sm, s>>>(g, p, st, t, TI, check);
   else k_dct_y<R, 0><<<grid, 256, sm, s>>>(g, p, st, t, TI, check);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dct_y<double>(const Geometry&, const DctPlan<double>&,
@@ -818,6 +828,7 @@ cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, do
   const unsigned int nb = tridiag_blocks(g);
   if (mode == 0) k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
   else k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_tridiag<double>(const Geometry&, PcgState*, double*, const double*,
@@ -838,6 +849,7 @@ cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, c
     k_inv_x<R, TZ, 1><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
   else
     k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
@@ -856,6 +868,7 @@ cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, co
                         double pout, double* partials, PcgState* st, cudaStream_t s) {
   k_flux<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, Bin, Bout, pin, pout,
                                                      partials, st);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -865,11 +878,13 @@ cudaError_t launch_true_residual(const Geometry& g, const double* x, const doubl
                                  double* partials, PcgState* st, cudaStream_t s) {
   k_true_residual<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, D, Bin, Bout, pin,
                                                               pout, partials, st);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s) {
   k_widen<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
+  count_launch();
   return cudaGetLastError();
 }
 

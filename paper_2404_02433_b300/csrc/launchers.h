@@ -50,6 +50,8 @@ cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s)
 template <typename R>
 cudaError_t set_smem_attrs();
 
+unsigned long long launch_count();
+
 // Grid sizes of the reduction kernels (to size the partials buffer).
 unsigned int matvec_blocks(const Geometry& g);
 unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes);

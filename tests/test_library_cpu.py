@@ -18,7 +18,8 @@ HEADER = os.path.join(ROOT, "include", "etc.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:etc_status|const char\*)\s+(etc_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:etc_status|const char\*|unsigned long long)\s+(etc_\w+)\s*\(",
+                                 text, re.M)))
 
 
 @pytest.fixture(scope="module")
