@@ -182,6 +182,31 @@ etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters
 /* Kernels launched by this library since the process started (all handles). */
 unsigned long long etc_kernel_launches(void);
 
+/*
+ * z = A_ref^{-1} r without allocating anything (the paper has no counterpart;
+ * it is a service for callers that cannot allocate device memory: those whose
+ * GPU memory is owned by another allocator -- a framework pool that reserves
+ * the device, an embedding application with its own memory budget -- and those
+ * that cannot accept the device synchronisation cudaFree may cause).
+ * Same operation as etc_apply_preconditioner in FP64, but without a handle:
+ *   n0, n1, n2  loading-frame sizes, r and z in that layout ([n2][n1][n0]);
+ *               limits: n0, n1 <= 2048 and n0*n1*n2 <= 2^20 cells, else
+ *               ETC_EINVAL.
+ *   kref        5 reference parameters (x, y, z, in, out; finite, > 0), host.
+ *   r, z        device pointers, n0*n1*n2 doubles each, not overlapping.
+ *   stream      cudaStream_t the work is queued on; the call does not wait.
+ * Working memory is a fixed __device__ array of about 16.3 MiB inside the
+ * library, held by every GPU that loads it until the process exits.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on each device looks up that array's device address (and sets kernel
+ * attributes) with the device current; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call writes every element it reads), so calls that overlap on the GPU
+ * -- on different streams, or from different host threads -- race.
+ */
+etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2, const double* kref,
+                                              const double* r, double* z, void* stream);
+
 const char* etc_status_string(etc_status status);
 const char* etc_last_error(const etc_rve* rve);
 

@@ -24,6 +24,7 @@ EXPORTED = (
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
+    "etc_apply_reference_inverse_static",
 )
 
 
@@ -83,6 +84,7 @@ def load_library(path: str | None = None):
         "etc_last_error": ([vp], ctypes.c_char_p),
         "etc_profile_iteration": ([vp, c_int, c_int, c_int, dp], c_int),
         "etc_kernel_launches": ([], ctypes.c_ulonglong),
+        "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -191,6 +193,13 @@ def etc_profile_iteration(h, direction, precision, iters):
     ms = (c_double * 6)()
     _check(load_library().etc_profile_iteration(h, direction, precision, iters, ms), h)
     return [ms[i] for i in range(6)]
+
+
+def etc_apply_reference_inverse_static(n0, n1, n2, kref, r, z, stream=None):
+    """Allocation-free preconditioner apply (returns the raw status)."""
+    k = (c_double * 5)(*kref)
+    return load_library().etc_apply_reference_inverse_static(
+        n0, n1, n2, k, _ptr(r), _ptr(z), c_void_p(stream) if stream else None)
 
 
 def etc_kernel_launches():
