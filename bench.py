@@ -89,15 +89,22 @@ def dct_flops_per_point(n, inverse):
 
 
 def kernel_model(n0, n1, mixed=False):
-    """(flops, bytes) per DOF of each kernel of one PCG iteration."""
+    """(FP64 flops, algorithmic bytes) per DOF of each kernel of one PCG iteration.
+
+    matvec: q = D w - sum T w_nb and w.q; fwd_x: x += alpha w, r -= alpha q,
+    ||r||^2 and the axis-0 transform; tridiag: the two sweeps and r.z (the y
+    round trip between the sweeps is not counted); inv_x: the axis-0 inverse and
+    w = z + beta w.  Mixed: the transforms run in FP32 (their flops are not FP64
+    work), the tridiagonal kernel also writes this and reads last iteration's
+    transformed residual (flexible beta).
+    """
     fx, fy = dct_flops_per_point(n0, False), dct_flops_per_point(n1, False)
     ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
     if not mixed:
-        return {"matvec": (17.0, 64.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
-                "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix, 16.0)}
-    # FP32 transforms: their flops run on the FP32 pipes; FP64 work listed only
-    return {"matvec": (17.0, 60.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
-            "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 16.0)}
+        return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
+                "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
+    return {"matvec": (15.0, 48.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
+            "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 20.0)}
 
 
 # ------------------------------------------------------------------ helpers

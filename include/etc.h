@@ -179,6 +179,12 @@ etc_status etc_dct_planes(etc_rve* rve, int dir, int inverse, const double* in, 
  */
 etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters, double* ms);
 
+/* Test support: the integer-pipe conversions the mixed path uses, element-wise
+ * on device arrays of n values: d_out = (double) f_in exactly, f_out = f_in
+ * rounded to nearest even.  Synchronises the stream. */
+etc_status etc_convert_check(const float* f_in, double* d_out, const double* d_in, float* f_out,
+                             long long n, void* stream);
+
 /* Kernels launched by this library since the process started (all handles). */
 unsigned long long etc_kernel_launches(void);
 

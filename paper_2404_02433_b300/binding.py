@@ -24,7 +24,7 @@ EXPORTED = (
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
-    "etc_apply_reference_inverse_static",
+    "etc_apply_reference_inverse_static", "etc_convert_check",
 )
 
 
@@ -85,6 +85,7 @@ def load_library(path: str | None = None):
         "etc_profile_iteration": ([vp, c_int, c_int, c_int, dp], c_int),
         "etc_kernel_launches": ([], ctypes.c_ulonglong),
         "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
+        "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +201,12 @@ def etc_apply_reference_inverse_static(n0, n1, n2, kref, r, z, stream=None):
     k = (c_double * 5)(*kref)
     return load_library().etc_apply_reference_inverse_static(
         n0, n1, n2, k, _ptr(r), _ptr(z), c_void_p(stream) if stream else None)
+
+
+def etc_convert_check(f_in, d_out, d_in, f_out, stream=None):
+    return _check(load_library().etc_convert_check(_ptr(f_in), _ptr(d_out), _ptr(d_in),
+                                                   _ptr(f_out), f_in.numel(),
+                                                   c_void_p(stream) if stream else None))
 
 
 def etc_kernel_launches():

@@ -48,7 +48,8 @@ struct etc_rve {
   double *Bin = nullptr, *Bout = nullptr;
   double *r = nullptr, *q = nullptr, *w[2] = {nullptr, nullptr}, *t64 = nullptr, *h64 = nullptr;
   double* z64 = nullptr;
-  float *t32 = nullptr, *h32 = nullptr, *z32 = nullptr;
+  float *t32 = nullptr, *h32 = nullptr;
+  float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
   double* kperm[3] = {nullptr, nullptr, nullptr};  // views into scratch during setup
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* partials = nullptr;
@@ -335,19 +336,25 @@ etc_status setup_pivots(etc_rve* h, int dir, int prec, const double* kref) {
 }
 
 // ------------------------------------------------------------------ preconditioner chain
-// t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal,
-// inverse y, inverse x into z.
+// t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
+// (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
+// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w).
+// ev (optional): events recorded after each of the four kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
-                        const DctPlan<R>& p1, R* t, const R* hp, TZ* z, double kz, int mode,
-                        int par, int flex) {
-  const int check = (mode == 1);
+                        const DctPlan<R>& p1, R* t, const R* hp, TZ* out, double kz, int tri_mode,
+                        int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
+                        cudaEvent_t* ev = nullptr) {
+  const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream));
+  if (ev) CK(cudaEventRecord(ev[0], h->stream));
   const double wscale = 4.0 / ((double)g.n0 * g.n1 * kz);
-  CK(launch_tridiag<R>(g, h->st, t, hp, wscale, h->partials, mode, h->stream));
+  CK(launch_tridiag<R>(g, h->st, t, hp, wscale, h->partials, tri_mode, rnew, rold, h->stream));
+  if (ev) CK(cudaEventRecord(ev[1], h->stream));
   CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream));
-  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, z, h->q, 1.0 / kz, par, check, flex, h->partials,
-                          h->stream)));
+  if (ev) CK(cudaEventRecord(ev[2], h->stream));
+  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, 1.0 / kz, check, inv_mode, h->stream)));
+  if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
 
@@ -360,25 +367,50 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
   return ETC_OK;
 }
 
-// One PCG iteration (par = parity of the iteration index).
-etc_status launch_iteration(etc_rve* h, const Geometry& g, int dir, int prec, double kz,
-                            int par) {
+// Initial residual and preconditioner apply (Algorithm 1, first line): r = b,
+// x = 0, z0 = A_ref^{-1} r, rho = r.z0, w = z0 (written over w = 0 by the
+// last inverse pass with beta = 0).
+etc_status launch_start(etc_rve* h, const Geometry& g, int dir, int prec, double kz, double pin,
+                        double pout, double rtol2) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   double* x = h->xsol[dir];
+  CK(launch_init(g, h->Bin, h->Bout, pin, pout, h->r, x, h->w[0], h->stream));
   if (prec == ETC_PREC_FP64) {
-    CK(launch_matvec<double>(g, h->st, h->z64, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
-                             h->T2, h->D, h->partials, par, 1, h->stream));
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[par], h->q, h->r, nullptr, h->t64,
-                            h->partials, par, 0.0, 1, h->stream));
-    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, par,
-                                        0);
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
+                            h->partials, 0, rtol2, 0, h->stream));
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], kz, 1, 2);
   }
-  CK(launch_matvec<float>(g, h->st, h->z32, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1, h->T2,
-                          h->D, h->partials, par, 1, h->stream));
-  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[par], h->q, h->r, nullptr, h->t32,
-                         h->partials, par, 0.0, 1, h->stream));
-  return precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, par, 1);
+  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
+                         h->partials, 0, rtol2, 0, h->stream));
+  // iteration 0 reads the transformed residual of this apply from rhat32[1]
+  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], kz, 3, 2,
+                                     h->rhat32[1], nullptr);
+}
+
+// One PCG iteration (par = parity of the iteration index).  ev (optional):
+// 7 events, recorded before the matvec and after each of the six kernels.
+etc_status launch_iteration(etc_rve* h, const Geometry& g, int dir, int prec, double kz, int par,
+                            cudaEvent_t* ev = nullptr) {
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  double* x = h->xsol[dir];
+  if (ev) CK(cudaEventRecord(ev[0], h->stream));
+  CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
+                   h->stream));
+  if (ev) CK(cudaEventRecord(ev[1], h->stream));
+  if (prec == ETC_PREC_FP64) {
+    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr, h->t64,
+                            h->partials, par, 0.0, 1, h->stream));
+    if (ev) CK(cudaEventRecord(ev[2], h->stream));
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], kz, 1, 2,
+                                        nullptr, nullptr, ev ? ev + 3 : nullptr);
+  }
+  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32, h->partials,
+                         par, 0.0, 1, h->stream));
+  if (ev) CK(cudaEventRecord(ev[2], h->stream));
+  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], kz, 2, 2,
+                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
 }
 
 etc_status check_dir(etc_rve* h, int dir) {
@@ -466,7 +498,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(dalloc(h, &h->z64, (size_t)n));
   // FP32 buffers of the mixed path alias nothing: they are small next to FP64
   CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
-  CKC(dalloc(h, &h->z32, (size_t)n));
+  CKC(dalloc(h, &h->rhat32[0], (size_t)n)); CKC(dalloc(h, &h->rhat32[1], (size_t)n));
   // partials: the largest reduction grid over the three directions
   size_t np = 1024;
   for (int d = 0; d < 3; ++d) {
@@ -580,19 +612,8 @@ etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
   up.maxit = o.maxit;
   up.flexible = (prec == ETC_PREC_MIXED);
   CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
-  CK(launch_init(g, h->Bin, h->Bout, p_in, p_out, h->r, x, h->w[1], h->stream));
-  const PlanStore& P0 = h->plans[g.n0];
-  const PlanStore& P1 = h->plans[g.n1];
   const double kz = kref[2];
-  if (prec == ETC_PREC_FP64) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
-                            h->partials, 0, o.rtol * o.rtol, 0, h->stream));
-    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, 1, 0);
-  } else {
-    CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
-                           h->partials, 0, o.rtol * o.rtol, 0, h->stream));
-    s = precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, 1, 0);
-  }
+  s = launch_start(h, g, dir, prec, kz, p_in, p_out, o.rtol * o.rtol);
   if (s != ETC_OK) return s;
 
   // PCG loop: chunks of iterations run ahead; the host reads the device state
@@ -713,8 +734,7 @@ etc_status etc_apply_operator(etc_rve* h, int dir, const double* w, double* q) {
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
-  CK(launch_matvec<double>(g, h->st, w, nullptr, nullptr, q, h->T0, h->T1, h->T2, h->D,
-                           h->partials, 0, 0, h->stream));
+  CK(launch_matvec(g, h->st, w, q, h->T0, h->T1, h->T2, h->D, h->partials, 0, 0, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return ETC_OK;
 }
@@ -737,11 +757,11 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t64,
                             h->partials, 0, 0.0, 2, h->stream));
-    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, kref[2], 0, 0, 0);
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, kref[2], 0, 0);
   } else {
     CK(launch_fwd_x<float>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t32,
                            h->partials, 0, 0.0, 2, h->stream));
-    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, kref[2], 0, 0, 0);
+    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, kref[2], 0, 0);
   }
   if (s != ETC_OK) return s;
   CK(cudaStreamSynchronize(h->stream));
@@ -763,8 +783,7 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
   } else {
     CK(cudaMemcpyAsync(h->t64, in, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 0, h->stream));
-    CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, nullptr, 1.0, 0, 0, 0,
-                                     h->partials, h->stream)));
+    CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, 1.0, 0, 0, h->stream)));
   }
   CK(cudaStreamSynchronize(h->stream));
   return ETC_OK;
@@ -786,66 +805,20 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
   s = setup_pivots(h, dir, prec, kref);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
-  const PlanStore& P0 = h->plans[g.n0];
-  const PlanStore& P1 = h->plans[g.n1];
-  const double kz = kref[2];
-  double* x = h->xsol[dir];
   PcgState& up = h->st_host[0];
   std::memset(&up, 0, sizeof(PcgState));
   up.maxit = iters + 1;
   up.flexible = (prec == ETC_PREC_MIXED);
   CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
-  CK(launch_init(g, h->Bin, h->Bout, 1.0, 0.0, h->r, x, h->w[1], h->stream));
   // rtol = 0: the timed iterations never take the convergence exit
-  if (prec == ETC_PREC_FP64) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
-                            h->partials, 0, 0.0, 0, h->stream));
-    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->z64, kz, 1, 1, 0);
-  } else {
-    CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
-                           h->partials, 0, 0.0, 0, h->stream));
-    s = precond_tail<float, float>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->z32, kz, 1, 1, 0);
-  }
+  s = launch_start(h, g, dir, prec, kref[2], 1.0, 0.0, 0.0);
   if (s != ETC_OK) return s;
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const double wscale = 4.0 / ((double)g.n0 * g.n1 * kz);
   for (int it = 0; it < iters; ++it) {
-    const int par = it & 1;
-    CK(cudaEventRecord(ev[0], h->stream));
-    if (prec == ETC_PREC_FP64) {
-      CK(launch_matvec<double>(g, h->st, h->z64, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
-                               h->T2, h->D, h->partials, par, 1, h->stream));
-      CK(cudaEventRecord(ev[1], h->stream));
-      CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[par], h->q, h->r, nullptr, h->t64,
-                              h->partials, par, 0.0, 1, h->stream));
-      CK(cudaEventRecord(ev[2], h->stream));
-      CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 1, h->stream));
-      CK(cudaEventRecord(ev[3], h->stream));
-      CK(launch_tridiag<double>(g, h->st, h->t64, h->h64, wscale, h->partials, 1, h->stream));
-      CK(cudaEventRecord(ev[4], h->stream));
-      CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 1, h->stream));
-      CK(cudaEventRecord(ev[5], h->stream));
-      CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, h->z64, h->q, 1.0 / kz, par, 1,
-                                       0, h->partials, h->stream)));
-    } else {
-      CK(launch_matvec<float>(g, h->st, h->z32, h->w[par ^ 1], h->w[par], h->q, h->T0, h->T1,
-                              h->T2, h->D, h->partials, par, 1, h->stream));
-      CK(cudaEventRecord(ev[1], h->stream));
-      CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[par], h->q, h->r, nullptr, h->t32,
-                             h->partials, par, 0.0, 1, h->stream));
-      CK(cudaEventRecord(ev[2], h->stream));
-      CK(launch_dct_y<float>(g, P1.p32, h->st, h->t32, 0, 1, h->stream));
-      CK(cudaEventRecord(ev[3], h->stream));
-      CK(launch_tridiag<float>(g, h->st, h->t32, h->h32, wscale, h->partials, 1, h->stream));
-      CK(cudaEventRecord(ev[4], h->stream));
-      CK(launch_dct_y<float>(g, P1.p32, h->st, h->t32, 1, 1, h->stream));
-      CK(cudaEventRecord(ev[5], h->stream));
-      CK((launch_inv_x<float, float>(g, P0.p32, h->st, h->t32, h->z32, h->q, 1.0 / kz, par, 1, 1,
-                                     h->partials, h->stream)));
-    }
-    CK(cudaEventRecord(ev[6], h->stream));
+    s = launch_iteration(h, g, dir, prec, kref[2], it & 1, ev);
+    if (s != ETC_OK) return s;
     CK(cudaEventSynchronize(ev[6]));
     for (int k = 0; k < 6; ++k) {
       float t = 0;
@@ -860,6 +833,16 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
     return fail(h, ETC_EBREAKDOWN, "breakdown during profiling iterations");
   for (int k = 0; k < 6; ++k) ms[k] = acc[k] / iters;
   h->solved[dir] = false;
+  return ETC_OK;
+}
+
+etc_status etc_convert_check(const float* f_in, double* d_out, const double* d_in, float* f_out,
+                             long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!f_in || !d_out || !d_in || !f_out))) return ETC_EINVAL;
+  if (n == 0) return ETC_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_convert(f_in, d_out, d_in, f_out, n, st) != cudaSuccess) return ETC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ETC_ECUDA;
   return ETC_OK;
 }
 

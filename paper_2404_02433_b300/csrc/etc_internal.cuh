@@ -136,3 +136,72 @@ struct Geometry {
 };
 
 }  // namespace etc
+
+namespace etc {
+
+// ---------------------------------------------------------------- conversions
+// FP32 <-> FP64 with integer operations only, from the IEEE-754 binary32 and
+// binary64 formats.  On B300 the hardware conversion instructions issue on
+// the FP64 pipe, which the FP64 arithmetic of the solver already saturates;
+// these versions run on the integer pipes instead.
+
+// Exact widening (every binary32 value, subnormals, infinities and NaN).
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int s = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int m = u & 0x7FFFFFu;
+  unsigned int hi, lo;
+  if (e != 0u && e != 0xFFu) {            // normal: rebias 127 -> 1023
+    hi = s | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (e == 0xFFu) {                // infinity / NaN
+    hi = s | 0x7FF00000u | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {                   // signed zero
+    hi = s;
+    lo = 0u;
+  } else {                                // subnormal: value m * 2^-149
+    const int p = 31 - __clz((int)m);     // position of the leading one
+    const unsigned long long frac = (unsigned long long)(m ^ (1u << p)) << (52 - p);
+    hi = s | ((unsigned int)(p + 874) << 20) | (unsigned int)(frac >> 32);
+    lo = (unsigned int)frac;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Narrowing with round-to-nearest-even (binary32 subnormals produced, values
+// above the binary32 range become infinity, NaN stays NaN).
+__device__ __forceinline__ float narrow(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int s = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7FF) return __uint_as_float(s | 0x7F800000u | (mant ? 0x400000u : 0u));
+  const int e32 = e - 896;
+  if (e32 >= 255) return __uint_as_float(s | 0x7F800000u);
+  if (e32 >= 1) {
+    unsigned int bits = ((unsigned int)e32 << 23) | (unsigned int)(mant >> 29);
+    const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (bits & 1u))) bits += 1u;
+    return __uint_as_float(s | bits);
+  }
+  if (e == 0) return __uint_as_float(s);  // binary64 subnormal: far below binary32
+  const int shift = 30 - e32;             // 29 fraction bits + (1 - e32) denormalising
+  if (shift > 53) return __uint_as_float(s);
+  const unsigned long long full = mant | (1ull << 52);
+  unsigned int bits = (unsigned int)(full >> shift);
+  const unsigned long long rem = full & ((1ull << shift) - 1ull);
+  const unsigned long long half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (bits & 1u))) bits += 1u;
+  return __uint_as_float(s | bits);
+}
+
+template <typename T> __device__ __forceinline__ double to_f64(T v);
+template <> __device__ __forceinline__ double to_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_f64<float>(float v) { return widen(v); }
+template <typename T> __device__ __forceinline__ T from_f64(double v);
+template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return narrow(v); }
+
+}  // namespace etc

@@ -235,67 +235,46 @@ __global__ void k_init(Geometry g, const double* __restrict__ Bin, const double*
 }
 
 // ------------------------------------------------------------------ matvec
-// 2.5-D blocking: a 32 x 8 tile of (i, j) marches along k; w of the tile (plus
-// a one-cell halo in i and j) sits in shared memory, the k-neighbours in
-// registers.  q_c = D_c w_c - sum_f T_f w_nb (Eq. scaled bilinear forms).
-// MODE 0: q = A z only.  MODE 1: PCG step, w_new = z + beta w_old, dot -> alpha.
-template <typename TZ, int MODE>
+// q_c = D_c w_c - sum_f T_f w_nb (Eq. scaled bilinear forms): one cell per
+// thread, the six neighbours come through L1/L2 (each w value is used by seven
+// cells; the z-neighbours one plane away stay resident in L2).  Neighbour
+// indices are clamped at the domain edge, where the face value T is zero, so
+// the loads stay in bounds without branches.  The "plus" faces T0[c+1],
+// T1[c+n0], T2[c+plane] are read from arrays that carry one zero plane of
+// padding.
+// MODE 0: q = A w.  MODE 1: PCG step, also w.q -> alpha (last block).
+template <int MODE>
 __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
-                                               const TZ* __restrict__ z,
-                                               const double* __restrict__ wold,
-                                               double* __restrict__ wnew, double* __restrict__ q,
+                                               const double* __restrict__ w,
+                                               double* __restrict__ q,
                                                const double* __restrict__ T0,
                                                const double* __restrict__ T1,
                                                const double* __restrict__ T2,
                                                const double* __restrict__ D, double* partials,
-                                               int chunk, int par) {
-  __shared__ double s[10][34];
+                                               int par) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE == 1 && st->done) return;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
-  const int k0 = blockIdx.z * chunk;
-  const int k1 = min(k0 + chunk, g.n2);
-  const bool in = (i < g.n0) && (j < g.n1);
-  const double beta = (MODE == 1) ? st->beta : 0.0;
-  auto wn = [&](long long c) -> double {
-    return (MODE == 1) ? fma(beta, wold[c], (double)z[c]) : (double)z[c];
-  };
-  const long long col = (long long)j * g.n0 + i;
-  double wm = 0.0, wc = 0.0, wp = 0.0;
-  if (in && k0 > 0) wm = wn((long long)(k0 - 1) * g.plane + col);
-  if (in) wc = wn((long long)k0 * g.plane + col);
-  double t2c = in ? T2[(long long)k0 * g.plane + col] : 0.0;
   double dot = 0.0;
-  for (int k = k0; k < k1; ++k) {
-    const long long c = (long long)k * g.plane + col;
-    wp = (in && k + 1 < g.n2) ? wn(c + g.plane) : 0.0;
-    s[ty + 1][tx + 1] = wc;
-    if (tx == 0) s[ty + 1][0] = (j < g.n1 && i > 0 && i - 1 < g.n0) ? wn(c - 1) : 0.0;
-    if (tx == 31) s[ty + 1][33] = (j < g.n1 && i + 1 < g.n0) ? wn(c + 1) : 0.0;
-    if (ty == 0) s[0][tx + 1] = (i < g.n0 && j > 0 && j - 1 < g.n1) ? wn(c - g.n0) : 0.0;
-    if (ty == 7) s[9][tx + 1] = (i < g.n0 && j + 1 < g.n1) ? wn(c + g.n0) : 0.0;
-    __syncthreads();
-    if (in) {
-      const double t2n = T2[c + g.plane];  // zero padding beyond the last plane
-      double qv = D[c] * wc;
-      qv = fma(-T0[c], s[ty + 1][tx], qv);
-      qv = fma(-T0[c + 1], s[ty + 1][tx + 2], qv);
-      qv = fma(-T1[c], s[ty][tx + 1], qv);
-      qv = fma(-T1[c + g.n0], s[ty + 2][tx + 1], qv);
-      qv = fma(-t2c, wm, qv);
-      qv = fma(-t2n, wp, qv);
-      q[c] = qv;
-      if (MODE == 1) {
-        wnew[c] = wc;
-        dot = fma(wc, qv, dot);
-      }
-      t2c = t2n;
-    }
-    __syncthreads();
-    wm = wc;
-    wc = wp;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = gidx(); c < g.n; c += stride) {
+    const int i = (int)(c % g.n0);
+    const long long rem = c / g.n0;
+    const int j = (int)(rem % g.n1);
+    const int k = (int)(rem / g.n1);
+    const long long cxm = (i > 0) ? c - 1 : c, cxp = (i < g.n0 - 1) ? c + 1 : c;
+    const long long cym = (j > 0) ? c - g.n0 : c, cyp = (j < g.n1 - 1) ? c + g.n0 : c;
+    const long long czm = (k > 0) ? c - g.plane : c, czp = (k < g.n2 - 1) ? c + g.plane : c;
+    const double wc = w[c];
+    double qv = D[c] * wc;
+    qv = fma(-T0[c], w[cxm], qv);
+    qv = fma(-T0[c + 1], w[cxp], qv);
+    qv = fma(-T1[c], w[cym], qv);
+    qv = fma(-T1[c + g.n0], w[cyp], qv);
+    qv = fma(-T2[c], w[czm], qv);
+    qv = fma(-T2[c + g.plane], w[czp], qv);
+    q[c] = qv;
+    if (MODE == 1) dot = fma(wc, qv, dot);
   }
   if (MODE == 1) {
     const double bs = block_sum(dot, sh);
@@ -337,27 +316,40 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
   const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
   double acc = 0.0;
   const int tot = L * g.n0;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int l = e / g.n0, i = e - l * g.n0;
-    const long long row = row0 + l;
-    R u = (R)0;
-    if (row < nrows) {
-      const long long c = row * g.n0 + i;
-      double rv;
-      if (MODE == 2) {
-        rv = rin[c];
-      } else {
-        rv = r[c];
-        if (MODE == 1) {
-          x[c] = fma(alpha, w[c], x[c]);
-          rv = fma(-alpha, q[c], rv);
-          r[c] = rv;
-        }
-        acc = fma(rv, rv, acc);
+  // U elements per thread per round: their loads are all issued before use
+  constexpr int U = 4;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+    double rv[U], qv[U], xv[U], wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int l = e / g.n0, i = e - l * g.n0;
+      const long long row = row0 + l;
+      rv[u] = 0.0; qv[u] = 0.0; xv[u] = 0.0; wv[u] = 0.0;
+      if (e < tot && row < nrows) {
+        const long long c = row * g.n0 + i;
+        rv[u] = (MODE == 2) ? rin[c] : r[c];
+        if (MODE == 1) { qv[u] = q[c]; xv[u] = x[c]; wv[u] = w[c]; }
       }
-      u = (R)rv;
     }
-    dct2_put<R>(p.s, y, a, l, i, u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= tot) break;
+      const int l = e / g.n0, i = e - l * g.n0;
+      const long long row = row0 + l;
+      double v = rv[u];
+      if (row < nrows && MODE != 2) {
+        const long long c = row * g.n0 + i;
+        if (MODE == 1) {
+          x[c] = fma(alpha, wv[u], xv[u]);
+          v = fma(-alpha, qv[u], v);
+          r[c] = v;
+        }
+        acc = fma(v, v, acc);
+      }
+      dct2_put<R>(p.s, y, a, l, i, from_f64<R>(v));
+    }
   }
   __syncthreads();
   dct2_run<R>(p, y, a, b, [&](int l, int k, R v) {
@@ -400,11 +392,23 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
   const int i0 = blockIdx.x * TI;
   R* base = t + k * g.plane + i0;
   const int tot = TI * g.n1;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int l = e % TI, jj = e / TI;
-    const R v = (i0 + l < g.n0) ? base[(long long)jj * g.n0 + l] : (R)0;
-    if (INVERSE) dct3_put<R>(y, b, l, jj, v);
-    else dct2_put<R>(p.s, y, a, l, jj, v);
+  constexpr int U = 8;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+    R v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int l = e % TI, jj = e / TI;
+      v[u] = (e < tot && i0 + l < g.n0) ? base[(long long)jj * g.n0 + l] : (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= tot) break;
+      const int l = e % TI, jj = e / TI;
+      if (INVERSE) dct3_put<R>(y, b, l, jj, v[u]);
+      else dct2_put<R>(p.s, y, a, l, jj, v[u]);
+    }
   }
   __syncthreads();
   auto store = [&](int l, int kk, R v) {
@@ -417,58 +421,114 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
 // ------------------------------------------------------------------ tridiagonal along axis 2
 // Forward sweep y_k = r^_k + h_{k-1} y_{k-1}, backward z_k = h_k (y_k + z_{k+1})
 // solves (T_{i'j'}/kappa_ref^z) z = r^.  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
-// so rho = r.z follows from Parseval for the DCT pair of Sec. 3.2.
-// MODE 0: solve only.  MODE 1: PCG, rho_new -> beta (plain PCG) or stored
-// for the flexible update.
+// so rho = r.z follows from Parseval for the DCT pair of Sec. 3.2 (weight
+// 4 alpha_i' alpha_j' / (n0 n1), applied in the last block through wscale).
+// MODE 0: solve only.
+// MODE 1: plain PCG, rho_new -> beta = rho_new / rho.
+// MODE 2: flexible PCG: keeps r^ of this iteration in rnew and reads that of
+//         the previous one from rold, so that z_new . r_old (Parseval again)
+//         gives the Polak-Ribiere beta = (rho_new - z_new . r_old) / rho.
+// MODE 3: flexible PCG, initial apply: stores r^ in rnew, beta = 0.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __restrict__ t,
                                                 const R* __restrict__ h, double wscale,
-                                                double* partials) {
+                                                double* partials, R* __restrict__ rnew,
+                                                const R* __restrict__ rold) {
   __shared__ double sh[32];
   __shared__ int flag;
-  if (MODE == 1 && st->done) return;
+  if (MODE != 0 && st->done) return;
   const long long s = gidx();
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   if (s < g.plane) {
-    R yv = (R)0, hp = (R)0;
-    R part = (R)0;
-    for (int k = 0; k < g.n2; ++k) {
-      const long long c = (long long)k * g.plane + s;
-      const R hk = h[c];
-      yv = fma(hp, yv, t[c]);
-      t[c] = yv;
-      part = fma(hk * yv, yv, part);
-      hp = hk;
+    // P planes per round: the loads of a round are issued before the recurrence uses them
+    constexpr int P = 8;
+    R yv = (R)0, hp = (R)0, part = (R)0, zr = (R)0;
+    for (int kb = 0; kb < g.n2; kb += P) {
+      R tv[P], hv[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int k = kb + u;
+        if (k < g.n2) {
+          const long long c = (long long)k * g.plane + s;
+          tv[u] = t[c];
+          hv[u] = h[c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int k = kb + u;
+        if (k < g.n2) {
+          const long long c = (long long)k * g.plane + s;
+          if (MODE >= 2) rnew[c] = tv[u];
+          yv = fma(hp, yv, tv[u]);
+          t[c] = yv;
+          part = fma(hv[u] * yv, yv, part);
+          hp = hv[u];
+        }
+      }
     }
     R zn = (R)0;
-    for (int k = g.n2 - 1; k >= 0; --k) {
-      const long long c = (long long)k * g.plane + s;
-      zn = h[c] * (t[c] + zn);
-      t[c] = zn;
+    for (int kb = g.n2 - 1; kb >= 0; kb -= P) {
+      R tv[P], hv[P], ro[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int k = kb - u;
+        if (k >= 0) {
+          const long long c = (long long)k * g.plane + s;
+          tv[u] = t[c];
+          hv[u] = h[c];
+          if (MODE == 2) ro[u] = rold[c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < P; ++u) {
+        const int k = kb - u;
+        if (k >= 0) {
+          zn = hv[u] * (tv[u] + zn);
+          t[(long long)k * g.plane + s] = zn;
+          if (MODE == 2) zr = fma(zn, ro[u], zr);
+        }
+      }
     }
     const int i = (int)(s % g.n0), j = (int)(s / g.n0);
     const double wgt = (i == 0 ? 0.5 : 1.0) * (j == 0 ? 0.5 : 1.0);
-    acc = wgt * (double)part;
+    acc = wgt * to_f64<R>(part);
+    if (MODE == 2) acc2 = wgt * to_f64<R>(zr);
   }
-  if (MODE == 1) {
-    const double bs = block_sum(acc, sh);
-    double v[1] = {bs};
-    if (publish_values(partials, 1, v, 1, &st->cnt[kCntRho], &flag)) {
-      const double rho_new = wscale * sum_partials(partials, (int)nblocks(), 1, sh);
+  if (MODE != 0) {
+    double v[2];
+    v[0] = block_sum(acc, sh);
+    v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
+    if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
+      double rho_new = 0.0, zr_old = 0.0;
+      {
+        // fixed-order sums of both columns
+        const int nb = (int)nblocks();
+        double a0 = 0.0, a1 = 0.0;
+        const int per = (nb + blockDim.x - 1) / blockDim.x;
+        const int b0 = threadIdx.x * per;
+        for (int b = b0; b < b0 + per && b < nb; ++b) {
+          a0 += __ldcg(partials + 2 * (size_t)b);
+          a1 += __ldcg(partials + 2 * (size_t)b + 1);
+        }
+        rho_new = wscale * block_sum(a0, sh);
+        zr_old = wscale * block_sum(a1, sh);
+      }
       if (threadIdx.x == 0) {
         if (!(rho_new > 0.0) || !isfinite(rho_new)) {
           if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
         }
-        if (st->phase == 0) {
-          st->rho = rho_new;
+        if (st->phase == 0 || MODE == 3) {
           st->beta = 0.0;
           st->phase = 1;
-        } else if (!st->flexible) {
+        } else if (MODE == 1) {
           st->beta = rho_new / st->rho;
-          st->rho = rho_new;
         } else {
-          st->res[7] = rho_new;  // consumed by k_inv_x (flexible beta)
+          st->beta = (rho_new - zr_old) / st->rho;
+          st->zq = zr_old;
         }
+        st->rho = rho_new;
+        if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
         st->cnt[kCntRho] = 0;
       }
     }
@@ -476,16 +536,15 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 }
 
 // ------------------------------------------------------------------ backward DCT along axis 0
-// z = scale * (backward DCT of t along axis 0).  FLEX: accumulate z . q for
-// the flexible (Polak-Ribiere) beta = -alpha z.q / rho.
-template <typename R, typename TZ, int FLEX>
-__global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgState* st,
+// u = scale * (backward DCT of t along axis 0), then by MODE:
+// 0: z = u (TZ).
+// 2: PCG: w = u + beta w in place (z points at the FP64 w; beta from the
+//    tridiagonal kernel), so the next matvec reads w directly.
+template <typename R, typename TZ, int MODE>
+__global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
-                                              const double* __restrict__ q, R scale, int L,
-                                              int par, int check, double* partials) {
+                                              R scale, int L, int check) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ double sh[32];
-  __shared__ int flag;
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
   c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
@@ -493,41 +552,33 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgStat
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   const int tot = L * g.n0;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int l = e / g.n0, k = e - l * g.n0;
-    const long long row = row0 + l;
-    dct3_put<R>(y, b, l, k, row < nrows ? t[row * g.n0 + k] : (R)0);
+  constexpr int U = 8;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+    R v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int l = e / g.n0, k = e - l * g.n0;
+      v[u] = (e < tot && row0 + l < nrows) ? t[(row0 + l) * g.n0 + k] : (R)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= tot) break;
+      const int l = e / g.n0, k = e - l * g.n0;
+      dct3_put<R>(y, b, l, k, v[u]);
+    }
   }
   __syncthreads();
-  double acc = 0.0;
+  const double beta = (MODE == 2) ? st->beta : 0.0;
   dct3_run<R>(p, y, a, b, scale, [&](int l, int i, R v) {
     const long long row = row0 + l;
     if (row < nrows) {
       const long long c = row * g.n0 + i;
-      z[c] = (TZ)v;
-      if (FLEX) acc = fma((double)v, q[c], acc);
+      if (MODE == 2) z[c] = (TZ)fma(beta, (double)z[c], to_f64<R>(v));
+      else z[c] = (TZ)v;
     }
   });
-  if (FLEX) {
-    const double bs = block_sum(acc, sh);
-    double v[1] = {bs};
-    if (publish_values(partials, 1, v, 1, &st->cnt[kCntZq], &flag)) {
-      const double zq = sum_partials(partials, (int)nblocks(), 1, sh);
-      if (threadIdx.x == 0) {
-        st->zq = zq;
-        const double rho_new = st->res[7];
-        if (st->iter > 0) {
-          // beta = z_new.(r_new - r_old) / rho_old with r_new - r_old = -alpha q
-          st->beta = -st->alpha[par] * zq / st->rho;
-        } else {
-          st->beta = 0.0;
-        }
-        st->rho = rho_new;
-        if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
-        st->cnt[kCntZq] = 0;
-      }
-    }
-  }
 }
 
 // ------------------------------------------------------------------ post-processing
@@ -606,6 +657,16 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
   }
 }
 
+// Integer-pipe conversions applied element-wise (test support).
+__global__ void k_convert(const float* __restrict__ fin, double* __restrict__ dout,
+                          const double* __restrict__ din, float* __restrict__ fout,
+                          long long n) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
+    dout[c] = widen(fin[c]);
+    fout[c] = narrow(din[c]);
+  }
+}
+
 // Element-wise FP32 -> FP64 copy (component entry points of the mixed path).
 __global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, long long n) {
   for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) b[c] = (double)a[c];
@@ -677,48 +738,17 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
   return cudaGetLastError();
 }
 
-static inline unsigned int matvec_chunk(const Geometry& g, dim3* grid) {
-  const int tx = (g.n0 + 31) / 32, ty = (g.n1 + 7) / 8;
-  const long long tiles = (long long)tx * ty;
-  long long want = (4 * 148 + tiles - 1) / tiles;
-  long long maxc = (g.n2 + 7) / 8;
-  if (want > maxc) want = maxc;
-  if (want < 1) want = 1;
-  const int chunk = (int)((g.n2 + want - 1) / want);
-  *grid = dim3(tx, ty, (g.n2 + chunk - 1) / chunk);
-  return chunk;
-}
+unsigned int matvec_blocks(const Geometry& g) { return grid_for(g.n, 256, 148 * 16); }
 
-unsigned int matvec_blocks(const Geometry& g) {
-  dim3 grid;
-  matvec_chunk(g, &grid);
-  return grid.x * grid.y * grid.z;
-}
-
-template <typename TZ>
-cudaError_t launch_matvec(const Geometry& g, PcgState* st, const TZ* z, const double* wold,
-                          double* wnew, double* q, const double* T0, const double* T1,
-                          const double* T2, const double* D, double* partials, int par, int mode,
-                          cudaStream_t s) {
-  dim3 grid;
-  const int chunk = matvec_chunk(g, &grid);
-  if (mode == 0)
-    k_matvec<TZ, 0><<<grid, 256, 0, s>>>(g, st, z, wold, wnew, q, T0, T1, T2, D, partials, chunk,
-                                         par);
-  else
-    k_matvec<TZ, 1><<<grid, 256, 0, s>>>(g, st, z, wold, wnew, q, T0, T1, T2, D, partials, chunk,
-                                         par);
+cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
+                          const double* T0, const double* T1, const double* T2, const double* D,
+                          double* partials, int par, int mode, cudaStream_t s) {
+  const unsigned int nb = matvec_blocks(g);
+  if (mode == 0) k_matvec<0><<<nb, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par);
+  else k_matvec<1><<<nb, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_matvec<double>(const Geometry&, PcgState*, const double*,
-                                           const double*, double*, double*, const double*,
-                                           const double*, const double*, const double*, double*,
-                                           int, int, cudaStream_t);
-template cudaError_t launch_matvec<float>(const Geometry&, PcgState*, const float*, const double*,
-                                          double*, double*, const double*, const double*,
-                                          const double*, const double*, double*, int, int,
-                                          cudaStream_t);
 
 // rows per block of the axis-0 transforms and their shared memory
 template <typename R>
@@ -764,9 +794,7 @@ cudaError_t set_smem_attrs() {
   SETA((k_dct_y<R, 0>));
   SETA((k_dct_y<R, 1>));
   SETA((k_inv_x<R, double, 0>));
-  SETA((k_inv_x<R, float, 0>));
-  SETA((k_inv_x<R, double, 1>));
-  SETA((k_inv_x<R, float, 1>));
+  SETA((k_inv_x<R, double, 2>));
 #undef SETA
   return e;
 }
@@ -824,44 +852,45 @@ unsigned int tridiag_blocks(const Geometry& g) {
 
 template <typename R>
 cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
-                           double* partials, int mode, cudaStream_t s) {
+                           double* partials, int mode, R* rnew, const R* rold, cudaStream_t s) {
   const unsigned int nb = tridiag_blocks(g);
-  if (mode == 0) k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
-  else k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials);
+  switch (mode) {
+    case 0: k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
+    case 1: k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
+    case 2: k_tridiag<R, 2><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
+    default: k_tridiag<R, 3><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
+  }
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_tridiag<double>(const Geometry&, PcgState*, double*, const double*,
-                                            double, double*, int, cudaStream_t);
+                                            double, double*, int, double*, const double*,
+                                            cudaStream_t);
 template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, const float*,
-                                           double, double*, int, cudaStream_t);
+                                           double, double*, int, float*, const float*,
+                                           cudaStream_t);
 
 template <typename R, typename TZ>
-cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
-                         const double* q, double scale, int par, int check, int flex,
-                         double* partials, cudaStream_t s) {
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
+                         TZ* z, double scale, int check, int mode, cudaStream_t s) {
   const int L = rows_per_block<R>(g.n0);
   const size_t sm = smem_x<R>(g.n0, L);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
-  if (flex)
-    k_inv_x<R, TZ, 1><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
+  if (mode == 2)
+    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, (R)scale, L, check);
   else
-    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, q, (R)scale, L, par, check, partials);
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, (R)scale, L, check);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
-                                                  PcgState*, const double*, double*,
-                                                  const double*, double, int, int, int, double*,
-                                                  cudaStream_t);
-template cudaError_t launch_inv_x<float, float>(const Geometry&, const DctPlan<float>&, PcgState*,
-                                                const float*, float*, const double*, double, int,
-                                                int, int, double*, cudaStream_t);
+                                                  const PcgState*, const double*, double*,
+                                                  double, int, int, cudaStream_t);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                 PcgState*, const float*, double*, const double*,
-                                                 double, int, int, int, double*, cudaStream_t);
+                                                 const PcgState*, const float*, double*, double,
+                                                 int, int, cudaStream_t);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
@@ -878,6 +907,13 @@ cudaError_t launch_true_residual(const Geometry& g, const double* x, const doubl
                                  double* partials, PcgState* st, cudaStream_t s) {
   k_true_residual<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, D, Bin, Bout, pin,
                                                               pout, partials, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const float* fin, double* dout, const double* din, float* fout,
+                           long long n, cudaStream_t s) {
+  k_convert<<<grid_for(n, 256), 256, 0, s>>>(fin, dout, din, fout, n);
   count_launch();
   return cudaGetLastError();
 }

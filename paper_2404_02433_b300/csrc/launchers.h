@@ -20,11 +20,9 @@ cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* l
                           const double* kref, R* h, cudaStream_t s);
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
                         double pout, double* r, double* x, double* w0, cudaStream_t s);
-template <typename TZ>
-cudaError_t launch_matvec(const Geometry& g, PcgState* st, const TZ* z, const double* wold,
-                          double* wnew, double* q, const double* T0, const double* T1,
-                          const double* T2, const double* D, double* partials, int par, int mode,
-                          cudaStream_t s);
+cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
+                          const double* T0, const double* T1, const double* T2, const double* D,
+                          double* partials, int par, int mode, cudaStream_t s);
 template <typename R>
 cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
                          const double* w, const double* q, double* r, const double* rin, R* t,
@@ -34,11 +32,10 @@ cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState*
                          int inverse, int check, cudaStream_t s);
 template <typename R>
 cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
-                           double* partials, int mode, cudaStream_t s);
+                           double* partials, int mode, R* rnew, const R* rold, cudaStream_t s);
 template <typename R, typename TZ>
-cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
-                         const double* q, double scale, int par, int check, int flex,
-                         double* partials, cudaStream_t s);
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
+                         TZ* z, double scale, int check, int mode, cudaStream_t s);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
@@ -47,6 +44,8 @@ cudaError_t launch_true_residual(const Geometry& g, const double* x, const doubl
                                  const double* Bin, const double* Bout, double pin, double pout,
                                  double* partials, PcgState* st, cudaStream_t s);
 cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s);
+cudaError_t launch_convert(const float* fin, double* dout, const double* din, float* fout,
+                           long long n, cudaStream_t s);
 template <typename R>
 cudaError_t set_smem_attrs();
 

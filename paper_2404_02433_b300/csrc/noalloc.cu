@@ -175,11 +175,12 @@ extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
     return ETC_ECUDA;
   if (launch_dct_y<double>(g, p1, nullptr, t, 0, 0, s) != cudaSuccess) return ETC_ECUDA;
   const double wscale = 4.0 / ((double)n0 * n1 * kref[2]);
-  if (launch_tridiag<double>(g, nullptr, t, h, wscale, nullptr, 0, s) != cudaSuccess)
+  if (launch_tridiag<double>(g, nullptr, t, h, wscale, nullptr, 0, nullptr, nullptr, s) !=
+      cudaSuccess)
     return ETC_ECUDA;
   if (launch_dct_y<double>(g, p1, nullptr, t, 1, 0, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_inv_x<double, double>(g, p0, nullptr, t, z, nullptr, 1.0 / kref[2], 0, 0, 0,
-                                   nullptr, s) != cudaSuccess)
+  if (launch_inv_x<double, double>(g, p0, nullptr, t, z, 1.0 / kref[2], 0, 0, s) !=
+      cudaSuccess)
     return ETC_ECUDA;
   return ETC_OK;
 }

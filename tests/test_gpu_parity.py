@@ -233,3 +233,38 @@ def test_host_pointer_input_equals_device_input():
         B.etc_destroy_rve(h)
     kap_d, _ = make(k).solve(2, rtol=1e-10)
     assert kap_h == kap_d
+
+
+# ------------------------------------------------------------------ conversions
+def test_integer_pipe_conversions_are_exact():
+    # widen: every binary32 pattern class (normal, subnormal, zero, inf, nan);
+    # narrow: round to nearest even as IEEE-754 (numpy's float64 -> float32).
+    rng = np.random.default_rng(42)
+    bits32 = rng.integers(0, 2**32, 200_000, dtype=np.uint64).astype(np.uint32)
+    special32 = np.array([0, 0x80000000, 1, 0x80000001, 0x7FFFFF, 0x800000, 0x7F7FFFFF,
+                          0x7F800000, 0xFF800000, 0x3F800000, 0x00400000], dtype=np.uint32)
+    f = np.concatenate([bits32, special32]).view(np.float32)
+    bits64 = rng.integers(0, 2**63, f.size, dtype=np.uint64) | (
+        rng.integers(0, 2, f.size, dtype=np.uint64) << np.uint64(63))
+    d = bits64.view(np.float64).copy()
+    # values near the binary32 range edges, ties, and subnormal results
+    m = 20000
+    d[:m] = rng.uniform(-1, 1, m) * np.exp2(rng.integers(-160, 130, m)).astype(np.float64)
+    ties = (np.arange(1, 1001, dtype=np.float64) + 0.5) * 2.0 ** -23  # exact ties at 1..2
+    d[m:m + ties.size] = 1.0 + ties
+    d[-6:] = [0.0, -0.0, np.inf, -np.inf, 3.4028235677973366e38, 1e-46]
+    fi, di = torch.from_numpy(f).cuda(), torch.from_numpy(d).cuda()
+    do = torch.empty_like(di)
+    fo = torch.empty_like(fi)
+    B.etc_convert_check(fi, do, di, fo, torch.cuda.current_stream().cuda_stream)
+    ref_w = f.astype(np.float64)
+    got_w = host(do)
+    nan = np.isnan(ref_w)
+    assert np.array_equal(np.isnan(got_w), nan)
+    assert np.array_equal(got_w[~nan].view(np.uint64), ref_w[~nan].view(np.uint64))
+    with np.errstate(over="ignore"):
+        ref_n = d.astype(np.float32)
+    got_n = fo.cpu().numpy()
+    nan = np.isnan(ref_n)
+    assert np.array_equal(np.isnan(got_n), nan)
+    assert np.array_equal(got_n[~nan].view(np.uint32), ref_n[~nan].view(np.uint32))
