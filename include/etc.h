@@ -147,6 +147,25 @@ etc_status etc_get_solution(etc_rve* rve, int dir, double* dst);
 etc_status etc_effective_tensor(etc_rve* rve, const etc_opts* opts, double* K,
                                 etc_info* info);
 
+/*
+ * Adjoint gradient of kappa_eff (Eq. effective formula dis, loading direction
+ * dir, Dirichlet data p_in, p_out) with respect to the logarithm of every voxel
+ * conductivity -- not in the paper; derived from its Sec. 2.2 discretisation.
+ * Runs the forward solve, one adjoint solve of the same operator (A symmetric;
+ * right-hand side dJ/dp = c b_out on the outflow plane, i.e. Dirichlet data
+ * (0, c) with c = L h / (n0 n1 (p_in - p_out))) and one gradient pass using the
+ * face derivatives dT/dlog kappa_a = T kappa~_b / (kappa~_a + kappa~_b).
+ *   per_component 0: grad has nx*ny*nz doubles, sum over the three components
+ *                    (the derivative for an isotropic medium kappa = exp(theta));
+ *                 1: grad has 3*nx*ny*nz doubles: components x, y, z in turn.
+ *   grad         ORIGINAL [nz][ny][nx] layout, device or host memory.
+ *   kappa_eff    receives the forward value (may be NULL).
+ *   info         NULL or 2 records: forward solve, adjoint solve.
+ * The solution of dir is kept as after etc_solve_direction.
+ */
+etc_status etc_gradient(etc_rve* rve, int dir, double p_in, double p_out, const etc_opts* opts,
+                        int per_component, double* grad, double* kappa_eff, etc_info* info);
+
 /* Loading-frame sizes (n0, n1, n2) of direction dir. */
 etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);
 

@@ -503,3 +503,60 @@ def effective_tensor(kx, ky=None, kz=None, lengths=(1.0, 1.0, 1.0), rtol=1e-10,
         K[d, d] = r.kappa_eff
         results.append(r)
     return K, results
+
+
+# --------------------------------------------------------------------------
+# Adjoint gradient d kappa_eff / d log kappa (derived from Sec. 2.2; the
+# paper has no adjoint).  J = kappa_eff of Eq. (effective formula dis).
+# --------------------------------------------------------------------------
+def adjoint_gradient(kx, ky, kz, direction, lengths=(1.0, 1.0, 1.0), p_in=1.0, p_out=0.0,
+                     rtol=1e-12, maxit=5000):
+    """Per-voxel dJ/d log kappa^a for a = x, y, z, shape (3, Nz, Ny, Nx).
+
+    J = c sum_ij b_out (p_{Nz-1} - p_out), c = L^z h^z / (Nx Ny (p_in - p_out)),
+    with A(kappa) p = b(kappa).  A is symmetric, so the adjoint lambda solves
+    A lambda = dJ/dp = c b_out on the last plane -- the right-hand side of the
+    same system with Dirichlet data (0, c).  Then
+      dJ/dtheta = dJ/dtheta|explicit + lambda.(db/dtheta - dA/dtheta p),
+    where, for theta = log kappa of one voxel and one component,
+      internal face T = 2ab/(a+b):  dT/dlog a = T b/(a+b),
+      Dirichlet faces b_in, b_out = 2 kappa~^z:  d/dlog = themselves,
+      dA/dtheta p . lambda = sum_F dT_F (p_c - p_nb)(lambda_c - lambda_nb)
+                              + d b_in p_0 lambda_0 + d b_out p_{Nz-1} lambda_{Nz-1},
+      db/dtheta . lambda = d b_in p_in lambda_0 + d b_out p_out lambda_{Nz-1},
+      dJ/dtheta|explicit = c d b_out (p_{Nz-1} - p_out).
+    Returns (grad, kappa_eff, p, lambda) with p and lambda in the loading frame.
+    """
+    (k0, k1, k2), lens = permute_medium(kx, ky, kz, lengths, direction)
+    nz, ny, nx = k0.shape
+    f = face_conductances(k0, k1, k2, lens)
+    kref = reference_parameters(group_extrema(f))
+    b = right_hand_side(f, p_in, p_out)
+    p = pcg(f, b, kref, rtol=rtol, maxit=maxit).p
+    hz = lens[2] / nz
+    c = lens[2] * hz / (nx * ny * (p_in - p_out))
+    kap = outflow_etc(f, p, lens, p_in, p_out)
+    lam = pcg(f, right_hand_side(f, 0.0, c), kref, rtol=rtol, maxit=maxit).p
+    h = (lens[0] / nx, lens[1] / ny, lens[2] / nz)
+    s = (scaled_conductivity(k0, h[0]), scaled_conductivity(k1, h[1]),
+         scaled_conductivity(k2, h[2]))
+    G = np.zeros((3,) + p.shape)
+    for ax, t in enumerate((f.t0, f.t1, f.t2)):
+        npax = 2 - ax
+        hi = [slice(None)] * 3
+        lo = [slice(None)] * 3
+        hi[npax] = slice(1, None)
+        lo[npax] = slice(None, -1)
+        hi, lo = tuple(hi), tuple(lo)
+        a, bb = s[ax][hi], s[ax][lo]
+        tf = t[hi]
+        prod = (p[hi] - p[lo]) * (lam[hi] - lam[lo])
+        G[ax][hi] -= tf * bb / (a + bb) * prod
+        G[ax][lo] -= tf * a / (a + bb) * prod
+    G[2][0] += f.b_in * lam[0] * (p_in - p[0])
+    G[2][-1] += c * f.b_out * (p[-1] - p_out) + f.b_out * lam[-1] * (p_out - p[-1])
+    frame = loading_frame(direction)
+    grad = np.zeros((3,) + kx.shape)
+    for local, axis in enumerate(frame):
+        grad[axis] = unpermute_field(G[local], direction)
+    return grad, kap, p, lam

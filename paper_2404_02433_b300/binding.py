@@ -24,7 +24,7 @@ EXPORTED = (
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
-    "etc_apply_reference_inverse_static", "etc_convert_check",
+    "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
 )
 
 
@@ -86,6 +86,8 @@ def load_library(path: str | None = None):
         "etc_kernel_launches": ([], ctypes.c_ulonglong),
         "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
         "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
+        "etc_gradient": ([vp, c_int, c_double, c_double, POINTER(EtcOpts), c_int, vp, dp,
+                          POINTER(EtcInfo)], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +211,15 @@ def etc_convert_check(f_in, d_out, d_in, f_out, stream=None):
                                                    c_void_p(stream) if stream else None))
 
 
+def etc_gradient(h, direction, grad, p_in=1.0, p_out=0.0, opts=None, per_component=0):
+    """Adjoint d kappa_eff / d log kappa into `grad`; returns (kappa_eff, [info fwd, info adj])."""
+    k = c_double()
+    info = (EtcInfo * 2)()
+    _check(load_library().etc_gradient(h, direction, p_in, p_out, byref(opts) if opts else None,
+                                       per_component, _ptr(grad), byref(k), info), h)
+    return k.value, [info[0], info[1]]
+
+
 def etc_kernel_launches():
     return int(load_library().etc_kernel_launches())
 
@@ -257,6 +268,16 @@ class RVE:
             out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
         etc_get_solution(self.h, direction, out)
         return out
+
+    def gradient(self, direction, p_in=1.0, p_out=0.0, rtol=1e-10, maxit=5000,
+                 per_component=False):
+        """(d kappa_eff / d log kappa as a CUDA tensor, kappa_eff, infos)."""
+        import torch
+        shape = ((3,) if per_component else ()) + self.shape
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        opts = make_opts(rtol, maxit, ETC_PREC_FP64, 1)
+        k, infos = etc_gradient(self.h, direction, out, p_in, p_out, opts, int(per_component))
+        return out, k, [i.as_dict() for i in infos]
 
     def loading_dims(self, direction):
         return etc_loading_dims(self.h, direction)

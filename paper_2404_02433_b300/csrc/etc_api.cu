@@ -52,6 +52,8 @@ struct etc_rve {
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
   double* kperm[3] = {nullptr, nullptr, nullptr};  // views into scratch during setup
   double* xsol[3] = {nullptr, nullptr, nullptr};
+  double* lam = nullptr;                          // adjoint field (etc_gradient)
+  double* gbuf[3] = {nullptr, nullptr, nullptr};  // loading-frame gradient components
   double* partials = nullptr;
   size_t npartials = 0;
   PcgState* st = nullptr;        // device
@@ -262,15 +264,11 @@ etc_status read_state(etc_rve* h, int slot) {
   return ETC_OK;
 }
 
-etc_status setup_faces(etc_rve* h, int dir) {
-  if (h->setup_dir == dir) return ETC_OK;
+// Loading-frame conductivity components (frame axis l carries kappa^{f[l]}),
+// permuted into the given scratch buffers unless dir is z.
+etc_status frame_components(etc_rve* h, int dir, double* const scratch[3], double* comp[3]) {
   int f[3];
   frame_of(dir, f);
-  const Geometry g = geom_of(h, dir);
-  const int N[3] = {h->nx, h->ny, h->nz};
-  double* comp[3];
-  // loading-frame component along frame axis l is kappa^{f[l]}
-  double* scratch[3] = {h->t64, h->z64, h->q};
   for (int l = 0; l < 3; ++l) {
     const double* src = h->kap[f[l]];
     bool reuse = false;
@@ -283,6 +281,19 @@ etc_status setup_faces(etc_rve* h, int dir) {
       comp[l] = scratch[l];
     }
   }
+  return ETC_OK;
+}
+
+etc_status setup_faces(etc_rve* h, int dir) {
+  if (h->setup_dir == dir) return ETC_OK;
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  const int N[3] = {h->nx, h->ny, h->nz};
+  double* comp[3];
+  double* const scratch[3] = {h->t64, h->z64, h->q};
+  etc_status cs = frame_components(h, dir, scratch, comp);
+  if (cs != ETC_OK) return cs;
   const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
   CK(launch_faces(g, 1.0 / (hh[0] * hh[0]), 1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), comp[0],
                   comp[1], comp[2], h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, h->partials,
@@ -370,11 +381,10 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
 // Initial residual and preconditioner apply (Algorithm 1, first line): r = b,
 // x = 0, z0 = A_ref^{-1} r, rho = r.z0, w = z0 (written over w = 0 by the
 // last inverse pass with beta = 0).
-etc_status launch_start(etc_rve* h, const Geometry& g, int dir, int prec, double kz, double pin,
-                        double pout, double rtol2) {
+etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, double kz,
+                        double pin, double pout, double rtol2) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
-  double* x = h->xsol[dir];
   CK(launch_init(g, h->Bin, h->Bout, pin, pout, h->r, x, h->w[0], h->stream));
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
@@ -390,11 +400,10 @@ etc_status launch_start(etc_rve* h, const Geometry& g, int dir, int prec, double
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
 // 7 events, recorded before the matvec and after each of the six kernels.
-etc_status launch_iteration(etc_rve* h, const Geometry& g, int dir, int prec, double kz, int par,
-                            cudaEvent_t* ev = nullptr) {
+etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, double kz,
+                            int par, cudaEvent_t* ev = nullptr) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
-  double* x = h->xsol[dir];
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
   CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
                    h->stream));
@@ -576,24 +585,18 @@ etc_status etc_set_reference_params(etc_rve* h, int dir, int mode, const double*
   return ETC_OK;
 }
 
-etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
-                               const etc_opts* opts_in, double* kappa_eff, etc_info* info) {
-  if (!h) return ETC_EINVAL;
-  etc_status s = check_dir(h, dir);
-  if (s != ETC_OK) return s;
-  if (!std::isfinite(p_in) || !std::isfinite(p_out) || p_in == p_out)
-    return fail(h, ETC_EINVAL, "p_in and p_out must be finite and different (Sec. 2.1)");
-  etc_opts o;
-  etc_default_opts(&o);
-  if (opts_in) o = *opts_in;
-  s = validate_opts(h, &o);
-  if (s != ETC_OK) return s;
+}  // extern "C"
+
+namespace {
+
+// One solve of direction dir into x (loading frame); arguments already valid.
+etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_opts& o,
+                      double* x, double* kappa_eff, etc_info* info) {
+  etc_status s = ETC_OK;
   const int prec = o.precision;
   const Geometry g = geom_of(h, dir);
   int f[3];
   frame_of(dir, f);
-  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
-  double* x = h->xsol[dir];
 
   cudaEvent_t e0, e1, e2;
   CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1)); CK(cudaEventCreate(&e2));
@@ -613,7 +616,7 @@ etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
   up.flexible = (prec == ETC_PREC_MIXED);
   CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
   const double kz = kref[2];
-  s = launch_start(h, g, dir, prec, kz, p_in, p_out, o.rtol * o.rtol);
+  s = launch_start(h, g, x, prec, kz, p_in, p_out, o.rtol * o.rtol);
   if (s != ETC_OK) return s;
 
   // PCG loop: chunks of iterations run ahead; the host reads the device state
@@ -628,7 +631,7 @@ etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
   const long long hard_cap = (long long)o.maxit + 64;
   for (;;) {
     for (int i = 0; i < chunk; ++i) {
-      s = launch_iteration(h, g, dir, prec, kz, launched & 1);
+      s = launch_iteration(h, g, x, prec, kz, launched & 1);
       if (s != ETC_OK) return s;
       ++launched;
     }
@@ -689,11 +692,92 @@ etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
     info->t_setup_ms = ms_setup;
     info->t_solve_ms = ms_solve;
   }
-  h->solved[dir] = true;
   if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
   if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
   return ETC_OK;
 }
+
+etc_status check_solve_args(etc_rve* h, int dir, double p_in, double p_out,
+                            const etc_opts* opts_in, etc_opts* o) {
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (!std::isfinite(p_in) || !std::isfinite(p_out) || p_in == p_out)
+    return fail(h, ETC_EINVAL, "p_in and p_out must be finite and different (Sec. 2.1)");
+  etc_default_opts(o);
+  if (opts_in) *o = *opts_in;
+  return validate_opts(h, o);
+}
+
+}  // namespace
+
+extern "C" {
+
+etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
+                               const etc_opts* opts_in, double* kappa_eff, etc_info* info) {
+  if (!h) return ETC_EINVAL;
+  etc_opts o;
+  etc_status s = check_solve_args(h, dir, p_in, p_out, opts_in, &o);
+  if (s != ETC_OK) return s;
+  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  s = solve_impl(h, dir, p_in, p_out, o, h->xsol[dir], kappa_eff, info);
+  if (s == ETC_OK || s == ETC_ENOCONV || s == ETC_EBREAKDOWN) h->solved[dir] = true;
+  return s;
+}
+
+etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const etc_opts* opts_in,
+                        int per_component, double* grad, double* kappa_eff, etc_info* info) {
+  if (!h || !grad) return ETC_EINVAL;
+  etc_opts o;
+  etc_status s = check_solve_args(h, dir, p_in, p_out, opts_in, &o);
+  if (s != ETC_OK) return s;
+  if (per_component != 0 && per_component != 1)
+    return fail(h, ETC_EINVAL, "per_component must be 0 or 1");
+  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  if (!h->lam) CK(dalloc(h, &h->lam, (size_t)h->n));
+  for (int a = 0; a < 3; ++a)
+    if (!h->gbuf[a]) CK(dalloc(h, &h->gbuf[a], (size_t)h->n));
+  etc_info inf[2];
+  double keff = 0.0, kadj = 0.0;
+  // forward solve
+  s = solve_impl(h, dir, p_in, p_out, o, h->xsol[dir], &keff, &inf[0]);
+  if (s != ETC_OK) return s;
+  h->solved[dir] = true;
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  const int N[3] = {h->nx, h->ny, h->nz};
+  const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
+  // adjoint: A lam = dJ/dx = cJ b_out on the last plane, i.e. Dirichlet data (0, cJ)
+  const double cJ = h->L[f[2]] * hh[2] / ((double)g.plane * (p_in - p_out));
+  s = solve_impl(h, dir, 0.0, cJ, o, h->lam, &kadj, &inf[1]);
+  if (s != ETC_OK) return s;
+  // loading-frame components (scratch t64, z64, q are free after the solves)
+  double* comp[3];
+  double* const scratch[3] = {h->t64, h->z64, h->q};
+  s = frame_components(h, dir, scratch, comp);
+  if (s != ETC_OK) return s;
+  CK(launch_gradient(g, h->xsol[dir], h->lam, comp[0], comp[1], comp[2], 1.0 / (hh[0] * hh[0]),
+                     1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), h->T0, h->T1, h->T2, p_in,
+                     p_out, cJ, h->gbuf[0], h->gbuf[1], h->gbuf[2], per_component ? 0 : 1,
+                     h->stream));
+  // back to the original layout; frame axis l is the component of physical axis f[l]
+  const int nout = per_component ? 3 : 1;
+  for (int l = 0; l < nout; ++l) {
+    double* dst = grad + (per_component ? (size_t)f[l] * h->n : 0);
+    if (dir == 2) {
+      CK(cudaMemcpyAsync(dst, h->gbuf[l], h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+    } else {
+      CK(from_frame(h, dir, h->gbuf[l], h->r));
+      CK(cudaMemcpyAsync(dst, h->r, h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  // the scratch permutes overwrote nothing the face cache depends on
+  if (kappa_eff) *kappa_eff = keff;
+  if (info) { info[0] = inf[0]; info[1] = inf[1]; }
+  return ETC_OK;
+}
+
 
 etc_status etc_get_solution(etc_rve* h, int dir, double* dst) {
   if (!h || !dst) return ETC_EINVAL;
@@ -811,13 +895,13 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
   up.flexible = (prec == ETC_PREC_MIXED);
   CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
   // rtol = 0: the timed iterations never take the convergence exit
-  s = launch_start(h, g, dir, prec, kref[2], 1.0, 0.0, 0.0);
+  s = launch_start(h, g, h->xsol[dir], prec, kref[2], 1.0, 0.0, 0.0);
   if (s != ETC_OK) return s;
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int it = 0; it < iters; ++it) {
-    s = launch_iteration(h, g, dir, prec, kref[2], it & 1, ev);
+    s = launch_iteration(h, g, h->xsol[dir], prec, kref[2], it & 1, ev);
     if (s != ETC_OK) return s;
     CK(cudaEventSynchronize(ev[6]));
     for (int k = 0; k < 6; ++k) {

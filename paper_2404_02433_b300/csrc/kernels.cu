@@ -657,6 +657,61 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
   }
 }
 
+// ------------------------------------------------------------------ adjoint gradient
+// d kappa_eff / d log kappa^a per cell (loading frame), from the forward field
+// x and the adjoint field lam (A lam = cJ b_out on the last plane):
+//   internal face T = 2ab/(a+b) between this cell (a) and a neighbour (b):
+//     dT/dlog a = T b/(a+b), contribution -dT (x_c - x_nb)(lam_c - lam_nb);
+//   Dirichlet faces B = 2 kappa~^z (d/dlog = B):
+//     plane 0:      B lam (p_in - x);
+//     plane n2-1:   cJ B (x - p_out) + B lam (p_out - x).
+// summed != 0 writes G0 = sum over the three components.
+__global__ void k_gradient(Geometry g, const double* __restrict__ x,
+                           const double* __restrict__ lam, const double* __restrict__ k0,
+                           const double* __restrict__ k1, const double* __restrict__ k2,
+                           double ih0, double ih1, double ih2, const double* __restrict__ T0,
+                           const double* __restrict__ T1, const double* __restrict__ T2,
+                           double pin, double pout, double cJ, double* __restrict__ G0,
+                           double* __restrict__ G1, double* __restrict__ G2, int summed) {
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n0);
+    const long long rem = c / g.n0;
+    const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
+    const double xc = x[c], lc = lam[c];
+    double gg[3] = {0.0, 0.0, 0.0};
+    const double* kk[3] = {k0, k1, k2};
+    const double* TT[3] = {T0, T1, T2};
+    const double ih[3] = {ih0, ih1, ih2};
+    const long long st[3] = {1, g.n0, g.plane};
+    const int idx[3] = {i, j, k};
+    const int nn[3] = {g.n0, g.n1, g.n2};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const double a = kk[ax][c] * ih[ax];
+      if (idx[ax] > 0) {
+        const long long m = c - st[ax];
+        const double b = kk[ax][m] * ih[ax];
+        const double dT = TT[ax][c] * b / (a + b);
+        gg[ax] -= dT * (xc - x[m]) * (lc - lam[m]);
+      }
+      if (idx[ax] < nn[ax] - 1) {
+        const long long m = c + st[ax];
+        const double b = kk[ax][m] * ih[ax];
+        const double dT = TT[ax][m] * b / (a + b);
+        gg[ax] -= dT * (xc - x[m]) * (lc - lam[m]);
+      }
+    }
+    const double B = 2.0 * k2[c] * ih2;
+    if (k == 0) gg[2] += B * lc * (pin - xc);
+    if (k == g.n2 - 1) gg[2] += cJ * B * (xc - pout) + B * lc * (pout - xc);
+    if (summed) {
+      G0[c] = gg[0] + gg[1] + gg[2];
+    } else {
+      G0[c] = gg[0]; G1[c] = gg[1]; G2[c] = gg[2];
+    }
+  }
+}
+
 // Integer-pipe conversions applied element-wise (test support).
 __global__ void k_convert(const float* __restrict__ fin, double* __restrict__ dout,
                           const double* __restrict__ din, float* __restrict__ fout,
@@ -914,6 +969,17 @@ cudaError_t launch_true_residual(const Geometry& g, const double* x, const doubl
 cudaError_t launch_convert(const float* fin, double* dout, const double* din, float* fout,
                            long long n, cudaStream_t s) {
   k_convert<<<grid_for(n, 256), 256, 0, s>>>(fin, dout, din, fout, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(const Geometry& g, const double* x, const double* lam,
+                            const double* k0, const double* k1, const double* k2, double ih0,
+                            double ih1, double ih2, const double* T0, const double* T1,
+                            const double* T2, double pin, double pout, double cJ, double* G0,
+                            double* G1, double* G2, int summed, cudaStream_t s) {
+  k_gradient<<<grid_for(g.n, 256), 256, 0, s>>>(g, x, lam, k0, k1, k2, ih0, ih1, ih2, T0, T1, T2,
+                                                pin, pout, cJ, G0, G1, G2, summed);
   count_launch();
   return cudaGetLastError();
 }

@@ -44,6 +44,11 @@ cudaError_t launch_true_residual(const Geometry& g, const double* x, const doubl
                                  const double* Bin, const double* Bout, double pin, double pout,
                                  double* partials, PcgState* st, cudaStream_t s);
 cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s);
+cudaError_t launch_gradient(const Geometry& g, const double* x, const double* lam,
+                            const double* k0, const double* k1, const double* k2, double ih0,
+                            double ih1, double ih2, const double* T0, const double* T1,
+                            const double* T2, double pin, double pout, double cJ, double* G0,
+                            double* G1, double* G2, int summed, cudaStream_t s);
 cudaError_t launch_convert(const float* fin, double* dout, const double* din, float* fout,
                            long long n, cudaStream_t s);
 template <typename R>

@@ -93,3 +93,66 @@ def two_phase_random(shape, seed, fraction=0.3, kappa_matrix=1.0, kappa_inclusio
     """Independent Bernoulli voxels (a cheap two-phase medium for tests)."""
     mask = np.random.default_rng(seed).random(shape) < fraction
     return np.where(mask, float(kappa_inclusion), float(kappa_matrix))
+
+
+def lognormal_field(shape, correlation_length, sigma, seed):
+    """kappa = exp(g), g a zero-mean Gaussian field with covariance
+    sigma^2 exp(-r / l) (r, l in voxels), by spectral synthesis on the periodic
+    box: white noise filtered by the square root of the exponential-covariance
+    spectral density, proportional to l^3 / (1 + |k|^2 l^2)^2 in 3-D; the sample
+    is then shifted and scaled to mean 0 and standard deviation sigma."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    kz = 2.0 * np.pi * np.fft.fftfreq(nz)[:, None, None]
+    ky = 2.0 * np.pi * np.fft.fftfreq(ny)[None, :, None]
+    kx = 2.0 * np.pi * np.fft.rfftfreq(nx)[None, None, :]
+    l = float(correlation_length)
+    amp = np.sqrt(l ** 3 / (1.0 + (kx ** 2 + ky ** 2 + kz ** 2) * l * l) ** 2)
+    g = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=shape, axes=(0, 1, 2))
+    g -= g.mean()
+    g *= sigma / g.std()
+    return np.exp(g)
+
+
+def random_ellipsoids(shape, semi_axes_range, fractions, kappas, seed, max_attempts=200_000):
+    """Multi-phase medium of randomly oriented ellipsoids.
+
+    Phase 0 (kappas[0]) is the matrix.  Ellipsoids of phases 1, 2, ... are
+    added in turn (semi-axes uniform in ``semi_axes_range`` voxels, centres
+    uniform over the box, orientation a uniformly random rotation) until each
+    phase p reaches voxel fraction fractions[p-1]; a voxel keeps the first phase
+    that covers it.  Returns (kappa, info) with the achieved fractions.
+    """
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    label = np.zeros(shape, dtype=np.int8)
+    total = nz * ny * nx
+    filled = [0] * len(fractions)
+    attempts = 0
+    active = [p for p in range(len(fractions)) if fractions[p] > 0]
+    while active and attempts < max_attempts:
+        for p in list(active):
+            attempts += 1
+            ax = rng.uniform(semi_axes_range[0], semi_axes_range[1], 3)
+            q, rmat = np.linalg.qr(rng.standard_normal((3, 3)))
+            q = q * np.sign(np.diag(rmat))
+            c = rng.uniform(0.0, 1.0, 3) * np.array([nx, ny, nz])
+            r = ax.max()
+            lo = np.maximum(np.floor(c - r).astype(int), 0)
+            hi = np.minimum(np.ceil(c + r).astype(int) + 1, [nx, ny, nz])
+            X = np.arange(lo[0], hi[0]) + 0.5 - c[0]
+            Y = np.arange(lo[1], hi[1]) + 0.5 - c[1]
+            Z = np.arange(lo[2], hi[2]) + 0.5 - c[2]
+            pts = np.stack(np.meshgrid(Z, Y, X, indexing="ij")[::-1], axis=-1)  # (..., xyz)
+            loc = pts @ q  # coordinates in the ellipsoid's frame
+            inside = ((loc / ax) ** 2).sum(axis=-1) <= 1.0
+            sub = label[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+            new = inside & (sub == 0)
+            sub[new] = p + 1
+            filled[p] += int(np.count_nonzero(new))
+            if filled[p] >= fractions[p] * total:
+                active.remove(p)
+    kappa = np.asarray(kappas, dtype=np.float64)[label]
+    info = {"fractions": [f / total for f in filled], "attempts": attempts}
+    return kappa, info

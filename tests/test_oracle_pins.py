@@ -291,3 +291,41 @@ def test_planted_eigenvalue_error_breaks_preconditioner_pin(monkeypatch):
     z = O.apply_reference_inverse(r, kref)
     back = O.apply_operator(O.reference_operator_faces(kref, r.shape), z)
     assert np.abs(back - r).max() > 1e-3
+
+
+# ---------------------------------------------------------------- adjoint pins
+def _kappa_eff(kx, ky, kz, d, lengths=(1.0, 1.0, 1.0)):
+    return O.solve_direction(kx, ky, kz, d, lengths, rtol=1e-13).kappa_eff
+
+
+@pytest.mark.parametrize("direction", [0, 2])
+def test_adjoint_gradient_matches_central_differences(direction):
+    shape = (4, 5, 3)
+    rng = np.random.default_rng(31 + direction)
+    kx, ky, kz = (rng.uniform(0.3, 6.0, shape) for _ in range(3))
+    lengths = (1.0, 1.2, 0.9)
+    G, kap, _, _ = O.adjoint_gradient(kx, ky, kz, direction, lengths, rtol=1e-13)
+    eps = 1e-4
+    for comp in range(3):
+        for idx in [(0, 0, 0), (3, 4, 2), (1, 2, 1), (2, 0, 2)]:
+            ks = [kx.copy(), ky.copy(), kz.copy()]
+            ks[comp][idx] *= np.exp(eps)
+            up = _kappa_eff(*ks, direction, lengths)
+            ks[comp][idx] *= np.exp(-2 * eps)
+            dn = _kappa_eff(*ks, direction, lengths)
+            fd = (up - dn) / (2 * eps)
+            assert G[comp][idx] == pytest.approx(fd, rel=1e-6, abs=1e-10 * kap)
+
+
+def test_adjoint_identities():
+    k = M.two_phase_random((6, 5, 7), seed=3, fraction=0.4, kappa_inclusion=30.0)
+    for d in range(3):
+        G, kap, p, lam = O.adjoint_gradient(k, k, k, d, p_in=2.0, p_out=0.5, rtol=1e-13)
+        # lambda = c (p_in - p) / (p_in - p_out): the constant field solves equal data
+        (k0, _, _), lens = O.permute_medium(k, k, k, (1.0, 1.0, 1.0), d)
+        nz, ny, nx = k0.shape
+        c = lens[2] * (lens[2] / nz) / (nx * ny * 1.5)
+        np.testing.assert_allclose(lam, c * (2.0 - p) / 1.5, atol=1e-10 * c)
+        # more conductance never lowers the flux; degree-1 homogeneity: sum = kappa_eff
+        assert G.min() > -1e-12 * kap
+        assert G.sum() == pytest.approx(kap, rel=1e-9)
