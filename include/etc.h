@@ -166,6 +166,31 @@ etc_status etc_effective_tensor(etc_rve* rve, const etc_opts* opts, double* K,
 etc_status etc_gradient(etc_rve* rve, int dir, double p_in, double p_out, const etc_opts* opts,
                         int per_component, double* grad, double* kappa_eff, etc_info* info);
 
+/*
+ * Batches: the full tensors of many RVEs in one CUDA graph.
+ * etc_batch_create captures, for every handle, a branch that runs its three
+ * loading directions (p_in = 1, p_out = 0) one after the other, each as a
+ * device-driven solve: face assembly, LP optimum and pivots on the device, the
+ * initial apply, a graph WHILE node whose body runs two PCG iterations and
+ * ends the loop once the device `done` flag is set (or after maxit/2 + 4
+ * passes), then the flux sums.  Branches of different handles run
+ * concurrently.  The handles must be distinct, must outlive the batch, and
+ * must not be used by other calls while a run is in progress; their reference
+ * modes are read at creation.
+ *   etc_batch_run launches the graph, waits, and fills K (count * 9 doubles,
+ *   handle i's tensor at K + 9 i, layout as etc_effective_tensor) and, if not
+ *   NULL, info (count * 3 records; t_solve_ms is the whole batch) and ms (the
+ *   batch time).  Returns the first non-OK solve status, else ETC_OK.
+ */
+typedef struct etc_batch etc_batch;
+etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opts,
+                            etc_batch** out);
+etc_status etc_batch_run(etc_batch* batch, double* K, etc_info* info, double* ms);
+etc_status etc_batch_destroy(etc_batch* batch);
+/* create + run + destroy. */
+etc_status etc_effective_tensor_batch(int count, etc_rve* const* rves, const etc_opts* opts,
+                                      double* K, etc_info* info);
+
 /* Loading-frame sizes (n0, n1, n2) of direction dir. */
 etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);
 

@@ -25,6 +25,7 @@ EXPORTED = (
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
+    "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
 )
 
 
@@ -88,6 +89,12 @@ def load_library(path: str | None = None):
         "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
         "etc_gradient": ([vp, c_int, c_double, c_double, POINTER(EtcOpts), c_int, vp, dp,
                           POINTER(EtcInfo)], c_int),
+        "etc_batch_create": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), POINTER(c_void_p)],
+                             c_int),
+        "etc_batch_run": ([vp, dp, POINTER(EtcInfo), dp], c_int),
+        "etc_batch_destroy": ([vp], c_int),
+        "etc_effective_tensor_batch": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), dp,
+                                        POINTER(EtcInfo)], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +225,41 @@ def etc_gradient(h, direction, grad, p_in=1.0, p_out=0.0, opts=None, per_compone
     _check(load_library().etc_gradient(h, direction, p_in, p_out, byref(opts) if opts else None,
                                        per_component, _ptr(grad), byref(k), info), h)
     return k.value, [info[0], info[1]]
+
+
+class Batch:
+    """Full tensors of several RVEs in one CUDA graph (etc_batch_*)."""
+
+    def __init__(self, rves, rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1):
+        lib = load_library()
+        self.rves = list(rves)
+        self.count = len(self.rves)
+        hs = (c_void_p * self.count)(*[r.h.value for r in self.rves])
+        self.opts = make_opts(rtol, maxit, precision, true_residual)
+        self.b = c_void_p()
+        _check(lib.etc_batch_create(self.count, hs, byref(self.opts), byref(self.b)))
+
+    def run(self):
+        """Returns (K as a list of 9-lists, info dicts per solve, batch ms, status)."""
+        lib = load_library()
+        K = (c_double * (9 * self.count))()
+        info = (EtcInfo * (3 * self.count))()
+        ms = c_double()
+        st = lib.etc_batch_run(self.b, K, info, byref(ms))
+        _check(st, ok=(ETC_OK, ETC_ENOCONV, ETC_EBREAKDOWN))
+        Ks = [[K[9 * i + j] for j in range(9)] for i in range(self.count)]
+        return Ks, [info[i].as_dict() for i in range(3 * self.count)], ms.value, st
+
+    def close(self):
+        if getattr(self, "b", None) and self.b.value:
+            load_library().etc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def etc_kernel_launches():

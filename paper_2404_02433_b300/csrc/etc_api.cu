@@ -8,6 +8,7 @@
 // (Algorithm 1 with Algorithm 3) on the handle's stream, then the outflow
 // formula (Eq. effective formula dis).
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -50,23 +51,17 @@ struct etc_rve {
   double* z64 = nullptr;
   float *t32 = nullptr, *h32 = nullptr;
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
-  double* kperm[3] = {nullptr, nullptr, nullptr};  // views into scratch during setup
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double* gbuf[3] = {nullptr, nullptr, nullptr};  // loading-frame gradient components
   double* partials = nullptr;
   size_t npartials = 0;
   PcgState* st = nullptr;        // device
-  PcgState* st_host = nullptr;   // pinned, 3 slots: [0] upload, [1], [2] readback
+  PcgState* st_host = nullptr;   // pinned, 3 slots used for read-backs
   std::map<int, PlanStore> plans;
-  int setup_dir = -1;            // direction whose faces are in T0..Bout
-  bool have_ext = false;
-  double ext[10];
+  int setup_dir = -1;            // direction whose faces are in T0..Bout (and st->ext)
   int ref_mode[3] = {ETC_REF_LP, ETC_REF_LP, ETC_REF_LP};
   double kref_user[3][5];
-  int pivots_for = -1;           // direction whose pivot tables are built
-  int pivots_prec = -1;
-  double pivots_kref[5];
   bool solved[3] = {false, false, false};
   std::string err;
   std::vector<void*> allocs;
@@ -264,6 +259,12 @@ etc_status read_state(etc_rve* h, int slot) {
   return ETC_OK;
 }
 
+// Device address of the reference parameters held in the state block.
+const double* kref_dev(const etc_rve* h) {
+  return reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->st) +
+                                         offsetof(PcgState, kref));
+}
+
 // Loading-frame conductivity components (frame axis l carries kappa^{f[l]}),
 // permuted into the given scratch buffers unless dir is z.
 etc_status frame_components(etc_rve* h, int dir, double* const scratch[3], double* comp[3]) {
@@ -284,8 +285,9 @@ etc_status frame_components(etc_rve* h, int dir, double* const scratch[3], doubl
   return ETC_OK;
 }
 
-etc_status setup_faces(etc_rve* h, int dir) {
-  if (h->setup_dir == dir) return ETC_OK;
+// Faces, diagonal, Dirichlet planes, group extrema and the LP optimum of dir
+// (all on the device, queued on h->stream).
+etc_status launch_setup(etc_rve* h, int dir) {
   int f[3];
   frame_of(dir, f);
   const Geometry g = geom_of(h, dir);
@@ -298,23 +300,18 @@ etc_status setup_faces(etc_rve* h, int dir) {
   CK(launch_faces(g, 1.0 / (hh[0] * hh[0]), 1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), comp[0],
                   comp[1], comp[2], h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, h->partials,
                   h->st, h->stream));
-  etc_status s = read_state(h, 1);
-  if (s != ETC_OK) return s;
-  std::memcpy(h->ext, h->st_host[1].ext, sizeof(h->ext));
-  h->setup_dir = dir;
-  h->pivots_for = -1;
   return ETC_OK;
 }
 
-// Algorithm 2: centred optimum of the LP, kappa_ref^g = sqrt(min_g max_g);
-// a group without faces gets 1.
-void lp_reference(const double* ext, double* kref) {
-  for (int gi = 0; gi < 5; ++gi) {
-    const double lo = ext[2 * gi], hi = ext[2 * gi + 1];
-    kref[gi] = (std::isfinite(lo) && std::isfinite(hi) && lo > 0) ? std::sqrt(lo * hi) : 1.0;
-  }
+etc_status setup_faces(etc_rve* h, int dir) {
+  if (h->setup_dir == dir) return ETC_OK;
+  etc_status s = launch_setup(h, dir);
+  if (s != ETC_OK) return s;
+  h->setup_dir = dir;
+  return ETC_OK;
 }
 
+// Lambda''/Lambda' of Lemma 3.1 over the groups that have faces.
 double cond_bound_of(const double* ext, const double* kref) {
   double lo = INFINITY, hi = 0.0;
   for (int gi = 0; gi < 5; ++gi) {
@@ -325,24 +322,16 @@ double cond_bound_of(const double* ext, const double* kref) {
   return hi / lo;
 }
 
-void reference_for(etc_rve* h, int dir, double* kref) {
-  if (h->ref_mode[dir] == ETC_REF_USER) std::memcpy(kref, h->kref_user[dir], 5 * sizeof(double));
-  else if (h->ref_mode[dir] == ETC_REF_ONES) for (int i = 0; i < 5; ++i) kref[i] = 1.0;
-  else lp_reference(h->ext, kref);
-}
-
-etc_status setup_pivots(etc_rve* h, int dir, int prec, const double* kref) {
-  if (h->pivots_for == dir && h->pivots_prec == prec &&
-      std::memcmp(h->pivots_kref, kref, sizeof(h->pivots_kref)) == 0)
-    return ETC_OK;
+// kref of dir's mode into the state, then the pivot tables of precision prec.
+etc_status launch_reference(etc_rve* h, int dir, int prec) {
+  CK(launch_select_kref(h->st, h->ref_mode[dir], h->kref_user[dir], h->stream));
   const Geometry g = geom_of(h, dir);
   const PlanStore& p0 = h->plans[g.n0];
   const PlanStore& p1 = h->plans[g.n1];
-  if (prec == ETC_PREC_FP64) CK(launch_pivots<double>(g, p0.lam, p1.lam, kref, h->h64, h->stream));
-  else CK(launch_pivots<float>(g, p0.lam, p1.lam, kref, h->h32, h->stream));
-  h->pivots_for = dir;
-  h->pivots_prec = prec;
-  std::memcpy(h->pivots_kref, kref, sizeof(h->pivots_kref));
+  if (prec == ETC_PREC_FP64)
+    CK(launch_pivots<double>(g, p0.lam, p1.lam, kref_dev(h), nullptr, h->h64, h->stream));
+  else
+    CK(launch_pivots<float>(g, p0.lam, p1.lam, kref_dev(h), nullptr, h->h32, h->stream));
   return ETC_OK;
 }
 
@@ -350,21 +339,22 @@ etc_status setup_pivots(etc_rve* h, int dir, int prec, const double* kref) {
 // t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
 // (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
 // inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w).
-// ev (optional): events recorded after each of the four kernels.
+// kappa_ref comes from the state.  ev (optional): events recorded after each
+// of the four kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
-                        const DctPlan<R>& p1, R* t, const R* hp, TZ* out, double kz, int tri_mode,
+                        const DctPlan<R>& p1, R* t, const R* hp, TZ* out, int tri_mode,
                         int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
                         cudaEvent_t* ev = nullptr) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  const double wscale = 4.0 / ((double)g.n0 * g.n1 * kz);
-  CK(launch_tridiag<R>(g, h->st, t, hp, wscale, h->partials, tri_mode, rnew, rold, h->stream));
+  CK(launch_tridiag<R>(g, h->st, t, hp, kref_dev(h), 1.0, h->partials, tri_mode, rnew, rold,
+                       h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, 1.0 / kz, check, inv_mode, h->stream)));
+  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream)));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
@@ -381,27 +371,27 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
 // Initial residual and preconditioner apply (Algorithm 1, first line): r = b,
 // x = 0, z0 = A_ref^{-1} r, rho = r.z0, w = z0 (written over w = 0 by the
 // last inverse pass with beta = 0).
-etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, double kz,
-                        double pin, double pout, double rtol2) {
+etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, double pin,
+                        double pout, double rtol2) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   CK(launch_init(g, h->Bin, h->Bout, pin, pout, h->r, x, h->w[0], h->stream));
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
                             h->partials, 0, rtol2, 0, h->stream));
-    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], kz, 1, 2);
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2);
   }
   CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
                          h->partials, 0, rtol2, 0, h->stream));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
-  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], kz, 3, 2,
+  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
                                      h->rhat32[1], nullptr);
 }
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
 // 7 events, recorded before the matvec and after each of the six kernels.
-etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, double kz,
-                            int par, cudaEvent_t* ev = nullptr) {
+etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, int par,
+                            cudaEvent_t* ev = nullptr) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
@@ -412,19 +402,232 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr, h->t64,
                             h->partials, par, 0.0, 1, h->stream));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
-    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], kz, 1, 2,
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2,
                                         nullptr, nullptr, ev ? ev + 3 : nullptr);
   }
   CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32, h->partials,
                          par, 0.0, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], kz, 2, 2,
+  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
                                      h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
+}
+
+// Post-processing of one solve: outflow/inflow sums, cross fluxes and the
+// true residual (queued on h->stream).
+etc_status launch_post(etc_rve* h, const Geometry& g, const double* x, double pin, double pout,
+                       int true_residual) {
+  CK(launch_flux(g, x, h->T0, h->T1, h->T2, h->Bin, h->Bout, pin, pout, h->partials, h->st,
+                 h->stream));
+  if (true_residual)
+    CK(launch_true_residual(g, x, h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, pin, pout,
+                            h->partials, h->st, h->stream));
+  return ETC_OK;
+}
+
+// kappa_eff (Eq. effective formula dis), inflow value, mean cross fluxes and
+// the info record from a finished state block.
+void fill_results(const etc_rve* h, int dir, double pin, double pout, int true_residual,
+                  const PcgState& st, double ms_setup, double ms_solve, double* kappa_eff,
+                  etc_info* info) {
+  int f[3];
+  frame_of(dir, f);
+  const Geometry g = geom_of(h, dir);
+  const int N[3] = {h->nx, h->ny, h->nz};
+  const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
+  const double dp = pin - pout;
+  const double L2 = h->L[f[2]];
+  const double keff = L2 * hh[2] * st.res[3] / ((double)g.plane * dp);
+  double vbar[3];
+  vbar[0] = hh[0] * st.res[0] / (double)g.n;
+  vbar[1] = hh[1] * st.res[1] / (double)g.n;
+  vbar[2] = hh[2] * (st.res[2] + 0.5 * st.res[3] + 0.5 * st.res[4]) / (double)g.n;
+  if (kappa_eff) *kappa_eff = keff;
+  if (info) {
+    info->iters = st.iter;
+    info->status = st.status;
+    info->relres = st.bb > 0 ? std::sqrt(st.rr / st.bb) : 0.0;
+    info->true_relres = (true_residual && st.bb > 0) ? std::sqrt(st.res[5] / st.bb) : -1.0;
+    std::memcpy(info->kref, st.kref, sizeof(info->kref));
+    info->cond_bound = cond_bound_of(st.ext, st.kref);
+    info->kappa_in = L2 * hh[2] * st.res[4] / ((double)g.plane * dp);
+    for (int l = 0; l < 3; ++l) info->column[f[l]] = h->L[dir] * vbar[l] / dp;
+    info->t_setup_ms = ms_setup;
+    info->t_solve_ms = ms_solve;
+  }
 }
 
 etc_status check_dir(etc_rve* h, int dir) {
   if (dir < 0 || dir > 2) return fail(h, ETC_EINVAL, "dir must be 0, 1 or 2");
   return ETC_OK;
+}
+
+// One solve of direction dir into x (loading frame); arguments already valid.
+// The host queues iterations in growing chunks and reads the device state of
+// the previous chunk while the next one runs.
+etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_opts& o,
+                      double* x, double* kappa_eff, etc_info* info) {
+  etc_status s = ETC_OK;
+  const int prec = o.precision;
+  const Geometry g = geom_of(h, dir);
+  cudaEvent_t e[3];
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&e[i]));
+  CK(cudaEventRecord(e[0], h->stream));
+  CK(launch_state_reset(h->st, o.maxit, h->stream));
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  s = launch_reference(h, dir, prec);
+  if (s != ETC_OK) return s;
+  CK(cudaEventRecord(e[1], h->stream));
+  s = launch_start(h, g, x, prec, p_in, p_out, o.rtol * o.rtol);
+  if (s != ETC_OK) return s;
+
+  int launched = 0, slot = 1, prev_slot = 2, chunk = 2;
+  bool have_prev = false;
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+  const long long hard_cap = (long long)o.maxit + 64;
+  for (;;) {
+    for (int i = 0; i < chunk; ++i) {
+      s = launch_iteration(h, g, x, prec, launched & 1);
+      if (s != ETC_OK) return s;
+      ++launched;
+    }
+    CK(cudaMemcpyAsync(&h->st_host[slot], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaEventRecord(ev[slot], h->stream));
+    if (have_prev) {
+      CK(cudaEventSynchronize(ev[prev_slot]));
+      if (h->st_host[prev_slot].done) break;
+    }
+    have_prev = true;
+    prev_slot = slot;
+    slot = (slot == 1) ? 2 : 1;
+    if (chunk < 16) chunk *= 2;
+    if (launched > hard_cap) {
+      CK(cudaEventSynchronize(ev[prev_slot]));
+      if (h->st_host[prev_slot].done) break;
+      return fail(h, ETC_ECUDA, "PCG did not report completion within maxit iterations");
+    }
+  }
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  s = launch_post(h, g, x, p_in, p_out, o.true_residual);
+  if (s != ETC_OK) return s;
+  CK(cudaEventRecord(e[2], h->stream));
+  s = read_state(h, 1);
+  if (s != ETC_OK) return s;
+  float ms_setup = 0, ms_solve = 0;
+  cudaEventElapsedTime(&ms_setup, e[0], e[1]);
+  cudaEventElapsedTime(&ms_solve, e[1], e[2]);
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+  const PcgState& st = h->st_host[1];
+  fill_results(h, dir, p_in, p_out, o.true_residual, st, ms_setup, ms_solve, kappa_eff, info);
+  if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
+  if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
+  return ETC_OK;
+}
+
+etc_status check_solve_args(etc_rve* h, int dir, double p_in, double p_out,
+                            const etc_opts* opts_in, etc_opts* o) {
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (!std::isfinite(p_in) || !std::isfinite(p_out) || p_in == p_out)
+    return fail(h, ETC_EINVAL, "p_in and p_out must be finite and different (Sec. 2.1)");
+  etc_default_opts(o);
+  if (opts_in) *o = *opts_in;
+  return validate_opts(h, o);
+}
+
+// Restores a handle's stream when a capture helper returns (any path).
+struct StreamSwap {
+  etc_rve* h;
+  cudaStream_t saved;
+  StreamSwap(etc_rve* hh, cudaStream_t s) : h(hh), saved(hh->stream) { h->stream = s; }
+  ~StreamSwap() { h->stream = saved; }
+};
+
+// Queue one complete device-driven solve of dir on capture stream cs: state
+// reset, setup, reference parameters, initial apply, a WHILE graph node whose
+// body runs two PCG iterations and the loop control, post-processing, and a
+// copy of the final state block into slot.  bs is the stream used to capture
+// the loop body.
+etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs,
+                         cudaStream_t bs, PcgState* slot) {
+  StreamSwap guard(h, cs);
+  const int prec = o.precision;
+  const Geometry g = geom_of(h, dir);
+  double* x = h->xsol[dir];
+  CK(launch_state_reset(h->st, o.maxit, cs));
+  etc_status s = launch_setup(h, dir);
+  if (s != ETC_OK) return s;
+  s = launch_reference(h, dir, prec);
+  if (s != ETC_OK) return s;
+  s = launch_start(h, g, x, prec, 1.0, 0.0, o.rtol * o.rtol);
+  if (s != ETC_OK) return s;
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps));
+  if (cst != cudaStreamCaptureStatusActive) return fail(h, ETC_ECUDA, "stream not capturing");
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, cg, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                         cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  {
+    StreamSwap inner(h, bs);
+    for (int par = 0; par < 2 && s == ETC_OK; ++par) s = launch_iteration(h, g, x, prec, par);
+    if (s == ETC_OK && launch_loop_control(h->st, cond, bs) != cudaSuccess) s = ETC_ECUDA;
+  }
+  cudaGraph_t ended = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(bs, &ended);
+  if (s != ETC_OK) return s;
+  CK(ee);
+  s = launch_post(h, g, x, 1.0, 0.0, o.true_residual);
+  if (s != ETC_OK) return s;
+  CK(cudaMemcpyAsync(slot, h->st, sizeof(PcgState), cudaMemcpyDeviceToDevice, cs));
+  return ETC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ batch object
+struct etc_batch {
+  int count = 0;
+  std::vector<etc_rve*> rves;
+  etc_opts o;
+  cudaStream_t main = nullptr, body = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  PcgState* slots = nullptr;       // device, count * 3
+  PcgState* slots_host = nullptr;  // pinned copy
+  std::string err;
+};
+
+namespace {
+
+void batch_release(etc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->branch) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
+  if (b->main) cudaStreamDestroy(b->main);
+  if (b->body) cudaStreamDestroy(b->body);
+  if (b->slots) cudaFree(b->slots);
+  if (b->slots_host) cudaFreeHost(b->slots_host);
 }
 
 }  // namespace
@@ -485,7 +688,6 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
     if (e_ != cudaSuccess)                                                                 \
       return bail(e_ == cudaErrorMemoryAllocation ? ETC_ENOMEM : ETC_ECUDA);               \
   } while (0)
-  // conductivities
   const double* src[3] = {kx, ky ? ky : kx, kz ? kz : kx};
   const int ncomp = h->iso ? 1 : 3;
   for (int c = 0; c < ncomp; ++c) {
@@ -493,7 +695,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
     CKC(cudaMemcpyAsync(h->kap[c], src[c], n * sizeof(double), cudaMemcpyDefault, h->stream));
   }
   if (h->iso) h->kap[1] = h->kap[2] = h->kap[0];
-  // working set; face arrays carry one extra zero plane for the matvec halo
+  // working set; face arrays carry one extra zero plane for the matvec
   const size_t nt = (size_t)n + (size_t)h->plane_max + 64;
   CKC(dalloc(h, &h->T0, nt)); CKC(dalloc(h, &h->T1, nt)); CKC(dalloc(h, &h->T2, nt));
   CKC(dalloc(h, &h->D, (size_t)n));
@@ -502,10 +704,9 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(cudaMemsetAsync(h->T2, 0, nt * sizeof(double), h->stream));
   CKC(dalloc(h, &h->Bin, (size_t)h->plane_max)); CKC(dalloc(h, &h->Bout, (size_t)h->plane_max));
   CKC(dalloc(h, &h->r, (size_t)n)); CKC(dalloc(h, &h->q, (size_t)n));
-  CKC(dalloc(h, &h->w[0], (size_t)n)); CKC(dalloc(h, &h->w[1], (size_t)n));
+  CKC(dalloc(h, &h->w[0], (size_t)n));
   CKC(dalloc(h, &h->t64, (size_t)n)); CKC(dalloc(h, &h->h64, (size_t)n));
   CKC(dalloc(h, &h->z64, (size_t)n));
-  // FP32 buffers of the mixed path alias nothing: they are small next to FP64
   CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
   CKC(dalloc(h, &h->rhat32[0], (size_t)n)); CKC(dalloc(h, &h->rhat32[1], (size_t)n));
   // partials: the largest reduction grid over the three directions
@@ -533,14 +734,13 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
     if (s != ETC_OK) return bail(s);
   }
   // validation of the conductivities (Sec. 2.1: bounded between positive constants)
-  for (int c = 0; c < ncomp; ++c) CKC(launch_kappa_stats(h->kap[c], n, h->partials, h->st, c, h->stream));
-  CKC(cudaMemcpyAsync(&h->st_host[1], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost, h->stream));
+  for (int c = 0; c < ncomp; ++c)
+    CKC(launch_kappa_stats(h->kap[c], n, h->partials, h->st, c, h->stream));
+  CKC(cudaMemcpyAsync(&h->st_host[1], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
+                      h->stream));
   CKC(cudaStreamSynchronize(h->stream));
   for (int c = 0; c < ncomp; ++c)
-    if (h->st_host[1].ext[3 * c + 2] != 0.0) {
-      release(h); delete h;
-      return ETC_EINVAL;
-    }
+    if (h->st_host[1].ext[3 * c + 2] != 0.0) return bail(ETC_EINVAL);
 #undef CKC
   *out = h;
   return ETC_OK;
@@ -580,137 +780,13 @@ etc_status etc_set_reference_params(etc_rve* h, int dir, int mode, const double*
   if (kout) {
     s = setup_faces(h, dir);
     if (s != ETC_OK) return s;
-    reference_for(h, dir, kout);
+    CK(launch_select_kref(h->st, h->ref_mode[dir], h->kref_user[dir], h->stream));
+    s = read_state(h, 1);
+    if (s != ETC_OK) return s;
+    std::memcpy(kout, h->st_host[1].kref, 5 * sizeof(double));
   }
   return ETC_OK;
 }
-
-}  // extern "C"
-
-namespace {
-
-// One solve of direction dir into x (loading frame); arguments already valid.
-etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_opts& o,
-                      double* x, double* kappa_eff, etc_info* info) {
-  etc_status s = ETC_OK;
-  const int prec = o.precision;
-  const Geometry g = geom_of(h, dir);
-  int f[3];
-  frame_of(dir, f);
-
-  cudaEvent_t e0, e1, e2;
-  CK(cudaEventCreate(&e0)); CK(cudaEventCreate(&e1)); CK(cudaEventCreate(&e2));
-  CK(cudaEventRecord(e0, h->stream));
-  s = setup_faces(h, dir);
-  if (s != ETC_OK) return s;
-  double kref[5];
-  reference_for(h, dir, kref);
-  s = setup_pivots(h, dir, prec, kref);
-  if (s != ETC_OK) return s;
-  CK(cudaEventRecord(e1, h->stream));
-
-  // initial state
-  PcgState& up = h->st_host[0];
-  std::memset(&up, 0, sizeof(PcgState));
-  up.maxit = o.maxit;
-  up.flexible = (prec == ETC_PREC_MIXED);
-  CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
-  const double kz = kref[2];
-  s = launch_start(h, g, x, prec, kz, p_in, p_out, o.rtol * o.rtol);
-  if (s != ETC_OK) return s;
-
-  // PCG loop: chunks of iterations run ahead; the host reads the device state
-  // of the previous chunk while the next one executes.
-  int launched = 0;
-  int slot = 1;
-  bool have_prev = false;
-  int prev_slot = 2;
-  cudaEvent_t ev[3];
-  for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
-  int chunk = 2;
-  const long long hard_cap = (long long)o.maxit + 64;
-  for (;;) {
-    for (int i = 0; i < chunk; ++i) {
-      s = launch_iteration(h, g, x, prec, kz, launched & 1);
-      if (s != ETC_OK) return s;
-      ++launched;
-    }
-    CK(cudaMemcpyAsync(&h->st_host[slot], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaEventRecord(ev[slot], h->stream));
-    if (have_prev) {
-      CK(cudaEventSynchronize(ev[prev_slot]));
-      if (h->st_host[prev_slot].done) break;
-    }
-    have_prev = true;
-    prev_slot = slot;
-    slot = (slot == 1) ? 2 : 1;
-    if (chunk < 16) chunk *= 2;
-    if (launched > hard_cap) {
-      CK(cudaEventSynchronize(ev[prev_slot]));
-      if (h->st_host[prev_slot].done) break;
-      return fail(h, ETC_ECUDA, "PCG did not report completion within maxit iterations");
-    }
-  }
-  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
-
-  // post-processing
-  CK(launch_flux(g, x, h->T0, h->T1, h->T2, h->Bin, h->Bout, p_in, p_out, h->partials, h->st,
-                 h->stream));
-  if (o.true_residual)
-    CK(launch_true_residual(g, x, h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, p_in, p_out,
-                            h->partials, h->st, h->stream));
-  CK(cudaEventRecord(e2, h->stream));
-  s = read_state(h, 1);
-  if (s != ETC_OK) return s;
-  const PcgState& st = h->st_host[1];
-  float ms_setup = 0, ms_solve = 0;
-  cudaEventElapsedTime(&ms_setup, e0, e1);
-  cudaEventElapsedTime(&ms_solve, e1, e2);
-  cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
-
-  const int N[3] = {h->nx, h->ny, h->nz};
-  const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
-  const double dp = p_in - p_out;
-  const double L2 = h->L[f[2]];
-  const double keff = L2 * hh[2] * st.res[3] / ((double)g.plane * dp);
-  const double kin_v = L2 * hh[2] * st.res[4] / ((double)g.plane * dp);
-  double vbar[3];
-  vbar[0] = hh[0] * st.res[0] / (double)g.n;
-  vbar[1] = hh[1] * st.res[1] / (double)g.n;
-  vbar[2] = hh[2] * (st.res[2] + 0.5 * st.res[3] + 0.5 * st.res[4]) / (double)g.n;
-  if (kappa_eff) *kappa_eff = keff;
-  if (info) {
-    info->iters = st.iter;
-    info->status = st.status;
-    info->relres = std::sqrt(st.rr / st.bb);
-    info->true_relres = o.true_residual ? std::sqrt(st.res[5] / st.bb) : -1.0;
-    std::memcpy(info->kref, kref, sizeof(kref));
-    info->cond_bound = cond_bound_of(h->ext, kref);
-    info->kappa_in = kin_v;
-    for (int l = 0; l < 3; ++l) info->column[f[l]] = h->L[dir] * vbar[l] / dp;
-    info->t_setup_ms = ms_setup;
-    info->t_solve_ms = ms_solve;
-  }
-  if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
-  if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
-  return ETC_OK;
-}
-
-etc_status check_solve_args(etc_rve* h, int dir, double p_in, double p_out,
-                            const etc_opts* opts_in, etc_opts* o) {
-  etc_status s = check_dir(h, dir);
-  if (s != ETC_OK) return s;
-  if (!std::isfinite(p_in) || !std::isfinite(p_out) || p_in == p_out)
-    return fail(h, ETC_EINVAL, "p_in and p_out must be finite and different (Sec. 2.1)");
-  etc_default_opts(o);
-  if (opts_in) *o = *opts_in;
-  return validate_opts(h, o);
-}
-
-}  // namespace
-
-extern "C" {
 
 etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
                                const etc_opts* opts_in, double* kappa_eff, etc_info* info) {
@@ -738,7 +814,6 @@ etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const et
     if (!h->gbuf[a]) CK(dalloc(h, &h->gbuf[a], (size_t)h->n));
   etc_info inf[2];
   double keff = 0.0, kadj = 0.0;
-  // forward solve
   s = solve_impl(h, dir, p_in, p_out, o, h->xsol[dir], &keff, &inf[0]);
   if (s != ETC_OK) return s;
   h->solved[dir] = true;
@@ -751,7 +826,6 @@ etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const et
   const double cJ = h->L[f[2]] * hh[2] / ((double)g.plane * (p_in - p_out));
   s = solve_impl(h, dir, 0.0, cJ, o, h->lam, &kadj, &inf[1]);
   if (s != ETC_OK) return s;
-  // loading-frame components (scratch t64, z64, q are free after the solves)
   double* comp[3];
   double* const scratch[3] = {h->t64, h->z64, h->q};
   s = frame_components(h, dir, scratch, comp);
@@ -772,12 +846,10 @@ etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const et
     }
   }
   CK(cudaStreamSynchronize(h->stream));
-  // the scratch permutes overwrote nothing the face cache depends on
   if (kappa_eff) *kappa_eff = keff;
   if (info) { info[0] = inf[0]; info[1] = inf[1]; }
   return ETC_OK;
 }
-
 
 etc_status etc_get_solution(etc_rve* h, int dir, double* dst) {
   if (!h || !dst) return ETC_EINVAL;
@@ -831,9 +903,7 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
     return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
-  double kref[5];
-  reference_for(h, dir, kref);
-  s = setup_pivots(h, dir, prec, kref);
+  s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
   const PlanStore& P0 = h->plans[g.n0];
@@ -841,11 +911,11 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t64,
                             h->partials, 0, 0.0, 2, h->stream));
-    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, kref[2], 0, 0);
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, 0, 0);
   } else {
     CK(launch_fwd_x<float>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t32,
                            h->partials, 0, 0.0, 2, h->stream));
-    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, kref[2], 0, 0);
+    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, 0, 0);
   }
   if (s != ETC_OK) return s;
   CK(cudaStreamSynchronize(h->stream));
@@ -867,7 +937,8 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
   } else {
     CK(cudaMemcpyAsync(h->t64, in, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 0, h->stream));
-    CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, 1.0, 0, 0, h->stream)));
+    CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, nullptr, 1.0, 0, 0,
+                                     h->stream)));
   }
   CK(cudaStreamSynchronize(h->stream));
   return ETC_OK;
@@ -882,26 +953,20 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
   if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED)
     return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
   if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  CK(launch_state_reset(h->st, iters + 1, h->stream));
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
-  double kref[5];
-  reference_for(h, dir, kref);
-  s = setup_pivots(h, dir, prec, kref);
+  s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
-  PcgState& up = h->st_host[0];
-  std::memset(&up, 0, sizeof(PcgState));
-  up.maxit = iters + 1;
-  up.flexible = (prec == ETC_PREC_MIXED);
-  CK(cudaMemcpyAsync(h->st, &up, sizeof(PcgState), cudaMemcpyHostToDevice, h->stream));
   // rtol = 0: the timed iterations never take the convergence exit
-  s = launch_start(h, g, h->xsol[dir], prec, kref[2], 1.0, 0.0, 0.0);
+  s = launch_start(h, g, h->xsol[dir], prec, 1.0, 0.0, 0.0);
   if (s != ETC_OK) return s;
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int it = 0; it < iters; ++it) {
-    s = launch_iteration(h, g, h->xsol[dir], prec, kref[2], it & 1, ev);
+    s = launch_iteration(h, g, h->xsol[dir], prec, it & 1, ev);
     if (s != ETC_OK) return s;
     CK(cudaEventSynchronize(ev[6]));
     for (int k = 0; k < 6; ++k) {
@@ -928,6 +993,124 @@ etc_status etc_convert_check(const float* f_in, double* d_out, const double* d_i
   if (launch_convert(f_in, d_out, d_in, f_out, n, st) != cudaSuccess) return ETC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return ETC_ECUDA;
   return ETC_OK;
+}
+
+// ------------------------------------------------------------------ batches
+etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opts_in,
+                            etc_batch** out) {
+  if (!out || count < 1 || !rves) return ETC_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!rves[i]) return ETC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (rves[j] == rves[i]) return ETC_EINVAL;
+  }
+  etc_opts o;
+  etc_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  if (validate_opts(nullptr, &o) != ETC_OK) return ETC_EINVAL;
+  etc_batch* b = new etc_batch();
+  b->count = count;
+  b->rves.assign(rves, rves + count);
+  b->o = o;
+  auto bail = [&](etc_status s) { batch_release(b); delete b; return s; };
+#define CKB(call)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(e_ == cudaErrorMemoryAllocation ? ETC_ENOMEM : ETC_ECUDA);               \
+  } while (0)
+  for (int i = 0; i < count; ++i) {
+    etc_rve* h = rves[i];
+    for (int d = 0; d < 3; ++d)
+      if (!h->xsol[d]) CKB(dalloc(h, &h->xsol[d], (size_t)h->n));
+    CKB(h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize());
+  }
+  CKB(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
+  CKB(cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking));
+  b->branch.assign(count, nullptr);
+  b->join.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    CKB(cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking));
+    CKB(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+  }
+  CKB(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  CKB(cudaEventCreate(&b->t0));
+  CKB(cudaEventCreate(&b->t1));
+  CKB(cudaMalloc(&b->slots, sizeof(PcgState) * 3 * (size_t)count));
+  CKB(cudaMallocHost(&b->slots_host, sizeof(PcgState) * 3 * (size_t)count));
+  // capture: one branch per RVE, its three directions in sequence
+  CKB(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed));
+  etc_status s = ETC_OK;
+  cudaError_t e = cudaEventRecord(b->fork, b->main);
+  for (int i = 0; i < count && s == ETC_OK && e == cudaSuccess; ++i) {
+    e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+    for (int d = 0; d < 3 && s == ETC_OK && e == cudaSuccess; ++d)
+      s = capture_solve(rves[i], d, o, b->branch[i], b->body, b->slots + 3 * i + d);
+    if (s == ETC_OK && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
+    if (s == ETC_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->main, &g);
+  b->graph = g;
+  if (s != ETC_OK) return bail(s);
+  CKB(e);
+  CKB(ee);
+  CKB(cudaGraphInstantiate(&b->exec, b->graph, 0));
+#undef CKB
+  *out = b;
+  return ETC_OK;
+}
+
+etc_status etc_batch_run(etc_batch* b, double* K, etc_info* info, double* ms) {
+  if (!b || !K) return ETC_EINVAL;
+  for (etc_rve* h : b->rves)
+    if ((h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize()) != cudaSuccess)
+      return ETC_ECUDA;
+  if (cudaEventRecord(b->t0, b->main) != cudaSuccess) return ETC_ECUDA;
+  if (cudaGraphLaunch(b->exec, b->main) != cudaSuccess) return ETC_ECUDA;
+  if (cudaEventRecord(b->t1, b->main) != cudaSuccess) return ETC_ECUDA;
+  if (cudaMemcpyAsync(b->slots_host, b->slots, sizeof(PcgState) * 3 * (size_t)b->count,
+                      cudaMemcpyDeviceToHost, b->main) != cudaSuccess)
+    return ETC_ECUDA;
+  if (cudaStreamSynchronize(b->main) != cudaSuccess) return ETC_ECUDA;
+  float t = 0;
+  cudaEventElapsedTime(&t, b->t0, b->t1);
+  if (ms) *ms = t;
+  etc_status worst = ETC_OK;
+  for (int i = 0; i < b->count; ++i) {
+    etc_rve* h = b->rves[i];
+    for (int d = 0; d < 3; ++d) {
+      const PcgState& st = b->slots_host[3 * i + d];
+      double keff = 0;
+      etc_info inf;
+      fill_results(h, d, 1.0, 0.0, b->o.true_residual, st, 0.0, t, &keff, &inf);
+      for (int a = 0; a < 3; ++a) K[9 * i + 3 * a + d] = inf.column[a];
+      K[9 * i + 3 * d + d] = keff;
+      if (info) info[3 * i + d] = inf;
+      if (st.status != ETC_OK && worst == ETC_OK) worst = st.status;
+      h->solved[d] = true;
+    }
+    h->setup_dir = 2;  // the last direction captured left its faces in place
+  }
+  return worst;
+}
+
+etc_status etc_batch_destroy(etc_batch* b) {
+  if (!b) return ETC_OK;
+  if (b->main) cudaStreamSynchronize(b->main);
+  batch_release(b);
+  delete b;
+  return ETC_OK;
+}
+
+etc_status etc_effective_tensor_batch(int count, etc_rve* const* rves, const etc_opts* opts,
+                                      double* K, etc_info* info) {
+  etc_batch* b = nullptr;
+  etc_status s = etc_batch_create(count, rves, opts, &b);
+  if (s != ETC_OK) return s;
+  s = etc_batch_run(b, K, info, nullptr);
+  etc_batch_destroy(b);
+  return s;
 }
 
 }  // extern "C"

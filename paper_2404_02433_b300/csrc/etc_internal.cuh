@@ -48,12 +48,15 @@ struct PcgState {
   double zq;         // flexible PCG: z_new . q_old
   double res[8];     // post-processing sums
   double ext[10];    // group extrema of the face assembly
+  double kref_lp[5]; // centred LP optimum sqrt(min_g max_g) (Algorithm 2), from ext
+  double kref[5];    // reference parameters in use (x, y, z, in, out)
   int iter;          // completed iterations (products with A)
   int maxit;
   int done;          // 1 once converged / stopped; kernels then return at entry
   int status;        // ETC_OK / ETC_ENOCONV / ETC_EBREAKDOWN
   int phase;         // 0 = initial preconditioner apply, 1 = iterating
-  int flexible;      // 1 = Polak-Ribiere beta (mixed precision path)
+  int passes;        // loop-body passes of a device-driven (graph) loop
+  int max_passes;    // hard cap on passes (ends the loop even without `done`)
   unsigned int cnt[8];  // arrival counters of the last-block reductions
 };
 

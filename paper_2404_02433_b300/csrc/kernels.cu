@@ -187,6 +187,11 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
           r[e + 1] = fmax(r[e + 1], __ldcg(partials + 10 * (size_t)b + e + 1));
         }
       for (int e = 0; e < 10; ++e) st->ext[e] = r[e];
+      // Algorithm 2, centred optimal point; a group without faces gets 1
+      for (int gi = 0; gi < 5; ++gi) {
+        const double lo = r[2 * gi], hi = r[2 * gi + 1];
+        st->kref_lp[gi] = (isfinite(lo) && isfinite(hi) && lo > 0.0) ? sqrt(lo * hi) : 1.0;
+      }
       st->cnt[kCntExt] = 0;
     }
   }
@@ -197,10 +202,11 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
 // stored as h_k = 1 / pivot_k in the layout of the transformed field.
 template <typename R>
 __global__ void k_pivots(Geometry g, const double* __restrict__ lam0,
-                         const double* __restrict__ lam1, double kx, double ky, double kz,
-                         double kin, double kout, R* __restrict__ h) {
+                         const double* __restrict__ lam1, const double* kd, double kx, double ky,
+                         double kz, double kin, double kout, R* __restrict__ h) {
   const long long s = gidx();
   if (s >= g.plane) return;
+  if (kd) { kx = kd[0]; ky = kd[1]; kz = kd[2]; kin = kd[3]; kout = kd[4]; }
   const int i = (int)(s % g.n0), j = (int)(s / g.n0);
   const double sv = (lam0[i] * kx + lam1[j] * ky) / kz;
   const double a_in = 2.0 * kin / kz, a_out = 2.0 * kout / kz;
@@ -215,6 +221,38 @@ __global__ void k_pivots(Geometry g, const double* __restrict__ lam0,
     hp = 1.0 / (dk - hp);
     h[(long long)k * g.plane + s] = (R)hp;
   }
+}
+
+// kref = LP optimum, all ones, or user values (Algorithm 2 / the paper's "one").
+__global__ void k_select_kref(PcgState* st, int mode, double u0, double u1, double u2, double u3,
+                              double u4) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double u[5] = {u0, u1, u2, u3, u4};
+  for (int gi = 0; gi < 5; ++gi)
+    st->kref[gi] = (mode == 0) ? st->kref_lp[gi] : (mode == 1 ? 1.0 : u[gi]);
+}
+
+// Clear the PCG part of the state before a solve (extrema and kref are kept).
+__global__ void k_state_reset(PcgState* st, int maxit) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->rho = 0.0; st->beta = 0.0; st->alpha[0] = 0.0; st->alpha[1] = 0.0;
+  st->rr = 0.0; st->bb = 0.0; st->thresh2 = 0.0; st->dq = 0.0; st->zq = 0.0;
+  for (int e = 0; e < 8; ++e) { st->res[e] = 0.0; st->cnt[e] = 0u; }
+  st->iter = 0; st->maxit = maxit; st->done = 0; st->status = kOK; st->phase = 0;
+  st->passes = 0;
+  st->max_passes = maxit / 2 + 4;  // the loop body runs two iterations
+}
+
+// End of one pass of a device-driven PCG loop (graph WHILE node): stop when
+// the solve is done, or after max_passes passes whatever happened.
+__global__ void k_loop_control(PcgState* st, cudaGraphConditionalHandle handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->passes += 1;
+  if (!st->done && st->passes >= st->max_passes) {
+    st->status = kENOCONV;
+    st->done = 1;
+  }
+  if (st->done) cudaGraphSetConditional(handle, 0u);
 }
 
 // ------------------------------------------------------------------ init
@@ -431,7 +469,8 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
 // MODE 3: flexible PCG, initial apply: stores r^ in rnew, beta = 0.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __restrict__ t,
-                                                const R* __restrict__ h, double wscale,
+                                                const R* __restrict__ h, double w4,
+                                                const double* kd, double kz_host,
                                                 double* partials, R* __restrict__ rnew,
                                                 const R* __restrict__ rold) {
   __shared__ double sh[32];
@@ -500,6 +539,7 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
     v[0] = block_sum(acc, sh);
     v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
     if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
+      const double wscale = w4 / (kd ? kd[2] : kz_host);
       double rho_new = 0.0, zr_old = 0.0;
       {
         // fixed-order sums of both columns
@@ -543,7 +583,8 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 template <typename R, typename TZ, int MODE>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
-                                              R scale, int L, int check) {
+                                              const double* kd, double kz_host, int L,
+                                              int check) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
@@ -571,6 +612,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
   }
   __syncthreads();
   const double beta = (MODE == 2) ? st->beta : 0.0;
+  const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
   dct3_run<R>(p, y, a, b, scale, [&](int l, int i, R v) {
     const long long row = row0 + l;
     if (row < nrows) {
@@ -775,16 +817,38 @@ cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, 
 
 template <typename R>
 cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* lam1,
-                          const double* kref, R* h, cudaStream_t s) {
-  k_pivots<R><<<grid_for(g.plane, 128, 1 << 30), 128, 0, s>>>(g, lam0, lam1, kref[0], kref[1],
-                                                             kref[2], kref[3], kref[4], h);
+                          const double* kref_dev, const double* kref_host, R* h, cudaStream_t s) {
+  const double* k = kref_host;
+  const double z[5] = {1, 1, 1, 1, 1};
+  if (!k) k = z;
+  k_pivots<R><<<grid_for(g.plane, 128, 1 << 30), 128, 0, s>>>(g, lam0, lam1, kref_dev, k[0], k[1],
+                                                             k[2], k[3], k[4], h);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_pivots<double>(const Geometry&, const double*, const double*,
-                                           const double*, double*, cudaStream_t);
+                                           const double*, const double*, double*, cudaStream_t);
 template cudaError_t launch_pivots<float>(const Geometry&, const double*, const double*,
-                                          const double*, float*, cudaStream_t);
+                                          const double*, const double*, float*, cudaStream_t);
+
+cudaError_t launch_select_kref(PcgState* st, int mode, const double* user, cudaStream_t s) {
+  k_select_kref<<<1, 32, 0, s>>>(st, mode, user[0], user[1], user[2], user[3], user[4]);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_reset(PcgState* st, int maxit, cudaStream_t s) {
+  k_state_reset<<<1, 32, 0, s>>>(st, maxit);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_control(PcgState* st, cudaGraphConditionalHandle handle,
+                                cudaStream_t s) {
+  k_loop_control<<<1, 32, 0, s>>>(st, handle);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
                         double pout, double* r, double* x, double* w0, cudaStream_t s) {
@@ -906,46 +970,57 @@ unsigned int tridiag_blocks(const Geometry& g) {
 }
 
 template <typename R>
-cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
-                           double* partials, int mode, R* rnew, const R* rold, cudaStream_t s) {
+cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, const double* kd,
+                           double kz_host, double* partials, int mode, R* rnew, const R* rold,
+                           cudaStream_t s) {
   const unsigned int nb = tridiag_blocks(g);
+  const double w4 = 4.0 / ((double)g.n0 * g.n1);
   switch (mode) {
-    case 0: k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
-    case 1: k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
-    case 2: k_tridiag<R, 2><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
-    default: k_tridiag<R, 3><<<nb, 128, 0, s>>>(g, st, t, h, wscale, partials, rnew, rold); break;
+    case 0:
+      k_tridiag<R, 0><<<nb, 128, 0, s>>>(g, st, t, h, w4, kd, kz_host, partials, rnew, rold);
+      break;
+    case 1:
+      k_tridiag<R, 1><<<nb, 128, 0, s>>>(g, st, t, h, w4, kd, kz_host, partials, rnew, rold);
+      break;
+    case 2:
+      k_tridiag<R, 2><<<nb, 128, 0, s>>>(g, st, t, h, w4, kd, kz_host, partials, rnew, rold);
+      break;
+    default:
+      k_tridiag<R, 3><<<nb, 128, 0, s>>>(g, st, t, h, w4, kd, kz_host, partials, rnew, rold);
+      break;
   }
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_tridiag<double>(const Geometry&, PcgState*, double*, const double*,
-                                            double, double*, int, double*, const double*,
-                                            cudaStream_t);
+                                            const double*, double, double*, int, double*,
+                                            const double*, cudaStream_t);
 template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, const float*,
-                                           double, double*, int, float*, const float*,
-                                           cudaStream_t);
+                                           const double*, double, double*, int, float*,
+                                           const float*, cudaStream_t);
 
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
-                         TZ* z, double scale, int check, int mode, cudaStream_t s) {
+                         TZ* z, const double* kd, double kz_host, int check, int mode,
+                         cudaStream_t s) {
   const int L = rows_per_block<R>(g.n0);
   const size_t sm = smem_x<R>(g.n0, L);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   if (mode == 2)
-    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, (R)scale, L, check);
+    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
   else
-    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, (R)scale, L, check);
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                   const PcgState*, const double*, double*,
-                                                  double, int, int, cudaStream_t);
+                                                  const double*, double, int, int, cudaStream_t);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                 const PcgState*, const float*, double*, double,
-                                                 int, int, cudaStream_t);
+                                                 const PcgState*, const float*, double*,
+                                                 const double*, double, int, int, cudaStream_t);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,

@@ -15,9 +15,14 @@ cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, 
                          const double* k1, const double* k2, double* T0, double* T1, double* T2,
                          double* D, double* Bin, double* Bout, double* partials, PcgState* st,
                          cudaStream_t s);
+// kref_dev (device, may be NULL) takes precedence over kref_host (host, 5 values).
 template <typename R>
 cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* lam1,
-                          const double* kref, R* h, cudaStream_t s);
+                          const double* kref_dev, const double* kref_host, R* h, cudaStream_t s);
+cudaError_t launch_select_kref(PcgState* st, int mode, const double* user, cudaStream_t s);
+cudaError_t launch_state_reset(PcgState* st, int maxit, cudaStream_t s);
+cudaError_t launch_loop_control(PcgState* st, cudaGraphConditionalHandle handle,
+                                cudaStream_t s);
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
                         double pout, double* r, double* x, double* w0, cudaStream_t s);
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
@@ -30,12 +35,15 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, d
 template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                          int inverse, int check, cudaStream_t s);
+// kd (device kref, may be NULL) supplies kappa_ref^z, else kz_host.
 template <typename R>
-cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, double wscale,
-                           double* partials, int mode, R* rnew, const R* rold, cudaStream_t s);
+cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, const double* kd,
+                           double kz_host, double* partials, int mode, R* rnew, const R* rold,
+                           cudaStream_t s);
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
-                         TZ* z, double scale, int check, int mode, cudaStream_t s);
+                         TZ* z, const double* kd, double kz_host, int check, int mode,
+                         cudaStream_t s);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);

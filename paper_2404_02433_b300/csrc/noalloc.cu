@@ -169,17 +169,16 @@ extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
   // the tables and pivots fully, the transform buffer by the first pass.
   if (static_plan(n0, tab0, &p0, &lam0, s) != cudaSuccess) return ETC_ECUDA;
   if (static_plan(n1, tab1, &p1, &lam1, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_pivots<double>(g, lam0, lam1, kref, h, s) != cudaSuccess) return ETC_ECUDA;
+  if (launch_pivots<double>(g, lam0, lam1, nullptr, kref, h, s) != cudaSuccess) return ETC_ECUDA;
   if (launch_fwd_x<double>(g, p0, nullptr, nullptr, nullptr, nullptr, nullptr, r, t, nullptr, 0,
                            0.0, 2, s) != cudaSuccess)
     return ETC_ECUDA;
   if (launch_dct_y<double>(g, p1, nullptr, t, 0, 0, s) != cudaSuccess) return ETC_ECUDA;
-  const double wscale = 4.0 / ((double)n0 * n1 * kref[2]);
-  if (launch_tridiag<double>(g, nullptr, t, h, wscale, nullptr, 0, nullptr, nullptr, s) !=
-      cudaSuccess)
+  if (launch_tridiag<double>(g, nullptr, t, h, nullptr, kref[2], nullptr, 0, nullptr, nullptr,
+                             s) != cudaSuccess)
     return ETC_ECUDA;
   if (launch_dct_y<double>(g, p1, nullptr, t, 1, 0, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_inv_x<double, double>(g, p0, nullptr, t, z, 1.0 / kref[2], 0, 0, s) !=
+  if (launch_inv_x<double, double>(g, p0, nullptr, t, z, nullptr, kref[2], 0, 0, s) !=
       cudaSuccess)
     return ETC_ECUDA;
   return ETC_OK;
