@@ -560,3 +560,32 @@ def adjoint_gradient(kx, ky, kz, direction, lengths=(1.0, 1.0, 1.0), p_in=1.0, p
     for local, axis in enumerate(frame):
         grad[axis] = unpermute_field(G[local], direction)
     return grad, kap, p, lam
+
+
+# --------------------------------------------------------------------------
+# General data: spatially varying Dirichlet values and a source term
+# (Sec. 4.1, the smooth test of Table 2).  Loading along z only.
+# --------------------------------------------------------------------------
+def general_right_hand_side(f: Faces, p_in_face, p_out_face, source):
+    """b for -div(K grad p) = source with p = p_in(x, y) on z = 0, p_out(x, y) on z = L^z.
+
+    Eq. (flux) with p~_F = -p_in(F) / p_out(F) gives the Dirichlet part as in
+    ``right_hand_side`` with face values instead of constants; the second
+    equation of the mixed system with div v = source adds the cell values of
+    the source (the scaled system divides both sides by the cell volume).
+    """
+    b = source.astype(np.float64).copy()
+    b[0] += f.b_in * p_in_face
+    b[-1] += f.b_out * p_out_face
+    return b
+
+
+def solve_general(kx, ky, kz, p_in_face, p_out_face, source, lengths=(1.0, 1.0, 1.0),
+                  rtol=1e-10, maxit=5000, kref=None):
+    """Solution of the TPFA system with general data (load along z): (p, iters)."""
+    f = face_conductances(kx, ky, kz, lengths)
+    if kref is None:
+        kref = reference_parameters(group_extrema(f))
+    b = general_right_hand_side(f, p_in_face, p_out_face, source)
+    res = pcg(f, b, kref, rtol=rtol, maxit=maxit)
+    return res.p, res.iters

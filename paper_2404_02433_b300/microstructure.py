@@ -156,3 +156,54 @@ def random_ellipsoids(shape, semi_axes_range, fractions, kappas, seed, max_attem
     kappa = np.asarray(kappas, dtype=np.float64)[label]
     info = {"fractions": [f / total for f in filled], "attempts": attempts}
     return kappa, info
+
+
+def batched_sphere_member(i, seed0=4001):
+    """Member i of the seeded batch of uneven RVEs: N from {64, 96, 128, 160,
+    192}, spheres with radius U[N/32, N/12] at fraction U[0.1, 0.4], inclusion
+    contrast log-uniform in [10, 1000].  Returns (N, fraction, contrast, kappa)."""
+    rng = np.random.default_rng(seed0 + i)
+    n = int(rng.choice([64, 96, 128, 160, 192]))
+    phi = rng.uniform(0.1, 0.4)
+    contrast = float(np.exp(rng.uniform(np.log(10.0), np.log(1000.0))))
+    mask, _ = random_spheres((n, n, n), (n / 32, n / 12), phi, seed0 + i, 0.0, 1.0)
+    return n, phi, contrast, 1.0 + (contrast - 1.0) * mask
+
+
+def smooth_problem(n):
+    """Data of the smooth test of Sec. 4.1 (Table 2) on an n^3 grid of the unit cube.
+
+    K = diag(cos(pi y) + 2, 2 e^z, 3 cos(pi x) + 4) and exact solution
+    p = cos(pi x) cos(pi y) e^z, so the source is f = -div(K grad p) =
+    cos(pi x) cos(pi y) [(cos(pi y) + 2) pi^2 e^z + 2 pi^2 e^{2z} - (3 cos(pi x) + 4) e^z]
+    (homogeneous Neumann data hold on the x and y faces).  Returns
+    (kx, ky, kz, p_in face values on z = 0, p_out face values on z = 1,
+    source at the voxel centres, exact p at the voxel centres).
+    """
+    c = voxel_centres(n)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    cx, cy = np.cos(np.pi * x), np.cos(np.pi * y)
+    kx = cy + 2.0
+    ky = 2.0 * np.exp(z)
+    kz = 3.0 * cx + 4.0
+    exact = cx * cy * np.exp(z)
+    src = cx * cy * ((cy + 2.0) * np.pi ** 2 * np.exp(z) + 2.0 * np.pi ** 2 * np.exp(2.0 * z)
+                     - (3.0 * cx + 4.0) * np.exp(z))
+    fy, fx = np.meshgrid(c, c, indexing="ij")
+    face = np.cos(np.pi * fx) * np.cos(np.pi * fy)
+    return kx, ky, kz, face, np.e * face, src, exact
+
+
+def channel_lattice(n, cells, psi):
+    """Anisotropic channel lattice of Sec. 4.4: the periodic cell has three
+    orthogonal channels (cross-section (3/8, 5/8)^2) with K = diag(2^psi, 5^psi,
+    10^psi), elsewhere diag(0.01, 0.1, 1); the RVE repeats the cell `cells` times
+    per axis.  Returns (kx, ky, kz)."""
+    c = np.modf(voxel_centres(n) * cells)[0]
+    inside = (c > 3.0 / 8.0) & (c < 5.0 / 8.0)
+    iz, iy, ix = np.meshgrid(inside, inside, inside, indexing="ij")
+    chan = (iy & iz) | (ix & iz) | (ix & iy)
+    kx = np.where(chan, 2.0 ** psi, 0.01)
+    ky = np.where(chan, 5.0 ** psi, 0.1)
+    kz = np.where(chan, 10.0 ** psi, 1.0)
+    return kx, ky, kz

@@ -329,3 +329,39 @@ def test_adjoint_identities():
         # more conductance never lowers the flux; degree-1 homogeneity: sum = kappa_eff
         assert G.min() > -1e-12 * kap
         assert G.sum() == pytest.approx(kap, rel=1e-9)
+
+
+# ---------------------------------------------------------------- Table 2 (smooth problem)
+def _table2():
+    rows = []
+    with open(os.path.join(GOLDEN, "table2_smooth.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                r, n, e, it = line.split()
+                rows.append((float(r), int(n), float(e), int(it)))
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in _table2() if r[1] in (32, 64) and r[0] <= 1e-8])
+def test_table2_smooth_problem(row):
+    # Sec. 4.1: L2 error (3 digits) and iteration count of the converged rows.
+    rtol, n, err, iters = row
+    kx, ky, kz, pin, pout, src, exact = M.smooth_problem(n)
+    p, it = O.solve_general(kx, ky, kz, pin, pout, src, rtol=rtol)
+    l2 = np.sqrt(((p - exact) ** 2).sum() / n ** 3)
+    # three printed digits: within half a unit of the third digit (+ slack)
+    assert abs(l2 - err) / err < 0.002
+    assert abs(it - iters) <= 1
+
+
+def test_smooth_problem_data_consistency():
+    # The source and boundary data must make the exact field a solution of the
+    # continuous problem: the TPFA residual of the exact centre values is O(1),
+    # while the residual of a wrong-sign source would be O(n^2) larger.
+    n = 24
+    kx, ky, kz, pin, pout, src, exact = M.smooth_problem(n)
+    f = O.face_conductances(kx, ky, kz, (1.0, 1.0, 1.0))
+    b = O.general_right_hand_side(f, pin, pout, src)
+    res = O.apply_operator(f, exact) - b
+    bad = O.apply_operator(f, exact) - O.general_right_hand_side(f, pin, pout, -src)
+    assert np.abs(res).max() < 0.05 * np.abs(bad).max()
