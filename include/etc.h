@@ -130,6 +130,24 @@ etc_status etc_set_reference_params(etc_rve* rve, int dir, int mode, const doubl
 etc_status etc_solve_direction(etc_rve* rve, int dir, double p_in, double p_out,
                                const etc_opts* opts, double* kappa_eff, etc_info* info);
 
+/*
+ * Solve -div(K grad p) = source with p = p_in_face on the low face and
+ * p_out_face on the high face of loading direction dir, zero flux elsewhere
+ * (Sec. 4.1, the data of the smooth test of Table 2).  Face values follow Eq.
+ * (flux) face by face; the source enters the second equation of the mixed
+ * system with one value per voxel (taken at the voxel centre by the caller).
+ *   p_in_face, p_out_face  n0*n1 doubles each in the loading-frame plane layout
+ *                          [n1][n0] (see etc_loading_dims), or NULL for zero;
+ *   source                 nx*ny*nz doubles, ORIGINAL layout, or NULL for zero;
+ *                          pointers may be device or host memory.
+ * At least one of the three must be given.  The solution is read with
+ * etc_get_solution(dir); info (may be NULL) carries iterations and residuals,
+ * its kappa fields are 0 (the ETC needs constant face data).
+ */
+etc_status etc_solve_general(etc_rve* rve, int dir, const double* p_in_face,
+                             const double* p_out_face, const double* source,
+                             const etc_opts* opts, etc_info* info);
+
 /* Copy the solution p of the last solve of dir into dst (nx*ny*nz doubles, the
  * ORIGINAL [nz][ny][nx] layout, device or host memory).  ETC_ESTATE if dir has
  * not been solved. */

@@ -26,6 +26,7 @@ EXPORTED = (
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
+    "etc_solve_general",
 )
 
 
@@ -93,6 +94,7 @@ def load_library(path: str | None = None):
                              c_int),
         "etc_batch_run": ([vp, dp, POINTER(EtcInfo), dp], c_int),
         "etc_batch_destroy": ([vp], c_int),
+        "etc_solve_general": ([vp, c_int, vp, vp, vp, POINTER(EtcOpts), POINTER(EtcInfo)], c_int),
         "etc_effective_tensor_batch": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), dp,
                                         POINTER(EtcInfo)], c_int),
     }
@@ -320,6 +322,16 @@ class RVE:
         opts = make_opts(rtol, maxit, ETC_PREC_FP64, 1)
         k, infos = etc_gradient(self.h, direction, out, p_in, p_out, opts, int(per_component))
         return out, k, [i.as_dict() for i in infos]
+
+    def solve_general(self, direction, p_in_face=None, p_out_face=None, source=None, rtol=1e-8,
+                      maxit=5000, precision=ETC_PREC_FP64):
+        """General face data (loading-frame planes) and source (original layout)."""
+        opts = make_opts(rtol, maxit, precision, 1)
+        info = EtcInfo()
+        st = load_library().etc_solve_general(self.h, direction, _ptr(p_in_face), _ptr(p_out_face),
+                                              _ptr(source), byref(opts), byref(info))
+        _check(st, self.h, ok=(ETC_OK, ETC_ENOCONV, ETC_EBREAKDOWN))
+        return info.as_dict()
 
     def loading_dims(self, direction):
         return etc_loading_dims(self.h, direction)

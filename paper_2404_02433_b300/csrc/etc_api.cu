@@ -13,7 +13,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -53,6 +55,8 @@ struct etc_rve {
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
+  double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
+  double *gen_src = nullptr, *gen_srcf = nullptr; // its source (input layout / loading frame)
   double* gbuf[3] = {nullptr, nullptr, nullptr};  // loading-frame gradient components
   double* partials = nullptr;
   size_t npartials = 0;
@@ -63,6 +67,7 @@ struct etc_rve {
   int ref_mode[3] = {ETC_REF_LP, ETC_REF_LP, ETC_REF_LP};
   double kref_user[3][5];
   bool solved[3] = {false, false, false};
+  int tiles[3] = {0, 0, 0};      // rows / columns per block of the transforms in use
   std::string err;
   std::vector<void*> allocs;
 };
@@ -265,6 +270,16 @@ const double* kref_dev(const etc_rve* h) {
                                          offsetof(PcgState, kref));
 }
 
+// Data of the right-hand side: constant Dirichlet values, or per-face values
+// (loading-frame planes) and a source term (loading-frame field) when given.
+struct Rhs {
+  double pin = 1.0, pout = 0.0;
+  const double* pin_f = nullptr;
+  const double* pout_f = nullptr;
+  const double* src = nullptr;
+  bool general() const { return pin_f || pout_f || src; }
+};
+
 // Loading-frame conductivity components (frame axis l carries kappa^{f[l]}),
 // permuted into the given scratch buffers unless dir is z.
 etc_status frame_components(etc_rve* h, int dir, double* const scratch[3], double* comp[3]) {
@@ -335,6 +350,103 @@ etc_status launch_reference(etc_rve* h, int dir, int prec) {
   return ETC_OK;
 }
 
+// ------------------------------------------------------------------ tile autotuner
+// Rows per block of the axis-0 transforms (forward and backward) and columns
+// per block of the axis-1 transforms are picked by timing candidates with CUDA
+// events on the handle's own buffers, once per (n0, n1, n2, precision) in the
+// process.  ETC_NO_AUTOTUNE=1 keeps the default formulas.
+struct Tiles {
+  int fx = 0, ix = 0, y = 0;
+};
+std::mutex g_tiles_mutex;
+std::map<std::array<int, 4>, Tiles> g_tiles;
+
+template <typename F>
+double time_launch(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F launch) {
+  if (launch() != cudaSuccess) return INFINITY;  // warm-up (and validity)
+  cudaEventRecord(e0, s);
+  for (int rep = 0; rep < 2; ++rep)
+    if (launch() != cudaSuccess) return INFINITY;
+  cudaEventRecord(e1, s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return INFINITY;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms;
+}
+
+template <typename R>
+Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, const DctPlan<R>& p1,
+                 cudaEvent_t e0, cudaEvent_t e1) {
+  Tiles best;
+  const int eb = (int)sizeof(R);
+  const long long nrows = (long long)g.n1 * g.n2;
+  double bx = INFINITY, bi = INFINITY, by = INFINITY;
+  for (int L = 1; L <= 64; L *= 2) {
+    if (L > nrows || smem_x_bytes(g.n0, L, eb) > smem_limit()) break;
+    const double tx = time_launch(h->stream, e0, e1, [&] {
+      return launch_fwd_x<R>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
+                             h->partials, 0, 0.0, 2, h->stream, L);
+    });
+    if (tx < bx) { bx = tx; best.fx = L; }
+    if (smem_x_bytes(g.n0, L, eb) + (size_t)L * g.n0 * sizeof(double) > smem_limit()) continue;
+    const double ti = time_launch(h->stream, e0, e1, [&] {
+      return launch_inv_x<R, double>(g, p0, h->st, t, h->z64, nullptr, 1.0, 0, 2, h->stream, L);
+    });
+    if (ti < bi) { bi = ti; best.ix = L; }
+  }
+  if (g.n1 > 1)
+    for (int TI = 1; TI <= 32; TI *= 2) {
+      if (TI > g.n0 || smem_y_bytes(g.n1, TI, eb) > smem_limit()) break;
+      const double ty = time_launch(h->stream, e0, e1, [&] {
+        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, TI);
+      });
+      if (ty < by) { by = ty; best.y = TI; }
+    }
+  return best;
+}
+
+// Choose (or recall) the tiles of dir / prec and make them current.  Uses r, t
+// and z64 as scratch: call it before the initial residual is formed.
+etc_status autotune(etc_rve* h, int dir, int prec) {
+  const Geometry g = geom_of(h, dir);
+  const std::array<int, 4> key = {g.n0, g.n1, g.n2, prec};
+  {
+    std::lock_guard<std::mutex> lock(g_tiles_mutex);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) {
+      h->tiles[0] = it->second.fx; h->tiles[1] = it->second.ix; h->tiles[2] = it->second.y;
+      return ETC_OK;
+    }
+  }
+  Tiles best;
+  const char* off = std::getenv("ETC_NO_AUTOTUNE");
+  if (!(off && off[0] == '1')) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaMemsetAsync(h->r, 0, h->n * sizeof(double), h->stream));
+    CK(cudaMemsetAsync(h->z64, 0, h->n * sizeof(double), h->stream));
+    const PlanStore& P0 = h->plans[g.n0];
+    const PlanStore& P1 = h->plans[g.n1];
+    if (prec == ETC_PREC_FP64) {
+      CK(cudaMemsetAsync(h->t64, 0, h->n * sizeof(double), h->stream));
+      best = tune_tiles<double>(h, g, h->t64, P0.p64, P1.p64, e0, e1);
+    } else {
+      CK(cudaMemsetAsync(h->t32, 0, h->n * sizeof(float), h->stream));
+      best = tune_tiles<float>(h, g, h->t32, P0.p32, P1.p32, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tiles_mutex);
+    g_tiles[key] = best;
+  }
+  h->tiles[0] = best.fx; h->tiles[1] = best.ix; h->tiles[2] = best.y;
+  return ETC_OK;
+}
+
 // ------------------------------------------------------------------ preconditioner chain
 // t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
 // (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
@@ -347,14 +459,15 @@ etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
                         int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
                         cudaEvent_t* ev = nullptr) {
   const int check = (tri_mode != 0);
-  CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream));
+  CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
   CK(launch_tridiag<R>(g, h->st, t, hp, kref_dev(h), 1.0, h->partials, tri_mode, rnew, rold,
                        h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
-  CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream));
+  CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream)));
+  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
+                          h->tiles[1])));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
@@ -371,18 +484,19 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
 // Initial residual and preconditioner apply (Algorithm 1, first line): r = b,
 // x = 0, z0 = A_ref^{-1} r, rho = r.z0, w = z0 (written over w = 0 by the
 // last inverse pass with beta = 0).
-etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, double pin,
-                        double pout, double rtol2) {
+etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, const Rhs& rhs,
+                        double rtol2) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
-  CK(launch_init(g, h->Bin, h->Bout, pin, pout, h->r, x, h->w[0], h->stream));
+  CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream, rhs.pin_f,
+                 rhs.pout_f, rhs.src));
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
-                            h->partials, 0, rtol2, 0, h->stream));
+                            h->partials, 0, rtol2, 0, h->stream, h->tiles[0]));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2);
   }
   CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
-                         h->partials, 0, rtol2, 0, h->stream));
+                         h->partials, 0, rtol2, 0, h->stream, h->tiles[0]));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
   return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
                                      h->rhat32[1], nullptr);
@@ -400,13 +514,13 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr, h->t64,
-                            h->partials, par, 0.0, 1, h->stream));
+                            h->partials, par, 0.0, 1, h->stream, h->tiles[0]));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2,
                                         nullptr, nullptr, ev ? ev + 3 : nullptr);
   }
   CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32, h->partials,
-                         par, 0.0, 1, h->stream));
+                         par, 0.0, 1, h->stream, h->tiles[0]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
                                      h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
@@ -414,29 +528,32 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
 
 // Post-processing of one solve: outflow/inflow sums, cross fluxes and the
 // true residual (queued on h->stream).
-etc_status launch_post(etc_rve* h, const Geometry& g, const double* x, double pin, double pout,
+etc_status launch_post(etc_rve* h, const Geometry& g, const double* x, const Rhs& rhs,
                        int true_residual) {
-  CK(launch_flux(g, x, h->T0, h->T1, h->T2, h->Bin, h->Bout, pin, pout, h->partials, h->st,
-                 h->stream));
+  if (!rhs.general())
+    CK(launch_flux(g, x, h->T0, h->T1, h->T2, h->Bin, h->Bout, rhs.pin, rhs.pout, h->partials,
+                   h->st, h->stream));
   if (true_residual)
-    CK(launch_true_residual(g, x, h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, pin, pout,
-                            h->partials, h->st, h->stream));
+    CK(launch_true_residual(g, x, h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, rhs.pin, rhs.pout,
+                            h->partials, h->st, h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
   return ETC_OK;
 }
 
 // kappa_eff (Eq. effective formula dis), inflow value, mean cross fluxes and
 // the info record from a finished state block.
-void fill_results(const etc_rve* h, int dir, double pin, double pout, int true_residual,
+void fill_results(const etc_rve* h, int dir, const Rhs& rhs, int true_residual,
                   const PcgState& st, double ms_setup, double ms_solve, double* kappa_eff,
                   etc_info* info) {
+  const double pin = rhs.pin, pout = rhs.pout;
+  const bool flux = !rhs.general();
   int f[3];
   frame_of(dir, f);
   const Geometry g = geom_of(h, dir);
   const int N[3] = {h->nx, h->ny, h->nz};
   const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
-  const double dp = pin - pout;
+  const double dp = flux ? pin - pout : 1.0;
   const double L2 = h->L[f[2]];
-  const double keff = L2 * hh[2] * st.res[3] / ((double)g.plane * dp);
+  const double keff = flux ? L2 * hh[2] * st.res[3] / ((double)g.plane * dp) : 0.0;
   double vbar[3];
   vbar[0] = hh[0] * st.res[0] / (double)g.n;
   vbar[1] = hh[1] * st.res[1] / (double)g.n;
@@ -449,8 +566,8 @@ void fill_results(const etc_rve* h, int dir, double pin, double pout, int true_r
     info->true_relres = (true_residual && st.bb > 0) ? std::sqrt(st.res[5] / st.bb) : -1.0;
     std::memcpy(info->kref, st.kref, sizeof(info->kref));
     info->cond_bound = cond_bound_of(st.ext, st.kref);
-    info->kappa_in = L2 * hh[2] * st.res[4] / ((double)g.plane * dp);
-    for (int l = 0; l < 3; ++l) info->column[f[l]] = h->L[dir] * vbar[l] / dp;
+    info->kappa_in = flux ? L2 * hh[2] * st.res[4] / ((double)g.plane * dp) : 0.0;
+    for (int l = 0; l < 3; ++l) info->column[f[l]] = flux ? h->L[dir] * vbar[l] / dp : 0.0;
     info->t_setup_ms = ms_setup;
     info->t_solve_ms = ms_solve;
   }
@@ -464,8 +581,8 @@ etc_status check_dir(etc_rve* h, int dir) {
 // One solve of direction dir into x (loading frame); arguments already valid.
 // The host queues iterations in growing chunks and reads the device state of
 // the previous chunk while the next one runs.
-etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_opts& o,
-                      double* x, double* kappa_eff, etc_info* info) {
+etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, double* x,
+                      double* kappa_eff, etc_info* info) {
   etc_status s = ETC_OK;
   const int prec = o.precision;
   const Geometry g = geom_of(h, dir);
@@ -475,10 +592,12 @@ etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_
   CK(launch_state_reset(h->st, o.maxit, h->stream));
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
+  s = autotune(h, dir, prec);
+  if (s != ETC_OK) return s;
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   CK(cudaEventRecord(e[1], h->stream));
-  s = launch_start(h, g, x, prec, p_in, p_out, o.rtol * o.rtol);
+  s = launch_start(h, g, x, prec, rhs, o.rtol * o.rtol);
   if (s != ETC_OK) return s;
 
   int launched = 0, slot = 1, prev_slot = 2, chunk = 2;
@@ -510,7 +629,7 @@ etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_
     }
   }
   for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
-  s = launch_post(h, g, x, p_in, p_out, o.true_residual);
+  s = launch_post(h, g, x, rhs, o.true_residual);
   if (s != ETC_OK) return s;
   CK(cudaEventRecord(e[2], h->stream));
   s = read_state(h, 1);
@@ -520,7 +639,7 @@ etc_status solve_impl(etc_rve* h, int dir, double p_in, double p_out, const etc_
   cudaEventElapsedTime(&ms_solve, e[1], e[2]);
   for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
   const PcgState& st = h->st_host[1];
-  fill_results(h, dir, p_in, p_out, o.true_residual, st, ms_setup, ms_solve, kappa_eff, info);
+  fill_results(h, dir, rhs, o.true_residual, st, ms_setup, ms_solve, kappa_eff, info);
   if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
   if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
   return ETC_OK;
@@ -556,12 +675,18 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   const int prec = o.precision;
   const Geometry g = geom_of(h, dir);
   double* x = h->xsol[dir];
+  {
+    std::lock_guard<std::mutex> lock(g_tiles_mutex);
+    const Tiles& tl = g_tiles[{g.n0, g.n1, g.n2, prec}];
+    h->tiles[0] = tl.fx; h->tiles[1] = tl.ix; h->tiles[2] = tl.y;
+  }
   CK(launch_state_reset(h->st, o.maxit, cs));
   etc_status s = launch_setup(h, dir);
   if (s != ETC_OK) return s;
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
-  s = launch_start(h, g, x, prec, 1.0, 0.0, o.rtol * o.rtol);
+  const Rhs unit;  // p_in = 1, p_out = 0
+  s = launch_start(h, g, x, prec, unit, o.rtol * o.rtol);
   if (s != ETC_OK) return s;
   cudaStreamCaptureStatus cst;
   cudaGraph_t cg = nullptr;
@@ -590,7 +715,7 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   const cudaError_t ee = cudaStreamEndCapture(bs, &ended);
   if (s != ETC_OK) return s;
   CK(ee);
-  s = launch_post(h, g, x, 1.0, 0.0, o.true_residual);
+  s = launch_post(h, g, x, unit, o.true_residual);
   if (s != ETC_OK) return s;
   CK(cudaMemcpyAsync(slot, h->st, sizeof(PcgState), cudaMemcpyDeviceToDevice, cs));
   return ETC_OK;
@@ -795,7 +920,54 @@ etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
   etc_status s = check_solve_args(h, dir, p_in, p_out, opts_in, &o);
   if (s != ETC_OK) return s;
   if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
-  s = solve_impl(h, dir, p_in, p_out, o, h->xsol[dir], kappa_eff, info);
+  Rhs rhs;
+  rhs.pin = p_in;
+  rhs.pout = p_out;
+  s = solve_impl(h, dir, rhs, o, h->xsol[dir], kappa_eff, info);
+  if (s == ETC_OK || s == ETC_ENOCONV || s == ETC_EBREAKDOWN) h->solved[dir] = true;
+  return s;
+}
+
+etc_status etc_solve_general(etc_rve* h, int dir, const double* p_in_face, const double* p_out_face,
+                             const double* source, const etc_opts* opts_in, etc_info* info) {
+  if (!h) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  etc_opts o;
+  etc_default_opts(&o);
+  if (opts_in) o = *opts_in;
+  s = validate_opts(h, &o);
+  if (s != ETC_OK) return s;
+  if (!p_in_face && !p_out_face && !source)
+    return fail(h, ETC_EINVAL, "give at least one of p_in_face, p_out_face, source");
+  const Geometry g = geom_of(h, dir);
+  if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
+  Rhs rhs;
+  rhs.pin = rhs.pout = 0.0;
+  if (p_in_face) {
+    if (!h->gen_in) CK(dalloc(h, &h->gen_in, (size_t)h->plane_max));
+    CK(cudaMemcpyAsync(h->gen_in, p_in_face, g.plane * sizeof(double), cudaMemcpyDefault,
+                       h->stream));
+    rhs.pin_f = h->gen_in;
+  }
+  if (p_out_face) {
+    if (!h->gen_out) CK(dalloc(h, &h->gen_out, (size_t)h->plane_max));
+    CK(cudaMemcpyAsync(h->gen_out, p_out_face, g.plane * sizeof(double), cudaMemcpyDefault,
+                       h->stream));
+    rhs.pout_f = h->gen_out;
+  }
+  if (source) {
+    if (!h->gen_src) CK(dalloc(h, &h->gen_src, (size_t)h->n));
+    CK(cudaMemcpyAsync(h->gen_src, source, h->n * sizeof(double), cudaMemcpyDefault, h->stream));
+    if (dir == 2) {
+      rhs.src = h->gen_src;
+    } else {
+      if (!h->gen_srcf) CK(dalloc(h, &h->gen_srcf, (size_t)h->n));
+      CK(to_frame(h, dir, h->gen_src, h->gen_srcf));
+      rhs.src = h->gen_srcf;
+    }
+  }
+  s = solve_impl(h, dir, rhs, o, h->xsol[dir], nullptr, info);
   if (s == ETC_OK || s == ETC_ENOCONV || s == ETC_EBREAKDOWN) h->solved[dir] = true;
   return s;
 }
@@ -814,7 +986,10 @@ etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const et
     if (!h->gbuf[a]) CK(dalloc(h, &h->gbuf[a], (size_t)h->n));
   etc_info inf[2];
   double keff = 0.0, kadj = 0.0;
-  s = solve_impl(h, dir, p_in, p_out, o, h->xsol[dir], &keff, &inf[0]);
+  Rhs fwd;
+  fwd.pin = p_in;
+  fwd.pout = p_out;
+  s = solve_impl(h, dir, fwd, o, h->xsol[dir], &keff, &inf[0]);
   if (s != ETC_OK) return s;
   h->solved[dir] = true;
   int f[3];
@@ -824,7 +999,10 @@ etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const et
   const double hh[3] = {h->L[f[0]] / N[f[0]], h->L[f[1]] / N[f[1]], h->L[f[2]] / N[f[2]]};
   // adjoint: A lam = dJ/dx = cJ b_out on the last plane, i.e. Dirichlet data (0, cJ)
   const double cJ = h->L[f[2]] * hh[2] / ((double)g.plane * (p_in - p_out));
-  s = solve_impl(h, dir, 0.0, cJ, o, h->lam, &kadj, &inf[1]);
+  Rhs adj;
+  adj.pin = 0.0;
+  adj.pout = cJ;
+  s = solve_impl(h, dir, adj, o, h->lam, &kadj, &inf[1]);
   if (s != ETC_OK) return s;
   double* comp[3];
   double* const scratch[3] = {h->t64, h->z64, h->q};
@@ -903,6 +1081,8 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
     return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
+  s = autotune(h, dir, prec);
+  if (s != ETC_OK) return s;
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
@@ -910,11 +1090,11 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   const PlanStore& P1 = h->plans[g.n1];
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t64,
-                            h->partials, 0, 0.0, 2, h->stream));
+                            h->partials, 0, 0.0, 2, h->stream, h->tiles[0]));
     s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, 0, 0);
   } else {
     CK(launch_fwd_x<float>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t32,
-                           h->partials, 0, 0.0, 2, h->stream));
+                           h->partials, 0, 0.0, 2, h->stream, h->tiles[0]));
     s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, 0, 0);
   }
   if (s != ETC_OK) return s;
@@ -956,11 +1136,14 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
   CK(launch_state_reset(h->st, iters + 1, h->stream));
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
+  s = autotune(h, dir, prec);
+  if (s != ETC_OK) return s;
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
   // rtol = 0: the timed iterations never take the convergence exit
-  s = launch_start(h, g, h->xsol[dir], prec, 1.0, 0.0, 0.0);
+  const Rhs unit;
+  s = launch_start(h, g, h->xsol[dir], prec, unit, 0.0);
   if (s != ETC_OK) return s;
   cudaEvent_t ev[7];
   for (int i = 0; i < 7; ++i) CK(cudaEventCreate(&ev[i]));
@@ -1023,6 +1206,10 @@ etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opt
     etc_rve* h = rves[i];
     for (int d = 0; d < 3; ++d)
       if (!h->xsol[d]) CKB(dalloc(h, &h->xsol[d], (size_t)h->n));
+    for (int d = 0; d < 3; ++d) {
+      const etc_status ts = autotune(h, d, o.precision);
+      if (ts != ETC_OK) return bail(ts);
+    }
     CKB(h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize());
   }
   CKB(cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking));
@@ -1083,7 +1270,8 @@ etc_status etc_batch_run(etc_batch* b, double* K, etc_info* info, double* ms) {
       const PcgState& st = b->slots_host[3 * i + d];
       double keff = 0;
       etc_info inf;
-      fill_results(h, d, 1.0, 0.0, b->o.true_residual, st, 0.0, t, &keff, &inf);
+      const Rhs unit;
+      fill_results(h, d, unit, b->o.true_residual, st, 0.0, t, &keff, &inf);
       for (int a = 0; a < 3; ++a) K[9 * i + 3 * a + d] = inf.column[a];
       K[9 * i + 3 * d + d] = keff;
       if (info) info[3 * i + d] = inf;

@@ -256,16 +256,18 @@ __global__ void k_loop_control(PcgState* st, cudaGraphConditionalHandle handle) 
 }
 
 // ------------------------------------------------------------------ init
-// r = b (Eq. flux: b_in p_in on plane 0, b_out p_out on plane n2-1), x = 0,
-// w_old = 0.
+// r = b, x = 0, w_old = 0.  b (Eq. flux): b_in p_in on plane 0 and b_out p_out
+// on plane n2-1, with per-face values pin_f / pout_f (plane layout) when given,
+// plus the source term src (loading-frame layout) when given.
 __global__ void k_init(Geometry g, const double* __restrict__ Bin, const double* __restrict__ Bout,
-                       double pin, double pout, double* __restrict__ r, double* __restrict__ x,
-                       double* __restrict__ w0) {
+                       double pin, double pout, const double* __restrict__ pin_f,
+                       const double* __restrict__ pout_f, const double* __restrict__ src,
+                       double* __restrict__ r, double* __restrict__ x, double* __restrict__ w0) {
   for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
     const long long k = c / g.plane, s = c - k * g.plane;
-    double b = 0.0;
-    if (k == 0) b += Bin[s] * pin;
-    if (k == g.n2 - 1) b += Bout[s] * pout;
+    double b = src ? src[c] : 0.0;
+    if (k == 0) b += Bin[s] * (pin_f ? pin_f[s] : pin);
+    if (k == g.n2 - 1) b += Bout[s] * (pout_f ? pout_f[s] : pout);
     r[c] = b;
     x[c] = 0.0;
     w0[c] = 0.0;
@@ -590,17 +592,22 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
   const Lay y = make_lay(L, g.n0, false);
   c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
   c2<R>* b = a + L * dct_half_alloc(g.n0);
+  // MODE 2: the old w of the block's rows, staged with the transform input
+  double* wsh = reinterpret_cast<double*>(b + L * dct_half_alloc(g.n0));
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   const int tot = L * g.n0;
   constexpr int U = 8;
   for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
     R v[U];
+    double wv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * blockDim.x;
       const int l = e / g.n0, k = e - l * g.n0;
-      v[u] = (e < tot && row0 + l < nrows) ? t[(row0 + l) * g.n0 + k] : (R)0;
+      const bool ok = (e < tot && row0 + l < nrows);
+      v[u] = ok ? t[(row0 + l) * g.n0 + k] : (R)0;
+      if (MODE == 2) wv[u] = ok ? (double)z[(row0 + l) * g.n0 + k] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -608,6 +615,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
       if (e >= tot) break;
       const int l = e / g.n0, k = e - l * g.n0;
       dct3_put<R>(y, b, l, k, v[u]);
+      if (MODE == 2) wsh[e] = wv[u];
     }
   }
   __syncthreads();
@@ -617,7 +625,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
     const long long row = row0 + l;
     if (row < nrows) {
       const long long c = row * g.n0 + i;
-      if (MODE == 2) z[c] = (TZ)fma(beta, (double)z[c], to_f64<R>(v));
+      if (MODE == 2) z[c] = (TZ)fma(beta, wsh[l * g.n0 + i], to_f64<R>(v));
       else z[c] = (TZ)v;
     }
   });
@@ -666,7 +674,9 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
                                 const double* __restrict__ T0, const double* __restrict__ T1,
                                 const double* __restrict__ T2, const double* __restrict__ D,
                                 const double* __restrict__ Bin, const double* __restrict__ Bout,
-                                double pin, double pout, double* partials, PcgState* st) {
+                                double pin, double pout, const double* __restrict__ pin_f,
+                                const double* __restrict__ pout_f,
+                                const double* __restrict__ src, double* partials, PcgState* st) {
   __shared__ double sh[32];
   __shared__ int flag;
   double acc = 0.0;
@@ -675,9 +685,9 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
     const long long rem = c / g.n0;
     const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
     const long long s = c - (long long)k * g.plane;
-    double b = 0.0;
-    if (k == 0) b += Bin[s] * pin;
-    if (k == g.n2 - 1) b += Bout[s] * pout;
+    double b = src ? src[c] : 0.0;
+    if (k == 0) b += Bin[s] * (pin_f ? pin_f[s] : pin);
+    if (k == g.n2 - 1) b += Bout[s] * (pout_f ? pout_f[s] : pout);
     double ax = D[c] * x[c];
     if (i > 0) ax -= T0[c] * x[c - 1];
     if (i < g.n0 - 1) ax -= T0[c + 1] * x[c + 1];
@@ -851,8 +861,9 @@ cudaError_t launch_loop_control(PcgState* st, cudaGraphConditionalHandle handle,
 }
 
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
-                        double pout, double* r, double* x, double* w0, cudaStream_t s) {
-  k_init<<<grid_for(g.n, 256), 256, 0, s>>>(g, Bin, Bout, pin, pout, r, x, w0);
+                        double pout, double* r, double* x, double* w0, cudaStream_t s,
+                        const double* pin_f, const double* pout_f, const double* src) {
+  k_init<<<grid_for(g.n, 256), 256, 0, s>>>(g, Bin, Bout, pin, pout, pin_f, pout_f, src, r, x, w0);
   count_launch();
   return cudaGetLastError();
 }
@@ -868,6 +879,8 @@ cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, doub
   count_launch();
   return cudaGetLastError();
 }
+
+static const size_t kMaxDyn = 200 * 1024;  // dynamic shared memory opt-in per block
 
 // rows per block of the axis-0 transforms and their shared memory
 template <typename R>
@@ -894,12 +907,18 @@ size_t smem_y(int n1, int TI) {
 }
 
 unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes) {
-  const int L = (elem_bytes == 8) ? rows_per_block<double>(g.n0) : rows_per_block<float>(g.n0);
-  const long long nrows = (long long)g.n1 * g.n2;
-  return (unsigned int)((nrows + L - 1) / L);
+  (void)elem_bytes;  // any tile down to one row per block
+  return (unsigned int)((long long)g.n1 * g.n2);
 }
 
-static const size_t kMaxDyn = 200 * 1024;
+size_t smem_x_bytes(int n0, int L, int elem_bytes) {
+  return elem_bytes == 8 ? smem_x<double>(n0, L) : smem_x<float>(n0, L);
+}
+size_t smem_y_bytes(int n1, int TI, int elem_bytes) {
+  return elem_bytes == 8 ? smem_y<double>(n1, TI) : smem_y<float>(n1, TI);
+}
+size_t smem_limit() { return kMaxDyn; }
+
 
 template <typename R>
 cudaError_t set_smem_attrs() {
@@ -923,8 +942,9 @@ template cudaError_t set_smem_attrs<float>();
 template <typename R>
 cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
                          const double* w, const double* q, double* r, const double* rin, R* t,
-                         double* partials, int par, double rtol2, int mode, cudaStream_t s) {
-  const int L = rows_per_block<R>(g.n0);
+                         double* partials, int par, double rtol2, int mode, cudaStream_t s,
+                         int L) {
+  if (L <= 0) L = rows_per_block<R>(g.n0);
   const size_t sm = smem_x<R>(g.n0, L);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
@@ -941,17 +961,17 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, d
 template cudaError_t launch_fwd_x<double>(const Geometry&, const DctPlan<double>&, PcgState*,
                                           double*, const double*, const double*, double*,
                                           const double*, double*, double*, int, double, int,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template cudaError_t launch_fwd_x<float>(const Geometry&, const DctPlan<float>&, PcgState*,
                                          double*, const double*, const double*, double*,
                                          const double*, float*, double*, int, double, int,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 
 template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
-                         int inverse, int check, cudaStream_t s) {
+                         int inverse, int check, cudaStream_t s, int TI) {
   if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
-  const int TI = cols_per_block<R>(g.n1);
+  if (TI <= 0) TI = cols_per_block<R>(g.n1);
   const size_t sm = smem_y<R>(g.n1, TI);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   dim3 grid((g.n0 + TI - 1) / TI, g.n2);
@@ -961,9 +981,9 @@ cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState*
   return cudaGetLastError();
 }
 template cudaError_t launch_dct_y<double>(const Geometry&, const DctPlan<double>&,
-                                          const PcgState*, double*, int, int, cudaStream_t);
+                                          const PcgState*, double*, int, int, cudaStream_t, int);
 template cudaError_t launch_dct_y<float>(const Geometry&, const DctPlan<float>&, const PcgState*,
-                                         float*, int, int, cudaStream_t);
+                                         float*, int, int, cudaStream_t, int);
 
 unsigned int tridiag_blocks(const Geometry& g) {
   return (unsigned int)((g.plane + 127) / 128);
@@ -1002,9 +1022,9 @@ template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, c
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s) {
-  const int L = rows_per_block<R>(g.n0);
-  const size_t sm = smem_x<R>(g.n0, L);
+                         cudaStream_t s, int L) {
+  if (L <= 0) L = rows_per_block<R>(g.n0);
+  const size_t sm = smem_x<R>(g.n0, L) + (mode == 2 ? (size_t)L * g.n0 * sizeof(double) : 0);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
@@ -1017,10 +1037,12 @@ cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState*
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                   const PcgState*, const double*, double*,
-                                                  const double*, double, int, int, cudaStream_t);
+                                                  const double*, double, int, int, cudaStream_t,
+                                                  int);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                  const PcgState*, const float*, double*,
-                                                 const double*, double, int, int, cudaStream_t);
+                                                 const double*, double, int, int, cudaStream_t,
+                                                 int);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
@@ -1034,9 +1056,11 @@ cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, co
 cudaError_t launch_true_residual(const Geometry& g, const double* x, const double* T0,
                                  const double* T1, const double* T2, const double* D,
                                  const double* Bin, const double* Bout, double pin, double pout,
-                                 double* partials, PcgState* st, cudaStream_t s) {
+                                 double* partials, PcgState* st, cudaStream_t s,
+                                 const double* pin_f, const double* pout_f, const double* src) {
   k_true_residual<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, x, T0, T1, T2, D, Bin, Bout, pin,
-                                                              pout, partials, st);
+                                                              pout, pin_f, pout_f, src, partials,
+                                                              st);
   count_launch();
   return cudaGetLastError();
 }

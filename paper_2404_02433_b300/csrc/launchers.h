@@ -24,17 +24,20 @@ cudaError_t launch_state_reset(PcgState* st, int maxit, cudaStream_t s);
 cudaError_t launch_loop_control(PcgState* st, cudaGraphConditionalHandle handle,
                                 cudaStream_t s);
 cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout, double pin,
-                        double pout, double* r, double* x, double* w0, cudaStream_t s);
+                        double pout, double* r, double* x, double* w0, cudaStream_t s,
+                        const double* pin_f = nullptr, const double* pout_f = nullptr,
+                        const double* src = nullptr);
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);
 template <typename R>
 cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
                          const double* w, const double* q, double* r, const double* rin, R* t,
-                         double* partials, int par, double rtol2, int mode, cudaStream_t s);
+                         double* partials, int par, double rtol2, int mode, cudaStream_t s,
+                         int L = 0);
 template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
-                         int inverse, int check, cudaStream_t s);
+                         int inverse, int check, cudaStream_t s, int TI = 0);
 // kd (device kref, may be NULL) supplies kappa_ref^z, else kz_host.
 template <typename R>
 cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, const double* kd,
@@ -43,14 +46,16 @@ cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, co
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s);
+                         cudaStream_t s, int L = 0);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
 cudaError_t launch_true_residual(const Geometry& g, const double* x, const double* T0,
                                  const double* T1, const double* T2, const double* D,
                                  const double* Bin, const double* Bout, double pin, double pout,
-                                 double* partials, PcgState* st, cudaStream_t s);
+                                 double* partials, PcgState* st, cudaStream_t s,
+                                 const double* pin_f = nullptr, const double* pout_f = nullptr,
+                                 const double* src = nullptr);
 cudaError_t launch_widen(const float* a, double* b, long long n, cudaStream_t s);
 cudaError_t launch_gradient(const Geometry& g, const double* x, const double* lam,
                             const double* k0, const double* k1, const double* k2, double ih0,
@@ -68,5 +73,9 @@ unsigned long long launch_count();
 unsigned int matvec_blocks(const Geometry& g);
 unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes);
 unsigned int tridiag_blocks(const Geometry& g);
+// Shared memory of the transform tiles (rows L / columns TI per block).
+size_t smem_x_bytes(int n0, int L, int elem_bytes);
+size_t smem_y_bytes(int n1, int TI, int elem_bytes);
+size_t smem_limit();
 
 }  // namespace etc

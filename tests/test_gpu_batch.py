@@ -59,18 +59,8 @@ def test_batch_reports_noconv():
     assert all(i["status"] == B.ETC_ENOCONV and i["iters"] == 4 for i in infos)
 
 
-def batched_workload(count=64, seed0=4001):
-    """64 RVEs: N from {64,96,128,160,192}, spheres with radius U[N/32, N/12],
-    fraction U[0.1, 0.4], inclusion contrast log-uniform in [10, 1000]."""
-    media = []
-    for i in range(count):
-        rng = np.random.default_rng(seed0 + i)
-        n = int(rng.choice([64, 96, 128, 160, 192]))
-        phi = rng.uniform(0.1, 0.4)
-        contrast = float(np.exp(rng.uniform(np.log(10.0), np.log(1000.0))))
-        mask, _ = M.random_spheres((n, n, n), (n / 32, n / 12), phi, seed0 + i, 0.0, 1.0)
-        media.append((n, phi, contrast, 1.0 + (contrast - 1.0) * mask))
-    return media
+def batched_workload(count=64):
+    return [M.batched_sphere_member(i) for i in range(count)]
 
 
 @pytest.mark.parametrize("precision", [B.ETC_PREC_FP64, B.ETC_PREC_MIXED])
