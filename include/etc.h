@@ -247,6 +247,14 @@ etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters
 etc_status etc_convert_check(const float* f_in, double* d_out, const double* d_in, float* f_out,
                              long long n, void* stream);
 
+/* Test support: the double-float split the mixed-precision matvec uses
+ * (Algorithm 1's A w on the FP32 pipe), element-wise on n device values d:
+ * hilo[2i] = hi = d rounded to binary32 (nearest even), hilo[2i+1] = lo = d - hi
+ * rounded to binary32; lo = 0 when |d| < 2^-74, for binary64 subnormals, and
+ * where hi is infinite or NaN.  hilo: 2n floats, 8-byte aligned.  Synchronises
+ * the stream. */
+etc_status etc_split_check(const double* d, float* hilo, long long n, void* stream);
+
 /* Kernels launched by this library since the process started (all handles). */
 unsigned long long etc_kernel_launches(void);
 

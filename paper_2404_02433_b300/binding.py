@@ -26,7 +26,7 @@ EXPORTED = (
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
-    "etc_solve_general",
+    "etc_solve_general", "etc_split_check",
 )
 
 
@@ -88,6 +88,7 @@ def load_library(path: str | None = None):
         "etc_kernel_launches": ([], ctypes.c_ulonglong),
         "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
         "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
+        "etc_split_check": ([vp, vp, ctypes.c_longlong, vp], c_int),
         "etc_gradient": ([vp, c_int, c_double, c_double, POINTER(EtcOpts), c_int, vp, dp,
                           POINTER(EtcInfo)], c_int),
         "etc_batch_create": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), POINTER(c_void_p)],
@@ -218,6 +219,12 @@ def etc_convert_check(f_in, d_out, d_in, f_out, stream=None):
     return _check(load_library().etc_convert_check(_ptr(f_in), _ptr(d_out), _ptr(d_in),
                                                    _ptr(f_out), f_in.numel(),
                                                    c_void_p(stream) if stream else None))
+
+
+def etc_split_check(d, hilo, stream=None):
+    """hilo (2n float32): (hi, lo) of each binary64 value of d, as the mixed matvec splits it."""
+    return _check(load_library().etc_split_check(_ptr(d), _ptr(hilo), d.numel(),
+                                                 c_void_p(stream) if stream else None))
 
 
 def etc_gradient(h, direction, grad, p_in=1.0, p_out=0.0, opts=None, per_component=0):

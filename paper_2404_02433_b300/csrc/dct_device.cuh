@@ -94,6 +94,46 @@ template <typename R, int SIGN> struct Bfly<R, 8, SIGN> {
   }
 };
 
+// x * exp(SIGN i phi) for a constant angle given by its cosine and sine
+template <typename R, int SIGN>
+__device__ __forceinline__ c2<R> crot(c2<R> x, R c, R s) {
+  const R ss = SIGN < 0 ? -s : s;
+  return mk2<R>(fma(x.x, c, -x.y * ss), fma(x.x, ss, x.y * c));
+}
+
+// Length 16 as 4 x 4: DFT-4 over s2 of x[s1 + 4 s2], twiddle exp(SIGN 2 pi i s1 k1 / 16),
+// DFT-4 over s1; output in natural order.
+template <typename R, int SIGN> struct Bfly<R, 16, SIGN> {
+  static __device__ __forceinline__ void run(c2<R>* v) {
+    constexpr R c8 = (R)0.92387953251128675613;  // cos(pi/8)
+    constexpr R s8 = (R)0.38268343236508977173;  // sin(pi/8)
+    constexpr R h = K<R>::s2;
+    c2<R> a[4][4];
+#pragma unroll
+    for (int s1 = 0; s1 < 4; ++s1) {
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2) a[s1][s2] = v[s1 + 4 * s2];
+      Bfly<R, 4, SIGN>::run(a[s1]);
+    }
+    a[1][1] = crot<R, SIGN>(a[1][1], c8, s8);   // e = 1
+    a[1][2] = crot<R, SIGN>(a[1][2], h, h);     // e = 2
+    a[1][3] = crot<R, SIGN>(a[1][3], s8, c8);   // e = 3
+    a[2][1] = crot<R, SIGN>(a[2][1], h, h);     // e = 2
+    a[2][2] = rot<R, SIGN>(a[2][2]);            // e = 4
+    a[2][3] = crot<R, SIGN>(a[2][3], -h, h);    // e = 6
+    a[3][1] = crot<R, SIGN>(a[3][1], s8, c8);   // e = 3
+    a[3][2] = crot<R, SIGN>(a[3][2], -h, h);    // e = 6
+    a[3][3] = crot<R, SIGN>(a[3][3], -c8, -s8); // e = 9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      c2<R> b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      Bfly<R, 4, SIGN>::run(b);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+    }
+  }
+};
+
 template <typename R, int SIGN> struct Bfly<R, 3, SIGN> {
   static __device__ __forceinline__ void run(c2<R>* v) {
     c2<R> t1 = add2<R>(v[1], v[2]);

@@ -53,6 +53,11 @@ struct etc_rve {
   double* z64 = nullptr;
   float *t32 = nullptr, *h32 = nullptr;
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
+  // double-float copies for the mixed-precision matvec: faces and diagonal
+  // (refreshed with every face assembly) and the search direction w
+  float2* Tdf[3] = {nullptr, nullptr, nullptr};
+  float2* Ddf = nullptr;
+  float2* wdf = nullptr;
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
@@ -148,7 +153,12 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
   const size_t ntw = s.fft ? 2 * (size_t)m : 0;
   const size_t npost = s.fft ? 4 * (size_t)(m + 1) : 0;
   const size_t ncos = 4 * (size_t)n;
-  std::vector<R> buf(ntw + 2 * npost + ncos);
+  // four-step twiddles of the register-resident transforms: P x Q complex
+  const bool fast = s.fft && fast_len(n);
+  const int fP = m >= 256 ? 16 : (m >= 64 ? 8 : 4), fQ = m / fP;
+  const size_t off4 = (ntw + 2 * npost + ncos + 3) / 4 * 4;  // 16-byte aligned
+  const size_t n4 = fast ? 2 * (size_t)m : 0;
+  std::vector<R> buf(off4 + n4);
   const long double pi = 3.141592653589793238462643383279502884L;
   R* tw = buf.data();
   R* fp = tw + ntw;
@@ -172,6 +182,13 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
       ip[4 * k + 3] = (R)sinl(4 * th);
     }
   for (int q = 0; q < 4 * n; ++q) cq[q] = (R)cosl(pi * q / (2.0L * n));
+  if (fast)
+    for (int tau = 0; tau < fP; ++tau)
+      for (int k1 = 0; k1 < fQ; ++k1) {
+        const long double a = -2.0L * pi * (long double)((tau * k1) % m) / m;
+        buf[off4 + 2 * (tau * fQ + k1)] = (R)cosl(a);
+        buf[off4 + 2 * (tau * fQ + k1) + 1] = (R)sinl(a);
+      }
   R* d = nullptr;
   cudaError_t e = dalloc(h, &d, buf.size());
   if (e != cudaSuccess) return e;
@@ -181,6 +198,7 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
   t->fpost = d + ntw;
   t->ipre = d + ntw + npost;
   t->cosq = d + ntw + 2 * npost;
+  t->tw4 = fast ? d + off4 : nullptr;
   *mem = d;
   return cudaSuccess;
 }
@@ -315,6 +333,12 @@ etc_status launch_setup(etc_rve* h, int dir) {
   CK(launch_faces(g, 1.0 / (hh[0] * hh[0]), 1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), comp[0],
                   comp[1], comp[2], h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, h->partials,
                   h->st, h->stream));
+  // double-float copies (with the zero padding plane) for the mixed-precision matvec
+  const long long nt = h->n + h->plane_max + 64;
+  CK(launch_split_df(h->T0, h->Tdf[0], nt, h->stream));
+  CK(launch_split_df(h->T1, h->Tdf[1], nt, h->stream));
+  CK(launch_split_df(h->T2, h->Tdf[2], nt, h->stream));
+  CK(launch_split_df(h->D, h->Ddf, h->n, h->stream));
   return ETC_OK;
 }
 
@@ -381,6 +405,24 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   const int eb = (int)sizeof(R);
   const long long nrows = (long long)g.n1 * g.n2;
   double bx = INFINITY, bi = INFINITY, by = INFINITY;
+  // tile -1: the register-resident kernels, where the line length allows them
+  if (fast_x_ok<R>(g, p0, h->r, h->z64, nullptr, nullptr)) {
+    bx = time_launch(h->stream, e0, e1, [&] {
+      return launch_fwd_x<R>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
+                             h->partials, 0, 0.0, 2, h->stream, -1);
+    });
+    best.fx = -1;
+    bi = time_launch(h->stream, e0, e1, [&] {
+      return launch_inv_x<R, double>(g, p0, h->st, t, h->z64, nullptr, 1.0, 0, 2, h->stream, -1);
+    });
+    best.ix = -1;
+  }
+  if (g.n1 > 1 && fast_y_ok<R>(g, p1)) {
+    by = time_launch(h->stream, e0, e1, [&] {
+      return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -1);
+    });
+    best.y = -1;
+  }
   for (int L = 1; L <= 64; L *= 2) {
     if (L > nrows || smem_x_bytes(g.n0, L, eb) > smem_limit()) break;
     const double tx = time_launch(h->stream, e0, e1, [&] {
@@ -450,14 +492,14 @@ etc_status autotune(etc_rve* h, int dir, int prec) {
 // ------------------------------------------------------------------ preconditioner chain
 // t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
 // (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
-// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w).
-// kappa_ref comes from the state.  ev (optional): events recorded after each
-// of the four kernels.
+// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w, and
+// its double-float copy into wdf when given).  kappa_ref comes from the state.
+// ev (optional): events recorded after each of the four kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
                         const DctPlan<R>& p1, R* t, const R* hp, TZ* out, int tri_mode,
                         int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
-                        cudaEvent_t* ev = nullptr) {
+                        cudaEvent_t* ev = nullptr, float2* wdf = nullptr) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
@@ -467,7 +509,7 @@ etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
   CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
-                          h->tiles[1])));
+                          h->tiles[1], wdf)));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
@@ -499,7 +541,7 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
                          h->partials, 0, rtol2, 0, h->stream, h->tiles[0]));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
   return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
-                                     h->rhat32[1], nullptr);
+                                     h->rhat32[1], nullptr, nullptr, h->wdf);
 }
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
@@ -509,8 +551,12 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
-                   h->stream));
+  if (prec == ETC_PREC_FP64)
+    CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
+                     h->stream));
+  else
+    CK(launch_matvec_df(g, h->st, h->wdf, h->q, h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
+                        h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   if (prec == ETC_PREC_FP64) {
     CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr, h->t64,
@@ -523,7 +569,8 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
                          par, 0.0, 1, h->stream, h->tiles[0]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
-                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
+                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
+                                     h->wdf);
 }
 
 // Post-processing of one solve: outflow/inflow sums, cross fluxes and the
@@ -834,11 +881,14 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(dalloc(h, &h->z64, (size_t)n));
   CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
   CKC(dalloc(h, &h->rhat32[0], (size_t)n)); CKC(dalloc(h, &h->rhat32[1], (size_t)n));
+  CKC(dalloc(h, &h->Tdf[0], nt)); CKC(dalloc(h, &h->Tdf[1], nt)); CKC(dalloc(h, &h->Tdf[2], nt));
+  CKC(dalloc(h, &h->Ddf, (size_t)n)); CKC(dalloc(h, &h->wdf, (size_t)n));
   // partials: the largest reduction grid over the three directions
   size_t np = 1024;
   for (int d = 0; d < 3; ++d) {
     const Geometry g = geom_of(h, d);
     np = std::max<size_t>(np, matvec_blocks(g));
+    np = std::max<size_t>(np, matvec_df_blocks(g));
     np = std::max<size_t>(np, fwd_x_blocks(g, 4));
     np = std::max<size_t>(np, fwd_x_blocks(g, 8));
     np = std::max<size_t>(np, tridiag_blocks(g));
@@ -1174,6 +1224,15 @@ etc_status etc_convert_check(const float* f_in, double* d_out, const double* d_i
   if (n == 0) return ETC_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (launch_convert(f_in, d_out, d_in, f_out, n, st) != cudaSuccess) return ETC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ETC_ECUDA;
+  return ETC_OK;
+}
+
+etc_status etc_split_check(const double* d, float* hilo, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!d || !hilo)) || ((uintptr_t)hilo & 7u)) return ETC_EINVAL;
+  if (n == 0) return ETC_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_split_df(d, reinterpret_cast<float2*>(hilo), n, st) != cudaSuccess) return ETC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return ETC_ECUDA;
   return ETC_OK;
 }

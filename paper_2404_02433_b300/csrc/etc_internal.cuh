@@ -22,6 +22,8 @@ struct DctTables {
   const R* fpost;  // (m+1) x 4: cos(t)/2, sin(t)/2, cos(5t)/2, sin(5t)/2, t = pi k / (2n)
   const R* ipre;   // (m+1) x 4: cos(t)/(2m), sin(t)/(2m), cos(4t), sin(4t)
   const R* cosq;   // 4n: cos(pi q / (2n))
+  const R* tw4 = nullptr;  // P x Q complex exp(-2 pi i tau k1 / m), [tau][k1], for the
+                           // register-resident transforms (n = 32..512); NULL: not built
 };
 
 struct DctShape {
@@ -131,6 +133,53 @@ __device__ __forceinline__ double sum_partials(const double* partials, int nb, i
   return t;
 }
 
+// Each block writes nv values, the last block to arrive gets true.
+__device__ __forceinline__ bool publish_values(double* partials, int stride, const double* vals,
+                                               int nv, unsigned int* counter, int* flag) {
+  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+  if (threadIdx.x == 0) {
+    for (int v = 0; v < nv; ++v) partials[(size_t)bid * stride + v] = vals[v];
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    *flag = (prev == nb - 1);
+  }
+  __syncthreads();
+  const bool last = *flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
+
+// End of the residual-update kernels (Algorithm 1, exit test): block partials
+// of ||r||^2, summed in block order by the last block, which records ||r||^2
+// (MODE 0: also ||b||^2 and the threshold rtol^2 ||b||^2) and decides
+// convergence, the iteration cap and breakdown.
+template <int MODE>
+__device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, double* partials,
+                                                    double rtol2, double* sh, int* flag) {
+  const double bs = block_sum(acc, sh);
+  double v[1] = {bs};
+  if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], flag)) {
+    const double rr = sum_partials(partials, (int)nblocks(), 1, sh);
+    if (threadIdx.x == 0) {
+      st->rr = rr;
+      if (MODE == 0) {
+        st->bb = rr;
+        st->thresh2 = rtol2 * rr;
+        if (!(rr > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+      } else {
+        st->iter += 1;
+        if (!isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+        else if (rr <= st->thresh2) { st->status = kOK; st->done = 1; }
+        else if (st->iter >= st->maxit) { st->status = kENOCONV; st->done = 1; }
+      }
+      st->cnt[kCntRes] = 0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host launchers
 struct Geometry {
   int n0, n1, n2;     // loading-frame sizes
@@ -206,5 +255,59 @@ template <> __device__ __forceinline__ double to_f64<float>(float v) { return wi
 template <typename T> __device__ __forceinline__ T from_f64(double v);
 template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_f64<float>(double v) { return narrow(v); }
+
+}  // namespace etc
+
+namespace etc {
+
+// ---------------------------------------------------------------- double-float
+// A value held as an unevaluated sum hi + lo of two binary32 numbers with
+// |lo| <= ulp(hi)/2 ("double-float", a 48-bit significand): the FP32 pipe,
+// 64 times faster than the FP64 pipe on B300, then does the FP64-class work of
+// the mixed-precision matvec.  The algorithms are the error-free
+// transformations TwoSum (Knuth) and TwoProduct by FMA, and the cascaded
+// summation Sum2 of Ogita, Rump and Oishi (2005).
+
+// Exact split of a binary64 value: hi = RN32(d), lo = RN32(d - hi), from the
+// bit fields with integer operations only (no FP64 instruction).  Values whose
+// remainder falls below the binary32 normal range (|d| < 2^-74), subnormal
+// binary64 input, infinities and NaN keep lo = 0.
+__device__ __forceinline__ float2 split_df(double d) {
+  const float hi = narrow(d);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int be = e - 948;  // biased binary32 exponent of 2^(e - 1075)
+  if (e - 896 < 1 || be < 1 || (__float_as_uint(hi) & 0x7F800000u) == 0x7F800000u)
+    return make_float2(hi, 0.0f);
+  const unsigned long long sig = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned int low = (unsigned int)(sig & 0x1FFFFFFFull);  // bits below hi's last bit
+  const bool up = low > 0x10000000u || (low == 0x10000000u && ((sig >> 29) & 1ull));
+  const int rem = up ? (int)low - 0x20000000 : (int)low;  // d - hi = rem * 2^(e - 1075)
+  float lo = __int2float_rn(rem) * __int_as_float(be << 23);
+  if (b >> 63) lo = -lo;
+  return make_float2(hi, lo);
+}
+
+// s + t = a + b exactly, s = RN(a + b)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+
+// Sum2 step: (s, e) <- (s, e) + sign * x * y for double-float x, y.  The
+// product keeps hi*hi exactly (FMA) plus the two cross terms; lo*lo is below
+// the format's precision.
+template <int SIGN>
+__device__ __forceinline__ void df_fma_acc(float2 x, float2 y, float& s, float& e) {
+  float p = x.x * y.x;
+  float pe = fma(x.x, y.x, -p);
+  pe = fma(x.x, y.y, pe);
+  pe = fma(x.y, y.x, pe);
+  if (SIGN < 0) { p = -p; pe = -pe; }
+  float t;
+  two_sum(s, p, s, t);
+  e += t + pe;
+}
 
 }  // namespace etc

@@ -1,0 +1,588 @@
+// Register-resident cosine transforms for line lengths n = 32, 64, ..., 512.
+//
+// Same transforms as the generic kernels (Eq. (forward DCT) and Eq. (backward
+// DCT), Sec. 3.2), reached through the same half-length complex FFT with the
+// even/odd reordering and the untangling twiddles, but with the FFT of length
+// M = n/2 split as M = P * Q in the four-step manner:
+//   thread tau of a line holds z_{tau + P s}, s < Q, and runs a length-Q DFT in
+//   registers; after the twiddle exp(-+2 pi i tau k1 / M) one shared-memory
+//   transpose hands each thread the values of Q/P indices k1, for which it runs
+//   length-P DFTs, giving Z_{k1 + Q k2}.
+// Every index is a compile-time shift or mask, which is what the generic
+// Stockham code (runtime stage loop, divisions by runtime line lengths) lacks.
+//
+// Axis-1 passes (columns of a plane, stride n0) keep one column per lane and P
+// warps per column tile, loading and storing global memory directly with the
+// lanes over adjacent columns.  Axis-0 passes (rows) stage the row through
+// shared memory so that the FP64 PCG vectors stay coalesced.
+#include <type_traits>
+
+#include "dct_device.cuh"
+#include "etc_internal.cuh"
+#include "launchers.h"
+
+namespace etc {
+
+// threads per line for FFT length m
+constexpr int fast_p(int m) { return m >= 256 ? 16 : (m >= 64 ? 8 : 4); }
+
+template <int N> struct Fast {
+  static constexpr int M = N / 2;
+  static constexpr int P = fast_p(M);
+  static constexpr int Q = M / P;
+  static constexpr int E = Q / P;  // length-P DFTs per thread in the second step
+  static_assert(P * Q == M && Q % P == 0, "four-step split");
+  // Axis-0 shared layout, in complex units per row: A holds the row (staging,
+  // then Z), B the transposed partial transforms.  The strides are P mod 16
+  // so that the rows met by one half-warp use disjoint banks.
+  static constexpr int SA = M + P;
+  static constexpr int BS0 = Q * (P + 1);
+  static constexpr int BS = BS0 + (((P - BS0) % 16) + 16) % 16;
+  static constexpr int L = 256 / P;  // rows per 256-thread block
+};
+
+template <typename R> struct FastCols {  // columns per block of the axis-1 passes
+  static constexpr int C = sizeof(R) == 4 ? 32 : 16;
+  // resident blocks per SM asked of the compiler: 1024 (FP32) or 512 (FP64)
+  // threads, i.e. at most 64 or 128 registers per thread
+  static constexpr int MinBlocks(int n) {
+    return (sizeof(R) == 4 ? 1024 : 512) / (C * fast_p(n / 2));
+  }
+};
+
+bool fast_len(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c,
+                                    double& d) {
+  const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p + 2));
+  a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
+// First four-step stage of thread tau: DFT of length Q over s, then the twiddle
+// exp(SIGN 2 pi i tau k1 / M) from the [tau][k1] table (forward sign stored).
+template <typename R, int N, int SIGN>
+__device__ __forceinline__ void four_step_a(c2<R>* v, const R* __restrict__ tw4, int tau) {
+  using F = Fast<N>;
+  Bfly<R, F::Q, SIGN>::run(v);
+  const c2<R>* tw = reinterpret_cast<const c2<R>*>(tw4) + tau * F::Q;
+#pragma unroll
+  for (int k1 = 1; k1 < F::Q; ++k1) {
+    c2<R> w = __ldg(tw + k1);
+    if (SIGN > 0) w.y = -w.y;
+    v[k1] = cmul<R>(v[k1], w);
+  }
+}
+
+// Forward untangling: X_k and X_{n-k} (X_m for k = 0) from Z_k and Z_{m-k},
+// with the fpost twiddles of k (and of m for k = 0).
+template <typename R>
+__device__ __forceinline__ void untangle(c2<R> zk, c2<R> zm, const R* __restrict__ fpost, int k,
+                                         int m, R& xa, R& xb) {
+  const R a1 = zk.x + zm.x, b1 = zk.y - zm.y, c1 = zk.y + zm.y, d1 = zk.x - zm.x;
+  R f0, f1, f2, f3;
+  ld4(fpost + 4 * k, f0, f1, f2, f3);
+  xa = fma(f0, a1, fma(f1, b1, fma(f2, c1, -f3 * d1)));
+  if (k != 0) {
+    xb = fma(f1, a1, fma(-f0, b1, fma(f2, d1, f3 * c1)));
+  } else {
+    R g0, g1, g2, g3;
+    ld4(fpost + 4 * m, g0, g1, g2, g3);
+    xb = fma(g0, a1, g2 * c1);
+  }
+}
+
+// Backward pre-twiddle of FFT input j from X_j, X_{n-j} (0 for j = 0), X_{m-j}
+// and X_{m+j}: V_j = e^{i t_j} (X_j - i X_{n-j}) / (2m), V_{m-j} likewise,
+// a_j = P + i O with P = V_j + conj(V_{m-j}), O = (V_j - conj(V_{m-j})) e^{4 i t_j}.
+template <typename R>
+__device__ __forceinline__ c2<R> inv_pre(const R* __restrict__ ipre, int j, int m, R xj, R xn,
+                                         R xm, R xp) {
+  R f0, f1, f2, f3, g0, g1, g2, g3;
+  ld4(ipre + 4 * j, f0, f1, f2, f3);
+  ld4(ipre + 4 * (m - j), g0, g1, g2, g3);
+  const R vr = fma(f0, xj, f1 * xn), vi = fma(f1, xj, -f0 * xn);
+  const R wr = fma(g0, xm, g1 * xp), wi = fma(g1, xm, -g0 * xp);
+  const R pr = vr + wr, pi = vi - wi;
+  const R qr = vr - wr, qi = vi + wi;
+  const R orr = fma(qr, f2, -qi * f3), oi = fma(qr, f3, qi * f2);
+  return mk2<R>(pr - oi, pi + orr);
+}
+
+// Row of v (reordered input) that feeds real slot a: v_a = u_{2a} for a < m,
+// u_{2(n-1-a)+1} otherwise.
+template <int N>
+__device__ __forceinline__ int vrow(int a) {
+  return a < N / 2 ? 2 * a : 2 * (N - 1 - a) + 1;
+}
+
+// ---------------------------------------------------------------- axis 1
+// In place on t: every block owns C adjacent columns of one plane k.
+template <typename R, int N, int INV>
+__global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinBlocks(N))
+    k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check) {
+  using F = Fast<N>;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = FastCols<R>::C;
+  constexpr int SIGN = INV ? 1 : -1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  c2<R>* sm = reinterpret_cast<c2<R>*>(smraw);  // C * M complex
+  if (check && st->done) return;
+  const int c = threadIdx.x % C, tau = threadIdx.x / C;
+  const int i = blockIdx.x * C + c;
+  const bool ok = i < g.n0;
+  const long long n0 = g.n0;
+  R* col = t + (long long)blockIdx.y * g.plane + (ok ? i : 0);
+  c2<R> v[Q];
+  if (!INV) {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int q = tau + P * s;  // z_q = (v_{2q}, v_{2q+1})
+      v[s] = ok ? mk2<R>(col[vrow<N>(2 * q) * n0], col[vrow<N>(2 * q + 1) * n0])
+                : mk2<R>((R)0, (R)0);
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      R xj = 0, xn = 0, xm = 0, xp = 0;
+      if (ok) {
+        xj = col[j * n0];
+        xn = j ? col[(N - j) * n0] : (R)0;
+        xm = col[(M - j) * n0];
+        xp = col[(M + j) * n0];
+      }
+      v[s] = inv_pre<R>(tb.ipre, j, M, xj, xn, xm, xp);
+    }
+  }
+  four_step_a<R, N, SIGN>(v, tb.tw4, tau);
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) sm[(k1 * P + tau) * C + c] = v[k1];
+  __syncthreads();
+  c2<R> u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = sm[((tau + P * e) * P + tt) * C + c];
+    Bfly<R, P, SIGN>::run(u + e * P);
+  }
+  if (!INV) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) sm[(tau + P * e + Q * k2) * C + c] = u[e * P + k2];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        const int k = tau + P * e + Q * k2;
+        R xa, xb;
+        untangle<R>(u[e * P + k2], sm[((M - k) & (M - 1)) * C + c], tb.fpost, k, M, xa, xb);
+        if (ok) {
+          col[k * n0] = xa;
+          col[(k ? N - k : M) * n0] = xb;
+        }
+      }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
+        if (ok) {
+          col[vrow<N>(2 * j) * n0] = u[e * P + k2].x;
+          col[vrow<N>(2 * j + 1) * n0] = u[e * P + k2].y;
+        }
+      }
+  }
+}
+
+// ---------------------------------------------------------------- axis 0, forward
+// Same contract as k_fwd_x (MODE 0 initial residual, 1 PCG update, 2 transform
+// only).  Rows [row0, row0 + L) are contiguous in memory: the vector phase
+// walks them as pairs of elements with 16-byte loads.
+template <typename R, int N, int MODE>
+__global__ void __launch_bounds__(256)
+    k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, double* __restrict__ x,
+                 const double* __restrict__ w, const double* __restrict__ q,
+                 double* __restrict__ r, const double* __restrict__ rin, R* __restrict__ t,
+                 double* partials, int par, double rtol2) {
+  using F = Fast<N>;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE != 2 && st->done) return;
+  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);
+  c2<R>* B = A + L * SA;
+  R* Ar = reinterpret_cast<R*>(A);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)blockIdx.x * L;
+  const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  double acc = 0.0;
+  constexpr int NP = L * M;  // element pairs of the block
+  constexpr int U = 2;
+  static_assert(NP % (256 * U) == 0, "pair rounds");
+  for (int p0 = threadIdx.x; p0 < NP; p0 += 256 * U) {
+    double2 rv[U], qv[U], xv[U], wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + 256 * u;
+      const int l = p / M, i2 = p % M;
+      const long long row = row0 + l;
+      rv[u] = make_double2(0.0, 0.0);
+      qv[u] = rv[u]; xv[u] = rv[u]; wv[u] = rv[u];
+      if (row < nrows) {
+        const long long c = row * N + 2 * i2;
+        rv[u] = *reinterpret_cast<const double2*>((MODE == 2 ? rin : r) + c);
+        if (MODE == 1) {
+          qv[u] = *reinterpret_cast<const double2*>(q + c);
+          xv[u] = *reinterpret_cast<const double2*>(x + c);
+          wv[u] = *reinterpret_cast<const double2*>(w + c);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + 256 * u;
+      const int l = p / M, i2 = p % M;
+      const long long row = row0 + l;
+      double2 v = rv[u];
+      if (row < nrows && MODE != 2) {
+        const long long c = row * N + 2 * i2;
+        if (MODE == 1) {
+          *reinterpret_cast<double2*>(x + c) =
+              make_double2(fma(alpha, wv[u].x, xv[u].x), fma(alpha, wv[u].y, xv[u].y));
+          v.x = fma(-alpha, qv[u].x, v.x);
+          v.y = fma(-alpha, qv[u].y, v.y);
+          *reinterpret_cast<double2*>(r + c) = v;
+        }
+        acc = fma(v.x, v.x, acc);
+        acc = fma(v.y, v.y, acc);
+      }
+      // element 2 i2 -> v_{i2}; element 2 i2 + 1 -> v_{n-1-i2}
+      Ar[l * 2 * SA + i2] = from_f64<R>(v.x);
+      Ar[l * 2 * SA + N - 1 - i2] = from_f64<R>(v.y);
+    }
+  }
+  __syncthreads();
+  const int l = threadIdx.x / P, tau = threadIdx.x % P;
+  c2<R> v[Q];
+#pragma unroll
+  for (int s = 0; s < Q; ++s) v[s] = A[l * SA + tau + P * s];
+  four_step_a<R, N, -1>(v, tb.tw4, tau);
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) B[l * BS + k1 * (P + 1) + tau] = v[k1];
+  __syncthreads();
+  c2<R> u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = B[l * BS + (tau + P * e) * (P + 1) + tt];
+    Bfly<R, P, -1>::run(u + e * P);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) A[l * SA + tau + P * e + Q * k2] = u[e * P + k2];
+  }
+  __syncthreads();
+  const long long row = row0 + l;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) {
+      const int k = tau + P * e + Q * k2;
+      R xa, xb;
+      untangle<R>(u[e * P + k2], A[l * SA + ((M - k) & (M - 1))], tb.fpost, k, M, xa, xb);
+      if (row < nrows) {
+        t[row * N + k] = xa;
+        t[row * N + (k ? N - k : M)] = xb;
+      }
+    }
+  if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag);
+}
+
+// ---------------------------------------------------------------- axis 0, backward
+// Same contract as k_inv_x: u = scale * (backward DCT of t along axis 0), then
+// MODE 0: z = u; MODE 2: w = u + beta w in place (z points at w).
+template <typename R, typename TZ, int N, int MODE>
+__global__ void __launch_bounds__(256)
+    k_fast_inv_x(Geometry g, DctTables<R> tb, const PcgState* st, const R* __restrict__ t,
+                 TZ* __restrict__ z, const double* kd, double kz_host, int check,
+                 float2* __restrict__ wdf) {
+  using F = Fast<N>;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
+  constexpr int SR = N + P;  // real stride of the staged input rows
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (check && st->done) return;
+  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);
+  c2<R>* B = A + L * SA;
+  R* Ar = reinterpret_cast<R*>(A);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)blockIdx.x * L;
+  // stage the block's rows in natural order, 16 bytes per access, all of a
+  // thread's loads issued before the first shared-memory store
+  using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  constexpr int VW = 16 / (int)sizeof(R);
+  constexpr int NR = L * N / VW / 256;
+  static_assert(NR * 256 * VW == L * N, "staging rounds");
+  {
+    V val[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      const int l = (e * VW) / N, i = (e * VW) % N;
+      const long long row = row0 + l;
+      val[r] = row < nrows ? *reinterpret_cast<const V*>(t + row * N + i) : V{};
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      const int l = (e * VW) / N, i = (e * VW) % N;
+      *reinterpret_cast<V*>(Ar + l * SR + i) = val[r];
+    }
+  }
+  __syncthreads();
+  const int l = threadIdx.x / P, tau = threadIdx.x % P;
+  const R* X = Ar + l * SR;
+  c2<R> v[Q];
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    const int j = tau + P * s;
+    v[s] = inv_pre<R>(tb.ipre, j, M, X[j], j ? X[N - j] : (R)0, X[M - j], X[M + j]);
+  }
+  four_step_a<R, N, 1>(v, tb.tw4, tau);
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) B[l * BS + k1 * (P + 1) + tau] = v[k1];
+  __syncthreads();
+  c2<R> u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = B[l * BS + (tau + P * e) * (P + 1) + tt];
+    Bfly<R, P, 1>::run(u + e * P);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) A[l * SA + tau + P * e + Q * k2] = u[e * P + k2];
+  }
+  __syncthreads();
+  // real view of A: slot a of row l holds v_a
+  const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
+  const double beta = (MODE == 2) ? st->beta : 0.0;
+  constexpr int NQ = L * M / 256;  // element pairs per thread
+  constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
+  static_assert(NQ % G == 0, "pair groups");
+#pragma unroll 1
+  for (int r0 = 0; r0 < NQ; r0 += G) {
+    double2 wo[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int p = threadIdx.x + 256 * (r0 + u);
+      const long long row = row0 + p / M;
+      wo[u] = make_double2(0.0, 0.0);
+      if (MODE == 2 && row < nrows)
+        wo[u] = *reinterpret_cast<const double2*>(z + row * N + 2 * (p % M));
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int p = threadIdx.x + 256 * (r0 + u);
+      const int lr = p / M, i2 = p % M;
+      const long long row = row0 + lr;
+      if (row >= nrows) continue;
+      const long long c = row * N + 2 * i2;
+      const R u0 = Ar[lr * 2 * SA + i2] * scale;          // element 2 i2     <- v_{i2}
+      const R u1 = Ar[lr * 2 * SA + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
+      if (MODE == 2) {
+        const double2 wn =
+            make_double2(fma(beta, wo[u].x, to_f64<R>(u0)), fma(beta, wo[u].y, to_f64<R>(u1)));
+        *reinterpret_cast<double2*>(z + c) = wn;
+        if (wdf) {
+          const float2 a = split_df(wn.x), b = split_df(wn.y);
+          *reinterpret_cast<float4*>(wdf + c) = make_float4(a.x, a.y, b.x, b.y);
+        }
+      } else {
+        z[c] = (TZ)u0;
+        z[c + 1] = (TZ)u1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+namespace {
+
+template <typename R, int N>
+size_t fast_x_smem() {
+  return (size_t)Fast<N>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>);
+}
+template <typename R, int N>
+size_t fast_y_smem() {
+  return (size_t)FastCols<R>::C * Fast<N>::M * sizeof(c2<R>);
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename R, int N>
+cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, double* x,
+                    const double* w, const double* q, double* r, const double* rin, R* t,
+                    double* partials, int par, double rtol2, int mode, cudaStream_t s) {
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
+  const size_t sm = fast_x_smem<R, N>();
+  if (mode == 0)
+    k_fast_fwd_x<R, N, 0><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+                                                rtol2);
+  else if (mode == 1)
+    k_fast_fwd_x<R, N, 1><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+                                                rtol2);
+  else
+    k_fast_fwd_x<R, N, 2><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+                                                rtol2);
+  return cudaGetLastError();
+}
+
+template <typename R, typename TZ, int N>
+cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, const R* t,
+                    TZ* z, const double* kd, double kz_host, int check, int mode,
+                    cudaStream_t s, float2* wdf) {
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
+  const size_t sm = fast_x_smem<R, N>();
+  if (mode == 2)
+    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, wdf);
+  else
+    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, wdf);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R* t,
+                int inverse, int check, cudaStream_t s) {
+  constexpr int C = FastCols<R>::C;
+  dim3 grid((g.n0 + C - 1) / C, g.n2);
+  const size_t sm = fast_y_smem<R, N>();
+  if (inverse)
+    k_fast_y<R, N, 1><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+  else
+    k_fast_y<R, N, 0><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+  return cudaGetLastError();
+}
+
+template <typename R, int N>
+cudaError_t attrs_n() {
+  cudaError_t e = cudaSuccess;
+  const int sx = (int)fast_x_smem<R, N>(), sy = (int)fast_y_smem<R, N>();
+#define SETF(fn, b) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  SETF((k_fast_fwd_x<R, N, 0>), sx);
+  SETF((k_fast_fwd_x<R, N, 1>), sx);
+  SETF((k_fast_fwd_x<R, N, 2>), sx);
+  SETF((k_fast_inv_x<R, double, N, 0>), sx);
+  SETF((k_fast_inv_x<R, double, N, 2>), sx);
+  SETF((k_fast_y<R, N, 0>), sy);
+  SETF((k_fast_y<R, N, 1>), sy);
+#undef SETF
+  return e;
+}
+
+}  // namespace
+
+template <typename R>
+bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void* b,
+               const void* c, const void* d) {
+  return p.t.tw4 != nullptr && fast_len(g.n0) && p.s.n == g.n0 && aligned16(a) &&
+         aligned16(b) && aligned16(c) && aligned16(d);
+}
+template bool fast_x_ok<double>(const Geometry&, const DctPlan<double>&, const void*,
+                                const void*, const void*, const void*);
+template bool fast_x_ok<float>(const Geometry&, const DctPlan<float>&, const void*, const void*,
+                               const void*, const void*);
+
+template <typename R>
+bool fast_y_ok(const Geometry& g, const DctPlan<R>& p) {
+  return p.t.tw4 != nullptr && fast_len(g.n1) && p.s.n == g.n1;
+}
+template bool fast_y_ok<double>(const Geometry&, const DctPlan<double>&);
+template bool fast_y_ok<float>(const Geometry&, const DctPlan<float>&);
+
+template <typename R>
+cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
+                              const double* w, const double* q, double* r, const double* rin,
+                              R* t, double* partials, int par, double rtol2, int mode,
+                              cudaStream_t s) {
+  switch (g.n0) {
+    case 32: return fwd_x_n<R, 32>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 64: return fwd_x_n<R, 64>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 128:
+      return fwd_x_n<R, 128>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 256:
+      return fwd_x_n<R, 256>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 512:
+      return fwd_x_n<R, 512>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_fast_fwd_x<double>(const Geometry&, const DctPlan<double>&,
+                                               PcgState*, double*, const double*,
+                                               const double*, double*, const double*, double*,
+                                               double*, int, double, int, cudaStream_t);
+template cudaError_t launch_fast_fwd_x<float>(const Geometry&, const DctPlan<float>&, PcgState*,
+                                              double*, const double*, const double*, double*,
+                                              const double*, float*, double*, int, double, int,
+                                              cudaStream_t);
+
+template <typename R, typename TZ>
+cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
+                              const R* t, TZ* z, const double* kd, double kz_host, int check,
+                              int mode, cudaStream_t s, float2* wdf) {
+  switch (g.n0) {
+    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_fast_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
+                                                       const PcgState*, const double*, double*,
+                                                       const double*, double, int, int,
+                                                       cudaStream_t, float2*);
+template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
+                                                      const PcgState*, const float*, double*,
+                                                      const double*, double, int, int,
+                                                      cudaStream_t, float2*);
+
+template <typename R>
+cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
+                          int inverse, int check, cudaStream_t s) {
+  switch (g.n1) {
+    case 32: return y_n<R, 32>(g, p.t, st, t, inverse, check, s);
+    case 64: return y_n<R, 64>(g, p.t, st, t, inverse, check, s);
+    case 128: return y_n<R, 128>(g, p.t, st, t, inverse, check, s);
+    case 256: return y_n<R, 256>(g, p.t, st, t, inverse, check, s);
+    case 512: return y_n<R, 512>(g, p.t, st, t, inverse, check, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_fast_y<double>(const Geometry&, const DctPlan<double>&,
+                                           const PcgState*, double*, int, int, cudaStream_t);
+template cudaError_t launch_fast_y<float>(const Geometry&, const DctPlan<float>&,
+                                          const PcgState*, float*, int, int, cudaStream_t);
+
+template <typename R>
+cudaError_t set_fast_attrs() {
+  cudaError_t e = attrs_n<R, 32>();
+  if (e == cudaSuccess) e = attrs_n<R, 64>();
+  if (e == cudaSuccess) e = attrs_n<R, 128>();
+  if (e == cudaSuccess) e = attrs_n<R, 256>();
+  if (e == cudaSuccess) e = attrs_n<R, 512>();
+  return e;
+}
+template cudaError_t set_fast_attrs<double>();
+template cudaError_t set_fast_attrs<float>();
+
+}  // namespace etc

@@ -24,25 +24,6 @@ __device__ __forceinline__ long long gidx() {
   return (long long)blockIdx.x * blockDim.x + threadIdx.x;
 }
 
-// Each block writes nv values, the last block to arrive gets true.
-__device__ __forceinline__ bool publish_values(double* partials, int stride, const double* vals,
-                                               int nv, unsigned int* counter, int* flag) {
-  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-  if (threadIdx.x == 0) {
-    for (int v = 0; v < nv; ++v) partials[(size_t)bid * stride + v] = vals[v];
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
-    *flag = (prev == nb - 1);
-  }
-  __syncthreads();
-  const bool last = *flag != 0;
-  if (last) __threadfence();
-  return last;
-}
-
-__device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
-
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
 // ------------------------------------------------------------------ setup: checks
@@ -332,6 +313,100 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
   }
 }
 
+// ------------------------------------------------------------------ double-float matvec
+// The mixed-precision path's q = A w (same operator as k_matvec) with the
+// FP64-class arithmetic on the FP32 pipe: faces, diagonal and w as
+// double-float pairs, the seven products summed by Sum2, q written as FP64.
+// Each thread owns one (i, j) column of a 32 x 8 tile and marches over kchunk
+// planes, so w at k-1, k, k+1 and the shared z face stay in registers; the
+// x/y neighbours come from the tile's own loads through L1.
+// MODE 1: also w.q (double-float partial per thread) -> alpha = rho / w.q.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
+                                                  const float2* __restrict__ w,
+                                                  double* __restrict__ q,
+                                                  const float2* __restrict__ T0,
+                                                  const float2* __restrict__ T1,
+                                                  const float2* __restrict__ T2,
+                                                  const float2* __restrict__ D,
+                                                  double* partials, int par, int kchunk) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE == 1 && st->done) return;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, g.n2);
+  float ds = 0.f, dc = 0.f;
+  if (i < g.n0 && j < g.n1 && k0 < k1) {
+    const long long n0 = g.n0, pl = g.plane;
+    const long long dxm = i > 0 ? -1 : 0, dxp = i < g.n0 - 1 ? 1 : 0;
+    const long long dym = j > 0 ? -n0 : 0, dyp = j < g.n1 - 1 ? n0 : 0;
+    long long c = (long long)k0 * pl + (long long)j * n0 + i;
+    // Operands of plane k are loaded during plane k-1 (software pipelining):
+    // every thread keeps a full plane's worth of loads in flight while it sums.
+    struct Ops { float2 d, x0, x1, y0, y1, wx0, wx1, wy0, wy1, wp, zp; };
+    auto load = [&](long long cc, int k, float2 wself) {
+      Ops o;
+      o.d = D[cc];
+      o.x0 = T0[cc];
+      o.x1 = T0[cc + 1];
+      o.y0 = T1[cc];
+      o.y1 = T1[cc + n0];
+      o.wx0 = w[cc + dxm];
+      o.wx1 = w[cc + dxp];
+      o.wy0 = w[cc + dym];
+      o.wy1 = w[cc + dyp];
+      o.wp = (k < g.n2 - 1) ? w[cc + pl] : wself;
+      o.zp = T2[cc + pl];  // the extra zero plane covers k = n2 - 1
+      return o;
+    };
+    float2 wc = w[c];
+    float2 wm = k0 > 0 ? w[c - pl] : wc;
+    float2 tz = T2[c];
+    Ops cur = load(c, k0, wc);
+    for (int k = k0; k < k1; ++k, c += pl) {
+      Ops nxt;
+      if (k + 1 < k1) nxt = load(c + pl, k + 1, cur.wp);
+      float sv = 0.f, ev = 0.f;
+      df_fma_acc<1>(cur.d, wc, sv, ev);
+      df_fma_acc<-1>(cur.x0, cur.wx0, sv, ev);
+      df_fma_acc<-1>(cur.x1, cur.wx1, sv, ev);
+      df_fma_acc<-1>(cur.y0, cur.wy0, sv, ev);
+      df_fma_acc<-1>(cur.y1, cur.wy1, sv, ev);
+      df_fma_acc<-1>(tz, wm, sv, ev);
+      df_fma_acc<-1>(cur.zp, cur.wp, sv, ev);
+      float qh, ql;
+      two_sum(sv, ev, qh, ql);
+      q[c] = widen(qh) + widen(ql);
+      if (MODE == 1) df_fma_acc<1>(wc, make_float2(qh, ql), ds, dc);
+      wm = wc;
+      wc = cur.wp;
+      tz = cur.zp;
+      cur = nxt;
+    }
+  }
+  if (MODE == 1) {
+    const double bs = block_sum(widen(ds) + widen(dc), sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag)) {
+      const double dq = sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        const double alpha = st->rho / dq;
+        st->dq = dq;
+        st->alpha[par] = alpha;
+        if (!(dq > 0.0) || !isfinite(alpha)) { st->status = kEBREAKDOWN; st->done = 1; }
+        st->cnt[kCntDot] = 0;
+      }
+    }
+  }
+}
+
+// Double-float copies of FP64 arrays (split_df per element).
+__global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b, long long n) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) b[c] = split_df(a[c]);
+}
+
 // ------------------------------------------------------------------ forward DCT along axis 0
 // MODE 0: initial residual (r = b already): ||r||^2 -> ||b||^2.
 // MODE 1: PCG update x += alpha w, r -= alpha q, ||r||^2 -> convergence test.
@@ -396,27 +471,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
     const long long row = row0 + l;
     if (row < nrows) t[row * g.n0 + k] = v;
   });
-  if (MODE != 2) {
-    const double bs = block_sum(acc, sh);
-    double v[1] = {bs};
-    if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], &flag)) {
-      const double rr = sum_partials(partials, (int)nblocks(), 1, sh);
-      if (threadIdx.x == 0) {
-        st->rr = rr;
-        if (MODE == 0) {
-          st->bb = rr;
-          st->thresh2 = rtol2 * rr;
-          if (!(rr > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
-        } else {
-          st->iter += 1;
-          if (!isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
-          else if (rr <= st->thresh2) { st->status = kOK; st->done = 1; }
-          else if (st->iter >= st->maxit) { st->status = kENOCONV; st->done = 1; }
-        }
-        st->cnt[kCntRes] = 0;
-      }
-    }
-  }
+  if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag);
 }
 
 // ------------------------------------------------------------------ DCT along axis 1 (in place)
@@ -586,7 +641,7 @@ template <typename R, typename TZ, int MODE>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
                                               const double* kd, double kz_host, int L,
-                                              int check) {
+                                              int check, float2* __restrict__ wdf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
@@ -625,8 +680,13 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
     const long long row = row0 + l;
     if (row < nrows) {
       const long long c = row * g.n0 + i;
-      if (MODE == 2) z[c] = (TZ)fma(beta, wsh[l * g.n0 + i], to_f64<R>(v));
-      else z[c] = (TZ)v;
+      if (MODE == 2) {
+        const double wn = fma(beta, wsh[l * g.n0 + i], to_f64<R>(v));
+        z[c] = (TZ)wn;
+        if (wdf) wdf[c] = split_df(wn);
+      } else {
+        z[c] = (TZ)v;
+      }
     }
   });
 }
@@ -869,6 +929,43 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 }
 
 unsigned int matvec_blocks(const Geometry& g) { return grid_for(g.n, 256, 148 * 16); }
+// 32 x 8 (i, j) tiles; planes per block chosen so that there are at most
+// about 4736 blocks (32 per SM), but every tile column gets a block.
+static dim3 matvec_df_grid(const Geometry& g, int* kchunk) {
+  const long long bx = (g.n0 + 31) / 32, by = (g.n1 + 7) / 8;
+  long long nz = 4736 / (bx * by);
+  if (nz < 1) nz = 1;
+  if (nz > g.n2) nz = g.n2;
+  *kchunk = (int)((g.n2 + nz - 1) / nz);
+  nz = (g.n2 + *kchunk - 1) / *kchunk;
+  return dim3((unsigned int)bx, (unsigned int)by, (unsigned int)nz);
+}
+unsigned int matvec_df_blocks(const Geometry& g) {
+  int kc;
+  const dim3 d = matvec_df_grid(g, &kc);
+  return d.x * d.y * d.z;
+}
+
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, double* q,
+                             const float2* T0, const float2* T1, const float2* T2,
+                             const float2* D, double* partials, int par, int mode,
+                             cudaStream_t s) {
+  int kc;
+  const dim3 grid = matvec_df_grid(g, &kc);
+  if (mode == 1)
+    k_matvec_df<1><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
+  else
+    k_matvec_df<0><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s) {
+  k_split_df<<<grid_for(n, 256), 256, 0, s>>>(a, b, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
@@ -934,6 +1031,7 @@ cudaError_t set_smem_attrs() {
   SETA((k_inv_x<R, double, 0>));
   SETA((k_inv_x<R, double, 2>));
 #undef SETA
+  if (e == cudaSuccess) e = set_fast_attrs<R>();
   return e;
 }
 template cudaError_t set_smem_attrs<double>();
@@ -944,7 +1042,14 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, d
                          const double* w, const double* q, double* r, const double* rin, R* t,
                          double* partials, int par, double rtol2, int mode, cudaStream_t s,
                          int L) {
-  if (L <= 0) L = rows_per_block<R>(g.n0);
+  if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? rin : r, x, w, q)) {
+    const cudaError_t e =
+        launch_fast_fwd_x<R>(g, p, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    count_launch();
+    return e;
+  }
+  if (L < 0) return cudaErrorInvalidValue;
+  if (L == 0) L = rows_per_block<R>(g.n0);
   const size_t sm = smem_x<R>(g.n0, L);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
@@ -971,7 +1076,13 @@ template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                          int inverse, int check, cudaStream_t s, int TI) {
   if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
-  if (TI <= 0) TI = cols_per_block<R>(g.n1);
+  if (TI <= 0 && fast_y_ok<R>(g, p)) {
+    const cudaError_t e = launch_fast_y<R>(g, p, st, t, inverse, check, s);
+    count_launch();
+    return e;
+  }
+  if (TI < 0) return cudaErrorInvalidValue;
+  if (TI == 0) TI = cols_per_block<R>(g.n1);
   const size_t sm = smem_y<R>(g.n1, TI);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   dim3 grid((g.n0 + TI - 1) / TI, g.n2);
@@ -1022,27 +1133,34 @@ template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, c
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L) {
-  if (L <= 0) L = rows_per_block<R>(g.n0);
+                         cudaStream_t s, int L, float2* wdf) {
+  if (L <= 0 && fast_x_ok<R>(g, p, t, z, wdf, z)) {
+    const cudaError_t e =
+        launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s, wdf);
+    count_launch();
+    return e;
+  }
+  if (L < 0) return cudaErrorInvalidValue;
+  if (L == 0) L = rows_per_block<R>(g.n0);
   const size_t sm = smem_x<R>(g.n0, L) + (mode == 2 ? (size_t)L * g.n0 * sizeof(double) : 0);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   if (mode == 2)
-    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
+    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, wdf);
   else
-    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, wdf);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                   const PcgState*, const double*, double*,
                                                   const double*, double, int, int, cudaStream_t,
-                                                  int);
+                                                  int, float2*);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                  const PcgState*, const float*, double*,
                                                  const double*, double, int, int, cudaStream_t,
-                                                 int);
+                                                 int, float2*);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,

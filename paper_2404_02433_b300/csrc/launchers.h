@@ -30,6 +30,12 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);
+// Mixed-precision matvec on double-float operands (q in FP64); mode 1 as k_matvec.
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, double* q,
+                             const float2* T0, const float2* T1, const float2* T2,
+                             const float2* D, double* partials, int par, int mode,
+                             cudaStream_t s);
+cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
 template <typename R>
 cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
                          const double* w, const double* q, double* r, const double* rin, R* t,
@@ -46,7 +52,7 @@ cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, co
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L = 0);
+                         cudaStream_t s, int L = 0, float2* wdf = nullptr);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
@@ -67,10 +73,35 @@ cudaError_t launch_convert(const float* fin, double* dout, const double* din, fl
 template <typename R>
 cudaError_t set_smem_attrs();
 
+// Register-resident transforms for line lengths 32..512 (fast_kernels.cu).
+// The launch_fwd_x / launch_dct_y / launch_inv_x entry points route to them
+// when the tile argument is -1 (required) or 0 (default) and fast_*_ok holds.
+bool fast_len(int n);
+template <typename R>
+bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void* b,
+               const void* c, const void* d);
+template <typename R>
+bool fast_y_ok(const Geometry& g, const DctPlan<R>& p);
+template <typename R>
+cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
+                              const double* w, const double* q, double* r, const double* rin,
+                              R* t, double* partials, int par, double rtol2, int mode,
+                              cudaStream_t s);
+template <typename R, typename TZ>
+cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
+                              const R* t, TZ* z, const double* kd, double kz_host, int check,
+                              int mode, cudaStream_t s, float2* wdf);
+template <typename R>
+cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
+                          int inverse, int check, cudaStream_t s);
+template <typename R>
+cudaError_t set_fast_attrs();
+
 unsigned long long launch_count();
 
 // Grid sizes of the reduction kernels (to size the partials buffer).
 unsigned int matvec_blocks(const Geometry& g);
+unsigned int matvec_df_blocks(const Geometry& g);
 unsigned int fwd_x_blocks(const Geometry& g, int elem_bytes);
 unsigned int tridiag_blocks(const Geometry& g);
 // Shared memory of the transform tiles (rows L / columns TI per block).

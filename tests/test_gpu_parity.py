@@ -270,3 +270,33 @@ def test_integer_pipe_conversions_are_exact():
     nan = np.isnan(ref_n)
     assert np.array_equal(np.isnan(got_n), nan)
     assert np.array_equal(got_n[~nan].view(np.uint32), ref_n[~nan].view(np.uint32))
+
+
+def test_double_float_split_is_exact():
+    # hi = RN32(d), lo = RN32(d - hi) for the mixed matvec; lo = 0 below 2^-74
+    # and where hi is not finite.
+    rng = np.random.default_rng(7)
+    m = 200_000
+    d = rng.uniform(-1, 1, m) * np.exp2(rng.integers(-140, 140, m)).astype(np.float64)
+    d[:1000] = 1.0 + (np.arange(1000) + 0.5) * 2.0 ** -23       # ties of hi
+    d[1000:2000] = 1.0 + (np.arange(1000) + 0.25) * 2.0 ** -23   # remainders of both signs
+    d[2000:2008] = [0.0, -0.0, np.inf, -np.inf, np.nan, 2.0 ** -74, 2.0 ** -75,
+                    np.nextafter(2.0 ** 128, 0.0)]
+    di = torch.from_numpy(d).cuda()
+    hilo = torch.empty(2 * m, dtype=torch.float32, device="cuda")
+    B.etc_split_check(di, hilo, torch.cuda.current_stream().cuda_stream)
+    got = hilo.cpu().numpy().reshape(m, 2)
+    with np.errstate(over="ignore", invalid="ignore"):
+        hi = d.astype(np.float32)
+        ok = np.isfinite(hi) & (np.abs(d) >= 2.0 ** -74)
+        lo = np.where(ok, (d - hi.astype(np.float64)).astype(np.float32), np.float32(0))
+    nan = np.isnan(hi)
+    assert np.array_equal(np.isnan(got[:, 0]), nan)
+    assert np.array_equal(got[~nan, 0].view(np.uint32), hi[~nan].view(np.uint32))
+    assert np.array_equal(np.abs(got[:, 1]).view(np.uint32), np.abs(lo).view(np.uint32))
+    assert np.array_equal(np.signbit(got[ok, 1]) | (got[ok, 1] == 0),
+                          np.signbit(lo[ok]) | (lo[ok] == 0))
+    # hi + lo carries 48 significant bits
+    sel = ok & (d != 0)
+    err = np.abs(got[sel, 0].astype(np.float64) + got[sel, 1] - d[sel]) / np.abs(d[sel])
+    assert err.max() <= 2.0 ** -47
