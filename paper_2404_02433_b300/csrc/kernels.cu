@@ -11,6 +11,7 @@
 //   inv_x    backward DCT along axis 0 -> z (flexible PCG: z.q -> beta)
 // Every kernel returns at entry once the device flag `done` is set, so the host
 // may launch iterations ahead of the convergence test.
+#include <algorithm>
 #include <cstdio>
 
 #include "dct_device.cuh"
@@ -513,6 +514,52 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
   else dct2_run<R>(p, y, a, b, store);
 }
 
+// End of the tridiagonal kernels: block partials of rho (and of z_new . r_old
+// for MODE 2), summed in block order by the last block, which forms beta.
+template <int MODE>
+__device__ __forceinline__ void tridiag_tail(double acc, double acc2, PcgState* st,
+                                             double* partials, double w4, const double* kd,
+                                             double kz_host, double* sh, int* flag_) {
+  int& flag = *flag_;
+  double v[2];
+  v[0] = block_sum(acc, sh);
+  v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
+  if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
+    const double wscale = w4 / (kd ? kd[2] : kz_host);
+    double rho_new = 0.0, zr_old = 0.0;
+    {
+      // fixed-order sums of both columns
+      const int nb = (int)nblocks();
+      double a0 = 0.0, a1 = 0.0;
+      const int per = (nb + blockDim.x - 1) / blockDim.x;
+      const int b0 = threadIdx.x * per;
+      for (int b = b0; b < b0 + per && b < nb; ++b) {
+        a0 += __ldcg(partials + 2 * (size_t)b);
+        a1 += __ldcg(partials + 2 * (size_t)b + 1);
+      }
+      rho_new = wscale * block_sum(a0, sh);
+      zr_old = wscale * block_sum(a1, sh);
+    }
+    if (threadIdx.x == 0) {
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
+      }
+      if (st->phase == 0 || MODE == 3) {
+        st->beta = 0.0;
+        st->phase = 1;
+      } else if (MODE == 1) {
+        st->beta = rho_new / st->rho;
+      } else {
+        st->beta = (rho_new - zr_old) / st->rho;
+        st->zq = zr_old;
+      }
+      st->rho = rho_new;
+      if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
+      st->cnt[kCntRho] = 0;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ tridiagonal along axis 2
 // Forward sweep y_k = r^_k + h_{k-1} y_{k-1}, backward z_k = h_k (y_k + z_{k+1})
 // solves (T_{i'j'}/kappa_ref^z) z = r^.  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
@@ -591,45 +638,7 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
     acc = wgt * to_f64<R>(part);
     if (MODE == 2) acc2 = wgt * to_f64<R>(zr);
   }
-  if (MODE != 0) {
-    double v[2];
-    v[0] = block_sum(acc, sh);
-    v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
-    if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
-      const double wscale = w4 / (kd ? kd[2] : kz_host);
-      double rho_new = 0.0, zr_old = 0.0;
-      {
-        // fixed-order sums of both columns
-        const int nb = (int)nblocks();
-        double a0 = 0.0, a1 = 0.0;
-        const int per = (nb + blockDim.x - 1) / blockDim.x;
-        const int b0 = threadIdx.x * per;
-        for (int b = b0; b < b0 + per && b < nb; ++b) {
-          a0 += __ldcg(partials + 2 * (size_t)b);
-          a1 += __ldcg(partials + 2 * (size_t)b + 1);
-        }
-        rho_new = wscale * block_sum(a0, sh);
-        zr_old = wscale * block_sum(a1, sh);
-      }
-      if (threadIdx.x == 0) {
-        if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-          if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
-        }
-        if (st->phase == 0 || MODE == 3) {
-          st->beta = 0.0;
-          st->phase = 1;
-        } else if (MODE == 1) {
-          st->beta = rho_new / st->rho;
-        } else {
-          st->beta = (rho_new - zr_old) / st->rho;
-          st->zq = zr_old;
-        }
-        st->rho = rho_new;
-        if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
-        st->cnt[kCntRho] = 0;
-      }
-    }
-  }
+  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, kz_host, sh, &flag);
 }
 
 // ------------------------------------------------------------------ backward DCT along axis 0

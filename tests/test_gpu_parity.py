@@ -101,6 +101,24 @@ def test_preconditioner_matches_oracle(shape, direction):
     assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 2e-5
 
 
+@pytest.mark.parametrize("shape", [(129, 5, 7), (200, 6, 10), (600, 4, 6), (1030, 3, 4)])
+def test_preconditioner_long_loading_axis(shape):
+    # long tridiagonal systems (up to 1030 planes) in FP64 and FP32
+    rng = np.random.default_rng(sum(shape))
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
+    rve.set_reference(2, B.ETC_REF_USER, ku)
+    _, fshape = oracle_faces(kx, ky, kz, (1.0, 1.0, 1.0), 2)
+    r = rng.standard_normal(fshape)
+    zo = O.apply_reference_inverse(r, ku)
+    z = torch.empty(fshape, dtype=torch.float64, device="cuda")
+    B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_FP64, dev(r), z)
+    assert relmax(host(z), zo) < 1e-11
+    B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_MIXED, dev(r), z)
+    assert relmax(host(z), zo) < 2e-5
+
+
 # ------------------------------------------------------------------ end to end
 def test_config_32_spheres_direction_x():
     # 32^3 two-phase random spheres (radius 3-5, fraction 0.3, 1:10), rtol 1e-10, load x
