@@ -53,8 +53,10 @@ struct etc_rve {
   double* z64 = nullptr;
   float *t32 = nullptr, *h32 = nullptr;
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
-  // double-float copies for the mixed-precision matvec: faces and diagonal
-  // (refreshed with every face assembly) and the search direction w
+  // mixed path: double-float copies of the faces and diagonal (refreshed with
+  // every face assembly) and the double-float search direction w; its x, r
+  // and q are double-float pairs in the FP64 buffers (same 8 bytes), and x
+  // returns to FP64 at the end of each solve
   float2* Tdf[3] = {nullptr, nullptr, nullptr};
   float2* Ddf = nullptr;
   float2* wdf = nullptr;
@@ -78,6 +80,9 @@ struct etc_rve {
 };
 
 namespace {
+
+// an FP64 buffer viewed as double-float pairs (the mixed path's storage)
+inline float2* df(double* p) { return reinterpret_cast<float2*>(p); }
 
 // ------------------------------------------------------------------ errors
 etc_status fail(etc_rve* h, etc_status s, const std::string& msg) {
@@ -408,8 +413,8 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   // tile -1: the register-resident kernels, where the line length allows them
   if (fast_x_ok<R>(g, p0, h->r, h->z64, nullptr, nullptr)) {
     bx = time_launch(h->stream, e0, e1, [&] {
-      return launch_fwd_x<R>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
-                             h->partials, 0, 0.0, 2, h->stream, -1);
+      return launch_fwd_x<R, double>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
+                                     h->partials, 0, 0.0, 2, h->stream, -1);
     });
     best.fx = -1;
     bi = time_launch(h->stream, e0, e1, [&] {
@@ -426,8 +431,8 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   for (int L = 1; L <= 64; L *= 2) {
     if (L > nrows || smem_x_bytes(g.n0, L, eb) > smem_limit()) break;
     const double tx = time_launch(h->stream, e0, e1, [&] {
-      return launch_fwd_x<R>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
-                             h->partials, 0, 0.0, 2, h->stream, L);
+      return launch_fwd_x<R, double>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
+                                     h->partials, 0, 0.0, 2, h->stream, L);
     });
     if (tx < bx) { bx = tx; best.fx = L; }
     if (smem_x_bytes(g.n0, L, eb) + (size_t)L * g.n0 * sizeof(double) > smem_limit()) continue;
@@ -492,14 +497,14 @@ etc_status autotune(etc_rve* h, int dir, int prec) {
 // ------------------------------------------------------------------ preconditioner chain
 // t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
 // (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
-// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w, and
-// its double-float copy into wdf when given).  kappa_ref comes from the state.
-// ev (optional): events recorded after each of the four kernels.
+// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w; TZ is
+// FP64 or double-float).  kappa_ref comes from the state.  ev (optional):
+// events recorded after each of the four kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
                         const DctPlan<R>& p1, R* t, const R* hp, TZ* out, int tri_mode,
                         int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
-                        cudaEvent_t* ev = nullptr, float2* wdf = nullptr) {
+                        cudaEvent_t* ev = nullptr) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
@@ -509,7 +514,7 @@ etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
   CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
-                          h->tiles[1], wdf)));
+                          h->tiles[1])));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
@@ -530,18 +535,22 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
                         double rtol2) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
-  CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream, rhs.pin_f,
-                 rhs.pout_f, rhs.src));
   if (prec == ETC_PREC_FP64) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr, h->t64,
-                            h->partials, 0, rtol2, 0, h->stream, h->tiles[0]));
+    CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream,
+                   rhs.pin_f, rhs.pout_f, rhs.src));
+    CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr,
+                                     h->t64, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2);
   }
-  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr, h->t32,
-                         h->partials, 0, rtol2, 0, h->stream, h->tiles[0]));
+  // mixed: x = 0 and w = 0 have the same bytes in both storages; r = b is split
+  CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
+                 reinterpret_cast<double*>(h->wdf), h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
+  CK(launch_df_inplace(h->r, h->n, 1, h->stream));
+  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, df(x), nullptr, nullptr, df(h->r), nullptr,
+                                  h->t32, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
-  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
-                                     h->rhat32[1], nullptr, nullptr, h->wdf);
+  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 3, 2,
+                                     h->rhat32[1], nullptr);
 }
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
@@ -551,26 +560,30 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  if (prec == ETC_PREC_FP64)
+  if (prec == ETC_PREC_FP64) {
     CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
                      h->stream));
-  else
-    CK(launch_matvec_df(g, h->st, h->wdf, h->q, h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
-                        h->partials, par, 1, h->stream));
-  if (ev) CK(cudaEventRecord(ev[1], h->stream));
-  if (prec == ETC_PREC_FP64) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr, h->t64,
-                            h->partials, par, 0.0, 1, h->stream, h->tiles[0]));
+    if (ev) CK(cudaEventRecord(ev[1], h->stream));
+    CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr,
+                                     h->t64, h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2,
                                         nullptr, nullptr, ev ? ev + 3 : nullptr);
   }
-  CK(launch_fwd_x<float>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32, h->partials,
-                         par, 0.0, 1, h->stream, h->tiles[0]));
+  CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
+                      h->partials, par, 1, h->stream));
+  if (ev) CK(cudaEventRecord(ev[1], h->stream));
+  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, df(x), h->wdf, df(h->q), df(h->r), nullptr,
+                                  h->t32, h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
-                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
-                                     h->wdf);
+  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 2, 2,
+                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
+}
+
+// End of the iterations of one solve: the mixed path's x returns to FP64.
+etc_status launch_finish_x(etc_rve* h, double* x, int prec) {
+  if (prec != ETC_PREC_FP64) CK(launch_df_inplace(x, h->n, 0, h->stream));
+  return ETC_OK;
 }
 
 // Post-processing of one solve: outflow/inflow sums, cross fluxes and the
@@ -676,6 +689,8 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
     }
   }
   for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
+  s = launch_finish_x(h, x, prec);
+  if (s != ETC_OK) return s;
   s = launch_post(h, g, x, rhs, o.true_residual);
   if (s != ETC_OK) return s;
   CK(cudaEventRecord(e[2], h->stream));
@@ -762,6 +777,8 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   const cudaError_t ee = cudaStreamEndCapture(bs, &ended);
   if (s != ETC_OK) return s;
   CK(ee);
+  s = launch_finish_x(h, x, prec);
+  if (s != ETC_OK) return s;
   s = launch_post(h, g, x, unit, o.true_residual);
   if (s != ETC_OK) return s;
   CK(cudaMemcpyAsync(slot, h->st, sizeof(PcgState), cudaMemcpyDeviceToDevice, cs));
@@ -1139,12 +1156,12 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (prec == ETC_PREC_FP64) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t64,
-                            h->partials, 0, 0.0, 2, h->stream, h->tiles[0]));
+    CK((launch_fwd_x<double, double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r,
+                                     h->t64, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
     s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, 0, 0);
   } else {
-    CK(launch_fwd_x<float>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r, h->t32,
-                           h->partials, 0, 0.0, 2, h->stream, h->tiles[0]));
+    CK((launch_fwd_x<float, double>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r,
+                                    h->t32, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
     s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, 0, 0);
   }
   if (s != ETC_OK) return s;
@@ -1160,8 +1177,8 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (!inverse) {
-    CK(launch_fwd_x<double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, in, h->t64,
-                            h->partials, 0, 0.0, 2, h->stream));
+    CK((launch_fwd_x<double, double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, in,
+                                     h->t64, h->partials, 0, 0.0, 2, h->stream)));
     CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 0, h->stream));
     CK(cudaMemcpyAsync(out, h->t64, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   } else {

@@ -311,3 +311,80 @@ __device__ __forceinline__ void df_fma_acc(float2 x, float2 y, float& s, float& 
 }
 
 }  // namespace etc
+
+namespace etc {
+
+// ---------------------------------------------------------------- PCG vector storage
+// The outer PCG vectors (x, r, w, q) are FP64 in the FP64 path and
+// double-float pairs (float2) in the mixed path; these overloads give the
+// kernels one source for both.
+
+// y + a x.  For double-float: TwoProduct of the high parts by FMA plus the
+// cross terms, TwoSum with y's high part, then renormalisation.
+__device__ __forceinline__ double vaxpy(double a, double x, double y) { return fma(a, x, y); }
+__device__ __forceinline__ float2 vaxpy(float2 a, float2 x, float2 y) {
+  const float p = a.x * x.x;
+  float pe = fma(a.x, x.x, -p);
+  pe = fma(a.x, x.y, pe);
+  pe = fma(a.y, x.x, pe);
+  float s, t;
+  two_sum(y.x, p, s, t);
+  t += y.y + pe;
+  const float hi = s + t;
+  return make_float2(hi, t - (hi - s));
+}
+
+template <typename V> struct Scalar;  // the scalar type a vector of V is scaled by
+template <> struct Scalar<double> {
+  using T = double;
+  static __device__ __forceinline__ double from(double a) { return a; }
+  static __device__ __forceinline__ double neg(double a) { return -a; }
+};
+template <> struct Scalar<float2> {
+  using T = float2;
+  static __device__ __forceinline__ float2 from(double a) { return split_df(a); }
+  static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+};
+
+// A vector value as the FP64 or FP32 input of the preconditioner's transforms
+// (double-float -> binary32: the high part, which is the nearest binary32).
+template <typename R> __device__ __forceinline__ R vround(double v) { return from_f64<R>(v); }
+template <typename R> __device__ __forceinline__ R vround(float2 v);
+template <> __device__ __forceinline__ float vround<float>(float2 v) { return v.x; }
+
+// ||v||^2 partial sums: FP64 for FP64 vectors; for double-float vectors the
+// square of the high part in FP32 (the sum feeds the exit test only).
+__device__ __forceinline__ void vsq_acc(double v, double& acc, float&) { acc = fma(v, v, acc); }
+__device__ __forceinline__ void vsq_acc(float2 v, double&, float& accf) {
+  accf = fma(v.x, v.x, accf);
+}
+
+// the value u (the transform's output, type R) as a vector element
+template <typename V, typename R> __device__ __forceinline__ V vfrom(R u);
+template <> __device__ __forceinline__ double vfrom<double, double>(double u) { return u; }
+template <> __device__ __forceinline__ double vfrom<double, float>(float u) { return widen(u); }
+template <> __device__ __forceinline__ float2 vfrom<float2, float>(float u) {
+  return make_float2(u, 0.f);
+}
+
+// two consecutive elements, 16 bytes
+template <typename V> struct VPair { V a, b; };
+__device__ __forceinline__ VPair<double> ld_pair(const double* p) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ VPair<float2> ld_pair(const float2* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ void st_pair(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+
+}  // namespace etc

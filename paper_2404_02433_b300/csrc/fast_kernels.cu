@@ -205,14 +205,14 @@ __global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinB
 
 // ---------------------------------------------------------------- axis 0, forward
 // Same contract as k_fwd_x (MODE 0 initial residual, 1 PCG update, 2 transform
-// only).  Rows [row0, row0 + L) are contiguous in memory: the vector phase
-// walks them as pairs of elements with 16-byte loads.
-template <typename R, int N, int MODE>
+// only; V the storage of x, w, q, r).  Rows [row0, row0 + L) are contiguous in
+// memory: the vector phase walks them as pairs of elements with 16-byte loads.
+template <typename R, int N, int MODE, typename V>
 __global__ void __launch_bounds__(256)
-    k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, double* __restrict__ x,
-                 const double* __restrict__ w, const double* __restrict__ q,
-                 double* __restrict__ r, const double* __restrict__ rin, R* __restrict__ t,
-                 double* partials, int par, double rtol2) {
+    k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, V* __restrict__ x,
+                 const V* __restrict__ w, const V* __restrict__ q, V* __restrict__ r,
+                 const double* __restrict__ rin, R* __restrict__ t, double* partials, int par,
+                 double rtol2) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -224,27 +224,33 @@ __global__ void __launch_bounds__(256)
   R* Ar = reinterpret_cast<R*>(A);
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
-  const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  using S = Scalar<V>;
+  const typename S::T alpha = S::from((MODE == 1) ? st->alpha[par] : 0.0);
+  const typename S::T nalpha = S::neg(alpha);
   double acc = 0.0;
+  float accf = 0.f;
   constexpr int NP = L * M;  // element pairs of the block
   constexpr int U = 2;
   static_assert(NP % (256 * U) == 0, "pair rounds");
   for (int p0 = threadIdx.x; p0 < NP; p0 += 256 * U) {
-    double2 rv[U], qv[U], xv[U], wv[U];
+    VPair<V> rv[U], qv[U], xv[U], wv[U];
+    double2 dv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = p0 + 256 * u;
       const int l = p / M, i2 = p % M;
       const long long row = row0 + l;
-      rv[u] = make_double2(0.0, 0.0);
+      rv[u].a = rv[u].b = vzero<V>();
       qv[u] = rv[u]; xv[u] = rv[u]; wv[u] = rv[u];
+      dv[u] = make_double2(0.0, 0.0);
       if (row < nrows) {
         const long long c = row * N + 2 * i2;
-        rv[u] = *reinterpret_cast<const double2*>((MODE == 2 ? rin : r) + c);
+        if (MODE == 2) dv[u] = *reinterpret_cast<const double2*>(rin + c);
+        else rv[u] = ld_pair(r + c);
         if (MODE == 1) {
-          qv[u] = *reinterpret_cast<const double2*>(q + c);
-          xv[u] = *reinterpret_cast<const double2*>(x + c);
-          wv[u] = *reinterpret_cast<const double2*>(w + c);
+          qv[u] = ld_pair(q + c);
+          xv[u] = ld_pair(x + c);
+          wv[u] = ld_pair(w + c);
         }
       }
     }
@@ -253,22 +259,29 @@ __global__ void __launch_bounds__(256)
       const int p = p0 + 256 * u;
       const int l = p / M, i2 = p % M;
       const long long row = row0 + l;
-      double2 v = rv[u];
-      if (row < nrows && MODE != 2) {
-        const long long c = row * N + 2 * i2;
-        if (MODE == 1) {
-          *reinterpret_cast<double2*>(x + c) =
-              make_double2(fma(alpha, wv[u].x, xv[u].x), fma(alpha, wv[u].y, xv[u].y));
-          v.x = fma(-alpha, qv[u].x, v.x);
-          v.y = fma(-alpha, qv[u].y, v.y);
-          *reinterpret_cast<double2*>(r + c) = v;
+      R in0, in1;
+      if (MODE == 2) {
+        in0 = from_f64<R>(dv[u].x);
+        in1 = from_f64<R>(dv[u].y);
+      } else {
+        V v0 = rv[u].a, v1 = rv[u].b;
+        if (row < nrows) {
+          const long long c = row * N + 2 * i2;
+          if (MODE == 1) {
+            st_pair(x + c, vaxpy(alpha, wv[u].a, xv[u].a), vaxpy(alpha, wv[u].b, xv[u].b));
+            v0 = vaxpy(nalpha, qv[u].a, v0);
+            v1 = vaxpy(nalpha, qv[u].b, v1);
+            st_pair(r + c, v0, v1);
+          }
+          vsq_acc(v0, acc, accf);
+          vsq_acc(v1, acc, accf);
         }
-        acc = fma(v.x, v.x, acc);
-        acc = fma(v.y, v.y, acc);
+        in0 = vround<R>(v0);
+        in1 = vround<R>(v1);
       }
       // element 2 i2 -> v_{i2}; element 2 i2 + 1 -> v_{n-1-i2}
-      Ar[l * 2 * SA + i2] = from_f64<R>(v.x);
-      Ar[l * 2 * SA + N - 1 - i2] = from_f64<R>(v.y);
+      Ar[l * 2 * SA + i2] = in0;
+      Ar[l * 2 * SA + N - 1 - i2] = in1;
     }
   }
   __syncthreads();
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(256)
         t[row * N + (k ? N - k : M)] = xb;
       }
     }
-  if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag);
+  if (MODE != 2) fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag);
 }
 
 // ---------------------------------------------------------------- axis 0, backward
@@ -312,8 +325,7 @@ __global__ void __launch_bounds__(256)
 template <typename R, typename TZ, int N, int MODE>
 __global__ void __launch_bounds__(256)
     k_fast_inv_x(Geometry g, DctTables<R> tb, const PcgState* st, const R* __restrict__ t,
-                 TZ* __restrict__ z, const double* kd, double kz_host, int check,
-                 float2* __restrict__ wdf) {
+                 TZ* __restrict__ z, const double* kd, double kz_host, int check) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
   constexpr int SR = N + P;  // real stride of the staged input rows
@@ -371,20 +383,19 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   // real view of A: slot a of row l holds v_a
   const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
-  const double beta = (MODE == 2) ? st->beta : 0.0;
+  const typename Scalar<TZ>::T beta = Scalar<TZ>::from((MODE == 2) ? st->beta : 0.0);
   constexpr int NQ = L * M / 256;  // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
   static_assert(NQ % G == 0, "pair groups");
 #pragma unroll 1
   for (int r0 = 0; r0 < NQ; r0 += G) {
-    double2 wo[G];
+    VPair<TZ> wo[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int p = threadIdx.x + 256 * (r0 + u);
       const long long row = row0 + p / M;
-      wo[u] = make_double2(0.0, 0.0);
-      if (MODE == 2 && row < nrows)
-        wo[u] = *reinterpret_cast<const double2*>(z + row * N + 2 * (p % M));
+      wo[u].a = wo[u].b = vzero<TZ>();
+      if (MODE == 2 && row < nrows) wo[u] = ld_pair(z + row * N + 2 * (p % M));
     }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
@@ -395,18 +406,11 @@ __global__ void __launch_bounds__(256)
       const long long c = row * N + 2 * i2;
       const R u0 = Ar[lr * 2 * SA + i2] * scale;          // element 2 i2     <- v_{i2}
       const R u1 = Ar[lr * 2 * SA + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
-      if (MODE == 2) {
-        const double2 wn =
-            make_double2(fma(beta, wo[u].x, to_f64<R>(u0)), fma(beta, wo[u].y, to_f64<R>(u1)));
-        *reinterpret_cast<double2*>(z + c) = wn;
-        if (wdf) {
-          const float2 a = split_df(wn.x), b = split_df(wn.y);
-          *reinterpret_cast<float4*>(wdf + c) = make_float4(a.x, a.y, b.x, b.y);
-        }
-      } else {
-        z[c] = (TZ)u0;
-        z[c + 1] = (TZ)u1;
-      }
+      if (MODE == 2)
+        st_pair(z + c, vaxpy(beta, wo[u].a, vfrom<TZ, R>(u0)),
+                vaxpy(beta, wo[u].b, vfrom<TZ, R>(u1)));
+      else
+        st_pair(z + c, vfrom<TZ, R>(u0), vfrom<TZ, R>(u1));
     }
   }
 }
@@ -425,21 +429,21 @@ size_t fast_y_smem() {
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-template <typename R, int N>
-cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, double* x,
-                    const double* w, const double* q, double* r, const double* rin, R* t,
-                    double* partials, int par, double rtol2, int mode, cudaStream_t s) {
+template <typename R, int N, typename V>
+cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* x, const V* w,
+                    const V* q, V* r, const double* rin, R* t, double* partials, int par,
+                    double rtol2, int mode, cudaStream_t s) {
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
   const size_t sm = fast_x_smem<R, N>();
   if (mode == 0)
-    k_fast_fwd_x<R, N, 0><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+    k_fast_fwd_x<R, N, 0, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
                                                 rtol2);
   else if (mode == 1)
-    k_fast_fwd_x<R, N, 1><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+    k_fast_fwd_x<R, N, 1, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
                                                 rtol2);
   else
-    k_fast_fwd_x<R, N, 2><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
+    k_fast_fwd_x<R, N, 2, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
                                                 rtol2);
   return cudaGetLastError();
 }
@@ -447,14 +451,14 @@ cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, dou
 template <typename R, typename TZ, int N>
 cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, const R* t,
                     TZ* z, const double* kd, double kz_host, int check, int mode,
-                    cudaStream_t s, float2* wdf) {
+                    cudaStream_t s) {
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
   const size_t sm = fast_x_smem<R, N>();
   if (mode == 2)
-    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, wdf);
+    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
   else
-    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, wdf);
+    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
   return cudaGetLastError();
 }
 
@@ -477,11 +481,17 @@ cudaError_t attrs_n() {
   const int sx = (int)fast_x_smem<R, N>(), sy = (int)fast_y_smem<R, N>();
 #define SETF(fn, b) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  SETF((k_fast_fwd_x<R, N, 0>), sx);
-  SETF((k_fast_fwd_x<R, N, 1>), sx);
-  SETF((k_fast_fwd_x<R, N, 2>), sx);
+  SETF((k_fast_fwd_x<R, N, 0, double>), sx);
+  SETF((k_fast_fwd_x<R, N, 1, double>), sx);
+  SETF((k_fast_fwd_x<R, N, 2, double>), sx);
   SETF((k_fast_inv_x<R, double, N, 0>), sx);
   SETF((k_fast_inv_x<R, double, N, 2>), sx);
+  if (sizeof(R) == 4) {
+    SETF((k_fast_fwd_x<float, N, 0, float2>), sx);
+    SETF((k_fast_fwd_x<float, N, 1, float2>), sx);
+    SETF((k_fast_inv_x<float, float2, N, 0>), sx);
+    SETF((k_fast_inv_x<float, float2, N, 2>), sx);
+  }
   SETF((k_fast_y<R, N, 0>), sy);
   SETF((k_fast_y<R, N, 1>), sy);
 #undef SETF
@@ -508,53 +518,66 @@ bool fast_y_ok(const Geometry& g, const DctPlan<R>& p) {
 template bool fast_y_ok<double>(const Geometry&, const DctPlan<double>&);
 template bool fast_y_ok<float>(const Geometry&, const DctPlan<float>&);
 
-template <typename R>
-cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
-                              const double* w, const double* q, double* r, const double* rin,
-                              R* t, double* partials, int par, double rtol2, int mode,
+template <typename R, typename V>
+cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
+                              const V* w, const V* q, V* r, const double* rin, R* t,
+                              double* partials, int par, double rtol2, int mode,
                               cudaStream_t s) {
   switch (g.n0) {
-    case 32: return fwd_x_n<R, 32>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
-    case 64: return fwd_x_n<R, 64>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 32:
+      return fwd_x_n<R, 32, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    case 64:
+      return fwd_x_n<R, 64, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     case 128:
-      return fwd_x_n<R, 128>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 128, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     case 256:
-      return fwd_x_n<R, 256>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 256, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     case 512:
-      return fwd_x_n<R, 512>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 512, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
-template cudaError_t launch_fast_fwd_x<double>(const Geometry&, const DctPlan<double>&,
-                                               PcgState*, double*, const double*,
-                                               const double*, double*, const double*, double*,
-                                               double*, int, double, int, cudaStream_t);
-template cudaError_t launch_fast_fwd_x<float>(const Geometry&, const DctPlan<float>&, PcgState*,
-                                              double*, const double*, const double*, double*,
-                                              const double*, float*, double*, int, double, int,
-                                              cudaStream_t);
+template cudaError_t launch_fast_fwd_x<double, double>(const Geometry&, const DctPlan<double>&,
+                                                       PcgState*, double*, const double*,
+                                                       const double*, double*, const double*,
+                                                       double*, double*, int, double, int,
+                                                       cudaStream_t);
+template cudaError_t launch_fast_fwd_x<float, double>(const Geometry&, const DctPlan<float>&,
+                                                      PcgState*, double*, const double*,
+                                                      const double*, double*, const double*,
+                                                      float*, double*, int, double, int,
+                                                      cudaStream_t);
+template cudaError_t launch_fast_fwd_x<float, float2>(const Geometry&, const DctPlan<float>&,
+                                                      PcgState*, float2*, const float2*,
+                                                      const float2*, float2*, const double*,
+                                                      float*, double*, int, double, int,
+                                                      cudaStream_t);
 
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
                               const R* t, TZ* z, const double* kd, double kz_host, int check,
-                              int mode, cudaStream_t s, float2* wdf) {
+                              int mode, cudaStream_t s) {
   switch (g.n0) {
-    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
-    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
-    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
-    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
-    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, wdf);
+    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
+    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
+    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
+    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
+    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_fast_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                        const PcgState*, const double*, double*,
                                                        const double*, double, int, int,
-                                                       cudaStream_t, float2*);
+                                                       cudaStream_t);
 template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                       const PcgState*, const float*, double*,
                                                       const double*, double, int, int,
-                                                      cudaStream_t, float2*);
+                                                      cudaStream_t);
+template cudaError_t launch_fast_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
+                                                      const PcgState*, const float*, float2*,
+                                                      const double*, double, int, int,
+                                                      cudaStream_t);
 
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,

@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
 
 // ------------------------------------------------------------------ double-float matvec
 // The mixed-precision path's q = A w (same operator as k_matvec) with the
-// FP64-class arithmetic on the FP32 pipe: faces, diagonal and w as
-// double-float pairs, the seven products summed by Sum2, q written as FP64.
+// FP64-class arithmetic on the FP32 pipe: faces, diagonal, w and q as
+// double-float pairs, the seven products summed by Sum2.
 // Each thread owns one (i, j) column of a 32 x 8 tile and marches over kchunk
 // planes, so w at k-1, k, k+1 and the shared z face stay in registers; the
 // x/y neighbours come from the tile's own loads through L1.
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
 template <int MODE>
 __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
                                                   const float2* __restrict__ w,
-                                                  double* __restrict__ q,
+                                                  float2* __restrict__ q,
                                                   const float2* __restrict__ T0,
                                                   const float2* __restrict__ T1,
                                                   const float2* __restrict__ T2,
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
       df_fma_acc<-1>(cur.zp, cur.wp, sv, ev);
       float qh, ql;
       two_sum(sv, ev, qh, ql);
-      q[c] = widen(qh) + widen(ql);
+      q[c] = make_float2(qh, ql);
       if (MODE == 1) df_fma_acc<1>(wc, make_float2(qh, ql), ds, dc);
       wm = wc;
       wc = cur.wp;
@@ -403,6 +403,21 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
   }
 }
 
+// In place between FP64 and double-float storage (8 bytes either way): the
+// mixed path's residual after the initial rhs, and its solution at the end.
+__global__ void k_f64_to_df_inplace(double* a, long long n) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
+    const float2 v = split_df(a[c]);
+    reinterpret_cast<float2*>(a)[c] = v;
+  }
+}
+__global__ void k_df_to_f64_inplace(double* a, long long n) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
+    const float2 v = reinterpret_cast<const float2*>(a)[c];
+    a[c] = widen(v.x) + widen(v.y);
+  }
+}
+
 // Double-float copies of FP64 arrays (split_df per element).
 __global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b, long long n) {
   for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) b[c] = split_df(a[c]);
@@ -411,13 +426,13 @@ __global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b,
 // ------------------------------------------------------------------ forward DCT along axis 0
 // MODE 0: initial residual (r = b already): ||r||^2 -> ||b||^2.
 // MODE 1: PCG update x += alpha w, r -= alpha q, ||r||^2 -> convergence test.
-// MODE 2: transform only (component entry point), no state.
-template <typename R, int MODE>
+// MODE 2: transform only (component entry point), no state; input rin (FP64).
+// V: storage of x, w, q, r (double, or float2 double-float pairs).
+template <typename R, int MODE, typename V>
 __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgState* st,
-                                              double* __restrict__ x,
-                                              const double* __restrict__ w,
-                                              const double* __restrict__ q,
-                                              double* __restrict__ r, const double* __restrict__ rin,
+                                              V* __restrict__ x, const V* __restrict__ w,
+                                              const V* __restrict__ q, V* __restrict__ r,
+                                              const double* __restrict__ rin,
                                               R* __restrict__ t, double* partials, int L, int par,
                                               double rtol2) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -429,22 +444,28 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
   c2<R>* b = a + L * dct_half_alloc(g.n0);
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
-  const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  using S = Scalar<V>;
+  const typename S::T alpha = S::from((MODE == 1) ? st->alpha[par] : 0.0);
+  const typename S::T nalpha = S::neg(alpha);
   double acc = 0.0;
+  float accf = 0.f;
   const int tot = L * g.n0;
   // U elements per thread per round: their loads are all issued before use
   constexpr int U = 4;
   for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
-    double rv[U], qv[U], xv[U], wv[U];
+    V rv[U], qv[U], xv[U], wv[U];
+    double dv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * blockDim.x;
       const int l = e / g.n0, i = e - l * g.n0;
       const long long row = row0 + l;
-      rv[u] = 0.0; qv[u] = 0.0; xv[u] = 0.0; wv[u] = 0.0;
+      rv[u] = vzero<V>(); qv[u] = rv[u]; xv[u] = rv[u]; wv[u] = rv[u];
+      dv[u] = 0.0;
       if (e < tot && row < nrows) {
         const long long c = row * g.n0 + i;
-        rv[u] = (MODE == 2) ? rin[c] : r[c];
+        if (MODE == 2) dv[u] = rin[c];
+        else rv[u] = r[c];
         if (MODE == 1) { qv[u] = q[c]; xv[u] = x[c]; wv[u] = w[c]; }
       }
     }
@@ -454,17 +475,23 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
       if (e >= tot) break;
       const int l = e / g.n0, i = e - l * g.n0;
       const long long row = row0 + l;
-      double v = rv[u];
-      if (row < nrows && MODE != 2) {
-        const long long c = row * g.n0 + i;
-        if (MODE == 1) {
-          x[c] = fma(alpha, wv[u], xv[u]);
-          v = fma(-alpha, qv[u], v);
-          r[c] = v;
+      R in;
+      if (MODE == 2) {
+        in = from_f64<R>(dv[u]);
+      } else {
+        V v = rv[u];
+        if (row < nrows) {
+          const long long c = row * g.n0 + i;
+          if (MODE == 1) {
+            x[c] = vaxpy(alpha, wv[u], xv[u]);
+            v = vaxpy(nalpha, qv[u], v);
+            r[c] = v;
+          }
+          vsq_acc(v, acc, accf);
         }
-        acc = fma(v, v, acc);
+        in = vround<R>(v);
       }
-      dct2_put<R>(p.s, y, a, l, i, from_f64<R>(v));
+      dct2_put<R>(p.s, y, a, l, i, in);
     }
   }
   __syncthreads();
@@ -472,7 +499,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
     const long long row = row0 + l;
     if (row < nrows) t[row * g.n0 + k] = v;
   });
-  if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag);
+  if (MODE != 2) fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag);
 }
 
 // ------------------------------------------------------------------ DCT along axis 1 (in place)
@@ -644,34 +671,34 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 // ------------------------------------------------------------------ backward DCT along axis 0
 // u = scale * (backward DCT of t along axis 0), then by MODE:
 // 0: z = u (TZ).
-// 2: PCG: w = u + beta w in place (z points at the FP64 w; beta from the
-//    tridiagonal kernel), so the next matvec reads w directly.
+// 2: PCG: w = u + beta w in place (z points at w, FP64 or double-float;
+//    beta from the tridiagonal kernel), so the next matvec reads w directly.
 template <typename R, typename TZ, int MODE>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
                                               const double* kd, double kz_host, int L,
-                                              int check, float2* __restrict__ wdf) {
+                                              int check) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
   c2<R>* a = reinterpret_cast<c2<R>*>(smraw);
   c2<R>* b = a + L * dct_half_alloc(g.n0);
   // MODE 2: the old w of the block's rows, staged with the transform input
-  double* wsh = reinterpret_cast<double*>(b + L * dct_half_alloc(g.n0));
+  TZ* wsh = reinterpret_cast<TZ*>(b + L * dct_half_alloc(g.n0));
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   const int tot = L * g.n0;
   constexpr int U = 8;
   for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
     R v[U];
-    double wv[U];
+    TZ wv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * blockDim.x;
       const int l = e / g.n0, k = e - l * g.n0;
       const bool ok = (e < tot && row0 + l < nrows);
       v[u] = ok ? t[(row0 + l) * g.n0 + k] : (R)0;
-      if (MODE == 2) wv[u] = ok ? (double)z[(row0 + l) * g.n0 + k] : 0.0;
+      if (MODE == 2) wv[u] = ok ? z[(row0 + l) * g.n0 + k] : vzero<TZ>();
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -683,19 +710,14 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
     }
   }
   __syncthreads();
-  const double beta = (MODE == 2) ? st->beta : 0.0;
+  const typename Scalar<TZ>::T beta = Scalar<TZ>::from((MODE == 2) ? st->beta : 0.0);
   const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
   dct3_run<R>(p, y, a, b, scale, [&](int l, int i, R v) {
     const long long row = row0 + l;
     if (row < nrows) {
       const long long c = row * g.n0 + i;
-      if (MODE == 2) {
-        const double wn = fma(beta, wsh[l * g.n0 + i], to_f64<R>(v));
-        z[c] = (TZ)wn;
-        if (wdf) wdf[c] = split_df(wn);
-      } else {
-        z[c] = (TZ)v;
-      }
+      if (MODE == 2) z[c] = vaxpy(beta, wsh[l * g.n0 + i], vfrom<TZ, R>(v));
+      else z[c] = vfrom<TZ, R>(v);
     }
   });
 }
@@ -955,7 +977,7 @@ unsigned int matvec_df_blocks(const Geometry& g) {
   return d.x * d.y * d.z;
 }
 
-cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, double* q,
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
                              const float2* D, double* partials, int par, int mode,
                              cudaStream_t s) {
@@ -965,6 +987,13 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, d
     k_matvec_df<1><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
   else
     k_matvec_df<0><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s) {
+  if (to_df) k_f64_to_df_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+  else k_df_to_f64_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
   count_launch();
   return cudaGetLastError();
 }
@@ -1026,34 +1055,47 @@ size_t smem_y_bytes(int n1, int TI, int elem_bytes) {
 size_t smem_limit() { return kMaxDyn; }
 
 
+// the mixed path's double-float instantiations (FP32 transforms only)
+static cudaError_t set_df_attrs() {
+  cudaError_t e = cudaSuccess;
+  const void* fns[] = {(const void*)k_fwd_x<float, 0, float2>, (const void*)k_fwd_x<float, 1, float2>,
+                       (const void*)k_fwd_x<float, 2, float2>, (const void*)k_inv_x<float, float2, 0>,
+                       (const void*)k_inv_x<float, float2, 2>};
+  for (const void* f : fns)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDyn);
+  return e;
+}
+
 template <typename R>
 cudaError_t set_smem_attrs() {
   cudaError_t e = cudaSuccess;
 #define SETA(fn)                                                                           \
   if (e == cudaSuccess)                                                                    \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDyn);
-  SETA((k_fwd_x<R, 0>));
-  SETA((k_fwd_x<R, 1>));
-  SETA((k_fwd_x<R, 2>));
+  SETA((k_fwd_x<R, 0, double>));
+  SETA((k_fwd_x<R, 1, double>));
+  SETA((k_fwd_x<R, 2, double>));
   SETA((k_dct_y<R, 0>));
   SETA((k_dct_y<R, 1>));
   SETA((k_inv_x<R, double, 0>));
   SETA((k_inv_x<R, double, 2>));
 #undef SETA
+  if (e == cudaSuccess && sizeof(R) == 4) e = set_df_attrs();
   if (e == cudaSuccess) e = set_fast_attrs<R>();
   return e;
 }
 template cudaError_t set_smem_attrs<double>();
 template cudaError_t set_smem_attrs<float>();
 
-template <typename R>
-cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
-                         const double* w, const double* q, double* r, const double* rin, R* t,
+template <typename R, typename V>
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
+                         const V* w, const V* q, V* r, const double* rin, R* t,
                          double* partials, int par, double rtol2, int mode, cudaStream_t s,
                          int L) {
-  if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? rin : r, x, w, q)) {
+  if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? (const void*)rin : (const void*)r, x, w, q)) {
     const cudaError_t e =
-        launch_fast_fwd_x<R>(g, p, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+        launch_fast_fwd_x<R, V>(g, p, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     count_launch();
     return e;
   }
@@ -1064,22 +1106,26 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, d
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   if (mode == 0)
-    k_fwd_x<R, 0><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+    k_fwd_x<R, 0, V><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
   else if (mode == 1)
-    k_fwd_x<R, 1><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+    k_fwd_x<R, 1, V><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
   else
-    k_fwd_x<R, 2><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
+    k_fwd_x<R, 2, V><<<nb, 256, sm, s>>>(g, p, st, x, w, q, r, rin, t, partials, L, par, rtol2);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t launch_fwd_x<double>(const Geometry&, const DctPlan<double>&, PcgState*,
-                                          double*, const double*, const double*, double*,
-                                          const double*, double*, double*, int, double, int,
-                                          cudaStream_t, int);
-template cudaError_t launch_fwd_x<float>(const Geometry&, const DctPlan<float>&, PcgState*,
-                                         double*, const double*, const double*, double*,
-                                         const double*, float*, double*, int, double, int,
-                                         cudaStream_t, int);
+template cudaError_t launch_fwd_x<double, double>(const Geometry&, const DctPlan<double>&,
+                                                  PcgState*, double*, const double*,
+                                                  const double*, double*, const double*, double*,
+                                                  double*, int, double, int, cudaStream_t, int);
+template cudaError_t launch_fwd_x<float, double>(const Geometry&, const DctPlan<float>&,
+                                                 PcgState*, double*, const double*,
+                                                 const double*, double*, const double*, float*,
+                                                 double*, int, double, int, cudaStream_t, int);
+template cudaError_t launch_fwd_x<float, float2>(const Geometry&, const DctPlan<float>&,
+                                                 PcgState*, float2*, const float2*,
+                                                 const float2*, float2*, const double*, float*,
+                                                 double*, int, double, int, cudaStream_t, int);
 
 template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
@@ -1142,34 +1188,37 @@ template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, c
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L, float2* wdf) {
-  if (L <= 0 && fast_x_ok<R>(g, p, t, z, wdf, z)) {
-    const cudaError_t e =
-        launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s, wdf);
+                         cudaStream_t s, int L) {
+  if (L <= 0 && fast_x_ok<R>(g, p, t, z, z, z)) {
+    const cudaError_t e = launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s);
     count_launch();
     return e;
   }
   if (L < 0) return cudaErrorInvalidValue;
   if (L == 0) L = rows_per_block<R>(g.n0);
-  const size_t sm = smem_x<R>(g.n0, L) + (mode == 2 ? (size_t)L * g.n0 * sizeof(double) : 0);
+  const size_t sm = smem_x<R>(g.n0, L) + (mode == 2 ? (size_t)L * g.n0 * sizeof(TZ) : 0);
   if (sm > kMaxDyn) return cudaErrorInvalidValue;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   if (mode == 2)
-    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, wdf);
+    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
   else
-    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, wdf);
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                   const PcgState*, const double*, double*,
                                                   const double*, double, int, int, cudaStream_t,
-                                                  int, float2*);
+                                                  int);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                  const PcgState*, const float*, double*,
                                                  const double*, double, int, int, cudaStream_t,
-                                                 int, float2*);
+                                                 int);
+template cudaError_t launch_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
+                                                 const PcgState*, const float*, float2*,
+                                                 const double*, double, int, int, cudaStream_t,
+                                                 int);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,

@@ -31,14 +31,18 @@ cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, doub
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);
 // Mixed-precision matvec on double-float operands (q in FP64); mode 1 as k_matvec.
-cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, double* q,
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
                              const float2* D, double* partials, int par, int mode,
                              cudaStream_t s);
 cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
-template <typename R>
-cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
-                         const double* w, const double* q, double* r, const double* rin, R* t,
+// FP64 <-> double-float storage in place (to_df = 1: split; 0: hi + lo in FP64).
+cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s);
+// V: storage of x, w, q, r (double, or float2 double-float pairs with R = float);
+// rin (mode 2) is FP64.
+template <typename R, typename V>
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
+                         const V* w, const V* q, V* r, const double* rin, R* t,
                          double* partials, int par, double rtol2, int mode, cudaStream_t s,
                          int L = 0);
 template <typename R>
@@ -52,7 +56,7 @@ cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, co
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
                          TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L = 0, float2* wdf = nullptr);
+                         cudaStream_t s, int L = 0);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
@@ -82,15 +86,15 @@ bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void
                const void* c, const void* d);
 template <typename R>
 bool fast_y_ok(const Geometry& g, const DctPlan<R>& p);
-template <typename R>
-cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, double* x,
-                              const double* w, const double* q, double* r, const double* rin,
-                              R* t, double* partials, int par, double rtol2, int mode,
+template <typename R, typename V>
+cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
+                              const V* w, const V* q, V* r, const double* rin, R* t,
+                              double* partials, int par, double rtol2, int mode,
                               cudaStream_t s);
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
                               const R* t, TZ* z, const double* kd, double kz_host, int check,
-                              int mode, cudaStream_t s, float2* wdf);
+                              int mode, cudaStream_t s);
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                           int inverse, int check, cudaStream_t s);

@@ -170,8 +170,8 @@ extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
   if (static_plan(n0, tab0, &p0, &lam0, s) != cudaSuccess) return ETC_ECUDA;
   if (static_plan(n1, tab1, &p1, &lam1, s) != cudaSuccess) return ETC_ECUDA;
   if (launch_pivots<double>(g, lam0, lam1, nullptr, kref, h, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_fwd_x<double>(g, p0, nullptr, nullptr, nullptr, nullptr, nullptr, r, t, nullptr, 0,
-                           0.0, 2, s) != cudaSuccess)
+  if (launch_fwd_x<double, double>(g, p0, nullptr, nullptr, nullptr, nullptr, nullptr, r, t,
+                                   nullptr, 0, 0.0, 2, s) != cudaSuccess)
     return ETC_ECUDA;
   if (launch_dct_y<double>(g, p1, nullptr, t, 0, 0, s) != cudaSuccess) return ETC_ECUDA;
   if (launch_tridiag<double>(g, nullptr, t, h, nullptr, kref[2], nullptr, 0, nullptr, nullptr,
