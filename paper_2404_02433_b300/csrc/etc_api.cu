@@ -497,14 +497,15 @@ etc_status autotune(etc_rve* h, int dir, int prec) {
 // ------------------------------------------------------------------ preconditioner chain
 // t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
 // (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
-// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w; TZ is
-// FP64 or double-float).  kappa_ref comes from the state.  ev (optional):
-// events recorded after each of the four kernels.
+// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w, after
+// x += alpha[par] w when x is given; TZ is FP64 or double-float).  kappa_ref
+// comes from the state.  ev (optional): events recorded after each of the four
+// kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
                         const DctPlan<R>& p1, R* t, const R* hp, TZ* out, int tri_mode,
                         int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
-                        cudaEvent_t* ev = nullptr) {
+                        cudaEvent_t* ev = nullptr, TZ* x = nullptr, int par = 0) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
@@ -514,7 +515,7 @@ etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
   CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
-                          h->tiles[1])));
+                          h->tiles[1], x, par)));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
 }
@@ -546,8 +547,9 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
   CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
                  reinterpret_cast<double*>(h->wdf), h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
   CK(launch_df_inplace(h->r, h->n, 1, h->stream));
-  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, df(x), nullptr, nullptr, df(h->r), nullptr,
-                                  h->t32, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
+  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, nullptr, df(h->r),
+                                  nullptr, h->t32, h->partials, 0, rtol2, 0, h->stream,
+                                  h->tiles[0])));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
   return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 3, 2,
                                      h->rhat32[1], nullptr);
@@ -564,6 +566,8 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
     CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
                      h->stream));
     if (ev) CK(cudaEventRecord(ev[1], h->stream));
+    // FP64 storage: x += alpha w in the residual-update kernel (its w-update
+    // kernel is FP64-bound)
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr,
                                      h->t64, h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
@@ -573,16 +577,23 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
                       h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
-  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, df(x), h->wdf, df(h->q), df(h->r), nullptr,
-                                  h->t32, h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
+  // double-float storage: x += alpha w moves to the w-update kernel, which
+  // reads w anyway (8 bytes per cell less)
+  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, df(h->q), df(h->r),
+                                  nullptr, h->t32, h->partials, par, 0.0, 1, h->stream,
+                                  h->tiles[0])));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
   return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 2, 2,
-                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr);
+                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
+                                     df(x), par);
 }
 
-// End of the iterations of one solve: the mixed path's x returns to FP64.
-etc_status launch_finish_x(etc_rve* h, double* x, int prec) {
-  if (prec != ETC_PREC_FP64) CK(launch_df_inplace(x, h->n, 0, h->stream));
+// End of the iterations of one solve: the last step of x if it is still due
+// (the iteration that converged stops before its w update, which carries x),
+// and the mixed path's x back to FP64.
+etc_status finish_solve_x(etc_rve* h, const Geometry& g, double* x, int prec) {
+  if (prec != ETC_PREC_FP64)
+    CK(launch_finish_x(g, h->st, x, reinterpret_cast<const double*>(h->wdf), 1, h->stream));
   return ETC_OK;
 }
 
@@ -689,7 +700,7 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
     }
   }
   for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
-  s = launch_finish_x(h, x, prec);
+  s = finish_solve_x(h, g, x, prec);
   if (s != ETC_OK) return s;
   s = launch_post(h, g, x, rhs, o.true_residual);
   if (s != ETC_OK) return s;
@@ -777,7 +788,7 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   const cudaError_t ee = cudaStreamEndCapture(bs, &ended);
   if (s != ETC_OK) return s;
   CK(ee);
-  s = launch_finish_x(h, x, prec);
+  s = finish_solve_x(h, g, x, prec);
   if (s != ETC_OK) return s;
   s = launch_post(h, g, x, unit, o.true_residual);
   if (s != ETC_OK) return s;

@@ -59,6 +59,8 @@ struct PcgState {
   int phase;         // 0 = initial preconditioner apply, 1 = iterating
   int passes;        // loop-body passes of a device-driven (graph) loop
   int max_passes;    // hard cap on passes (ends the loop even without `done`)
+  int xpend;         // 1 + parity of an iteration whose x += alpha w is still due
+                     // (r was updated, the w update that carries x has not run)
   unsigned int cnt[8];  // arrival counters of the last-block reductions
 };
 
@@ -155,10 +157,12 @@ __device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y
 // End of the residual-update kernels (Algorithm 1, exit test): block partials
 // of ||r||^2, summed in block order by the last block, which records ||r||^2
 // (MODE 0: also ||b||^2 and the threshold rtol^2 ||b||^2) and decides
-// convergence, the iteration cap and breakdown.
+// convergence, the iteration cap and breakdown.  MODE 1 with `defer` marks
+// this iteration's x += alpha w as due (the w-update kernel applies it).
 template <int MODE>
 __device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, double* partials,
-                                                    double rtol2, double* sh, int* flag) {
+                                                    double rtol2, double* sh, int* flag,
+                                                    int par, bool defer) {
   const double bs = block_sum(acc, sh);
   double v[1] = {bs};
   if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], flag)) {
@@ -171,6 +175,7 @@ __device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, do
         if (!(rr > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
       } else {
         st->iter += 1;
+        st->xpend = defer ? par + 1 : 0;
         if (!isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
         else if (rr <= st->thresh2) { st->status = kOK; st->done = 1; }
         else if (st->iter >= st->maxit) { st->status = kENOCONV; st->done = 1; }
@@ -383,6 +388,10 @@ __device__ __forceinline__ void st_pair(double* p, double a, double b) {
 __device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
   *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
+// element as FP64 (double-float: hi + lo rounded once)
+__device__ __forceinline__ void store_f64(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_f64(double* p, float2 v) { *p = widen(v.x) + widen(v.y); }
+
 template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }

@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinB
 
 // ---------------------------------------------------------------- axis 0, forward
 // Same contract as k_fwd_x (MODE 0 initial residual, 1 PCG update, 2 transform
-// only; V the storage of x, w, q, r).  Rows [row0, row0 + L) are contiguous in
-// memory: the vector phase walks them as pairs of elements with 16-byte loads.
+// only; V the storage of x, w, q, r; x moves here for FP64 storage only).
+// Rows [row0, row0 + L) are contiguous in memory: the vector phase walks them
+// as pairs of elements with 16-byte loads.
 template <typename R, int N, int MODE, typename V>
 __global__ void __launch_bounds__(256)
     k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, V* __restrict__ x,
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(256)
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   using S = Scalar<V>;
+  constexpr bool XHERE = (MODE == 1) && std::is_same<V, double>::value;
   const typename S::T alpha = S::from((MODE == 1) ? st->alpha[par] : 0.0);
   const typename S::T nalpha = S::neg(alpha);
   double acc = 0.0;
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(256)
         const long long c = row * N + 2 * i2;
         if (MODE == 2) dv[u] = *reinterpret_cast<const double2*>(rin + c);
         else rv[u] = ld_pair(r + c);
-        if (MODE == 1) {
-          qv[u] = ld_pair(q + c);
+        if (MODE == 1) qv[u] = ld_pair(q + c);
+        if (XHERE) {
           xv[u] = ld_pair(x + c);
           wv[u] = ld_pair(w + c);
         }
@@ -268,7 +270,8 @@ __global__ void __launch_bounds__(256)
         if (row < nrows) {
           const long long c = row * N + 2 * i2;
           if (MODE == 1) {
-            st_pair(x + c, vaxpy(alpha, wv[u].a, xv[u].a), vaxpy(alpha, wv[u].b, xv[u].b));
+            if (XHERE)
+              st_pair(x + c, vaxpy(alpha, wv[u].a, xv[u].a), vaxpy(alpha, wv[u].b, xv[u].b));
             v0 = vaxpy(nalpha, qv[u].a, v0);
             v1 = vaxpy(nalpha, qv[u].b, v1);
             st_pair(r + c, v0, v1);
@@ -316,16 +319,19 @@ __global__ void __launch_bounds__(256)
         t[row * N + (k ? N - k : M)] = xb;
       }
     }
-  if (MODE != 2) fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag);
+  if (MODE != 2)
+    fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag, par, !XHERE);
 }
 
 // ---------------------------------------------------------------- axis 0, backward
 // Same contract as k_inv_x: u = scale * (backward DCT of t along axis 0), then
-// MODE 0: z = u; MODE 2: w = u + beta w in place (z points at w).
+// MODE 0: z = u; MODE 2: w = u + beta w in place (z points at w), after
+// x += alpha w with the old w when x is given.
 template <typename R, typename TZ, int N, int MODE>
 __global__ void __launch_bounds__(256)
-    k_fast_inv_x(Geometry g, DctTables<R> tb, const PcgState* st, const R* __restrict__ t,
-                 TZ* __restrict__ z, const double* kd, double kz_host, int check) {
+    k_fast_inv_x(Geometry g, DctTables<R> tb, PcgState* st, const R* __restrict__ t,
+                 TZ* __restrict__ z, const double* kd, double kz_host, int check,
+                 TZ* __restrict__ x, int par) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
   constexpr int SR = N + P;  // real stride of the staged input rows
@@ -384,18 +390,25 @@ __global__ void __launch_bounds__(256)
   // real view of A: slot a of row l holds v_a
   const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
   const typename Scalar<TZ>::T beta = Scalar<TZ>::from((MODE == 2) ? st->beta : 0.0);
+  const bool upd = (MODE == 2) && x != nullptr;
+  const typename Scalar<TZ>::T alpha = Scalar<TZ>::from(upd ? st->alpha[par] : 0.0);
+  if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
   constexpr int NQ = L * M / 256;  // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
   static_assert(NQ % G == 0, "pair groups");
 #pragma unroll 1
   for (int r0 = 0; r0 < NQ; r0 += G) {
-    VPair<TZ> wo[G];
+    VPair<TZ> wo[G], xo[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int p = threadIdx.x + 256 * (r0 + u);
       const long long row = row0 + p / M;
       wo[u].a = wo[u].b = vzero<TZ>();
-      if (MODE == 2 && row < nrows) wo[u] = ld_pair(z + row * N + 2 * (p % M));
+      xo[u] = wo[u];
+      if (MODE == 2 && row < nrows) {
+        wo[u] = ld_pair(z + row * N + 2 * (p % M));
+        if (upd) xo[u] = ld_pair(x + row * N + 2 * (p % M));
+      }
     }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
@@ -406,9 +419,11 @@ __global__ void __launch_bounds__(256)
       const long long c = row * N + 2 * i2;
       const R u0 = Ar[lr * 2 * SA + i2] * scale;          // element 2 i2     <- v_{i2}
       const R u1 = Ar[lr * 2 * SA + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
-      if (MODE == 2)
+      if (MODE == 2) {
+        if (upd) st_pair(x + c, vaxpy(alpha, wo[u].a, xo[u].a), vaxpy(alpha, wo[u].b, xo[u].b));
         st_pair(z + c, vaxpy(beta, wo[u].a, vfrom<TZ, R>(u0)),
                 vaxpy(beta, wo[u].b, vfrom<TZ, R>(u1)));
+      }
       else
         st_pair(z + c, vfrom<TZ, R>(u0), vfrom<TZ, R>(u1));
     }
@@ -449,16 +464,16 @@ cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* 
 }
 
 template <typename R, typename TZ, int N>
-cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, const R* t,
-                    TZ* z, const double* kd, double kz_host, int check, int mode,
-                    cudaStream_t s) {
+cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
+                    const double* kd, double kz_host, int check, int mode, cudaStream_t s,
+                    TZ* x, int par) {
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
   const size_t sm = fast_x_smem<R, N>();
   if (mode == 2)
-    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
+    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
   else
-    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
+    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
   return cudaGetLastError();
 }
 
@@ -554,30 +569,30 @@ template cudaError_t launch_fast_fwd_x<float, float2>(const Geometry&, const Dct
                                                       cudaStream_t);
 
 template <typename R, typename TZ>
-cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
-                              const R* t, TZ* z, const double* kd, double kz_host, int check,
-                              int mode, cudaStream_t s) {
+cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
+                              TZ* z, const double* kd, double kz_host, int check, int mode,
+                              cudaStream_t s, TZ* x, int par) {
   switch (g.n0) {
-    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
-    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
-    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
-    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
-    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s);
+    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
+    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
+    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
+    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
+    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_fast_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
-                                                       const PcgState*, const double*, double*,
+                                                       PcgState*, const double*, double*,
                                                        const double*, double, int, int,
-                                                       cudaStream_t);
+                                                       cudaStream_t, double*, int);
 template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                      const PcgState*, const float*, double*,
+                                                      PcgState*, const float*, double*,
                                                       const double*, double, int, int,
-                                                      cudaStream_t);
+                                                      cudaStream_t, double*, int);
 template cudaError_t launch_fast_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                      const PcgState*, const float*, float2*,
+                                                      PcgState*, const float*, float2*,
                                                       const double*, double, int, int,
-                                                      cudaStream_t);
+                                                      cudaStream_t, float2*, int);
 
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,

@@ -13,6 +13,7 @@
 // may launch iterations ahead of the convergence test.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "dct_device.cuh"
 #include "etc_internal.cuh"
@@ -223,6 +224,7 @@ __global__ void k_state_reset(PcgState* st, int maxit) {
   st->iter = 0; st->maxit = maxit; st->done = 0; st->status = kOK; st->phase = 0;
   st->passes = 0;
   st->max_passes = maxit / 2 + 4;  // the loop body runs two iterations
+  st->xpend = 0;
 }
 
 // End of one pass of a device-driven PCG loop (graph WHILE node): stop when
@@ -418,6 +420,20 @@ __global__ void k_df_to_f64_inplace(double* a, long long n) {
   }
 }
 
+// End of a solve (see PcgState::xpend): x += alpha w if the last residual
+// update's step is still due, then, for double-float storage, x to FP64 in
+// place.  The element arrays are viewed as V.
+template <typename V>
+__global__ void k_finish_x(Geometry g, const PcgState* st, V* x, const V* w) {
+  const int pend = st->xpend;
+  const typename Scalar<V>::T alpha = Scalar<V>::from(pend ? st->alpha[pend - 1] : 0.0);
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    V v = x[c];
+    if (pend) v = vaxpy(alpha, w[c], v);
+    store_f64(reinterpret_cast<double*>(x) + c, v);
+  }
+}
+
 // Double-float copies of FP64 arrays (split_df per element).
 __global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b, long long n) {
   for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) b[c] = split_df(a[c]);
@@ -425,7 +441,10 @@ __global__ void k_split_df(const double* __restrict__ a, float2* __restrict__ b,
 
 // ------------------------------------------------------------------ forward DCT along axis 0
 // MODE 0: initial residual (r = b already): ||r||^2 -> ||b||^2.
-// MODE 1: PCG update x += alpha w, r -= alpha q, ||r||^2 -> convergence test.
+// MODE 1: PCG update r -= alpha q, ||r||^2 -> convergence test, and
+//         x += alpha w for FP64 storage; with double-float storage the x step
+//         follows in the w-update kernel, which reads w anyway (the FP64 path
+//         keeps it here: its w-update kernel is FP64-bound).
 // MODE 2: transform only (component entry point), no state; input rin (FP64).
 // V: storage of x, w, q, r (double, or float2 double-float pairs).
 template <typename R, int MODE, typename V>
@@ -445,6 +464,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   using S = Scalar<V>;
+  constexpr bool XHERE = (MODE == 1) && std::is_same<V, double>::value;
   const typename S::T alpha = S::from((MODE == 1) ? st->alpha[par] : 0.0);
   const typename S::T nalpha = S::neg(alpha);
   double acc = 0.0;
@@ -460,13 +480,14 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
       const int e = e0 + u * blockDim.x;
       const int l = e / g.n0, i = e - l * g.n0;
       const long long row = row0 + l;
-      rv[u] = vzero<V>(); qv[u] = rv[u]; xv[u] = rv[u]; wv[u] = rv[u];
+      rv[u] = vzero<V>(); qv[u] = rv[u];
       dv[u] = 0.0;
       if (e < tot && row < nrows) {
         const long long c = row * g.n0 + i;
         if (MODE == 2) dv[u] = rin[c];
         else rv[u] = r[c];
-        if (MODE == 1) { qv[u] = q[c]; xv[u] = x[c]; wv[u] = w[c]; }
+        if (MODE == 1) qv[u] = q[c];
+        if (XHERE) { xv[u] = x[c]; wv[u] = w[c]; }
       }
     }
 #pragma unroll
@@ -483,7 +504,7 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
         if (row < nrows) {
           const long long c = row * g.n0 + i;
           if (MODE == 1) {
-            x[c] = vaxpy(alpha, wv[u], xv[u]);
+            if (XHERE) x[c] = vaxpy(alpha, wv[u], xv[u]);
             v = vaxpy(nalpha, qv[u], v);
             r[c] = v;
           }
@@ -499,7 +520,8 @@ __global__ void __launch_bounds__(256) k_fwd_x(Geometry g, DctPlan<R> p, PcgStat
     const long long row = row0 + l;
     if (row < nrows) t[row * g.n0 + k] = v;
   });
-  if (MODE != 2) fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag);
+  if (MODE != 2)
+    fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag, par, !XHERE);
 }
 
 // ------------------------------------------------------------------ DCT along axis 1 (in place)
@@ -672,12 +694,14 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 // u = scale * (backward DCT of t along axis 0), then by MODE:
 // 0: z = u (TZ).
 // 2: PCG: w = u + beta w in place (z points at w, FP64 or double-float;
-//    beta from the tridiagonal kernel), so the next matvec reads w directly.
+//    beta from the tridiagonal kernel), so the next matvec reads w directly;
+//    with x given, first x += alpha w with the old w (this iteration's step),
+//    which clears the pending mark of the residual-update kernel.
 template <typename R, typename TZ, int MODE>
-__global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const PcgState* st,
+__global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
                                               const double* kd, double kz_host, int L,
-                                              int check) {
+                                              int check, TZ* __restrict__ x, int par) {
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
@@ -688,10 +712,13 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
   const int tot = L * g.n0;
+  const bool upd = (MODE == 2) && x != nullptr;
+  const typename Scalar<TZ>::T alpha = Scalar<TZ>::from(upd ? st->alpha[par] : 0.0);
+  if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
   constexpr int U = 8;
   for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
     R v[U];
-    TZ wv[U];
+    TZ wv[U], xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * blockDim.x;
@@ -699,6 +726,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
       const bool ok = (e < tot && row0 + l < nrows);
       v[u] = ok ? t[(row0 + l) * g.n0 + k] : (R)0;
       if (MODE == 2) wv[u] = ok ? z[(row0 + l) * g.n0 + k] : vzero<TZ>();
+      if (MODE == 2 && upd && ok) xv[u] = x[(row0 + l) * g.n0 + k];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -707,6 +735,8 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, const P
       const int l = e / g.n0, k = e - l * g.n0;
       dct3_put<R>(y, b, l, k, v[u]);
       if (MODE == 2) wsh[e] = wv[u];
+      if (MODE == 2 && upd && row0 + l < nrows)
+        x[(row0 + l) * g.n0 + k] = vaxpy(alpha, wv[u], xv[u]);
     }
   }
   __syncthreads();
@@ -991,6 +1021,17 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, f
   return cudaGetLastError();
 }
 
+cudaError_t launch_finish_x(const Geometry& g, const PcgState* st, double* x, const double* w,
+                            int df, cudaStream_t s) {
+  if (df)
+    k_finish_x<float2><<<grid_for(g.n, 256), 256, 0, s>>>(
+        g, st, reinterpret_cast<float2*>(x), reinterpret_cast<const float2*>(w));
+  else
+    k_finish_x<double><<<grid_for(g.n, 256), 256, 0, s>>>(g, st, x, w);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s) {
   if (to_df) k_f64_to_df_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
   else k_df_to_f64_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
@@ -1089,11 +1130,10 @@ template cudaError_t set_smem_attrs<double>();
 template cudaError_t set_smem_attrs<float>();
 
 template <typename R, typename V>
-cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
-                         const V* w, const V* q, V* r, const double* rin, R* t,
-                         double* partials, int par, double rtol2, int mode, cudaStream_t s,
-                         int L) {
-  if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? (const void*)rin : (const void*)r, x, w, q)) {
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x, const V* w,
+                         const V* q, V* r, const double* rin, R* t, double* partials, int par,
+                         double rtol2, int mode, cudaStream_t s, int L) {
+  if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? (const void*)rin : (const void*)r, q, x, w)) {
     const cudaError_t e =
         launch_fast_fwd_x<R, V>(g, p, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
     count_launch();
@@ -1186,11 +1226,12 @@ template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, c
                                            const float*, cudaStream_t);
 
 template <typename R, typename TZ>
-cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
-                         TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L) {
-  if (L <= 0 && fast_x_ok<R>(g, p, t, z, z, z)) {
-    const cudaError_t e = launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s);
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
+                         const double* kd, double kz_host, int check, int mode, cudaStream_t s,
+                         int L, TZ* x, int par) {
+  if (L <= 0 && fast_x_ok<R>(g, p, t, z, x, z)) {
+    const cudaError_t e =
+        launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s, x, par);
     count_launch();
     return e;
   }
@@ -1201,24 +1242,24 @@ cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState*
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   if (mode == 2)
-    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
+    k_inv_x<R, TZ, 2><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, x, par);
   else
-    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check);
+    k_inv_x<R, TZ, 0><<<nb, 256, sm, s>>>(g, p, st, t, z, kd, kz_host, L, check, x, par);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
-                                                  const PcgState*, const double*, double*,
+                                                  PcgState*, const double*, double*,
                                                   const double*, double, int, int, cudaStream_t,
-                                                  int);
+                                                  int, double*, int);
 template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                 const PcgState*, const float*, double*,
+                                                 PcgState*, const float*, double*,
                                                  const double*, double, int, int, cudaStream_t,
-                                                 int);
+                                                 int, double*, int);
 template cudaError_t launch_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                 const PcgState*, const float*, float2*,
+                                                 PcgState*, const float*, float2*,
                                                  const double*, double, int, int, cudaStream_t,
-                                                 int);
+                                                 int, float2*, int);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,

@@ -38,13 +38,13 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, f
 cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
 // FP64 <-> double-float storage in place (to_df = 1: split; 0: hi + lo in FP64).
 cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s);
-// V: storage of x, w, q, r (double, or float2 double-float pairs with R = float);
+// V: storage of x, w, q, r (double, or float2 double-float pairs with
+// R = float); x += alpha w happens here for FP64 storage only (mode 1);
 // rin (mode 2) is FP64.
 template <typename R, typename V>
-cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
-                         const V* w, const V* q, V* r, const double* rin, R* t,
-                         double* partials, int par, double rtol2, int mode, cudaStream_t s,
-                         int L = 0);
+cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x, const V* w,
+                         const V* q, V* r, const double* rin, R* t, double* partials, int par,
+                         double rtol2, int mode, cudaStream_t s, int L = 0);
 template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                          int inverse, int check, cudaStream_t s, int TI = 0);
@@ -53,10 +53,15 @@ template <typename R>
 cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, const double* kd,
                            double kz_host, double* partials, int mode, R* rnew, const R* rold,
                            cudaStream_t s);
+// mode 2 with x: also x += alpha[par] w (old w) before w is replaced.
 template <typename R, typename TZ>
-cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st, const R* t,
-                         TZ* z, const double* kd, double kz_host, int check, int mode,
-                         cudaStream_t s, int L = 0);
+cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
+                         const double* kd, double kz_host, int check, int mode, cudaStream_t s,
+                         int L = 0, TZ* x = nullptr, int par = 0);
+// End of a solve: the x += alpha w still due (see PcgState::xpend), then for
+// double-float storage (df = 1) x back to FP64 in place.
+cudaError_t launch_finish_x(const Geometry& g, const PcgState* st, double* x, const double* w,
+                            int df, cudaStream_t s);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
@@ -92,9 +97,9 @@ cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* 
                               double* partials, int par, double rtol2, int mode,
                               cudaStream_t s);
 template <typename R, typename TZ>
-cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, const PcgState* st,
-                              const R* t, TZ* z, const double* kd, double kz_host, int check,
-                              int mode, cudaStream_t s);
+cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
+                              TZ* z, const double* kd, double kz_host, int check, int mode,
+                              cudaStream_t s, TZ* x, int par);
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                           int inverse, int check, cudaStream_t s);
