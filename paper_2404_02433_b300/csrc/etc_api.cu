@@ -410,17 +410,21 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   const int eb = (int)sizeof(R);
   const long long nrows = (long long)g.n1 * g.n2;
   double bx = INFINITY, bi = INFINITY, by = INFINITY;
-  // tile -1: the register-resident kernels, where the line length allows them
+  // tiles -1 and -2: the register-resident kernels (blocks of 256 and 128
+  // threads), where the line length allows them
   if (fast_x_ok<R>(g, p0, h->r, h->z64, nullptr, nullptr)) {
-    bx = time_launch(h->stream, e0, e1, [&] {
-      return launch_fwd_x<R, double>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r, t,
-                                     h->partials, 0, 0.0, 2, h->stream, -1);
-    });
-    best.fx = -1;
-    bi = time_launch(h->stream, e0, e1, [&] {
-      return launch_inv_x<R, double>(g, p0, h->st, t, h->z64, nullptr, 1.0, 0, 2, h->stream, -1);
-    });
-    best.ix = -1;
+    for (int T = -1; T >= -2; --T) {
+      const double tx = time_launch(h->stream, e0, e1, [&] {
+        return launch_fwd_x<R, double>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr, h->r,
+                                       t, h->partials, 0, 0.0, 2, h->stream, T);
+      });
+      if (tx < bx) { bx = tx; best.fx = T; }
+      const double ti = time_launch(h->stream, e0, e1, [&] {
+        return launch_inv_x<R, double>(g, p0, h->st, t, h->z64, nullptr, 1.0, 0, 2, h->stream,
+                                       T);
+      });
+      if (ti < bi) { bi = ti; best.ix = T; }
+    }
   }
   if (g.n1 > 1 && fast_y_ok<R>(g, p1)) {
     by = time_launch(h->stream, e0, e1, [&] {

@@ -38,7 +38,12 @@ template <int N> struct Fast {
   static constexpr int SA = M + P;
   static constexpr int BS0 = Q * (P + 1);
   static constexpr int BS = BS0 + (((P - BS0) % 16) + 16) % 16;
-  static constexpr int L = 256 / P;  // rows per 256-thread block
+};
+
+// Axis-0 blocks of NT threads (256 or 128): L = NT / P rows each.
+template <int N, int NT> struct FastX {
+  static constexpr int L = NT / Fast<N>::P;
+  static_assert(L * Fast<N>::P == NT, "rows per block");
 };
 
 template <typename R> struct FastCols {  // columns per block of the axis-1 passes
@@ -208,14 +213,15 @@ __global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinB
 // only; V the storage of x, w, q, r; x moves here for FP64 storage only).
 // Rows [row0, row0 + L) are contiguous in memory: the vector phase walks them
 // as pairs of elements with 16-byte loads.
-template <typename R, int N, int MODE, typename V>
-__global__ void __launch_bounds__(256)
+template <typename R, int N, int MODE, typename V, int NT>
+__global__ void __launch_bounds__(NT)
     k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, V* __restrict__ x,
                  const V* __restrict__ w, const V* __restrict__ q, V* __restrict__ r,
                  const double* __restrict__ rin, R* __restrict__ t, double* partials, int par,
                  double rtol2) {
   using F = Fast<N>;
-  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS;
+  constexpr int L = FastX<N, NT>::L;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32];
   __shared__ int flag;
@@ -233,13 +239,13 @@ __global__ void __launch_bounds__(256)
   float accf = 0.f;
   constexpr int NP = L * M;  // element pairs of the block
   constexpr int U = 2;
-  static_assert(NP % (256 * U) == 0, "pair rounds");
-  for (int p0 = threadIdx.x; p0 < NP; p0 += 256 * U) {
+  static_assert(NP % (NT * U) == 0, "pair rounds");
+  for (int p0 = threadIdx.x; p0 < NP; p0 += NT * U) {
     VPair<V> rv[U], qv[U], xv[U], wv[U];
     double2 dv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int p = p0 + 256 * u;
+      const int p = p0 + NT * u;
       const int l = p / M, i2 = p % M;
       const long long row = row0 + l;
       rv[u].a = rv[u].b = vzero<V>();
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int p = p0 + 256 * u;
+      const int p = p0 + NT * u;
       const int l = p / M, i2 = p % M;
       const long long row = row0 + l;
       R in0, in1;
@@ -327,13 +333,14 @@ __global__ void __launch_bounds__(256)
 // Same contract as k_inv_x: u = scale * (backward DCT of t along axis 0), then
 // MODE 0: z = u; MODE 2: w = u + beta w in place (z points at w), after
 // x += alpha w with the old w when x is given.
-template <typename R, typename TZ, int N, int MODE>
-__global__ void __launch_bounds__(256)
+template <typename R, typename TZ, int N, int MODE, int NT>
+__global__ void __launch_bounds__(NT)
     k_fast_inv_x(Geometry g, DctTables<R> tb, PcgState* st, const R* __restrict__ t,
                  TZ* __restrict__ z, const double* kd, double kz_host, int check,
                  TZ* __restrict__ x, int par) {
   using F = Fast<N>;
-  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS, L = F::L;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS;
+  constexpr int L = FastX<N, NT>::L;
   constexpr int SR = N + P;  // real stride of the staged input rows
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
@@ -346,20 +353,20 @@ __global__ void __launch_bounds__(256)
   // thread's loads issued before the first shared-memory store
   using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
   constexpr int VW = 16 / (int)sizeof(R);
-  constexpr int NR = L * N / VW / 256;
-  static_assert(NR * 256 * VW == L * N, "staging rounds");
+  constexpr int NR = L * N / VW / NT;
+  static_assert(NR * NT * VW == L * N, "staging rounds");
   {
     V val[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      const int e = threadIdx.x + 256 * r;
+      const int e = threadIdx.x + NT * r;
       const int l = (e * VW) / N, i = (e * VW) % N;
       const long long row = row0 + l;
       val[r] = row < nrows ? *reinterpret_cast<const V*>(t + row * N + i) : V{};
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-      const int e = threadIdx.x + 256 * r;
+      const int e = threadIdx.x + NT * r;
       const int l = (e * VW) / N, i = (e * VW) % N;
       *reinterpret_cast<V*>(Ar + l * SR + i) = val[r];
     }
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(256)
   const bool upd = (MODE == 2) && x != nullptr;
   const typename Scalar<TZ>::T alpha = Scalar<TZ>::from(upd ? st->alpha[par] : 0.0);
   if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
-  constexpr int NQ = L * M / 256;  // element pairs per thread
+  constexpr int NQ = L * M / NT;  // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
   static_assert(NQ % G == 0, "pair groups");
 #pragma unroll 1
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(256)
     VPair<TZ> wo[G], xo[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
-      const int p = threadIdx.x + 256 * (r0 + u);
+      const int p = threadIdx.x + NT * (r0 + u);
       const long long row = row0 + p / M;
       wo[u].a = wo[u].b = vzero<TZ>();
       xo[u] = wo[u];
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(256)
     }
 #pragma unroll
     for (int u = 0; u < G; ++u) {
-      const int p = threadIdx.x + 256 * (r0 + u);
+      const int p = threadIdx.x + NT * (r0 + u);
       const int lr = p / M, i2 = p % M;
       const long long row = row0 + lr;
       if (row >= nrows) continue;
@@ -433,9 +440,9 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------- launchers
 namespace {
 
-template <typename R, int N>
+template <typename R, int N, int NT>
 size_t fast_x_smem() {
-  return (size_t)Fast<N>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>);
+  return (size_t)FastX<N, NT>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>);
 }
 template <typename R, int N>
 size_t fast_y_smem() {
@@ -444,37 +451,55 @@ size_t fast_y_smem() {
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+template <typename R, int N, typename V, int NT>
+cudaError_t fwd_x_nt(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* x, const V* w,
+                     const V* q, V* r, const double* rin, R* t, double* partials, int par,
+                     double rtol2, int mode, cudaStream_t s) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<R, N, NT>();
+  if (mode == 0)
+    k_fast_fwd_x<R, N, 0, V, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials,
+                                                    par, rtol2);
+  else if (mode == 1)
+    k_fast_fwd_x<R, N, 1, V, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials,
+                                                    par, rtol2);
+  else
+    k_fast_fwd_x<R, N, 2, V, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials,
+                                                    par, rtol2);
+  return cudaGetLastError();
+}
 template <typename R, int N, typename V>
 cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* x, const V* w,
                     const V* q, V* r, const double* rin, R* t, double* partials, int par,
-                    double rtol2, int mode, cudaStream_t s) {
-  const long long nrows = (long long)g.n1 * g.n2;
-  const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
-  const size_t sm = fast_x_smem<R, N>();
-  if (mode == 0)
-    k_fast_fwd_x<R, N, 0, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
-                                                rtol2);
-  else if (mode == 1)
-    k_fast_fwd_x<R, N, 1, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
-                                                rtol2);
-  else
-    k_fast_fwd_x<R, N, 2, V><<<nb, 256, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par,
-                                                rtol2);
-  return cudaGetLastError();
+                    double rtol2, int mode, cudaStream_t s, int nt) {
+  if (nt == 128)
+    return fwd_x_nt<R, N, V, 128>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+  return fwd_x_nt<R, N, V, 256>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
 }
 
+template <typename R, typename TZ, int N, int NT>
+cudaError_t inv_x_nt(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
+                     const double* kd, double kz_host, int check, int mode, cudaStream_t s,
+                     TZ* x, int par) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<R, N, NT>();
+  if (mode == 2)
+    k_fast_inv_x<R, TZ, N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
+  else
+    k_fast_inv_x<R, TZ, N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
+  return cudaGetLastError();
+}
 template <typename R, typename TZ, int N>
 cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
                     const double* kd, double kz_host, int check, int mode, cudaStream_t s,
-                    TZ* x, int par) {
-  const long long nrows = (long long)g.n1 * g.n2;
-  const unsigned int nb = (unsigned int)((nrows + Fast<N>::L - 1) / Fast<N>::L);
-  const size_t sm = fast_x_smem<R, N>();
-  if (mode == 2)
-    k_fast_inv_x<R, TZ, N, 2><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
-  else
-    k_fast_inv_x<R, TZ, N, 0><<<nb, 256, sm, s>>>(g, tb, st, t, z, kd, kz_host, check, x, par);
-  return cudaGetLastError();
+                    TZ* x, int par, int nt) {
+  if (nt == 128)
+    return inv_x_nt<R, TZ, N, 128>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
+  return inv_x_nt<R, TZ, N, 256>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
 }
 
 template <typename R, int N>
@@ -490,26 +515,36 @@ cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R
   return cudaGetLastError();
 }
 
-template <typename R, int N>
-cudaError_t attrs_n() {
+template <typename R, int N, int NT>
+cudaError_t attrs_nt() {
   cudaError_t e = cudaSuccess;
-  const int sx = (int)fast_x_smem<R, N>(), sy = (int)fast_y_smem<R, N>();
+  const int sx = (int)fast_x_smem<R, N, NT>();
 #define SETF(fn, b) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  SETF((k_fast_fwd_x<R, N, 0, double>), sx);
-  SETF((k_fast_fwd_x<R, N, 1, double>), sx);
-  SETF((k_fast_fwd_x<R, N, 2, double>), sx);
-  SETF((k_fast_inv_x<R, double, N, 0>), sx);
-  SETF((k_fast_inv_x<R, double, N, 2>), sx);
+  SETF((k_fast_fwd_x<R, N, 0, double, NT>), sx);
+  SETF((k_fast_fwd_x<R, N, 1, double, NT>), sx);
+  SETF((k_fast_fwd_x<R, N, 2, double, NT>), sx);
+  SETF((k_fast_inv_x<R, double, N, 0, NT>), sx);
+  SETF((k_fast_inv_x<R, double, N, 2, NT>), sx);
   if (sizeof(R) == 4) {
-    SETF((k_fast_fwd_x<float, N, 0, float2>), sx);
-    SETF((k_fast_fwd_x<float, N, 1, float2>), sx);
-    SETF((k_fast_inv_x<float, float2, N, 0>), sx);
-    SETF((k_fast_inv_x<float, float2, N, 2>), sx);
+    SETF((k_fast_fwd_x<float, N, 0, float2, NT>), sx);
+    SETF((k_fast_fwd_x<float, N, 1, float2, NT>), sx);
+    SETF((k_fast_inv_x<float, float2, N, 0, NT>), sx);
+    SETF((k_fast_inv_x<float, float2, N, 2, NT>), sx);
   }
-  SETF((k_fast_y<R, N, 0>), sy);
-  SETF((k_fast_y<R, N, 1>), sy);
 #undef SETF
+  return e;
+}
+
+template <typename R, int N>
+cudaError_t attrs_n() {
+  cudaError_t e = attrs_nt<R, N, 256>();
+  if (e == cudaSuccess) e = attrs_nt<R, N, 128>();
+  const int sy = (int)fast_y_smem<R, N>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fast_y<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fast_y<R, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
   return e;
 }
 
@@ -537,18 +572,23 @@ template <typename R, typename V>
 cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
                               const V* w, const V* q, V* r, const double* rin, R* t,
                               double* partials, int par, double rtol2, int mode,
-                              cudaStream_t s) {
+                              cudaStream_t s, int nt) {
   switch (g.n0) {
     case 32:
-      return fwd_x_n<R, 32, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 32, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
+                               mode, s, nt);
     case 64:
-      return fwd_x_n<R, 64, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 64, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
+                               mode, s, nt);
     case 128:
-      return fwd_x_n<R, 128, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 128, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
+                                mode, s, nt);
     case 256:
-      return fwd_x_n<R, 256, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 256, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
+                                mode, s, nt);
     case 512:
-      return fwd_x_n<R, 512, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+      return fwd_x_n<R, 512, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
+                                mode, s, nt);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -556,43 +596,53 @@ template cudaError_t launch_fast_fwd_x<double, double>(const Geometry&, const Dc
                                                        PcgState*, double*, const double*,
                                                        const double*, double*, const double*,
                                                        double*, double*, int, double, int,
-                                                       cudaStream_t);
+                                                       cudaStream_t, int);
 template cudaError_t launch_fast_fwd_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                       PcgState*, double*, const double*,
                                                       const double*, double*, const double*,
                                                       float*, double*, int, double, int,
-                                                      cudaStream_t);
+                                                      cudaStream_t, int);
 template cudaError_t launch_fast_fwd_x<float, float2>(const Geometry&, const DctPlan<float>&,
                                                       PcgState*, float2*, const float2*,
                                                       const float2*, float2*, const double*,
                                                       float*, double*, int, double, int,
-                                                      cudaStream_t);
+                                                      cudaStream_t, int);
 
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
                               TZ* z, const double* kd, double kz_host, int check, int mode,
-                              cudaStream_t s, TZ* x, int par) {
+                              cudaStream_t s, TZ* x, int par, int nt) {
   switch (g.n0) {
-    case 32: return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
-    case 64: return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
-    case 128: return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
-    case 256: return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
-    case 512: return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par);
+    case 32:
+      return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
+                                par, nt);
+    case 64:
+      return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
+                                par, nt);
+    case 128:
+      return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
+                                 par, nt);
+    case 256:
+      return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
+                                 par, nt);
+    case 512:
+      return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
+                                 par, nt);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_fast_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
                                                        PcgState*, const double*, double*,
                                                        const double*, double, int, int,
-                                                       cudaStream_t, double*, int);
+                                                       cudaStream_t, double*, int, int);
 template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
                                                       PcgState*, const float*, double*,
                                                       const double*, double, int, int,
-                                                      cudaStream_t, double*, int);
+                                                      cudaStream_t, double*, int, int);
 template cudaError_t launch_fast_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
                                                       PcgState*, const float*, float2*,
                                                       const double*, double, int, int,
-                                                      cudaStream_t, float2*, int);
+                                                      cudaStream_t, float2*, int, int);
 
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,

@@ -1134,8 +1134,8 @@ cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V
                          const V* q, V* r, const double* rin, R* t, double* partials, int par,
                          double rtol2, int mode, cudaStream_t s, int L) {
   if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? (const void*)rin : (const void*)r, q, x, w)) {
-    const cudaError_t e =
-        launch_fast_fwd_x<R, V>(g, p, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+    const cudaError_t e = launch_fast_fwd_x<R, V>(g, p, st, x, w, q, r, rin, t, partials, par,
+                                                  rtol2, mode, s, L == -2 ? 128 : 256);
     count_launch();
     return e;
   }
@@ -1230,8 +1230,8 @@ cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, c
                          const double* kd, double kz_host, int check, int mode, cudaStream_t s,
                          int L, TZ* x, int par) {
   if (L <= 0 && fast_x_ok<R>(g, p, t, z, x, z)) {
-    const cudaError_t e =
-        launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s, x, par);
+    const cudaError_t e = launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s,
+                                                   x, par, L == -2 ? 128 : 256);
     count_launch();
     return e;
   }

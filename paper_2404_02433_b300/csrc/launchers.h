@@ -84,7 +84,8 @@ cudaError_t set_smem_attrs();
 
 // Register-resident transforms for line lengths 32..512 (fast_kernels.cu).
 // The launch_fwd_x / launch_dct_y / launch_inv_x entry points route to them
-// when the tile argument is -1 (required) or 0 (default) and fast_*_ok holds.
+// when fast_*_ok holds and the tile argument is 0 (default) or negative:
+// axis 0, -1 = blocks of 256 threads, -2 = blocks of 128; axis 1, -1.
 bool fast_len(int n);
 template <typename R>
 bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void* b,
@@ -95,11 +96,11 @@ template <typename R, typename V>
 cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
                               const V* w, const V* q, V* r, const double* rin, R* t,
                               double* partials, int par, double rtol2, int mode,
-                              cudaStream_t s);
+                              cudaStream_t s, int nt);
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
                               TZ* z, const double* kd, double kz_host, int check, int mode,
-                              cudaStream_t s, TZ* x, int par);
+                              cudaStream_t s, TZ* x, int par, int nt);
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                           int inverse, int check, cudaStream_t s);
