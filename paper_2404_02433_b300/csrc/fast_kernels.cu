@@ -151,18 +151,25 @@ __global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinB
                 : mk2<R>((R)0, (R)0);
     }
   } else {
+    // every input j needs X_j, X_{n-j}, X_{m-j}, X_{m+j}: stage the tile's
+    // columns once (real view of the buffer, row-major over the C columns)
+    R* sr = reinterpret_cast<R*>(smraw);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // rows tau + P s, s < 2Q, in two halves
+      R xs[Q];
+#pragma unroll
+      for (int s = 0; s < Q; ++s) xs[s] = ok ? col[(tau + P * (s + h * Q)) * n0] : (R)0;
+#pragma unroll
+      for (int s = 0; s < Q; ++s) sr[(tau + P * (s + h * Q)) * C + c] = xs[s];
+    }
+    __syncthreads();
 #pragma unroll
     for (int s = 0; s < Q; ++s) {
       const int j = tau + P * s;
-      R xj = 0, xn = 0, xm = 0, xp = 0;
-      if (ok) {
-        xj = col[j * n0];
-        xn = j ? col[(N - j) * n0] : (R)0;
-        xm = col[(M - j) * n0];
-        xp = col[(M + j) * n0];
-      }
-      v[s] = inv_pre<R>(tb.ipre, j, M, xj, xn, xm, xp);
+      v[s] = inv_pre<R>(tb.ipre, j, M, sr[j * C + c], j ? sr[(N - j) * C + c] : (R)0,
+                        sr[(M - j) * C + c], sr[(M + j) * C + c]);
     }
+    __syncthreads();  // the staged tile is read before the transpose reuses the buffer
   }
   four_step_a<R, N, SIGN>(v, tb.tw4, tau);
 #pragma unroll
