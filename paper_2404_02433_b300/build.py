@@ -1,6 +1,7 @@
 """Build libetc.so (the C-ABI CUDA library) in-tree for sm_103a with nvcc."""
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import subprocess
@@ -9,9 +10,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libetc.so")
+OBJ = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-         "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
 
 def sources():
@@ -32,16 +33,35 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
-    """Compile every .cu under csrc/ into one shared library; returns its path."""
+    """Compile every .cu under csrc/ (one nvcc per file, in parallel) and link
+    them into one shared library; returns its path."""
     if not force and up_to_date():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
+    os.makedirs(OBJ, exist_ok=True)
+    inc = ["-I", os.path.join(HERE, "..", "include")]
+    jobs = []
+    for src in sources():
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        jobs.append((obj, [nvcc, *ARCH, *FLAGS, *inc, "-c", src, "-o", obj]))
+
+    def run(job):
+        if verbose:
+            print(" ".join(job[1]), file=sys.stderr)
+        return subprocess.run(job[1], capture_output=True, text=True)
+
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as pool:
+        results = list(pool.map(run, jobs))
+    for (obj, cmd), res in zip(jobs, results):
+        if res.returncode != 0:
+            sys.stderr.write(res.stdout + res.stderr)
+            raise subprocess.CalledProcessError(res.returncode, cmd)
     tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, *FLAGS, "-I", os.path.join(HERE, "..", "include"), *sources(),
-           "-o", tmp, "-lcudart"]
+    link = [nvcc, *ARCH, "-shared", *[o for o, _ in jobs], "-o", tmp, "-lcudart"]
     if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+        print(" ".join(link), file=sys.stderr)
+    subprocess.run(link, check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -12,6 +12,8 @@
 // reduced cosine table.  R is the arithmetic type (double or float).
 #pragma once
 
+#include <type_traits>
+
 #include "etc_internal.cuh"
 
 namespace etc {
@@ -133,6 +135,96 @@ template <typename R, int SIGN> struct Bfly<R, 16, SIGN> {
     }
   }
 };
+
+// exp(2 pi i m / q) at compile time, for the twiddles of the composite
+// lengths below.  The angle 2 pi (m mod q) / q is written exactly as
+// k pi/2 +- psi with psi in [0, pi/4] (integer octant arithmetic), and cos psi,
+// sin psi are summed from their Taylor series (14 terms; the first omitted
+// term is below 1e-30).
+struct CosSin {
+  double c, s;
+};
+constexpr double kPiD = 3.14159265358979323846264338327950288;
+constexpr double taylor_sin(double x) {
+  double t = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += t;
+  }
+  return sum;
+}
+constexpr double taylor_cos(double x) {
+  double t = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += t;
+  }
+  return sum;
+}
+constexpr CosSin cis2pi(int m, int q) {
+  const int r = ((m % q) + q) % q;
+  const int o = (8 * r) / q, rem = 8 * r - o * q;  // angle = o pi/4 + pi rem / (4q)
+  const bool even = (o % 2) == 0;
+  const int k = even ? o / 2 : (o + 1) / 2;       // angle = k pi/2 + th
+  const double psi = even ? kPiD * rem / (4.0 * q) : kPiD * (q - rem) / (4.0 * q);
+  const double c0 = taylor_cos(psi), s0 = even ? taylor_sin(psi) : -taylor_sin(psi);
+  switch (k & 3) {
+    case 0: return {c0, s0};
+    case 1: return {-s0, c0};
+    case 2: return {-c0, -s0};
+    default: return {s0, -c0};
+  }
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [I0, I1)
+template <int I, int I1> struct SFor {
+  template <class F>
+  static __device__ __forceinline__ void run(F&& f) {
+    f(std::integral_constant<int, I>{});
+    SFor<I + 1, I1>::run(f);
+  }
+};
+template <int I1> struct SFor<I1, I1> {
+  template <class F>
+  static __device__ __forceinline__ void run(F&&) {}
+};
+
+// Length A*B by Cooley-Tukey: DFT-B over s2 of x[s1 + A s2] for each s1,
+// twiddle exp(SIGN 2 pi i s1 k1 / (A B)), DFT-A over s1 for each k1; output
+// X[k1 + B k2] in natural order.
+template <typename R, int A, int B, int SIGN> struct BflyCT {
+  static __device__ __forceinline__ void run(c2<R>* v) {
+    c2<R> y[A][B];
+#pragma unroll
+    for (int s1 = 0; s1 < A; ++s1) {
+#pragma unroll
+      for (int s2 = 0; s2 < B; ++s2) y[s1][s2] = v[s1 + A * s2];
+      Bfly<R, B, SIGN>::run(y[s1]);
+    }
+    SFor<1, A>::run([&](auto i1) {
+      constexpr int s1 = decltype(i1)::value;
+      SFor<1, B>::run([&](auto j1) {
+        constexpr int k1 = decltype(j1)::value;
+        constexpr CosSin w = cis2pi(s1 * k1, A * B);
+        y[s1][k1] = crot<R, SIGN>(y[s1][k1], (R)w.c, (R)w.s);
+      });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < B; ++k1) {
+      c2<R> z[A];
+#pragma unroll
+      for (int s1 = 0; s1 < A; ++s1) z[s1] = y[s1][k1];
+      Bfly<R, A, SIGN>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < A; ++k2) v[k1 + B * k2] = z[k2];
+    }
+  }
+};
+
+template <typename R, int SIGN> struct Bfly<R, 12, SIGN> : BflyCT<R, 4, 3, SIGN> {};
+template <typename R, int SIGN> struct Bfly<R, 20, SIGN> : BflyCT<R, 4, 5, SIGN> {};
+template <typename R, int SIGN> struct Bfly<R, 24, SIGN> : BflyCT<R, 8, 3, SIGN> {};
+template <typename R, int SIGN> struct Bfly<R, 32, SIGN> : BflyCT<R, 8, 4, SIGN> {};
 
 template <typename R, int SIGN> struct Bfly<R, 3, SIGN> {
   static __device__ __forceinline__ void run(c2<R>* v) {

@@ -160,7 +160,7 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
   const size_t ncos = 4 * (size_t)n;
   // four-step twiddles of the register-resident transforms: P x Q complex
   const bool fast = s.fft && fast_len(n);
-  const int fP = m >= 256 ? 16 : (m >= 64 ? 8 : 4), fQ = m / fP;
+  const int fP = fast ? fast_threads_per_line(n) : 1, fQ = m / fP;
   const size_t off4 = (ntw + 2 * npost + ncos + 3) / 4 * 4;  // 16-byte aligned
   const size_t n4 = fast ? 2 * (size_t)m : 0;
   std::vector<R> buf(off4 + n4);

@@ -1,4 +1,5 @@
-// Register-resident cosine transforms for line lengths n = 32, 64, ..., 512.
+// Register-resident cosine transforms for the line lengths n whose half m = n/2
+// splits as below (n = 32, 64, 96, 128, 160, 192, 256, 384, 512, 1024).
 //
 // Same transforms as the generic kernels (Eq. (forward DCT) and Eq. (backward
 // DCT), Sec. 3.2), reached through the same half-length complex FFT with the
@@ -15,6 +16,8 @@
 // warps per column tile, loading and storing global memory directly with the
 // lanes over adjacent columns.  Axis-0 passes (rows) stage the row through
 // shared memory so that the FP64 PCG vectors stay coalesced.
+#pragma once
+
 #include <type_traits>
 
 #include "dct_device.cuh"
@@ -23,8 +26,19 @@
 
 namespace etc {
 
-// threads per line for FFT length m
-constexpr int fast_p(int m) { return m >= 256 ? 16 : (m >= 64 ? 8 : 4); }
+// Four-step split m = P * Q: P threads per line (16, 8 or 4, the largest that
+// works), Q values per thread with P | Q, Q a length with a register DFT
+// (4, 8, 16 by radix 4; 12, 20, 24, 32 by Cooley-Tukey over 3, 4, 5, 8);
+// 0 if m has no such split.
+constexpr bool fast_q_ok(int q) {
+  return q == 4 || q == 8 || q == 12 || q == 16 || q == 20 || q == 24 || q == 32;
+}
+constexpr int fast_p(int m) {
+  return (m % 16 == 0 && m / 16 >= 16 && (m / 16) % 16 == 0 && fast_q_ok(m / 16)) ? 16
+         : (m % 8 == 0 && m / 8 >= 8 && (m / 8) % 8 == 0 && fast_q_ok(m / 8))    ? 8
+         : (m % 4 == 0 && m / 4 >= 4 && (m / 4) % 4 == 0 && fast_q_ok(m / 4))    ? 4
+                                                                                  : 0;
+}
 
 template <int N> struct Fast {
   static constexpr int M = N / 2;
@@ -49,13 +63,15 @@ template <int N, int NT> struct FastX {
 template <typename R> struct FastCols {  // columns per block of the axis-1 passes
   static constexpr int C = sizeof(R) == 4 ? 32 : 16;
   // resident blocks per SM asked of the compiler: 1024 (FP32) or 512 (FP64)
-  // threads, i.e. at most 64 or 128 registers per thread
+  // threads, i.e. at most 64 or 128 registers per thread; half that for
+  // Q > 16 values per thread
   static constexpr int MinBlocks(int n) {
-    return (sizeof(R) == 4 ? 1024 : 512) / (C * fast_p(n / 2));
+    return ((sizeof(R) == 4 ? 1024 : 512) >> ((n / 2) / fast_p(n / 2) > 16 ? 1 : 0)) /
+           (C * fast_p(n / 2));
   }
 };
 
-bool fast_len(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
@@ -195,7 +211,7 @@ __global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinB
       for (int k2 = 0; k2 < P; ++k2) {
         const int k = tau + P * e + Q * k2;
         R xa, xb;
-        untangle<R>(u[e * P + k2], sm[((M - k) & (M - 1)) * C + c], tb.fpost, k, M, xa, xb);
+        untangle<R>(u[e * P + k2], sm[(k ? M - k : 0) * C + c], tb.fpost, k, M, xa, xb);
         if (ok) {
           col[k * n0] = xa;
           col[(k ? N - k : M) * n0] = xb;
@@ -326,7 +342,7 @@ __global__ void __launch_bounds__(NT)
     for (int k2 = 0; k2 < P; ++k2) {
       const int k = tau + P * e + Q * k2;
       R xa, xb;
-      untangle<R>(u[e * P + k2], A[l * SA + ((M - k) & (M - 1))], tb.fpost, k, M, xa, xb);
+      untangle<R>(u[e * P + k2], A[l * SA + (k ? M - k : 0)], tb.fpost, k, M, xa, xb);
       if (row < nrows) {
         t[row * N + k] = xa;
         t[row * N + (k ? N - k : M)] = xb;
@@ -444,8 +460,9 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
-// ---------------------------------------------------------------- launchers
-namespace {
+// ---------------------------------------------------------------- per-size launchers
+// Defined here, instantiated per length in fast_sizes_*.cu (several translation
+// units, so that the library builds in parallel), called by fast_dispatch.cu.
 
 template <typename R, int N, int NT>
 size_t fast_x_smem() {
@@ -456,7 +473,12 @@ size_t fast_y_smem() {
   return (size_t)FastCols<R>::C * Fast<N>::M * sizeof(c2<R>);
 }
 
-inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+constexpr size_t kFastSmemMax = 200 * 1024;  // dynamic shared memory opt-in per block
+template <typename R, int N, int NT>
+constexpr bool fast_x_fits() {
+  return (size_t)FastX<N, NT>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>) <= kFastSmemMax;
+}
 
 template <typename R, int N, typename V, int NT>
 cudaError_t fwd_x_nt(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* x, const V* w,
@@ -481,7 +503,7 @@ template <typename R, int N, typename V>
 cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* x, const V* w,
                     const V* q, V* r, const double* rin, R* t, double* partials, int par,
                     double rtol2, int mode, cudaStream_t s, int nt) {
-  if (nt == 128)
+  if (nt == 128 || !fast_x_fits<R, N, 256>())
     return fwd_x_nt<R, N, V, 128>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
   return fwd_x_nt<R, N, V, 256>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
 }
@@ -504,7 +526,7 @@ template <typename R, typename TZ, int N>
 cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
                     const double* kd, double kz_host, int check, int mode, cudaStream_t s,
                     TZ* x, int par, int nt) {
-  if (nt == 128)
+  if (nt == 128 || !fast_x_fits<R, N, 256>())
     return inv_x_nt<R, TZ, N, 128>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
   return inv_x_nt<R, TZ, N, 256>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
 }
@@ -525,6 +547,7 @@ cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R
 template <typename R, int N, int NT>
 cudaError_t attrs_nt() {
   cudaError_t e = cudaSuccess;
+  if (!fast_x_fits<R, N, NT>()) return e;  // never launched
   const int sx = (int)fast_x_smem<R, N, NT>();
 #define SETF(fn, b) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
@@ -555,129 +578,41 @@ cudaError_t attrs_n() {
   return e;
 }
 
-}  // namespace
 
-template <typename R>
-bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void* b,
-               const void* c, const void* d) {
-  return p.t.tw4 != nullptr && fast_len(g.n0) && p.s.n == g.n0 && aligned16(a) &&
-         aligned16(b) && aligned16(c) && aligned16(d);
-}
-template bool fast_x_ok<double>(const Geometry&, const DctPlan<double>&, const void*,
-                                const void*, const void*, const void*);
-template bool fast_x_ok<float>(const Geometry&, const DctPlan<float>&, const void*, const void*,
-                               const void*, const void*);
+// The lengths with register-resident transforms, and the per-length launchers
+// each of them instantiates (PREFIX: "template" in fast_sizes_*.cu, "extern
+// template" where they are only called).
+#define ETC_FAST_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(1024)
 
-template <typename R>
-bool fast_y_ok(const Geometry& g, const DctPlan<R>& p) {
-  return p.t.tw4 != nullptr && fast_len(g.n1) && p.s.n == g.n1;
-}
-template bool fast_y_ok<double>(const Geometry&, const DctPlan<double>&);
-template bool fast_y_ok<float>(const Geometry&, const DctPlan<float>&);
-
-template <typename R, typename V>
-cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x,
-                              const V* w, const V* q, V* r, const double* rin, R* t,
-                              double* partials, int par, double rtol2, int mode,
-                              cudaStream_t s, int nt) {
-  switch (g.n0) {
-    case 32:
-      return fwd_x_n<R, 32, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
-                               mode, s, nt);
-    case 64:
-      return fwd_x_n<R, 64, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
-                               mode, s, nt);
-    case 128:
-      return fwd_x_n<R, 128, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
-                                mode, s, nt);
-    case 256:
-      return fwd_x_n<R, 256, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
-                                mode, s, nt);
-    case 512:
-      return fwd_x_n<R, 512, V>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2,
-                                mode, s, nt);
-    default: return cudaErrorInvalidValue;
-  }
-}
-template cudaError_t launch_fast_fwd_x<double, double>(const Geometry&, const DctPlan<double>&,
-                                                       PcgState*, double*, const double*,
-                                                       const double*, double*, const double*,
-                                                       double*, double*, int, double, int,
-                                                       cudaStream_t, int);
-template cudaError_t launch_fast_fwd_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                      PcgState*, double*, const double*,
-                                                      const double*, double*, const double*,
-                                                      float*, double*, int, double, int,
-                                                      cudaStream_t, int);
-template cudaError_t launch_fast_fwd_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                      PcgState*, float2*, const float2*,
-                                                      const float2*, float2*, const double*,
-                                                      float*, double*, int, double, int,
-                                                      cudaStream_t, int);
-
-template <typename R, typename TZ>
-cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
-                              TZ* z, const double* kd, double kz_host, int check, int mode,
-                              cudaStream_t s, TZ* x, int par, int nt) {
-  switch (g.n0) {
-    case 32:
-      return inv_x_n<R, TZ, 32>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
-                                par, nt);
-    case 64:
-      return inv_x_n<R, TZ, 64>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
-                                par, nt);
-    case 128:
-      return inv_x_n<R, TZ, 128>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
-                                 par, nt);
-    case 256:
-      return inv_x_n<R, TZ, 256>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
-                                 par, nt);
-    case 512:
-      return inv_x_n<R, TZ, 512>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x,
-                                 par, nt);
-    default: return cudaErrorInvalidValue;
-  }
-}
-template cudaError_t launch_fast_inv_x<double, double>(const Geometry&, const DctPlan<double>&,
-                                                       PcgState*, const double*, double*,
-                                                       const double*, double, int, int,
-                                                       cudaStream_t, double*, int, int);
-template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const DctPlan<float>&,
-                                                      PcgState*, const float*, double*,
-                                                      const double*, double, int, int,
-                                                      cudaStream_t, double*, int, int);
-template cudaError_t launch_fast_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                      PcgState*, const float*, float2*,
-                                                      const double*, double, int, int,
-                                                      cudaStream_t, float2*, int, int);
-
-template <typename R>
-cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
-                          int inverse, int check, cudaStream_t s) {
-  switch (g.n1) {
-    case 32: return y_n<R, 32>(g, p.t, st, t, inverse, check, s);
-    case 64: return y_n<R, 64>(g, p.t, st, t, inverse, check, s);
-    case 128: return y_n<R, 128>(g, p.t, st, t, inverse, check, s);
-    case 256: return y_n<R, 256>(g, p.t, st, t, inverse, check, s);
-    case 512: return y_n<R, 512>(g, p.t, st, t, inverse, check, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-template cudaError_t launch_fast_y<double>(const Geometry&, const DctPlan<double>&,
-                                           const PcgState*, double*, int, int, cudaStream_t);
-template cudaError_t launch_fast_y<float>(const Geometry&, const DctPlan<float>&,
-                                          const PcgState*, float*, int, int, cudaStream_t);
-
-template <typename R>
-cudaError_t set_fast_attrs() {
-  cudaError_t e = attrs_n<R, 32>();
-  if (e == cudaSuccess) e = attrs_n<R, 64>();
-  if (e == cudaSuccess) e = attrs_n<R, 128>();
-  if (e == cudaSuccess) e = attrs_n<R, 256>();
-  if (e == cudaSuccess) e = attrs_n<R, 512>();
-  return e;
-}
-template cudaError_t set_fast_attrs<double>();
-template cudaError_t set_fast_attrs<float>();
+#define ETC_FAST_LAUNCHERS(PREFIX, N)                                                        \
+  PREFIX cudaError_t fwd_x_n<double, N, double>(                                             \
+      const Geometry&, const DctTables<double>&, PcgState*, double*, const double*,          \
+      const double*, double*, const double*, double*, double*, int, double, int, cudaStream_t, \
+      int);                                                                                  \
+  PREFIX cudaError_t fwd_x_n<float, N, double>(                                              \
+      const Geometry&, const DctTables<float>&, PcgState*, double*, const double*,           \
+      const double*, double*, const double*, float*, double*, int, double, int, cudaStream_t, \
+      int);                                                                                  \
+  PREFIX cudaError_t fwd_x_n<float, N, float2>(                                              \
+      const Geometry&, const DctTables<float>&, PcgState*, float2*, const float2*,           \
+      const float2*, float2*, const double*, float*, double*, int, double, int, cudaStream_t, \
+      int);                                                                                  \
+  PREFIX cudaError_t inv_x_n<double, double, N>(                                             \
+      const Geometry&, const DctTables<double>&, PcgState*, const double*, double*,          \
+      const double*, double, int, int, cudaStream_t, double*, int, int);                     \
+  PREFIX cudaError_t inv_x_n<float, double, N>(                                              \
+      const Geometry&, const DctTables<float>&, PcgState*, const float*, double*,            \
+      const double*, double, int, int, cudaStream_t, double*, int, int);                     \
+  PREFIX cudaError_t inv_x_n<float, float2, N>(                                              \
+      const Geometry&, const DctTables<float>&, PcgState*, const float*, float2*,            \
+      const double*, double, int, int, cudaStream_t, float2*, int, int);                     \
+  PREFIX cudaError_t y_n<double, N>(const Geometry&, const DctTables<double>&, const PcgState*, \
+                                    double*, int, int, cudaStream_t);                        \
+  PREFIX cudaError_t y_n<float, N>(const Geometry&, const DctTables<float>&, const PcgState*, \
+                                   float*, int, int, cudaStream_t);                          \
+  PREFIX cudaError_t attrs_n<double, N>();                                                   \
+  PREFIX cudaError_t attrs_n<float, N>();
+#define ETC_FAST_EXTERN(N) ETC_FAST_LAUNCHERS(extern template, N)
+#define ETC_FAST_INSTANTIATE(N) ETC_FAST_LAUNCHERS(template, N)
 
 }  // namespace etc

@@ -87,6 +87,7 @@ cudaError_t set_smem_attrs();
 // when fast_*_ok holds and the tile argument is 0 (default) or negative:
 // axis 0, -1 = blocks of 256 threads, -2 = blocks of 128; axis 1, -1.
 bool fast_len(int n);
+int fast_threads_per_line(int n);  // P of the split n/2 = P * Q
 template <typename R>
 bool fast_x_ok(const Geometry& g, const DctPlan<R>& p, const void* a, const void* b,
                const void* c, const void* d);

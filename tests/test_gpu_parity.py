@@ -61,7 +61,8 @@ def test_operator_matches_oracle(shape, direction):
     assert relmax(host(q), O.apply_operator(f, w)) < 1e-12
 
 
-@pytest.mark.parametrize("shape", SHAPES + [(8, 64, 96), (4, 160, 192), (3, 200, 50)])
+@pytest.mark.parametrize("shape", SHAPES + [(8, 64, 96), (4, 160, 192), (3, 200, 50),
+                                   (2, 1024, 32), (2, 96, 384)])
 def test_dct_planes_match_oracle(shape):
     rng = np.random.default_rng(sum(shape))
     k = rng.uniform(1.0, 2.0, shape)
@@ -99,6 +100,26 @@ def test_preconditioner_matches_oracle(shape, direction):
     # FP32 transforms and solves (mixed path)
     B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_MIXED, dev(r), z)
     assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 2e-5
+
+
+@pytest.mark.parametrize("shape", [(4, 96, 160), (3, 192, 384), (2, 32, 1024), (2, 1024, 64),
+                                   (5, 64, 96)])
+def test_preconditioner_register_resident_lengths(shape):
+    # every line length of the register-resident transforms beyond the powers
+    # of two (96, 160, 192, 384 and 1024 on both transform axes), FP64 and FP32
+    rng = np.random.default_rng(3 * sum(shape))
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
+    rve.set_reference(2, B.ETC_REF_USER, ku)
+    _, fshape = oracle_faces(kx, ky, kz, (1.0, 1.0, 1.0), 2)
+    r = rng.standard_normal(fshape)
+    zo = O.apply_reference_inverse(r, ku)
+    z = torch.empty(fshape, dtype=torch.float64, device="cuda")
+    B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_FP64, dev(r), z)
+    assert relmax(host(z), zo) < 1e-11
+    B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_MIXED, dev(r), z)
+    assert relmax(host(z), zo) < 2e-5
 
 
 @pytest.mark.parametrize("shape", [(129, 5, 7), (200, 6, 10), (600, 4, 6), (1030, 3, 4)])
