@@ -96,17 +96,18 @@ def kernel_model(n0, n1, mixed=False):
     round trip between the sweeps is not counted); inv_x: the axis-0 inverse and
     w = z + beta w.  Mixed: the transforms run in FP32 (their flops are not FP64
     work), the tridiagonal kernel also writes this and reads last iteration's
-    transformed residual (flexible beta), the matvec reads double-float w, faces
-    and diagonal (same bytes) and does its arithmetic on the FP32 pipe (one FP64
-    add per DOF remains), and inv_x also writes the double-float copy of w.
+    transformed residual (flexible beta).  Its x, r, w and q are double-float
+    pairs (same bytes as FP64) updated on the FP32 pipe; the matvec reads
+    double-float faces and diagonal; x += alpha w moves from fwd_x (r, q in, r
+    and the FP32 transform out) to inv_x (t, w and x in, w and x out).
     """
     fx, fy = dct_flops_per_point(n0, False), dct_flops_per_point(n1, False)
     ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
     if not mixed:
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
                 "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
-    return {"matvec": (1.0, 48.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
-            "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 28.0)}
+    return {"matvec": (0.0, 48.0), "fwd_x": (0.0, 28.0), "fwd_y": (0.0, 8.0),
+            "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (0.0, 36.0)}
 
 
 # ------------------------------------------------------------------ helpers
