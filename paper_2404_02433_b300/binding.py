@@ -321,12 +321,12 @@ class RVE:
         return out
 
     def gradient(self, direction, p_in=1.0, p_out=0.0, rtol=1e-10, maxit=5000,
-                 per_component=False):
+                 per_component=False, precision=ETC_PREC_FP64):
         """(d kappa_eff / d log kappa as a CUDA tensor, kappa_eff, infos)."""
         import torch
         shape = ((3,) if per_component else ()) + self.shape
         out = torch.empty(shape, dtype=torch.float64, device="cuda")
-        opts = make_opts(rtol, maxit, ETC_PREC_FP64, 1)
+        opts = make_opts(rtol, maxit, precision, 1)
         k, infos = etc_gradient(self.h, direction, out, p_in, p_out, opts, int(per_component))
         return out, k, [i.as_dict() for i in infos]
 

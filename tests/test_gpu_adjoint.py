@@ -36,6 +36,18 @@ def test_gradient_matches_oracle_adjoint(direction):
     assert np.abs(Gs.cpu().numpy() - G_o.sum(axis=0)).max() <= 1e-8 * np.abs(G_o).max()
 
 
+def test_gradient_mixed_precision_matches_fp64():
+    # both solves (state and adjoint) through the double-float vectors
+    k = M.lognormal_field((32, 40, 24), 8.0, 1.0, 5004)
+    rve = B.RVE(dev(k))
+    G64, kap64, _ = rve.gradient(2, rtol=1e-10)
+    Gm, kapm, infos = rve.gradient(2, rtol=1e-10, precision=B.ETC_PREC_MIXED)
+    G64, Gm = G64.cpu().numpy(), Gm.cpu().numpy()
+    assert kapm == pytest.approx(kap64, rel=1e-8)
+    assert np.abs(Gm - G64).max() <= 1e-6 * np.abs(G64).max()
+    assert all(i["status"] == B.ETC_OK and i["true_relres"] < 1e-9 for i in infos)
+
+
 def test_gradient_central_differences():
     k = M.lognormal_field((16, 16, 16), 8.0, 1.0, 5002)
     rve = B.RVE(dev(k))

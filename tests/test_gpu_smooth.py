@@ -30,10 +30,10 @@ def table2():
     return rows
 
 
-def gpu_smooth(n, rtol):
+def gpu_smooth(n, rtol, precision=B.ETC_PREC_FP64):
     kx, ky, kz, pin, pout, src, exact = M.smooth_problem(n)
     rve = B.RVE(dev(kx), dev(ky), dev(kz))
-    info = rve.solve_general(2, dev(pin), dev(pout), dev(src), rtol=rtol)
+    info = rve.solve_general(2, dev(pin), dev(pout), dev(src), rtol=rtol, precision=precision)
     p = rve.solution(2).cpu().numpy()
     rve.close()
     return p, exact, info
@@ -56,6 +56,19 @@ def test_table2_on_gpu(n, rtol):
     l2 = np.sqrt(((p - exact) ** 2).sum() / n ** 3)
     assert abs(l2 - err) / err < 0.01
     assert abs(info["iters"] - iters) <= 1
+
+
+@pytest.mark.parametrize("n", [64, 96])
+def test_table2_mixed_precision(n):
+    # general face data and source through the mixed path (FP32 preconditioner,
+    # double-float vectors): the L2 error of Table 2's converged rows
+    kx, ky, kz, pin, pout, src, exact = M.smooth_problem(n)
+    p64, _, i64 = gpu_smooth(n, 1e-10)
+    pm, _, im = gpu_smooth(n, 1e-10, precision=B.ETC_PREC_MIXED)
+    assert np.abs(pm - p64).max() <= 1e-7 * np.abs(p64).max()
+    assert im["true_relres"] < 2e-10
+    l2 = lambda p: np.sqrt(((p - exact) ** 2).sum() / n ** 3)
+    assert abs(l2(pm) - l2(p64)) <= 1e-3 * l2(p64)
 
 
 def test_general_data_in_x_direction_matches_oracle():
