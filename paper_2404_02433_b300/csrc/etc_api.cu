@@ -338,12 +338,9 @@ etc_status launch_setup(etc_rve* h, int dir) {
   CK(launch_faces(g, 1.0 / (hh[0] * hh[0]), 1.0 / (hh[1] * hh[1]), 1.0 / (hh[2] * hh[2]), comp[0],
                   comp[1], comp[2], h->T0, h->T1, h->T2, h->D, h->Bin, h->Bout, h->partials,
                   h->st, h->stream));
-  // double-float copies (with the zero padding plane) for the mixed-precision matvec
-  const long long nt = h->n + h->plane_max + 64;
-  CK(launch_split_df(h->T0, h->Tdf[0], nt, h->stream));
-  CK(launch_split_df(h->T1, h->Tdf[1], nt, h->stream));
-  CK(launch_split_df(h->T2, h->Tdf[2], nt, h->stream));
-  CK(launch_split_df(h->D, h->Ddf, h->n, h->stream));
+  // the diagonal, and the double-float copies for the mixed-precision matvec
+  CK(launch_diag_split(g, h->T0, h->T1, h->T2, h->Bin, h->Bout, h->D, h->Tdf[0], h->Tdf[1],
+                       h->Tdf[2], h->Ddf, h->stream));
   return ETC_OK;
 }
 
@@ -921,6 +918,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
     const Geometry g = geom_of(h, d);
     np = std::max<size_t>(np, matvec_blocks(g));
     np = std::max<size_t>(np, matvec_df_blocks(g));
+    np = std::max<size_t>(np, faces_blocks(g));
     np = std::max<size_t>(np, fwd_x_blocks(g, 4));
     np = std::max<size_t>(np, fwd_x_blocks(g, 8));
     np = std::max<size_t>(np, tridiag_blocks(g));

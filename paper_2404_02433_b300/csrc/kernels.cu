@@ -118,24 +118,24 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
   __shared__ int flag;
   double ext[10];
   for (int e = 0; e < 10; e += 2) { ext[e] = INFINITY; ext[e + 1] = -INFINITY; }
-  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % g.n0);
-    const long long rem = c / g.n0;
-    const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
+  // threads stride over the cells of a plane and blocks over the planes
+  // (k = blockIdx.y + m gridDim.y): the three "minus" faces of each cell (each
+  // face once; the diagonal follows in k_diag_split from the neighbours' faces)
+  for (long long sidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; sidx < g.plane;
+       sidx += (long long)gridDim.x * blockDim.x)
+  for (int k = blockIdx.y; k < g.n2; k += gridDim.y) {
+    const int j = (int)(sidx / g.n0), i = (int)(sidx - (long long)j * g.n0);
+    const long long c = (long long)k * g.plane + sidx;
     const double s0 = k0[c] * ih0, s1 = k1[c] * ih1, s2 = k2[c] * ih2;
     const double t0 = (i > 0) ? harmonic(k0[c - 1] * ih0, s0) : 0.0;
     const double t1 = (j > 0) ? harmonic(k1[c - g.n0] * ih1, s1) : 0.0;
     const double t2 = (k > 0) ? harmonic(k2[c - g.plane] * ih2, s2) : 0.0;
-    const double p0 = (i < g.n0 - 1) ? harmonic(s0, k0[c + 1] * ih0) : 0.0;
-    const double p1 = (j < g.n1 - 1) ? harmonic(s1, k1[c + g.n0] * ih1) : 0.0;
-    const double p2 = (k < g.n2 - 1) ? harmonic(s2, k2[c + g.plane] * ih2) : 0.0;
-    double d = t0 + p0 + t1 + p1 + t2 + p2;
-    if (k == 0) { d += 2.0 * s2; Bin[c] = 2.0 * s2; ext[6] = fmin(ext[6], s2); ext[7] = fmax(ext[7], s2); }
+    if (k == 0) { Bin[sidx] = 2.0 * s2; ext[6] = fmin(ext[6], s2); ext[7] = fmax(ext[7], s2); }
     if (k == g.n2 - 1) {
-      d += 2.0 * s2; Bout[c - (long long)k * g.plane] = 2.0 * s2;
+      Bout[sidx] = 2.0 * s2;
       ext[8] = fmin(ext[8], s2); ext[9] = fmax(ext[9], s2);
     }
-    T0[c] = t0; T1[c] = t1; T2[c] = t2; D[c] = d;
+    T0[c] = t0; T1[c] = t1; T2[c] = t2;
     if (i > 0) { ext[0] = fmin(ext[0], t0); ext[1] = fmax(ext[1], t0); }
     if (j > 0) { ext[2] = fmin(ext[2], t1); ext[3] = fmax(ext[3], t1); }
     if (k > 0) { ext[4] = fmin(ext[4], t2); ext[5] = fmax(ext[5], t2); }
@@ -432,6 +432,34 @@ __global__ void k_finish_x(Geometry g, const PcgState* st, V* x, const V* w) {
     if (pend) v = vaxpy(alpha, w[c], v);
     store_f64(reinterpret_cast<double*>(x) + c, v);
   }
+}
+
+// The diagonal of A (Eq. scaled bilinear forms): the six faces of each cell
+// (the minus faces at c, the plus faces as the minus faces of the neighbours;
+// zero on Neumann faces and in the extra plane) plus the Dirichlet terms, then
+// the double-float copies of T0, T1, T2 and D for the mixed-precision matvec.
+// Grid: blockIdx.y = plane k (n2 planes and the extra zero plane).
+__global__ void k_diag_split(Geometry g, const double* __restrict__ T0,
+                             const double* __restrict__ T1, const double* __restrict__ T2,
+                             const double* __restrict__ Bin, const double* __restrict__ Bout,
+                             double* __restrict__ D, float2* __restrict__ F0,
+                             float2* __restrict__ F1, float2* __restrict__ F2,
+                             float2* __restrict__ FD) {
+  const int k = blockIdx.y;
+  const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sidx >= g.plane) return;
+  const long long c = (long long)k * g.plane + sidx;
+  F0[c] = split_df(T0[c]);
+  F1[c] = split_df(T1[c]);
+  F2[c] = split_df(T2[c]);
+  if (k == g.n2) return;  // the extra plane has faces only
+  const double t0 = T0[c], t1 = T1[c], t2 = T2[c];
+  const double p0 = T0[c + 1], p1 = T1[c + g.n0], p2 = T2[c + g.plane];
+  double d = t0 + p0 + t1 + p1 + t2 + p2;
+  if (k == 0) d += Bin[sidx];
+  if (k == g.n2 - 1) d += Bout[sidx];
+  D[c] = d;
+  FD[c] = split_df(d);
 }
 
 // Double-float copies of FP64 arrays (split_df per element).
@@ -936,12 +964,37 @@ cudaError_t launch_permute(const double* in, double* out, int d0, int d1, int d2
   return cudaGetLastError();
 }
 
+// planes x row blocks of the face assembly, capped near 8 blocks per SM so that
+// the last block's extrema reduction stays short
+static dim3 faces_grid(const Geometry& g) {
+  long long bx = (g.plane + 255) / 256;
+  if (bx > 148 * 8) bx = 148 * 8;
+  long long by = (148 * 8) / bx;
+  if (by < 1) by = 1;
+  if (by > g.n2) by = g.n2;
+  return dim3((unsigned int)bx, (unsigned int)by);
+}
+
 cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, const double* k0,
                          const double* k1, const double* k2, double* T0, double* T1, double* T2,
                          double* D, double* Bin, double* Bout, double* partials, PcgState* st,
                          cudaStream_t s) {
-  k_faces<<<grid_for(g.n, 256, 148 * 8), 256, 0, s>>>(g, ih0, ih1, ih2, k0, k1, k2, T0, T1, T2, D,
-                                                     Bin, Bout, partials, st);
+  k_faces<<<faces_grid(g), 256, 0, s>>>(g, ih0, ih1, ih2, k0, k1, k2, T0, T1, T2, D, Bin, Bout,
+                                        partials, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+unsigned int faces_blocks(const Geometry& g) {
+  const dim3 d = faces_grid(g);
+  return d.x * d.y;
+}
+
+cudaError_t launch_diag_split(const Geometry& g, const double* T0, const double* T1,
+                              const double* T2, const double* Bin, const double* Bout, double* D,
+                              float2* F0, float2* F1, float2* F2, float2* FD, cudaStream_t s) {
+  const dim3 grid((unsigned int)((g.plane + 255) / 256), (unsigned int)g.n2 + 1);
+  k_diag_split<<<grid, 256, 0, s>>>(g, T0, T1, T2, Bin, Bout, D, F0, F1, F2, FD);
   count_launch();
   return cudaGetLastError();
 }

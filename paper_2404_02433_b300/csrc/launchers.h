@@ -15,6 +15,12 @@ cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, 
                          const double* k1, const double* k2, double* T0, double* T1, double* T2,
                          double* D, double* Bin, double* Bout, double* partials, PcgState* st,
                          cudaStream_t s);
+// The diagonal D from the faces and Bin/Bout, and the double-float copies of
+// T0, T1, T2 (with the extra plane) and D.
+cudaError_t launch_diag_split(const Geometry& g, const double* T0, const double* T1,
+                              const double* T2, const double* Bin, const double* Bout, double* D,
+                              float2* F0, float2* F1, float2* F2, float2* FD, cudaStream_t s);
+unsigned int faces_blocks(const Geometry& g);
 // kref_dev (device, may be NULL) takes precedence over kref_host (host, 5 values).
 template <typename R>
 cudaError_t launch_pivots(const Geometry& g, const double* lam0, const double* lam1,
