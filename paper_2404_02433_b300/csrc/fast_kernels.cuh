@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(NT)
   double acc = 0.0;
   float accf = 0.f;
   constexpr int NP = L * M;  // element pairs of the block
-  constexpr int U = 2;
+  // pairs per thread whose loads are in flight together (2 or 4 vectors of 16 bytes each)
+  constexpr int U = std::is_same<V, float2>::value ? 4 : 2;
   static_assert(NP % (NT * U) == 0, "pair rounds");
   for (int p0 = threadIdx.x; p0 < NP; p0 += NT * U) {
     VPair<V> rv[U], qv[U], xv[U], wv[U];

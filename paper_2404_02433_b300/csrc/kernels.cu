@@ -160,14 +160,30 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
       }
   }
   if (publish_values(partials, 10, vals, 10, &st->cnt[kCntExt], &flag)) {
+    // min / max over the blocks' extrema: every thread a stride of blocks, then
+    // the warps and the block (min and max do not depend on the order)
+    double r[10];
+    for (int e = 0; e < 10; e += 2) { r[e] = INFINITY; r[e + 1] = -INFINITY; }
+    const unsigned int nb = nblocks();
+    for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x)
+      for (int e = 0; e < 10; e += 2) {
+        r[e] = fmin(r[e], __ldcg(partials + 10 * (size_t)b + e));
+        r[e + 1] = fmax(r[e + 1], __ldcg(partials + 10 * (size_t)b + e + 1));
+      }
+    for (int o = 16; o > 0; o >>= 1)
+      for (int e = 0; e < 10; e += 2) {
+        r[e] = fmin(r[e], __shfl_down_sync(0xffffffffu, r[e], o));
+        r[e + 1] = fmax(r[e + 1], __shfl_down_sync(0xffffffffu, r[e + 1], o));
+      }
+    __syncthreads();
+    if (lane == 0)
+      for (int e = 0; e < 10; ++e) we[wid][e] = r[e];
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double r[10];
-      for (int e = 0; e < 10; e += 2) { r[e] = INFINITY; r[e + 1] = -INFINITY; }
-      const unsigned int nb = nblocks();
-      for (unsigned int b = 0; b < nb; ++b)
+      for (int w = 1; w < nw; ++w)
         for (int e = 0; e < 10; e += 2) {
-          r[e] = fmin(r[e], __ldcg(partials + 10 * (size_t)b + e));
-          r[e + 1] = fmax(r[e + 1], __ldcg(partials + 10 * (size_t)b + e + 1));
+          r[e] = fmin(r[e], we[w][e]);
+          r[e + 1] = fmax(r[e + 1], we[w][e + 1]);
         }
       for (int e = 0; e < 10; ++e) st->ext[e] = r[e];
       // Algorithm 2, centred optimal point; a group without faces gets 1
