@@ -547,7 +547,7 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
   // mixed: x = 0 and w = 0 have the same bytes in both storages; r = b is split
   CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
                  reinterpret_cast<double*>(h->wdf), h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
-  CK(launch_df_inplace(h->r, h->n, 1, h->stream));
+  CK(launch_split_inplace(h->r, h->n, h->stream));
   CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, nullptr, df(h->r),
                                   nullptr, h->t32, h->partials, 0, rtol2, 0, h->stream,
                                   h->tiles[0])));

@@ -421,18 +421,13 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
   }
 }
 
-// In place between FP64 and double-float storage (8 bytes either way): the
-// mixed path's residual after the initial rhs, and its solution at the end.
+// FP64 to double-float storage in place (8 bytes either way): the mixed
+// path's residual after the initial right-hand side.  (The solution returns
+// to FP64 in k_finish_x.)
 __global__ void k_f64_to_df_inplace(double* a, long long n) {
   for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
     const float2 v = split_df(a[c]);
     reinterpret_cast<float2*>(a)[c] = v;
-  }
-}
-__global__ void k_df_to_f64_inplace(double* a, long long n) {
-  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) {
-    const float2 v = reinterpret_cast<const float2*>(a)[c];
-    a[c] = widen(v.x) + widen(v.y);
   }
 }
 
@@ -1101,9 +1096,8 @@ cudaError_t launch_finish_x(const Geometry& g, const PcgState* st, double* x, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s) {
-  if (to_df) k_f64_to_df_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
-  else k_df_to_f64_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+cudaError_t launch_split_inplace(double* a, long long n, cudaStream_t s) {
+  k_f64_to_df_inplace<<<grid_for(n, 256), 256, 0, s>>>(a, n);
   count_launch();
   return cudaGetLastError();
 }

@@ -42,8 +42,8 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, f
                              const float2* D, double* partials, int par, int mode,
                              cudaStream_t s);
 cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
-// FP64 <-> double-float storage in place (to_df = 1: split; 0: hi + lo in FP64).
-cudaError_t launch_df_inplace(double* a, long long n, int to_df, cudaStream_t s);
+// FP64 values to double-float pairs in place.
+cudaError_t launch_split_inplace(double* a, long long n, cudaStream_t s);
 // V: storage of x, w, q, r (double, or float2 double-float pairs with
 // R = float); x += alpha w happens here for FP64 storage only (mode 1);
 // rin (mode 2) is FP64.
