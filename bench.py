@@ -88,7 +88,7 @@ def dct_flops_per_point(n, inverse):
     return fft / 2.0 + (9.0 if inverse else 8.0)
 
 
-def kernel_model(n0, n1, mixed=False):
+def kernel_model(n0, n1, mixed=False, f64_vectors=False):
     """(FP64 flops, algorithmic bytes) per DOF of each kernel of one PCG iteration.
 
     matvec: q = D w - sum T w_nb and w.q; fwd_x: x += alpha w, r -= alpha q,
@@ -103,6 +103,9 @@ def kernel_model(n0, n1, mixed=False):
     """
     fx, fy = dct_flops_per_point(n0, False), dct_flops_per_point(n1, False)
     ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
+    if mixed and f64_vectors:  # FP32 Algorithm 3 between FP64 vectors and operator
+        return {"matvec": (15.0, 48.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
+                "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 20.0)}
     if not mixed:
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
                 "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
@@ -195,9 +198,10 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, mixed):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    kernel sources are unchanged since that capture; else None."""
+def recorded_traffic(kernel, label):
+    """Per-launch DRAM bytes of `kernel` of the path `label` (fp64, mixed,
+    mixed_f64) from the committed ncu summary, if the kernel sources are
+    unchanged since that capture; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic_512.txt")
     try:
         lines = open(path).read().splitlines()
@@ -206,7 +210,7 @@ def recorded_traffic(kernel, mixed):
     meta = dict(l.split(":", 1) for l in lines if ":" in l and not l.startswith("#"))
     if meta.get("source_hash", "").strip() != src_hash():
         return None
-    key = ("mixed_" if mixed else "fp64_") + kernel
+    key = label + "_" + kernel
     try:
         return float(meta[key].split()[0])
     except (KeyError, ValueError, IndexError):
@@ -359,16 +363,23 @@ def run_ours(args, rank, world, local_rank):
     value_m = sumr(float(n) ** 3 * itm) / tmaxm
     etc_err = max(abs(a - b) / abs(b) for K1, K2 in zip(Km, K64) for a, b in
                   ((K1[3 * d + d], K2[3 * d + d]) for d in range(3)))
+    # ---- mixed precision with FP64 vectors and operator
+    msf, _, itf, Kf, _, _ = timed(B.ETC_PREC_MIXED_F64, args.steps, 1)
+    tmaxf = maxr(msf / 1e3)
+    value_f = sumr(float(n) ** 3 * itf) / tmaxf
+    etc_err_f = max(abs(a - b) / abs(b) for K1, K2 in zip(Kf, K64) for a, b in
+                    ((K1[3 * d + d], K2[3 * d + d]) for d in range(3)))
 
     # ---- per-kernel timing of the dominant kernel (FP64 and mixed, load z, contrast 1000)
     hbm, hbm_src = peaks()
     prof = {}
-    for label, prec in (("fp64", B.ETC_PREC_FP64), ("mixed", B.ETC_PREC_MIXED)):
+    for label, prec in (("fp64", B.ETC_PREC_FP64), ("mixed", B.ETC_PREC_MIXED),
+                        ("mixed_f64", B.ETC_PREC_MIXED_F64)):
         ms = B.etc_profile_iteration(rves[-1].h, 2, prec, 4)
         prof[label] = dict(zip(KERNELS, ms))
 
     def roofline(label, mixed):
-        model = kernel_model(n, n, mixed)
+        model = kernel_model(n, n, mixed, label == "mixed_f64")
         ms = prof[label]
         k = max(ms, key=ms.get)
         flops, byts = model[k]
@@ -376,7 +387,7 @@ def run_ours(args, rank, world, local_rank):
         t_alu = flops * dof / (FP64_PEAK_TFLOPS * 1e12)
         t_hbm = byts * dof / (hbm * 1e9)
         sec = ms[k] / 1e3
-        traffic = recorded_traffic(k, mixed)
+        traffic = recorded_traffic(k, label)
         if t_alu >= t_hbm:
             ach = flops * dof / sec / 1e12
             return {"kernel": k, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
@@ -390,6 +401,7 @@ def run_ours(args, rank, world, local_rank):
 
     roof = roofline("fp64", False)
     roof_m = roofline("mixed", True)
+    roof_f = roofline("mixed_f64", True)
 
     # ---- end to end through the C ABI from pinned host memory
     pinned = [torch.from_numpy(k).pin_memory() for k in kap_host]
@@ -441,10 +453,18 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (1 GiB per vector)",
                    "parallelism": f"replicas x{world}"},
         "mixed": {"value": value_m, "unit": UNIT, "ms_per_step": msm / args.steps,
-                  "pcg_iters_per_step": itm / args.steps, "dtype": "f64 outer, f32 preconditioner",
+                  "pcg_iters_per_step": itm / args.steps,
+                  "dtype": "f32 preconditioner; double-float (f32 pairs) vectors and operator; "
+                           "f64 scalars",
                   "max_rel_diff_kappa_eff_vs_fp64": etc_err,
                   "time_to_solution_s_per_tensor": msm / args.steps / 2e3,
                   "roofline": roof_m, "kernel_ms": prof["mixed"]},
+        "mixed_f64": {"value": value_f, "unit": UNIT, "ms_per_step": msf / args.steps,
+                      "pcg_iters_per_step": itf / args.steps,
+                      "dtype": "f32 preconditioner; f64 vectors, operator and scalars",
+                      "max_rel_diff_kappa_eff_vs_fp64": etc_err_f,
+                      "time_to_solution_s_per_tensor": msf / args.steps / 2e3,
+                      "roofline": roof_f, "kernel_ms": prof["mixed_f64"]},
         "roofline": roof,
         "kernel_ms": prof["fp64"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

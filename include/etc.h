@@ -52,10 +52,13 @@ enum {
   ETC_ESTATE = 6       /* call out of order (e.g. solution of an unsolved dir) */
 };
 
-/* Arithmetic of the preconditioner apply. */
+/* Arithmetic of a solve.  The mixed forms run Algorithm 3 in FP32 inside a
+ * flexible (Polak-Ribiere) PCG; their scalars and reductions are FP64. */
 enum {
-  ETC_PREC_FP64 = 0,   /* everything in FP64: plain PCG (Algorithm 1) */
-  ETC_PREC_MIXED = 1   /* Algorithm 3 in FP32, the rest FP64, flexible PCG */
+  ETC_PREC_FP64 = 0,      /* everything in FP64: plain PCG (Algorithm 1) */
+  ETC_PREC_MIXED = 1,     /* x, r, w, q and the operator in double-float (pairs of
+                             FP32 values, 48-bit significand) on the FP32 pipe */
+  ETC_PREC_MIXED_F64 = 2  /* x, r, w, q and the operator in FP64 */
 };
 
 /* How the five reference parameters of Eq. (refer bilinear forms) are chosen. */
@@ -222,7 +225,8 @@ etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);
 etc_status etc_apply_operator(etc_rve* rve, int dir, const double* w, double* q);
 
 /* z = A_ref^{-1} r by Algorithm 3 with the kref that the next solve of dir uses;
- * precision = ETC_PREC_FP64 or ETC_PREC_MIXED (FP32 transforms and solves). */
+ * precision = ETC_PREC_FP64, or one of the mixed forms (FP32 transforms and
+ * solves). */
 etc_status etc_apply_preconditioner(etc_rve* rve, int dir, int precision, const double* r,
                                     double* z);
 

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libetc.so")
 
 ETC_OK, ETC_EINVAL, ETC_ENOMEM, ETC_ECUDA, ETC_ENOCONV, ETC_EBREAKDOWN, ETC_ESTATE = range(7)
-ETC_PREC_FP64, ETC_PREC_MIXED = 0, 1
+ETC_PREC_FP64, ETC_PREC_MIXED, ETC_PREC_MIXED_F64 = 0, 1, 2
 ETC_REF_LP, ETC_REF_ONES, ETC_REF_USER = 0, 1, 2
 
 EXPORTED = (

@@ -525,8 +525,9 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
   if (!(o->rtol > 0.0) || !std::isfinite(o->rtol))
     return fail(h, ETC_EINVAL, "rtol must be finite and > 0");
   if (o->maxit < 1) return fail(h, ETC_EINVAL, "maxit must be >= 1");
-  if (o->precision != ETC_PREC_FP64 && o->precision != ETC_PREC_MIXED)
-    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  if (o->precision != ETC_PREC_FP64 && o->precision != ETC_PREC_MIXED &&
+      o->precision != ETC_PREC_MIXED_F64)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64, _MIXED or _MIXED_F64");
   return ETC_OK;
 }
 
@@ -543,6 +544,14 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr,
                                      h->t64, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2);
+  }
+  if (prec == ETC_PREC_MIXED_F64) {
+    CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream,
+                   rhs.pin_f, rhs.pout_f, rhs.src));
+    CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr,
+                                    h->t32, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
+    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
+                                       h->rhat32[1], nullptr);
   }
   // mixed: x = 0 and w = 0 have the same bytes in both storages; r = b is split
   CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
@@ -575,6 +584,18 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2,
                                         nullptr, nullptr, ev ? ev + 3 : nullptr);
   }
+  if (prec == ETC_PREC_MIXED_F64) {
+    // FP64 vectors and operator around the FP32 Algorithm 3
+    CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
+                     h->stream));
+    if (ev) CK(cudaEventRecord(ev[1], h->stream));
+    CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32,
+                                    h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
+    if (ev) CK(cudaEventRecord(ev[2], h->stream));
+    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
+                                       h->rhat32[par], h->rhat32[par ^ 1],
+                                       ev ? ev + 3 : nullptr);
+  }
   CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
                       h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
@@ -593,7 +614,7 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
 // (the iteration that converged stops before its w update, which carries x),
 // and the mixed path's x back to FP64.
 etc_status finish_solve_x(etc_rve* h, const Geometry& g, double* x, int prec) {
-  if (prec != ETC_PREC_FP64)
+  if (prec == ETC_PREC_MIXED)
     CK(launch_finish_x(g, h->st, x, reinterpret_cast<const double*>(h->wdf), 1, h->stream));
   return ETC_OK;
 }
@@ -1157,8 +1178,8 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   if (!h || !r || !z) return ETC_EINVAL;
   etc_status s = check_dir(h, dir);
   if (s != ETC_OK) return s;
-  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED)
-    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED && prec != ETC_PREC_MIXED_F64)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64, _MIXED or _MIXED_F64");
   s = setup_faces(h, dir);
   if (s != ETC_OK) return s;
   s = autotune(h, dir, prec);
@@ -1210,8 +1231,8 @@ etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, doubl
   if (!h || !ms || iters < 1) return ETC_EINVAL;
   etc_status s = check_dir(h, dir);
   if (s != ETC_OK) return s;
-  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED)
-    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64 or ETC_PREC_MIXED");
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED && prec != ETC_PREC_MIXED_F64)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64, _MIXED or _MIXED_F64");
   if (!h->xsol[dir]) CK(dalloc(h, &h->xsol[dir], (size_t)h->n));
   CK(launch_state_reset(h->st, iters + 1, h->stream));
   s = setup_faces(h, dir);

@@ -29,7 +29,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--dir", type=int, default=2)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f64"], default="fp64")
     ap.add_argument("--contrast", type=float, default=1000.0)
     ap.add_argument("--maxit", type=int, default=5000)
     ap.add_argument("--warm", action="store_true")
@@ -39,7 +39,8 @@ def main():
     k = torch.from_numpy(np.ascontiguousarray(1.0 + (args.contrast - 1.0) * mask)).cuda()
     rve = B.RVE(k)
     del k
-    prec = B.ETC_PREC_FP64 if args.precision == "fp64" else B.ETC_PREC_MIXED
+    prec = {"fp64": B.ETC_PREC_FP64, "mixed": B.ETC_PREC_MIXED,
+            "mixed_f64": B.ETC_PREC_MIXED_F64}[args.precision]
     if args.warm:
         rve.solve(args.dir, rtol=1e-8, maxit=2, precision=prec)
         torch.cuda.synchronize()

@@ -22,7 +22,8 @@ def small_media():
             M.two_phase_random((11, 13, 17), 13, 0.3, 1.0, 8.0)]
 
 
-@pytest.mark.parametrize("precision", [B.ETC_PREC_FP64, B.ETC_PREC_MIXED])
+@pytest.mark.parametrize("precision", [B.ETC_PREC_FP64, B.ETC_PREC_MIXED,
+                                       B.ETC_PREC_MIXED_F64])
 def test_batch_matches_individual_tensors(precision):
     media = small_media()
     rves = [B.RVE(dev(k)) for k in media]

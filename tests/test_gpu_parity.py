@@ -97,9 +97,10 @@ def test_preconditioner_matches_oracle(shape, direction):
     rve.set_reference(direction, B.ETC_REF_USER, ku)
     B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_FP64, dev(r), z)
     assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 1e-11
-    # FP32 transforms and solves (mixed path)
-    B.etc_apply_preconditioner(rve.h, direction, B.ETC_PREC_MIXED, dev(r), z)
-    assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 2e-5
+    # FP32 transforms and solves (mixed paths)
+    for prec in (B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64):
+        B.etc_apply_preconditioner(rve.h, direction, prec, dev(r), z)
+        assert relmax(host(z), O.apply_reference_inverse(r, ku)) < 2e-5
 
 
 @pytest.mark.parametrize("shape", [(4, 96, 160), (3, 192, 384), (2, 32, 1024), (2, 1024, 64),
@@ -196,14 +197,18 @@ def test_series_laminate_harmonic_mean():
     assert kap == pytest.approx(20 / sum(1 / v for v in layer), rel=1e-10)
 
 
-def test_mixed_precision_matches_fp64_oracle():
+@pytest.mark.parametrize("precision", [B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64])
+def test_mixed_precision_matches_fp64_oracle(precision):
     k, _ = M.random_spheres((40, 36, 48), (3, 6), 0.3, 77, 1.0, 100.0)
     ref = O.solve_direction(k, k, k, 2, rtol=1e-10)
     rve = make(k)
-    kap, inf = rve.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
+    kap, inf = rve.solve(2, rtol=1e-8, precision=precision)
     assert inf["status"] == B.ETC_OK
     assert abs(kap - ref.kappa_eff) <= 1e-6 * ref.kappa_eff
     assert inf["true_relres"] < 1e-7
+    # the solution field too (each form returns x in FP64)
+    p = host(rve.solution(2))
+    assert relmax(p, ref.p) < 1e-5
 
 
 def test_solution_unpermuted_each_direction():
