@@ -344,3 +344,22 @@ def test_double_float_split_is_exact():
     sel = ok & (d != 0)
     err = np.abs(got[sel, 0].astype(np.float64) + got[sel, 1] - d[sel]) / np.abs(d[sel])
     assert err.max() <= 2.0 ** -47
+
+
+def test_allocation_failure_reports_enomem_and_recovers():
+    # ETC_FAIL_ALLOC_AFTER=k: the (k+1)-th device allocation of a handle fails;
+    # creation must report ETC_ENOMEM and release what it took, and the next
+    # handle must work
+    import os
+    k = np.ones((8, 8, 8))
+    try:
+        for budget in (0, 1, 5, 12, 20):
+            os.environ["ETC_FAIL_ALLOC_AFTER"] = str(budget)
+            with pytest.raises(B.EtcError) as e:
+                make(k)
+            assert e.value.status == B.ETC_ENOMEM
+    finally:
+        os.environ.pop("ETC_FAIL_ALLOC_AFTER", None)
+    rve = make(k)
+    kap, info = rve.solve(2, rtol=1e-12)
+    assert kap == pytest.approx(1.0, rel=1e-12) and info["iters"] <= 2
