@@ -52,6 +52,9 @@ template <int N> struct Fast {
   static constexpr int SA = M + P;
   static constexpr int BS0 = Q * (P + 1);
   static constexpr int BS = BS0 + (((P - BS0) % 16) + 16) % 16;
+  // one region per row serves both (they are never live together): stride
+  // max(SA, BS), still P mod 16
+  static constexpr int RS = SA > BS ? SA : BS;
 };
 
 // Axis-0 blocks of NT threads (256 or 128): L = NT / P rows each.
@@ -243,14 +246,13 @@ __global__ void __launch_bounds__(NT)
                  const double* __restrict__ rin, R* __restrict__ t, double* partials, int par,
                  double rtol2) {
   using F = Fast<N>;
-  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
   constexpr int L = FastX<N, NT>::L;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE != 2 && st->done) return;
-  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);
-  c2<R>* B = A + L * SA;
+  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);  // rows of RS complex: staging, transpose, Z
   R* Ar = reinterpret_cast<R*>(A);
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
@@ -313,28 +315,32 @@ __global__ void __launch_bounds__(NT)
         in1 = vround<R>(v1);
       }
       // element 2 i2 -> v_{i2}; element 2 i2 + 1 -> v_{n-1-i2}
-      Ar[l * 2 * SA + i2] = in0;
-      Ar[l * 2 * SA + N - 1 - i2] = in1;
+      Ar[l * 2 * RS + i2] = in0;
+      Ar[l * 2 * RS + N - 1 - i2] = in1;
     }
   }
   __syncthreads();
   const int l = threadIdx.x / P, tau = threadIdx.x % P;
   c2<R> v[Q];
 #pragma unroll
-  for (int s = 0; s < Q; ++s) v[s] = A[l * SA + tau + P * s];
+  for (int s = 0; s < Q; ++s) v[s] = A[l * RS + tau + P * s];
   four_step_a<R, N, -1>(v, tb.tw4, tau);
+  __syncthreads();  // the row is read before the transpose overwrites it
 #pragma unroll
-  for (int k1 = 0; k1 < Q; ++k1) B[l * BS + k1 * (P + 1) + tau] = v[k1];
+  for (int k1 = 0; k1 < Q; ++k1) A[l * RS + k1 * (P + 1) + tau] = v[k1];
   __syncthreads();
   c2<R> u[Q];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
 #pragma unroll
-    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = B[l * BS + (tau + P * e) * (P + 1) + tt];
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = A[l * RS + (tau + P * e) * (P + 1) + tt];
     Bfly<R, P, -1>::run(u + e * P);
-#pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) A[l * SA + tau + P * e + Q * k2] = u[e * P + k2];
   }
+  __syncthreads();  // the transpose is read before Z overwrites it
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) A[l * RS + tau + P * e + Q * k2] = u[e * P + k2];
   __syncthreads();
   const long long row = row0 + l;
 #pragma unroll
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(NT)
     for (int k2 = 0; k2 < P; ++k2) {
       const int k = tau + P * e + Q * k2;
       R xa, xb;
-      untangle<R>(u[e * P + k2], A[l * SA + (k ? M - k : 0)], tb.fpost, k, M, xa, xb);
+      untangle<R>(u[e * P + k2], A[l * RS + (k ? M - k : 0)], tb.fpost, k, M, xa, xb);
       if (row < nrows) {
         t[row * N + k] = xa;
         t[row * N + (k ? N - k : M)] = xb;
@@ -363,13 +369,12 @@ __global__ void __launch_bounds__(NT)
                  TZ* __restrict__ z, const double* kd, double kz_host, int check,
                  TZ* __restrict__ x, int par) {
   using F = Fast<N>;
-  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, SA = F::SA, BS = F::BS;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
   constexpr int L = FastX<N, NT>::L;
   constexpr int SR = N + P;  // real stride of the staged input rows
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
-  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);
-  c2<R>* B = A + L * SA;
+  c2<R>* A = reinterpret_cast<c2<R>*>(smraw);  // rows of RS complex: staging, transpose, z
   R* Ar = reinterpret_cast<R*>(A);
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)blockIdx.x * L;
@@ -405,18 +410,22 @@ __global__ void __launch_bounds__(NT)
     v[s] = inv_pre<R>(tb.ipre, j, M, X[j], j ? X[N - j] : (R)0, X[M - j], X[M + j]);
   }
   four_step_a<R, N, 1>(v, tb.tw4, tau);
+  __syncthreads();  // the staged row is read before the transpose overwrites it
 #pragma unroll
-  for (int k1 = 0; k1 < Q; ++k1) B[l * BS + k1 * (P + 1) + tau] = v[k1];
+  for (int k1 = 0; k1 < Q; ++k1) A[l * RS + k1 * (P + 1) + tau] = v[k1];
   __syncthreads();
   c2<R> u[Q];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
 #pragma unroll
-    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = B[l * BS + (tau + P * e) * (P + 1) + tt];
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = A[l * RS + (tau + P * e) * (P + 1) + tt];
     Bfly<R, P, 1>::run(u + e * P);
-#pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) A[l * SA + tau + P * e + Q * k2] = u[e * P + k2];
   }
+  __syncthreads();  // the transpose is read before z overwrites it
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) A[l * RS + tau + P * e + Q * k2] = u[e * P + k2];
   __syncthreads();
   // real view of A: slot a of row l holds v_a
   const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
@@ -448,8 +457,8 @@ __global__ void __launch_bounds__(NT)
       const long long row = row0 + lr;
       if (row >= nrows) continue;
       const long long c = row * N + 2 * i2;
-      const R u0 = Ar[lr * 2 * SA + i2] * scale;          // element 2 i2     <- v_{i2}
-      const R u1 = Ar[lr * 2 * SA + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
+      const R u0 = Ar[lr * 2 * RS + i2] * scale;          // element 2 i2     <- v_{i2}
+      const R u1 = Ar[lr * 2 * RS + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
       if (MODE == 2) {
         if (upd) st_pair(x + c, vaxpy(alpha, wo[u].a, xo[u].a), vaxpy(alpha, wo[u].b, xo[u].b));
         st_pair(z + c, vaxpy(beta, wo[u].a, vfrom<TZ, R>(u0)),
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(NT)
 
 template <typename R, int N, int NT>
 size_t fast_x_smem() {
-  return (size_t)FastX<N, NT>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>);
+  return (size_t)FastX<N, NT>::L * Fast<N>::RS * sizeof(c2<R>);
 }
 template <typename R, int N>
 size_t fast_y_smem() {
@@ -478,7 +487,7 @@ size_t fast_y_smem() {
 constexpr size_t kFastSmemMax = 200 * 1024;  // dynamic shared memory opt-in per block
 template <typename R, int N, int NT>
 constexpr bool fast_x_fits() {
-  return (size_t)FastX<N, NT>::L * (Fast<N>::SA + Fast<N>::BS) * sizeof(c2<R>) <= kFastSmemMax;
+  return (size_t)FastX<N, NT>::L * Fast<N>::RS * sizeof(c2<R>) <= kFastSmemMax;
 }
 
 template <typename R, int N, typename V, int NT>

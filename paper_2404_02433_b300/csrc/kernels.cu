@@ -671,8 +671,9 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
   const long long s = gidx();
   double acc = 0.0, acc2 = 0.0;
   if (s < g.plane) {
-    // P planes per round: the loads of a round are issued before the recurrence uses them
-    constexpr int P = 8;
+    // P planes per round (4 in FP64, 8 in FP32, the faster depths measured):
+    // the loads of a round are issued before the recurrence uses them
+    constexpr int P = sizeof(R) == 8 ? 4 : 8;
     R yv = (R)0, hp = (R)0, part = (R)0, zr = (R)0;
     for (int kb = 0; kb < g.n2; kb += P) {
       R tv[P], hv[P];
