@@ -53,12 +53,12 @@ struct etc_rve {
   double* z64 = nullptr;
   float *t32 = nullptr, *h32 = nullptr;
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
-  // mixed path: double-float copies of the faces and diagonal (refreshed with
-  // every face assembly) and the double-float search direction w; its x, r
+  // mixed path: double-float copies of the faces and Dirichlet planes
+  // (refreshed with every face assembly) and the double-float search direction w; its x, r
   // and q are double-float pairs in the FP64 buffers (same 8 bytes), and x
   // returns to FP64 at the end of each solve
   float2* Tdf[3] = {nullptr, nullptr, nullptr};
-  float2* Ddf = nullptr;
+  float2* Bdf = nullptr;  // B_in then B_out, plane_max each
   float2* wdf = nullptr;
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
@@ -340,7 +340,7 @@ etc_status launch_setup(etc_rve* h, int dir) {
                   h->st, h->stream));
   // the diagonal, and the double-float copies for the mixed-precision matvec
   CK(launch_diag_split(g, h->T0, h->T1, h->T2, h->Bin, h->Bout, h->D, h->Tdf[0], h->Tdf[1],
-                       h->Tdf[2], h->Ddf, h->stream));
+                       h->Tdf[2], h->Bdf, h->stream));
   return ETC_OK;
 }
 
@@ -596,7 +596,7 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
                                        h->rhat32[par], h->rhat32[par ^ 1],
                                        ev ? ev + 3 : nullptr);
   }
-  CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Ddf,
+  CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
                       h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   // double-float storage: x += alpha w moves to the w-update kernel, which
@@ -932,7 +932,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
   CKC(dalloc(h, &h->rhat32[0], (size_t)n)); CKC(dalloc(h, &h->rhat32[1], (size_t)n));
   CKC(dalloc(h, &h->Tdf[0], nt)); CKC(dalloc(h, &h->Tdf[1], nt)); CKC(dalloc(h, &h->Tdf[2], nt));
-  CKC(dalloc(h, &h->Ddf, (size_t)n)); CKC(dalloc(h, &h->wdf, (size_t)n));
+  CKC(dalloc(h, &h->Bdf, 2 * (size_t)h->plane_max)); CKC(dalloc(h, &h->wdf, (size_t)n));
   // partials: the largest reduction grid over the three directions
   size_t np = 1024;
   for (int d = 0; d < 3; ++d) {

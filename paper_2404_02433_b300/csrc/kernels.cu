@@ -333,13 +333,32 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
 }
 
 // ------------------------------------------------------------------ double-float matvec
-// The mixed-precision path's q = A w (same operator as k_matvec) with the
-// FP64-class arithmetic on the FP32 pipe: faces, diagonal, w and q as
-// double-float pairs, the seven products summed by Sum2.
-// Each thread owns one (i, j) column of a 32 x 8 tile and marches over kchunk
-// planes, so w at k-1, k, k+1 and the shared z face stay in registers; the
-// x/y neighbours come from the tile's own loads through L1.
+// The mixed-precision path's q = A w with the FP64-class arithmetic on the
+// FP32 pipe: faces, Dirichlet planes, w and q as double-float pairs.  The
+// operator is taken in its face-difference form
+//   (Aw)_c = sum_f T_f (w_c - w_f) + [k = 0] B_in w_c + [k = n2-1] B_out w_c
+// (Eq. scaled bilinear forms; the same operator as D w - sum T w with
+// D = sum T + B), so no diagonal is read and no cancellation between D w and
+// the neighbour terms occurs; the terms are summed by Sum2.  Each thread owns
+// one (i, j) column of a 32 x 8 tile and marches over kchunk planes, so w at
+// k-1, k, k+1 and the shared z face stay in registers; the x/y neighbours
+// come from the tile's own loads through L1.
 // MODE 1: also w.q (double-float partial per thread) -> alpha = rho / w.q.
+
+// (s, e) += T (a - b) for double-float T, a, b
+__device__ __forceinline__ void df_diff_acc(float2 T, float2 a, float2 b, float& s, float& e) {
+  float dh, dl;
+  two_sum(a.x, -b.x, dh, dl);
+  dl += a.y - b.y;
+  const float p = T.x * dh;
+  float pe = fma(T.x, dh, -p);
+  pe = fma(T.x, dl, pe);
+  pe = fma(T.y, dh, pe);
+  float t;
+  two_sum(s, p, s, t);
+  e += t + pe;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
                                                   const float2* __restrict__ w,
@@ -347,7 +366,8 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
                                                   const float2* __restrict__ T0,
                                                   const float2* __restrict__ T1,
                                                   const float2* __restrict__ T2,
-                                                  const float2* __restrict__ D,
+                                                  const float2* __restrict__ Bin,
+                                                  const float2* __restrict__ Bout,
                                                   double* partials, int par, int kchunk) {
   __shared__ double sh[32];
   __shared__ int flag;
@@ -361,13 +381,13 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
     const long long n0 = g.n0, pl = g.plane;
     const long long dxm = i > 0 ? -1 : 0, dxp = i < g.n0 - 1 ? 1 : 0;
     const long long dym = j > 0 ? -n0 : 0, dyp = j < g.n1 - 1 ? n0 : 0;
-    long long c = (long long)k0 * pl + (long long)j * n0 + i;
+    const long long sidx = (long long)j * n0 + i;
+    long long c = (long long)k0 * pl + sidx;
     // Operands of plane k are loaded during plane k-1 (software pipelining):
     // every thread keeps a full plane's worth of loads in flight while it sums.
-    struct Ops { float2 d, x0, x1, y0, y1, wx0, wx1, wy0, wy1, wp, zp; };
+    struct Ops { float2 x0, x1, y0, y1, wx0, wx1, wy0, wy1, wp, zp; };
     auto load = [&](long long cc, int k, float2 wself) {
       Ops o;
-      o.d = D[cc];
       o.x0 = T0[cc];
       o.x1 = T0[cc + 1];
       o.y0 = T1[cc];
@@ -388,13 +408,14 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
       Ops nxt;
       if (k + 1 < k1) nxt = load(c + pl, k + 1, cur.wp);
       float sv = 0.f, ev = 0.f;
-      df_fma_acc<1>(cur.d, wc, sv, ev);
-      df_fma_acc<-1>(cur.x0, cur.wx0, sv, ev);
-      df_fma_acc<-1>(cur.x1, cur.wx1, sv, ev);
-      df_fma_acc<-1>(cur.y0, cur.wy0, sv, ev);
-      df_fma_acc<-1>(cur.y1, cur.wy1, sv, ev);
-      df_fma_acc<-1>(tz, wm, sv, ev);
-      df_fma_acc<-1>(cur.zp, cur.wp, sv, ev);
+      df_diff_acc(cur.x0, wc, cur.wx0, sv, ev);
+      df_diff_acc(cur.x1, wc, cur.wx1, sv, ev);
+      df_diff_acc(cur.y0, wc, cur.wy0, sv, ev);
+      df_diff_acc(cur.y1, wc, cur.wy1, sv, ev);
+      df_diff_acc(tz, wc, wm, sv, ev);
+      df_diff_acc(cur.zp, wc, cur.wp, sv, ev);
+      if (k == 0) df_fma_acc<1>(Bin[sidx], wc, sv, ev);
+      if (k == g.n2 - 1) df_fma_acc<1>(Bout[sidx], wc, sv, ev);
       float qh, ql;
       two_sum(sv, ev, qh, ql);
       q[c] = make_float2(qh, ql);
@@ -448,14 +469,15 @@ __global__ void k_finish_x(Geometry g, const PcgState* st, V* x, const V* w) {
 // The diagonal of A (Eq. scaled bilinear forms): the six faces of each cell
 // (the minus faces at c, the plus faces as the minus faces of the neighbours;
 // zero on Neumann faces and in the extra plane) plus the Dirichlet terms, then
-// the double-float copies of T0, T1, T2 and D for the mixed-precision matvec.
+// the double-float copies of T0, T1, T2 and of B_in, B_out (FB: the two
+// planes one after the other) for the mixed-precision matvec.
 // Grid: blockIdx.y = plane k (n2 planes and the extra zero plane).
 __global__ void k_diag_split(Geometry g, const double* __restrict__ T0,
                              const double* __restrict__ T1, const double* __restrict__ T2,
                              const double* __restrict__ Bin, const double* __restrict__ Bout,
                              double* __restrict__ D, float2* __restrict__ F0,
                              float2* __restrict__ F1, float2* __restrict__ F2,
-                             float2* __restrict__ FD) {
+                             float2* __restrict__ FB) {
   const int k = blockIdx.y;
   const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
   if (sidx >= g.plane) return;
@@ -467,10 +489,15 @@ __global__ void k_diag_split(Geometry g, const double* __restrict__ T0,
   const double t0 = T0[c], t1 = T1[c], t2 = T2[c];
   const double p0 = T0[c + 1], p1 = T1[c + g.n0], p2 = T2[c + g.plane];
   double d = t0 + p0 + t1 + p1 + t2 + p2;
-  if (k == 0) d += Bin[sidx];
-  if (k == g.n2 - 1) d += Bout[sidx];
+  if (k == 0) {
+    d += Bin[sidx];
+    FB[sidx] = split_df(Bin[sidx]);
+  }
+  if (k == g.n2 - 1) {
+    d += Bout[sidx];
+    FB[g.plane + sidx] = split_df(Bout[sidx]);
+  }
   D[c] = d;
-  FD[c] = split_df(d);
 }
 
 // Double-float copies of FP64 arrays (split_df per element).
@@ -1004,9 +1031,9 @@ unsigned int faces_blocks(const Geometry& g) {
 
 cudaError_t launch_diag_split(const Geometry& g, const double* T0, const double* T1,
                               const double* T2, const double* Bin, const double* Bout, double* D,
-                              float2* F0, float2* F1, float2* F2, float2* FD, cudaStream_t s) {
+                              float2* F0, float2* F1, float2* F2, float2* FB, cudaStream_t s) {
   const dim3 grid((unsigned int)((g.plane + 255) / 256), (unsigned int)g.n2 + 1);
-  k_diag_split<<<grid, 256, 0, s>>>(g, T0, T1, T2, Bin, Bout, D, F0, F1, F2, FD);
+  k_diag_split<<<grid, 256, 0, s>>>(g, T0, T1, T2, Bin, Bout, D, F0, F1, F2, FB);
   count_launch();
   return cudaGetLastError();
 }
@@ -1074,14 +1101,15 @@ unsigned int matvec_df_blocks(const Geometry& g) {
 
 cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
-                             const float2* D, double* partials, int par, int mode,
+                             const float2* FB, double* partials, int par, int mode,
                              cudaStream_t s) {
   int kc;
   const dim3 grid = matvec_df_grid(g, &kc);
+  const float2* Bout = FB + g.plane;
   if (mode == 1)
-    k_matvec_df<1><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
+    k_matvec_df<1><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, FB, Bout, partials, par, kc);
   else
-    k_matvec_df<0><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par, kc);
+    k_matvec_df<0><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, FB, Bout, partials, par, kc);
   count_launch();
   return cudaGetLastError();
 }

@@ -16,10 +16,10 @@ cudaError_t launch_faces(const Geometry& g, double ih0, double ih1, double ih2, 
                          double* D, double* Bin, double* Bout, double* partials, PcgState* st,
                          cudaStream_t s);
 // The diagonal D from the faces and Bin/Bout, and the double-float copies of
-// T0, T1, T2 (with the extra plane) and D.
+// T0, T1, T2 (with the extra plane) and of Bin, Bout (FB: 2 planes).
 cudaError_t launch_diag_split(const Geometry& g, const double* T0, const double* T1,
                               const double* T2, const double* Bin, const double* Bout, double* D,
-                              float2* F0, float2* F1, float2* F2, float2* FD, cudaStream_t s);
+                              float2* F0, float2* F1, float2* F2, float2* FB, cudaStream_t s);
 unsigned int faces_blocks(const Geometry& g);
 // kref_dev (device, may be NULL) takes precedence over kref_host (host, 5 values).
 template <typename R>
@@ -36,10 +36,11 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);
-// Mixed-precision matvec on double-float operands (q in FP64); mode 1 as k_matvec.
+// Mixed-precision matvec on double-float operands (faces, Dirichlet planes FB
+// as in launch_diag_split, w, q); mode 1 as k_matvec.
 cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
-                             const float2* D, double* partials, int par, int mode,
+                             const float2* FB, double* partials, int par, int mode,
                              cudaStream_t s);
 cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
 // FP64 values to double-float pairs in place.
