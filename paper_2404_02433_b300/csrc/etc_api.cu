@@ -51,15 +51,16 @@ struct etc_rve {
   double *Bin = nullptr, *Bout = nullptr;
   double *r = nullptr, *q = nullptr, *w[2] = {nullptr, nullptr}, *t64 = nullptr, *h64 = nullptr;
   double* z64 = nullptr;
-  float *t32 = nullptr, *h32 = nullptr;
+  float* t32 = nullptr;                   // z^ and z of the FP32 preconditioner
   float* rhat32[2] = {nullptr, nullptr};  // transformed residual of the last two iterations
+  float2* ck32 = nullptr;                 // checkpoints of the FP32 tridiagonal sweeps
   // mixed path: double-float copies of the faces and Dirichlet planes
   // (refreshed with every face assembly) and the double-float search direction w; its x, r
   // and q are double-float pairs in the FP64 buffers (same 8 bytes), and x
   // returns to FP64 at the end of each solve
   float2* Tdf[3] = {nullptr, nullptr, nullptr};
   float2* Bdf = nullptr;  // B_in then B_out, plane_max each
-  float2* wdf = nullptr;
+  float2* wdf = nullptr;  // inside an allocation with zero guards (see create)
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
@@ -369,10 +370,9 @@ etc_status launch_reference(etc_rve* h, int dir, int prec) {
   const Geometry g = geom_of(h, dir);
   const PlanStore& p0 = h->plans[g.n0];
   const PlanStore& p1 = h->plans[g.n1];
+  // (the FP32 solves generate their pivots per column)
   if (prec == ETC_PREC_FP64)
     CK(launch_pivots<double>(g, p0.lam, p1.lam, kref_dev(h), nullptr, h->h64, h->stream));
-  else
-    CK(launch_pivots<float>(g, p0.lam, p1.lam, kref_dev(h), nullptr, h->h32, h->stream));
   return ETC_OK;
 }
 
@@ -496,26 +496,35 @@ etc_status autotune(etc_rve* h, int dir, int prec) {
 }
 
 // ------------------------------------------------------------------ preconditioner chain
-// t <- forward DCT(r) (fwd_x launched by the caller), then y-DCT, tridiagonal
-// (tri_mode as in k_tridiag, rnew/rold for the flexible beta), inverse y,
-// inverse x into out (inv_mode 0: out = z; 2: out = w <- z + beta w, after
-// x += alpha[par] w when x is given; TZ is FP64 or double-float).  kappa_ref
-// comes from the state.  ev (optional): events recorded after each of the four
-// kernels.
+// t holds the axis-0 forward transform of r (fwd_x, launched by the caller).
+// Then the axis-1 forward transform in place, the tridiagonal solves into zt,
+// the axis-1 backward transform in place in zt and the axis-0 backward
+// transform into out (inv_mode 0: out = z; 2: out = w <- z + beta w, after
+// x += alpha[par] w when x is given; TZ is FP64 or double-float).
+// tri_mode as in k_tridiag.  FP64 (R = double): the pivot table hp, in place
+// (zt = t).  FP32: pivots generated per column; zt may differ from t, so that
+// t keeps r^ for the next iteration's flexible beta, which reads it as rold.
+// kappa_ref comes from the state.  ev (optional): events recorded after each
+// of the four kernels.
 template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
-                        const DctPlan<R>& p1, R* t, const R* hp, TZ* out, int tri_mode,
-                        int inv_mode, R* rnew = nullptr, const R* rold = nullptr,
-                        cudaEvent_t* ev = nullptr, TZ* x = nullptr, int par = 0) {
+                        const DctPlan<R>& p1, R* t, R* zt, const R* hp, TZ* out, int tri_mode,
+                        int inv_mode, const R* rold = nullptr, cudaEvent_t* ev = nullptr,
+                        TZ* x = nullptr, int par = 0) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  CK(launch_tridiag<R>(g, h->st, t, hp, kref_dev(h), 1.0, h->partials, tri_mode, rnew, rold,
-                       h->stream));
+  if constexpr (sizeof(R) == 8) {
+    CK(launch_tridiag<R>(g, h->st, t, hp, kref_dev(h), 1.0, h->partials, tri_mode, nullptr,
+                         nullptr, h->stream));
+  } else {
+    CK(launch_tridiag_otf(g, h->st, t, zt, h->ck32, h->plans[g.n0].lam, h->plans[g.n1].lam,
+                          kref_dev(h), h->partials, tri_mode, rold, h->stream));
+  }
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
-  CK(launch_dct_y<R>(g, p1, h->st, t, 1, check, h->stream, h->tiles[2]));
+  CK(launch_dct_y<R>(g, p1, h->st, zt, 1, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  CK((launch_inv_x<R, TZ>(g, p0, h->st, t, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
+  CK((launch_inv_x<R, TZ>(g, p0, h->st, zt, out, kref_dev(h), 1.0, check, inv_mode, h->stream,
                           h->tiles[1], x, par)));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   return ETC_OK;
@@ -543,26 +552,29 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
                    rhs.pin_f, rhs.pout_f, rhs.src));
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr,
                                      h->t64, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
-    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2);
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->t64, h->h64, h->w[0],
+                                        1, 2);
   }
   if (prec == ETC_PREC_MIXED_F64) {
     CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream,
                    rhs.pin_f, rhs.pout_f, rhs.src));
+    // iteration 0 reads the transformed residual of this apply from rhat32[1]
     CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr,
-                                    h->t32, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
-    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 3, 2,
-                                       h->rhat32[1], nullptr);
+                                    h->rhat32[1], h->partials, 0, rtol2, 0, h->stream,
+                                    h->tiles[0])));
+    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr,
+                                       h->w[0], 3, 2);
   }
   // mixed: x = 0 and w = 0 have the same bytes in both storages; r = b is split
   CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
                  reinterpret_cast<double*>(h->wdf), h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
   CK(launch_split_inplace(h->r, h->n, h->stream));
-  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, nullptr, df(h->r),
-                                  nullptr, h->t32, h->partials, 0, rtol2, 0, h->stream,
-                                  h->tiles[0])));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
-  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 3, 2,
-                                     h->rhat32[1], nullptr);
+  CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, nullptr, df(h->r),
+                                  nullptr, h->rhat32[1], h->partials, 0, rtol2, 0, h->stream,
+                                  h->tiles[0])));
+  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr,
+                                     h->wdf, 3, 2);
 }
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
@@ -581,19 +593,20 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, h->w[0], h->q, h->r, nullptr,
                                      h->t64, h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
-    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, h->w[0], 1, 2,
-                                        nullptr, nullptr, ev ? ev + 3 : nullptr);
+    return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->t64, h->h64, h->w[0],
+                                        1, 2, nullptr, ev ? ev + 3 : nullptr);
   }
   if (prec == ETC_PREC_MIXED_F64) {
     // FP64 vectors and operator around the FP32 Algorithm 3
     CK(launch_matvec(g, h->st, h->w[0], h->q, h->T0, h->T1, h->T2, h->D, h->partials, par, 1,
                      h->stream));
     if (ev) CK(cudaEventRecord(ev[1], h->stream));
-    CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr, h->t32,
-                                    h->partials, par, 0.0, 1, h->stream, h->tiles[0])));
+    CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, h->w[0], h->q, h->r, nullptr,
+                                    h->rhat32[par], h->partials, par, 0.0, 1, h->stream,
+                                    h->tiles[0])));
     if (ev) CK(cudaEventRecord(ev[2], h->stream));
-    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->w[0], 2, 2,
-                                       h->rhat32[par], h->rhat32[par ^ 1],
+    return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->rhat32[par], h->t32, nullptr,
+                                       h->w[0], 2, 2, h->rhat32[par ^ 1],
                                        ev ? ev + 3 : nullptr);
   }
   CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
@@ -602,11 +615,11 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   // double-float storage: x += alpha w moves to the w-update kernel, which
   // reads w anyway (8 bytes per cell less)
   CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, df(h->q), df(h->r),
-                                  nullptr, h->t32, h->partials, par, 0.0, 1, h->stream,
+                                  nullptr, h->rhat32[par], h->partials, par, 0.0, 1, h->stream,
                                   h->tiles[0])));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->t32, h->h32, h->wdf, 2, 2,
-                                     h->rhat32[par], h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
+  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->rhat32[par], h->t32, nullptr,
+                                     h->wdf, 2, 2, h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
                                      df(x), par);
 }
 
@@ -929,10 +942,24 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(dalloc(h, &h->w[0], (size_t)n));
   CKC(dalloc(h, &h->t64, (size_t)n)); CKC(dalloc(h, &h->h64, (size_t)n));
   CKC(dalloc(h, &h->z64, (size_t)n));
-  CKC(dalloc(h, &h->t32, (size_t)n)); CKC(dalloc(h, &h->h32, (size_t)n));
+  CKC(dalloc(h, &h->t32, (size_t)n));
+  {
+    size_t nck = 1;
+    for (int d = 0; d < 3; ++d) nck = std::max(nck, tridiag_ck_pairs(geom_of(h, d)));
+    CKC(dalloc(h, &h->ck32, nck));
+  }
   CKC(dalloc(h, &h->rhat32[0], (size_t)n)); CKC(dalloc(h, &h->rhat32[1], (size_t)n));
   CKC(dalloc(h, &h->Tdf[0], nt)); CKC(dalloc(h, &h->Tdf[1], nt)); CKC(dalloc(h, &h->Tdf[2], nt));
-  CKC(dalloc(h, &h->Bdf, 2 * (size_t)h->plane_max)); CKC(dalloc(h, &h->wdf, (size_t)n));
+  CKC(dalloc(h, &h->Bdf, 2 * (size_t)h->plane_max));
+  {
+    // w of the mixed path with zero guards of the longest axis on both sides
+    // (the double-float matvec reads w[c +- n0] without bounds tests)
+    const size_t guard = (size_t)std::max(nx, std::max(ny, nz));
+    float2* wbase = nullptr;
+    CKC(dalloc(h, &wbase, (size_t)n + 2 * guard));
+    CKC(cudaMemsetAsync(wbase, 0, ((size_t)n + 2 * guard) * sizeof(float2), h->stream));
+    h->wdf = wbase + guard;
+  }
   // partials: the largest reduction grid over the three directions
   size_t np = 1024;
   for (int d = 0; d < 3; ++d) {
@@ -1192,11 +1219,11 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
   if (prec == ETC_PREC_FP64) {
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, r,
                                      h->t64, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
-    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->h64, z, 0, 0);
+    s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->t64, h->h64, z, 0, 0);
   } else {
     CK((launch_fwd_x<float, double>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r,
                                     h->t32, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
-    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->h32, z, 0, 0);
+    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->t32, nullptr, z, 0, 0);
   }
   if (s != ETC_OK) return s;
   CK(cudaStreamSynchronize(h->stream));

@@ -117,10 +117,20 @@ __device__ __forceinline__ bool publish_partial(double* partials, int nparts, do
 __device__ __forceinline__ double sum_partials(const double* partials, int nb, int stride,
                                                double* sh) {
   double v = 0.0;
-  // each thread sums a contiguous chunk, then the chunks are added in order
+  // each thread sums a contiguous chunk, then the chunks are added in order;
+  // the chunk's loads are issued eight at a time ahead of the additions
   const int per = (nb + blockDim.x - 1) / blockDim.x;
   const int b0 = threadIdx.x * per;
-  for (int b = b0; b < b0 + per && b < nb; ++b) v += __ldcg(partials + (size_t)b * stride);
+  const int b1 = min(b0 + per, nb);
+  int b = b0;
+  for (; b + 8 <= b1; b += 8) {
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = __ldcg(partials + (size_t)(b + u) * stride);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v += t[u];
+  }
+  for (; b < b1; ++b) v += __ldcg(partials + (size_t)b * stride);
   // ordered combination of the per-thread chunks
   __syncthreads();
   const int nw = (blockDim.x + 31) >> 5;

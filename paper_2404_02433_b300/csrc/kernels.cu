@@ -55,14 +55,25 @@ __global__ void k_kappa_stats(const double* __restrict__ a, long long n, double*
       vals[0] = fmin(vals[0], wl[w]); vals[1] = fmax(vals[1], wh[w]); vals[2] += wb[w];
     }
   if (publish_values(partials, 3, vals, 3, &st->cnt[kCntExt], &flag)) {
+    // every thread a stride of blocks, then warps and block (min, max and the
+    // integer-valued count do not depend on the order)
+    double l2 = INFINITY, h2 = -INFINITY, b2 = 0.0;
+    const unsigned int nb = nblocks();
+    for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) {
+      l2 = fmin(l2, __ldcg(partials + 3 * (size_t)b));
+      h2 = fmax(h2, __ldcg(partials + 3 * (size_t)b + 1));
+      b2 += __ldcg(partials + 3 * (size_t)b + 2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      l2 = fmin(l2, __shfl_down_sync(0xffffffffu, l2, o));
+      h2 = fmax(h2, __shfl_down_sync(0xffffffffu, h2, o));
+      b2 += __shfl_down_sync(0xffffffffu, b2, o);
+    }
+    __syncthreads();
+    if (lane == 0) { wl[wid] = l2; wh[wid] = h2; wb[wid] = b2; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double l2 = INFINITY, h2 = -INFINITY, b2 = 0.0;
-      const unsigned int nb = nblocks();
-      for (unsigned int b = 0; b < nb; ++b) {
-        l2 = fmin(l2, __ldcg(partials + 3 * b));
-        h2 = fmax(h2, __ldcg(partials + 3 * b + 1));
-        b2 += __ldcg(partials + 3 * b + 2);
-      }
+      for (int w = 1; w < nw; ++w) { l2 = fmin(l2, wl[w]); h2 = fmax(h2, wh[w]); b2 += wb[w]; }
       st->ext[3 * slot] = l2; st->ext[3 * slot + 1] = h2; st->ext[3 * slot + 2] = b2;
       st->cnt[kCntExt] = 0;
     }
@@ -340,35 +351,45 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
 // (Eq. scaled bilinear forms; the same operator as D w - sum T w with
 // D = sum T + B), so no diagonal is read and no cancellation between D w and
 // the neighbour terms occurs; the terms are summed by Sum2.  Each thread owns
-// one (i, j) column of a 32 x 8 tile and marches over kchunk planes, so w at
-// k-1, k, k+1 and the shared z face stay in registers; the x/y neighbours
-// come from the tile's own loads through L1.
+// one (i, j) column of a 32 x 8 tile and marches over kchunk planes: w at k
+// and k+1 stay in registers, and the flux through the face below plane k is
+// the one computed through the face above plane k-1, negated.  The x/y
+// neighbours come from the tile's own loads through L1.
+// Neighbour offsets are the constants +-1 and +-n0 at every cell: where such
+// a neighbour lies outside the box (or in the next/previous row) its face
+// conductance is the zero of a Neumann face, so the value read only has to be
+// finite.  w therefore needs n0 finite guard elements before w[0] and after
+// w[n-1]; the z neighbour above the last plane is not read.
 // MODE 1: also w.q (double-float partial per thread) -> alpha = rho / w.q.
 
-// (s, e) += T (a - b) for double-float T, a, b
-__device__ __forceinline__ void df_diff_acc(float2 T, float2 a, float2 b, float& s, float& e) {
+// p + pe ~ T (a - b) for double-float T, a, b: the difference by TwoSum (plus
+// the low parts), the product with hi*hi exact by FMA plus the cross terms
+__device__ __forceinline__ void df_flux(float2 T, float2 a, float2 b, float& p, float& pe) {
   float dh, dl;
   two_sum(a.x, -b.x, dh, dl);
   dl += a.y - b.y;
-  const float p = T.x * dh;
-  float pe = fma(T.x, dh, -p);
+  p = T.x * dh;
+  pe = fma(T.x, dh, -p);
   pe = fma(T.x, dl, pe);
   pe = fma(T.y, dh, pe);
+}
+// Sum2 step (s, e) += p + pe
+__device__ __forceinline__ void df_acc(float p, float pe, float& s, float& e) {
   float t;
   two_sum(s, p, s, t);
   e += t + pe;
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
-                                                  const float2* __restrict__ w,
-                                                  float2* __restrict__ q,
-                                                  const float2* __restrict__ T0,
-                                                  const float2* __restrict__ T1,
-                                                  const float2* __restrict__ T2,
-                                                  const float2* __restrict__ Bin,
-                                                  const float2* __restrict__ Bout,
-                                                  double* partials, int par, int kchunk) {
+__global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
+                                                     const float2* __restrict__ w,
+                                                     float2* __restrict__ q,
+                                                     const float2* __restrict__ T0,
+                                                     const float2* __restrict__ T1,
+                                                     const float2* __restrict__ T2,
+                                                     const float2* __restrict__ Bin,
+                                                     const float2* __restrict__ Bout,
+                                                     double* partials, int par, int kchunk) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE == 1 && st->done) return;
@@ -378,51 +399,60 @@ __global__ void __launch_bounds__(256) k_matvec_df(Geometry g, PcgState* st,
   const int k1 = min(k0 + kchunk, g.n2);
   float ds = 0.f, dc = 0.f;
   if (i < g.n0 && j < g.n1 && k0 < k1) {
-    const long long n0 = g.n0, pl = g.plane;
-    const long long dxm = i > 0 ? -1 : 0, dxp = i < g.n0 - 1 ? 1 : 0;
-    const long long dym = j > 0 ? -n0 : 0, dyp = j < g.n1 - 1 ? n0 : 0;
+    const int n0 = g.n0;
+    const long long pl = g.plane;
     const long long sidx = (long long)j * n0 + i;
-    long long c = (long long)k0 * pl + sidx;
-    // Operands of plane k are loaded during plane k-1 (software pipelining):
+    const long long c0 = (long long)k0 * pl + sidx;
+    // per-thread pointers, advanced by one plane per step
+    const float2* pw = w + c0;
+    const float2* p0 = T0 + c0;
+    const float2* p1 = T1 + c0;
+    const float2* p2 = T2 + c0;
+    float2* pq = q + c0;
+    // Operands of plane k+1 are loaded during plane k (software pipelining):
     // every thread keeps a full plane's worth of loads in flight while it sums.
     struct Ops { float2 x0, x1, y0, y1, wx0, wx1, wy0, wy1, wp, zp; };
-    auto load = [&](long long cc, int k, float2 wself) {
+    auto load = [&](bool last, float2 wself) {
       Ops o;
-      o.x0 = T0[cc];
-      o.x1 = T0[cc + 1];
-      o.y0 = T1[cc];
-      o.y1 = T1[cc + n0];
-      o.wx0 = w[cc + dxm];
-      o.wx1 = w[cc + dxp];
-      o.wy0 = w[cc + dym];
-      o.wy1 = w[cc + dyp];
-      o.wp = (k < g.n2 - 1) ? w[cc + pl] : wself;
-      o.zp = T2[cc + pl];  // the extra zero plane covers k = n2 - 1
+      o.x0 = p0[0];
+      o.x1 = p0[1];
+      o.y0 = p1[0];
+      o.y1 = p1[n0];
+      o.wx0 = pw[-1];
+      o.wx1 = pw[1];
+      o.wy0 = pw[-n0];
+      o.wy1 = pw[n0];
+      o.wp = last ? wself : pw[pl];
+      o.zp = p2[pl];  // the extra zero plane covers k = n2 - 1
       return o;
     };
-    float2 wc = w[c];
-    float2 wm = k0 > 0 ? w[c - pl] : wc;
-    float2 tz = T2[c];
-    Ops cur = load(c, k0, wc);
-    for (int k = k0; k < k1; ++k, c += pl) {
+    float2 wc = pw[0];
+    float fz, fze;  // flux T2 (w_{k-1} - w_k) through the face below plane k
+    df_flux(p2[0], k0 > 0 ? pw[-pl] : wc, wc, fz, fze);
+    Ops cur = load(k0 == g.n2 - 1, wc);
+    for (int k = k0; k < k1; ++k) {
       Ops nxt;
-      if (k + 1 < k1) nxt = load(c + pl, k + 1, cur.wp);
-      float sv = 0.f, ev = 0.f;
-      df_diff_acc(cur.x0, wc, cur.wx0, sv, ev);
-      df_diff_acc(cur.x1, wc, cur.wx1, sv, ev);
-      df_diff_acc(cur.y0, wc, cur.wy0, sv, ev);
-      df_diff_acc(cur.y1, wc, cur.wy1, sv, ev);
-      df_diff_acc(tz, wc, wm, sv, ev);
-      df_diff_acc(cur.zp, wc, cur.wp, sv, ev);
+      pw += pl; p0 += pl; p1 += pl; p2 += pl;
+      if (k + 1 < k1) nxt = load(k + 1 == g.n2 - 1, cur.wp);
+      float sv, ev, p, pe;
+      df_flux(cur.x0, wc, cur.wx0, sv, ev);
+      df_flux(cur.x1, wc, cur.wx1, p, pe);
+      df_acc(p, pe, sv, ev);
+      df_flux(cur.y0, wc, cur.wy0, p, pe);
+      df_acc(p, pe, sv, ev);
+      df_flux(cur.y1, wc, cur.wy1, p, pe);
+      df_acc(p, pe, sv, ev);
+      df_acc(-fz, -fze, sv, ev);
+      df_flux(cur.zp, wc, cur.wp, fz, fze);
+      df_acc(fz, fze, sv, ev);
       if (k == 0) df_fma_acc<1>(Bin[sidx], wc, sv, ev);
       if (k == g.n2 - 1) df_fma_acc<1>(Bout[sidx], wc, sv, ev);
       float qh, ql;
       two_sum(sv, ev, qh, ql);
-      q[c] = make_float2(qh, ql);
+      *pq = make_float2(qh, ql);
+      pq += pl;
       if (MODE == 1) df_fma_acc<1>(wc, make_float2(qh, ql), ds, dc);
-      wm = wc;
       wc = cur.wp;
-      tz = cur.zp;
       cur = nxt;
     }
   }
@@ -648,7 +678,17 @@ __device__ __forceinline__ void tridiag_tail(double acc, double acc2, PcgState* 
       double a0 = 0.0, a1 = 0.0;
       const int per = (nb + blockDim.x - 1) / blockDim.x;
       const int b0 = threadIdx.x * per;
-      for (int b = b0; b < b0 + per && b < nb; ++b) {
+      const int b1 = min(b0 + per, nb);
+      int b = b0;
+      for (; b + 4 <= b1; b += 4) {  // loads ahead of the in-order additions
+        double2 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[u] = __ldcg(reinterpret_cast<const double2*>(partials) + b + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { a0 += t[u].x; a1 += t[u].y; }
+      }
+      for (; b < b1; ++b) {
         a0 += __ldcg(partials + 2 * (size_t)b);
         a1 += __ldcg(partials + 2 * (size_t)b + 1);
       }
@@ -757,6 +797,182 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
   if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, kz_host, sh, &flag);
 }
 
+// ------------------------------------------------------------------ tridiagonal, FP32, pivots on the fly
+// The FP32 form of the solves above for the mixed-precision paths, without a
+// pivot table.  The pivots of T_{i'j'}/kappa_ref^z depend on the column only
+// through sigma = s_{i'j'}/kappa_ref^z and the Dirichlet corners (Sec. 3.2:
+// diagonal sigma + 2 inside, sigma + 1 + 2 kappa_in/kappa_z at k = 0 and
+// sigma + 1 + 2 kappa_out/kappa_z at k = n2-1), so each thread generates them
+// as it sweeps.  The pivot is carried as d_k = 1 + e_k with
+//   e_0 = sigma + a_in,   e_k = sigma + e_{k-1} h_{k-1},   h_k = 1 / (1 + e_k)
+// (the recurrence d_k = a - 1/d_{k-1} rewritten with 1 - h = e h), and the
+// last pivot as d = sigma + a_out + e h.  Every term is positive, so no
+// cancellation occurs: for the slowly converging low modes (sigma -> 0) the
+// direct FP32 form a - h_{k-1} loses up to 1e-2 of the solution over 1000
+// planes, this form stays within a few 1e-6, as the FP64 table rounded to FP32.
+// The forward sweep keeps the state (e, y) at the start of every chunk of
+// kTriChunk planes in ck; the backward sweep walks the chunks downwards,
+// regenerates each chunk's h_k and y_k from its checkpoint in registers (the
+// same operations on the same values, so bit-identical) and runs
+// z_k = h_k (y_k + z_{k+1}) down it.
+// Traffic per cell: r^ twice, z once (and r_old once for MODE 2) plus
+// 2 x 8 / kTriChunk bytes of checkpoints, against r^, y twice, h twice, z
+// (and r_new, r_old) for the table-driven kernel.  in and out may be the same
+// buffer: each chunk's r^ (and the next lower chunk's, prefetched) is read
+// before the chunk's z is written, and the chunks below are read later.
+// ck holds (ceil(n2 / kTriChunk) - 1) * plane pairs.
+// MODE as k_tridiag; MODE 2 reads r_old (the previous iteration's r^, kept by
+// the caller) for z_new . r_old.
+constexpr int kTriChunk = 8;
+
+struct TriCol {
+  float sig;     // sigma
+  float first;   // sigma + a_in (n2 = 1: the whole diagonal sigma + a_in + a_out)
+  float last;    // sigma + a_out
+};
+// 1/d for the pivots (d >= 1 away from the corners, always > 0 and finite):
+// the hardware approximation refined by one Newton-Raphson step
+// r <- r + r (1 - d r), which leaves an error within about one ulp.  Both
+// sweeps use this same function, so the regenerated pivots are bit-identical.
+__device__ __forceinline__ float tri_rcp(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+// One plane of the forward recurrence: y_k = r_k + h_{k-1} y_{k-1}, then the
+// pivot of plane k.  State before plane 0: e = h = y = 0.
+__device__ __forceinline__ void tri_step(const TriCol& a, int k, int n2, float r, float& e,
+                                         float& h, float& y) {
+  y = fmaf(h, y, r);
+  float d;
+  if (n2 == 1) {
+    d = a.first;
+  } else if (k == n2 - 1) {
+    d = fmaf(e, h, a.last);
+  } else {
+    e = fmaf(e, h, k == 0 ? a.first : a.sig);
+    d = 1.0f + e;
+  }
+  h = tri_rcp(d);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_tridiag_otf(Geometry g, PcgState* st, const float* in,
+                                                    float* out, float2* __restrict__ ck,
+                                                    const double* __restrict__ lam0,
+                                                    const double* __restrict__ lam1,
+                                                    const double* __restrict__ kd, double w4,
+                                                    double* partials,
+                                                    const float* __restrict__ rold) {
+  __shared__ double sh[32];
+  __shared__ float coef[4];
+  __shared__ int flag;
+  if (MODE != 0 && st->done) return;
+  if (threadIdx.x == 0) {
+    // kappa_ref ratios, once per block
+    const double kz = kd[2];
+    coef[0] = narrow(kd[0] / kz);
+    coef[1] = narrow(kd[1] / kz);
+    coef[2] = narrow(2.0 * kd[3] / kz);
+    coef[3] = narrow(2.0 * kd[4] / kz);
+  }
+  __syncthreads();
+  const long long s = gidx();
+  double acc = 0.0, acc2 = 0.0;
+  if (s < g.plane) {
+    const int i = (int)(s % g.n0), j = (int)(s / g.n0);
+    TriCol a;
+    a.sig = fmaf(narrow(lam0[i]), coef[0], narrow(lam1[j]) * coef[1]);
+    a.first = a.sig + coef[2];
+    a.last = a.sig + coef[3];
+    if (g.n2 == 1) a.first = a.first + coef[3];
+    const int n2 = g.n2;
+    const int nch = (n2 + kTriChunk - 1) / kTriChunk;
+    const long long pl = g.plane;
+    // Each sweep loads the next chunk's operands before it runs the
+    // recurrence of the current one (one chunk of loads always in flight).
+    float e = 0.f, h = 0.f, y = 0.f, part = 0.f;
+    float tv[kTriChunk];
+#pragma unroll
+    for (int u = 0; u < kTriChunk; ++u)
+      if (u < n2) tv[u] = in[(long long)u * pl + s];
+    for (int ch = 0; ch < nch; ++ch) {
+      const int kb = ch * kTriChunk;
+      float tn[kTriChunk];
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int u = 0; u < kTriChunk; ++u)
+          if (kb + kTriChunk + u < n2) tn[u] = in[(long long)(kb + kTriChunk + u) * pl + s];
+      }
+      if (ch > 0) ck[(long long)(ch - 1) * pl + s] = make_float2(e, y);
+#pragma unroll
+      for (int u = 0; u < kTriChunk; ++u) {
+        const int k = kb + u;
+        if (k < n2) {
+          tri_step(a, k, n2, tv[u], e, h, y);
+          part = fmaf(h * y, y, part);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kTriChunk; ++u) tv[u] = tn[u];
+    }
+    float zn = 0.f, zr = 0.f;
+    // operands of chunk ch: r^ (tv), r_old (ro) and the checkpoint (cp)
+    float ro[kTriChunk];
+    float2 cp = make_float2(0.f, 0.f);
+    auto load_chunk = [&](int ch, float* t_, float* r_, float2& c_) {
+      const int kb = ch * kTriChunk;
+#pragma unroll
+      for (int u = 0; u < kTriChunk; ++u)
+        if (kb + u < n2) {
+          t_[u] = in[(long long)(kb + u) * pl + s];
+          if (MODE == 2) r_[u] = rold[(long long)(kb + u) * pl + s];
+        }
+      c_ = ch > 0 ? ck[(long long)(ch - 1) * pl + s] : make_float2(0.f, 0.f);
+    };
+    load_chunk(nch - 1, tv, ro, cp);
+    for (int ch = nch - 1; ch >= 0; --ch) {
+      const int kb = ch * kTriChunk;
+      float tn[kTriChunk], rn[kTriChunk];
+      float2 cn;
+      if (ch > 0) load_chunk(ch - 1, tn, rn, cn);
+      // state before the chunk: h = 1 / (1 + e) as the forward sweep formed it
+      float ec = cp.x, yc = cp.y, hc = ch > 0 ? tri_rcp(1.0f + cp.x) : 0.f;
+      float hv[kTriChunk], yv[kTriChunk];
+#pragma unroll
+      for (int u = 0; u < kTriChunk; ++u) {
+        const int k = kb + u;
+        if (k < n2) {
+          tri_step(a, k, n2, tv[u], ec, hc, yc);
+          hv[u] = hc;
+          yv[u] = yc;
+        }
+      }
+#pragma unroll
+      for (int u = kTriChunk - 1; u >= 0; --u) {
+        const int k = kb + u;
+        if (k < n2) {
+          zn = hv[u] * (yv[u] + zn);
+          out[(long long)k * pl + s] = zn;
+          if (MODE == 2) zr = fmaf(zn, ro[u], zr);
+        }
+      }
+      if (ch > 0) {
+#pragma unroll
+        for (int u = 0; u < kTriChunk; ++u) {
+          tv[u] = tn[u];
+          if (MODE == 2) ro[u] = rn[u];
+        }
+        cp = cn;
+      }
+    }
+    const double wgt = (i == 0 ? 0.5 : 1.0) * (j == 0 ? 0.5 : 1.0);
+    acc = wgt * widen(part);
+    if (MODE == 2) acc2 = wgt * widen(zr);
+  }
+  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, 1.0, sh, &flag);
+}
+
 // ------------------------------------------------------------------ backward DCT along axis 0
 // u = scale * (backward DCT of t along axis 0), then by MODE:
 // 0: z = u (TZ).
@@ -845,13 +1061,10 @@ __global__ void k_flux(Geometry g, const double* __restrict__ x, const double* _
   double vals[5];
   for (int e = 0; e < 5; ++e) vals[e] = block_sum(a[e], sh);
   if (publish_values(partials, 5, vals, 5, &st->cnt[kCntFlux], &flag)) {
+    double tot[5];
+    for (int e = 0; e < 5; ++e) tot[e] = sum_partials(partials + e, (int)nblocks(), 5, sh);
     if (threadIdx.x == 0) {
-      const unsigned int nb = nblocks();
-      for (int e = 0; e < 5; ++e) {
-        double v = 0.0;
-        for (unsigned int b = 0; b < nb; ++b) v += __ldcg(partials + 5 * (size_t)b + e);
-        st->res[e] = v;
-      }
+      for (int e = 0; e < 5; ++e) st->res[e] = tot[e];
       st->cnt[kCntFlux] = 0;
     }
   }
@@ -1084,13 +1297,21 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 unsigned int matvec_blocks(const Geometry& g) { return grid_for(g.n, 256, 148 * 16); }
 // 32 x 8 (i, j) tiles; planes per block chosen so that there are at most
 // about 4736 blocks (32 per SM), but every tile column gets a block.
+// Planes per thread: enough blocks for 32 warps on each of the 148 SMs, but
+// at least 8 planes (a thread's first plane costs three w loads and one extra
+// face flux, which short marches do not amortise; measured 2.7x faster at
+// 128^3 than 2 planes), and 16 where that still leaves two waves of blocks.
 static dim3 matvec_df_grid(const Geometry& g, int* kchunk) {
   const long long bx = (g.n0 + 31) / 32, by = (g.n1 + 7) / 8;
   long long nz = 4736 / (bx * by);
   if (nz < 1) nz = 1;
   if (nz > g.n2) nz = g.n2;
-  *kchunk = (int)((g.n2 + nz - 1) / nz);
-  nz = (g.n2 + *kchunk - 1) / *kchunk;
+  long long kc = (g.n2 + nz - 1) / nz;
+  if (kc < 8) kc = 8;
+  if (kc < 16 && bx * by * ((g.n2 + 15) / 16) >= 2 * 4 * 148) kc = 16;
+  if (kc > g.n2) kc = g.n2;
+  *kchunk = (int)kc;
+  nz = (g.n2 + kc - 1) / kc;
   return dim3((unsigned int)bx, (unsigned int)by, (unsigned int)nz);
 }
 unsigned int matvec_df_blocks(const Geometry& g) {
@@ -1316,6 +1537,33 @@ template cudaError_t launch_tridiag<double>(const Geometry&, PcgState*, double*,
 template cudaError_t launch_tridiag<float>(const Geometry&, PcgState*, float*, const float*,
                                            const double*, double, double*, int, float*,
                                            const float*, cudaStream_t);
+
+cudaError_t launch_tridiag_otf(const Geometry& g, PcgState* st, const float* in, float* out,
+                               float2* ck, const double* lam0, const double* lam1,
+                               const double* kd, double* partials, int mode, const float* rold,
+                               cudaStream_t s) {
+  const unsigned int nb = tridiag_blocks(g);
+  const double w4 = 4.0 / ((double)g.n0 * g.n1);
+  switch (mode) {
+    case 0:
+      k_tridiag_otf<0><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
+      break;
+    case 1:
+      k_tridiag_otf<1><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
+      break;
+    case 2:
+      k_tridiag_otf<2><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
+      break;
+    default:
+      k_tridiag_otf<3><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
+      break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+size_t tridiag_ck_pairs(const Geometry& g) {
+  return (size_t)((g.n2 + kTriChunk - 1) / kTriChunk - 1) * (size_t)g.plane;
+}
 
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,

@@ -60,6 +60,14 @@ template <typename R>
 cudaError_t launch_tridiag(const Geometry& g, PcgState* st, R* t, const R* h, const double* kd,
                            double kz_host, double* partials, int mode, R* rnew, const R* rold,
                            cudaStream_t s);
+// FP32 tridiagonal solves with the pivots generated per column (mixed paths):
+// r^ from in, z to out (may be in), checkpoints in ck (tridiag_ck_pairs(g)
+// pairs), kd the device kref; mode as launch_tridiag, rold for mode 2.
+cudaError_t launch_tridiag_otf(const Geometry& g, PcgState* st, const float* in, float* out,
+                               float2* ck, const double* lam0, const double* lam1,
+                               const double* kd, double* partials, int mode, const float* rold,
+                               cudaStream_t s);
+size_t tridiag_ck_pairs(const Geometry& g);
 // mode 2 with x: also x += alpha[par] w (old w) before w is replaced.
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,

@@ -123,13 +123,21 @@ def test_preconditioner_register_resident_lengths(shape):
     assert relmax(host(z), zo) < 2e-5
 
 
-@pytest.mark.parametrize("shape", [(129, 5, 7), (200, 6, 10), (600, 4, 6), (1030, 3, 4)])
-def test_preconditioner_long_loading_axis(shape):
+@pytest.mark.parametrize("shape,ku", [
+    ((129, 5, 7), [0.7, 1.9, 3.1, 0.4, 2.2]),
+    ((200, 6, 10), [0.7, 1.9, 3.1, 0.4, 2.2]),
+    ((600, 4, 6), [0.7, 1.9, 3.1, 0.4, 2.2]),
+    ((1030, 3, 4), [0.7, 1.9, 3.1, 0.4, 2.2]),
+    # kappa_ref^x,y << kappa_ref^z: every column has a small shift
+    # s/kappa_ref^z, whose pivots converge slowly along the loading axis
+    ((1030, 8, 8), [1e-4, 3e-4, 3.0, 0.4, 2.2]),
+    ((600, 6, 5), [1e-6, 1e-6, 2.0, 1e-3, 5.0]),
+])
+def test_preconditioner_long_loading_axis(shape, ku):
     # long tridiagonal systems (up to 1030 planes) in FP64 and FP32
     rng = np.random.default_rng(sum(shape))
     kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
     rve = make(kx, ky, kz)
-    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
     rve.set_reference(2, B.ETC_REF_USER, ku)
     _, fshape = oracle_faces(kx, ky, kz, (1.0, 1.0, 1.0), 2)
     r = rng.standard_normal(fshape)
