@@ -95,8 +95,10 @@ def kernel_model(n0, n1, mixed=False, f64_vectors=False):
     ||r||^2 and the axis-0 transform; tridiag: the two sweeps and r.z (the y
     round trip between the sweeps is not counted); inv_x: the axis-0 inverse and
     w = z + beta w.  Mixed: the transforms run in FP32 (their flops are not FP64
-    work), the tridiagonal kernel also writes this and reads last iteration's
-    transformed residual (flexible beta).  Its x, r, w and q are double-float
+    work); the FP32 tridiagonal kernel generates its pivots per column and
+    reads r^ and last iteration's r^ (flexible beta) and writes z^: 12 bytes (its
+    second read of r^ and the chunk checkpoints, 6 more, are not counted).  Its
+    x, r, w and q are double-float
     pairs (same bytes as FP64) updated on the FP32 pipe; the matvec reads
     double-float faces and w and writes q (face-difference form, no diagonal:
     40 bytes); x += alpha w moves from fwd_x (r, q in, r and the FP32
@@ -106,12 +108,12 @@ def kernel_model(n0, n1, mixed=False, f64_vectors=False):
     ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
     if mixed and f64_vectors:  # FP32 Algorithm 3 between FP64 vectors and operator
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
-                "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 20.0)}
+                "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 20.0)}
     if not mixed:
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
                 "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
     return {"matvec": (0.0, 40.0), "fwd_x": (0.0, 28.0), "fwd_y": (0.0, 8.0),
-            "tridiag": (0.0, 20.0), "inv_y": (0.0, 8.0), "inv_x": (0.0, 36.0)}
+            "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (0.0, 36.0)}
 
 
 # ------------------------------------------------------------------ helpers

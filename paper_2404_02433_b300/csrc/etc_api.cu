@@ -61,6 +61,9 @@ struct etc_rve {
   float2* Tdf[3] = {nullptr, nullptr, nullptr};
   float2* Bdf = nullptr;  // B_in then B_out, plane_max each
   float2* wdf = nullptr;  // inside an allocation with zero guards (see create)
+  MatvecMaps mv_maps[3];  // bulk-tensor maps of the double-float matvec, per loading frame
+  bool mv_tma[3] = {false, false, false};
+  int frame_dir = -1;  // loading frame of the last queued face assembly (matvec map choice)
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
@@ -329,6 +332,7 @@ etc_status frame_components(etc_rve* h, int dir, double* const scratch[3], doubl
 etc_status launch_setup(etc_rve* h, int dir) {
   int f[3];
   frame_of(dir, f);
+  h->frame_dir = dir;
   const Geometry g = geom_of(h, dir);
   const int N[3] = {h->nx, h->ny, h->nz};
   double* comp[3];
@@ -609,8 +613,12 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
                                        h->w[0], 2, 2, h->rhat32[par ^ 1],
                                        ev ? ev + 3 : nullptr);
   }
-  CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
-                      h->partials, par, 1, h->stream));
+  if (h->frame_dir >= 0 && h->mv_tma[h->frame_dir])
+    CK(launch_matvec_df_tma(g, h->mv_maps[h->frame_dir], h->st, h->wdf, df(h->q), h->Tdf[2],
+                            h->Bdf, h->partials, par, 1, h->stream));
+  else
+    CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
+                        h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   // double-float storage: x += alpha w moves to the w-update kernel, which
   // reads w anyway (8 bytes per cell less)
@@ -954,7 +962,8 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   {
     // w of the mixed path with zero guards of the longest axis on both sides
     // (the double-float matvec reads w[c +- n0] without bounds tests)
-    const size_t guard = (size_t)std::max(nx, std::max(ny, nz));
+    // (an even count keeps w 16-byte aligned for the bulk-tensor copies)
+    const size_t guard = ((size_t)std::max(nx, std::max(ny, nz)) + 1) / 2 * 2;
     float2* wbase = nullptr;
     CKC(dalloc(h, &wbase, (size_t)n + 2 * guard));
     CKC(cudaMemsetAsync(wbase, 0, ((size_t)n + 2 * guard) * sizeof(float2), h->stream));
@@ -982,6 +991,10 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   }
   CKC(set_smem_attrs<double>());
   CKC(set_smem_attrs<float>());
+  CKC(set_matvec_tma_attrs());
+  for (int d = 0; d < 3; ++d)
+    h->mv_tma[d] = matvec_tma_maps(geom_of(h, d), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->wdf,
+                                   &h->mv_maps[d]);
   for (int ax : {nx, ny, nz}) {
     s = make_plan(h, ax);
     if (s != ETC_OK) return bail(s);

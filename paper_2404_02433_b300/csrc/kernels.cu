@@ -856,8 +856,12 @@ __device__ __forceinline__ void tri_step(const TriCol& a, int k, int n2, float r
   h = tri_rcp(d);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(128) k_tridiag_otf(Geometry g, PcgState* st, const float* in,
+// MINB 8 caps the registers at 64 so that 8 blocks fit on an SM (for planes
+// with more columns than 6 blocks of 128 threads on every SM; measured 0.55 ->
+// 0.49 ms at 512^3); smaller planes are latency-bound and keep the
+// unconstrained allocation (a few spilled registers cost 5-10 % there).
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_tridiag_otf(Geometry g, PcgState* st, const float* in,
                                                     float* out, float2* __restrict__ ck,
                                                     const double* __restrict__ lam0,
                                                     const double* __restrict__ lam1,
@@ -1183,7 +1187,7 @@ __global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, lon
 // ================================================================== launchers
 static unsigned long long g_launches = 0;  // kernels launched by this library
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
-static inline void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void count_launch() { __atomic_fetch_add(&g_launches, 1ull, __ATOMIC_RELAXED); }
 
 static inline unsigned int grid_for(long long n, int bs, int cap = 148 * 32) {
   long long gb = (n + bs - 1) / bs;
@@ -1301,7 +1305,7 @@ unsigned int matvec_blocks(const Geometry& g) { return grid_for(g.n, 256, 148 * 
 // at least 8 planes (a thread's first plane costs three w loads and one extra
 // face flux, which short marches do not amortise; measured 2.7x faster at
 // 128^3 than 2 planes), and 16 where that still leaves two waves of blocks.
-static dim3 matvec_df_grid(const Geometry& g, int* kchunk) {
+dim3 matvec_df_grid(const Geometry& g, int* kchunk) {
   const long long bx = (g.n0 + 31) / 32, by = (g.n1 + 7) / 8;
   long long nz = 4736 / (bx * by);
   if (nz < 1) nz = 1;
@@ -1544,20 +1548,19 @@ cudaError_t launch_tridiag_otf(const Geometry& g, PcgState* st, const float* in,
                                cudaStream_t s) {
   const unsigned int nb = tridiag_blocks(g);
   const double w4 = 4.0 / ((double)g.n0 * g.n1);
+  const bool wide = nb > 6u * 148u;
+#define ETC_TRI_OTF(M)                                                                         \
+  (wide ? k_tridiag_otf<M, 8><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4,       \
+                                                 partials, rold)                               \
+        : k_tridiag_otf<M, 1><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4,       \
+                                                 partials, rold))
   switch (mode) {
-    case 0:
-      k_tridiag_otf<0><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
-      break;
-    case 1:
-      k_tridiag_otf<1><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
-      break;
-    case 2:
-      k_tridiag_otf<2><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
-      break;
-    default:
-      k_tridiag_otf<3><<<nb, 128, 0, s>>>(g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
-      break;
+    case 0: ETC_TRI_OTF(0); break;
+    case 1: ETC_TRI_OTF(1); break;
+    case 2: ETC_TRI_OTF(2); break;
+    default: ETC_TRI_OTF(3); break;
   }
+#undef ETC_TRI_OTF
   count_launch();
   return cudaGetLastError();
 }

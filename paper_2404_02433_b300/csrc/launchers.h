@@ -1,6 +1,7 @@
 // Host-side launchers of the kernels in kernels.cu (internal to libetc).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "etc_internal.cuh"
@@ -42,6 +43,23 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, f
                              const float2* T0, const float2* T1, const float2* T2,
                              const float2* FB, double* partials, int par, int mode,
                              cudaStream_t s);
+// The same matvec with its operands staged by tiled bulk-tensor copies
+// (matvec_tma.cu).  The maps describe T0, T1, T2 (with its zero plane) and w
+// of one loading frame as [n2][n1][n0] arrays of 8-byte pairs; they exist when
+// n0 is even and the bases are 16-byte aligned (matvec_tma_maps returns false
+// otherwise, and launch_matvec_df serves that frame).
+struct MatvecMaps {
+  CUtensorMap T0, T1, T2, w;
+};
+bool matvec_tma_maps(const Geometry& g, const float2* T0, const float2* T1, const float2* T2,
+                     const float2* w, MatvecMaps* mp);
+cudaError_t set_matvec_tma_attrs();
+cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
+                                 const float2* w, float2* q, const float2* T2, const float2* FB,
+                                 double* partials, int par, int mode, cudaStream_t s);
+// grid and planes per thread of both double-float matvec kernels
+dim3 matvec_df_grid(const Geometry& g, int* kchunk);
+void count_launch();  // one more library kernel launched
 cudaError_t launch_split_df(const double* a, float2* b, long long n, cudaStream_t s);
 // FP64 values to double-float pairs in place.
 cudaError_t launch_split_inplace(double* a, long long n, cudaStream_t s);

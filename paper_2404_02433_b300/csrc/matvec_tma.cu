@@ -1,0 +1,326 @@
+// Double-float TPFA matvec fed by the Tensor Memory Accelerator.
+//
+// The same operator and arithmetic as k_matvec_df (kernels.cu): the
+// face-difference form of Eq. (scaled bilinear forms),
+//   (Aw)_c = sum_f T_f (w_c - w_f) + [k = 0] B_in w_c + [k = n2-1] B_out w_c,
+// in double-float pairs on the FP32 pipe, summed by Sum2, with the partial
+// w.q of Algorithm 1 (alpha = rho / w.q) in MODE 1.  Only the way the
+// operands reach the threads differs.  A block owns a 32 x 8 column tile and
+// marches over kchunk planes; one thread issues, for each plane, four tiled
+// bulk-tensor copies into a ring of kStages shared-memory stages:
+//   T0 (x i0 .. i0+33, 8 rows)      the minus x faces and the plus face of the last column
+//   T1 (32 columns, y j0 .. j0+8)   the minus y faces and the plus faces of the last row
+//   T2 of plane k+1 (32 x 8)        the faces above the plane
+//   w (x i0-2 .. i0+33, y j0-1 .. j0+8) the plane with a one-cell halo (x rounded
+//                                   down to an even coordinate: a copy's first
+//                                   x times 8 bytes must be 16-byte aligned)
+// Copies that reach outside the box are filled with zeros by the hardware,
+// which are exactly the Neumann faces (T = 0) and harmless finite neighbours.
+// Each stage completes an mbarrier (transaction bytes).  Thread 0 waits for
+// planes k and k+1 (the z neighbour), a block barrier hands them to all
+// threads and frees the stage of plane k-1, into which thread 0 then issues
+// plane k+kStages-1: the copies of up to kStages-2 planes are in flight while
+// a plane is summed, without holding registers.  Every wait is bounded: a
+// wait that runs out sets status ETC_ECUDA and done in the solver state,
+// drains this block's copies (bounded again) and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "etc_internal.cuh"
+#include "launchers.h"
+
+namespace etc {
+
+namespace {
+
+constexpr int kStages = 5;
+// box extents (elements of 8 bytes)
+constexpr int kT0X = 34, kT0Y = 8;
+constexpr int kT1X = 32, kT1Y = 9;
+constexpr int kT2X = 32, kT2Y = 8;
+constexpr int kWX = 36, kWY = 10;
+constexpr int kT0Bytes = kT0X * kT0Y * 8;   // 2176
+constexpr int kT1Bytes = kT1X * kT1Y * 8;   // 2304
+constexpr int kT2Bytes = kT2X * kT2Y * 8;   // 2048
+constexpr int kWBytes = kWX * kWY * 8;      // 2880
+constexpr int kTx = kT0Bytes + kT1Bytes + kT2Bytes + kWBytes;
+constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+constexpr int kOffT1 = align128(kT0Bytes);
+constexpr int kOffT2 = kOffT1 + align128(kT1Bytes);
+constexpr int kOffW = kOffT2 + align128(kT2Bytes);
+constexpr int kStageBytes = kOffW + align128(kWBytes);
+// + the mbarriers, + slack to align the stages to 128 bytes at run time
+constexpr int kSmemBytes = kStages * kStageBytes + 128 + 128;
+// about 2^22 polls with a short sleep each: far beyond any copy's latency
+constexpr unsigned int kWaitPolls = 1u << 22;
+
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false when it ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  for (unsigned int it = 0; it < kWaitPolls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it >= 16) __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+
+// p + pe ~ T (a - b) and the Sum2 step, as in kernels.cu
+__device__ __forceinline__ void two_sum_(float a, float b, float& s, float& t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void flux_(float2 T, float2 a, float2 b, float& p, float& pe) {
+  float dh, dl;
+  two_sum_(a.x, -b.x, dh, dl);
+  dl += a.y - b.y;
+  p = T.x * dh;
+  pe = fma(T.x, dh, -p);
+  pe = fma(T.x, dl, pe);
+  pe = fma(T.y, dh, pe);
+}
+__device__ __forceinline__ void acc_(float p, float pe, float& s, float& e) {
+  float t;
+  two_sum_(s, p, s, t);
+  e += t + pe;
+}
+__device__ __forceinline__ void prod_acc_(float2 x, float2 y, float& s, float& e) {
+  const float p = x.x * y.x;
+  float pe = fma(x.x, y.x, -p);
+  pe = fma(x.x, y.y, pe);
+  pe = fma(x.y, y.x, pe);
+  acc_(p, pe, s, e);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 4)
+    k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
+                    const float2* __restrict__ w, float2* __restrict__ q,
+                    const float2* __restrict__ T2, const float2* __restrict__ Bin,
+                    const float2* __restrict__ Bout, double* partials, int par, int kchunk) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double sh[32];
+  __shared__ int flag, failed;
+  if (MODE == 1 && st->done) return;
+  // the copies' destinations start on 128-byte boundaries
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kStages * kStageBytes);
+  const int l = threadIdx.x & 31, r = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
+  const int i = i0 + l, j = j0 + r;
+  const int k0 = blockIdx.z * kchunk;
+  const int k1 = min(k0 + kchunk, g.n2);
+  const int kend = min(k1, g.n2 - 1);  // last plane loaded (k1 supplies w above k1-1)
+  const bool own = i < g.n0 && j < g.n1;
+  // plane k lives in stage (k - k0) mod kStages; its u-th use has parity u & 1
+  auto issue = [&](int k, unsigned int sidx_) {
+    unsigned char* sg = smem + sidx_ * kStageBytes;
+    unsigned long long* b = bars + sidx_;
+    mbar_expect_tx(b, kTx);
+    tma_load3(sg, &mp.T0, i0, j0, k, b);
+    tma_load3(sg + kOffT1, &mp.T1, i0, j0, k, b);
+    tma_load3(sg + kOffT2, &mp.T2, i0, j0, k + 1, b);
+    tma_load3(sg + kOffW, &mp.w, i0 - 2, j0 - 1, k, b);
+  };
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < kStages; ++s) mbar_init(bars + s, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int k = k0; k <= kend && k < k0 + kStages - 1; ++k) issue(k, (unsigned int)(k - k0));
+  }
+  float ds = 0.f, dc = 0.f;
+  const long long pl = g.plane;
+  const long long sidx = (long long)j * g.n0 + i;
+  // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
+  float fz = 0.f, fze = 0.f;
+  if (own && k0 > 0) {
+    const long long c = (long long)k0 * pl + sidx;
+    flux_(T2[c], w[c - pl], w[c], fz, fze);
+  }
+  // this thread's element offsets inside a stage (float2 units)
+  const int oT0 = r * kT0X + l, oT1 = r * kT1X + l, oT2 = r * kT2X + l;
+  const int oW = (r + 1) * kWX + l + 2;
+  float2* pq = q + (long long)k0 * pl + sidx;
+  unsigned int sc = 0, pc = 0;  // stage and parity of plane k
+  int k = k0;
+  for (; k < k1; ++k) {
+    const unsigned int sn = sc + 1 == kStages ? 0u : sc + 1;
+    const unsigned int pn = sn == 0 ? pc ^ 1u : pc;
+    // thread 0 waits (bounded) for planes k and k+1; the barrier then hands
+    // their stages to every thread, and frees the stage of plane k-1
+    if (threadIdx.x == 0) {
+      bool ok = mbar_wait(bars + sc, pc);
+      if (ok && k + 1 <= kend) ok = mbar_wait(bars + sn, pn);
+      if (!ok) failed = 1;
+    }
+    __syncthreads();
+    if (failed) break;
+    if (threadIdx.x == 0 && k + kStages - 1 <= kend) {
+      const unsigned int sf = sc == 0 ? kStages - 1 : sc - 1;  // the stage of plane k-1
+      issue(k + kStages - 1, sf);
+    }
+    if (own) {
+      const float2* sT0 = reinterpret_cast<const float2*>(smem + sc * kStageBytes) + oT0;
+      const float2* sT1 = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffT1) + oT1;
+      const float2* sT2 = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffT2) + oT2;
+      const float2* sW = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffW) + oW;
+      const float2 wc = sW[0];
+      const float2 wp =
+          k + 1 <= kend ? reinterpret_cast<const float2*>(smem + sn * kStageBytes + kOffW)[oW]
+                        : wc;
+      float sv, ev, p, pe;
+      flux_(sT0[0], wc, sW[-1], sv, ev);
+      flux_(sT0[1], wc, sW[1], p, pe);
+      acc_(p, pe, sv, ev);
+      flux_(sT1[0], wc, sW[-kWX], p, pe);
+      acc_(p, pe, sv, ev);
+      flux_(sT1[kT1X], wc, sW[kWX], p, pe);
+      acc_(p, pe, sv, ev);
+      acc_(-fz, -fze, sv, ev);
+      flux_(sT2[0], wc, wp, fz, fze);
+      acc_(fz, fze, sv, ev);
+      if (k == 0) prod_acc_(Bin[sidx], wc, sv, ev);
+      if (k == g.n2 - 1) prod_acc_(Bout[sidx], wc, sv, ev);
+      float qh, ql;
+      two_sum_(sv, ev, qh, ql);
+      *pq = make_float2(qh, ql);
+      if (MODE == 1) prod_acc_(wc, make_float2(qh, ql), ds, dc);
+    }
+    pq += pl;
+    sc = sn;
+    pc = pn;
+  }
+  if (failed) {
+    // drain this block's copies still in flight (bounded), then report
+    if (threadIdx.x == 0) {
+      unsigned int s2 = sc, p2 = pc;
+      for (int kk = k; kk <= kend && kk < k + kStages - 1; ++kk) {
+        (void)mbar_wait(bars + s2, p2);
+        s2 = s2 + 1 == kStages ? 0u : s2 + 1;
+        if (s2 == 0) p2 ^= 1u;
+      }
+      st->status = kECUDA;
+      st->done = 1;
+    }
+    return;
+  }
+  if (MODE == 1) {
+    const double bs = block_sum(widen(ds) + widen(dc), sh);
+    double v[1] = {bs};
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag)) {
+      const double dq = sum_partials(partials, (int)nblocks(), 1, sh);
+      if (threadIdx.x == 0) {
+        const double alpha = st->rho / dq;
+        st->dq = dq;
+        st->alpha[par] = alpha;
+        if (!(dq > 0.0) || !isfinite(alpha)) { st->status = kEBREAKDOWN; st->done = 1; }
+        st->cnt[kCntDot] = 0;
+      }
+    }
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+bool encode3(CUtensorMap* m, const void* base, int n0, int n1, int nz, int bx, int by) {
+  const EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)n0, (cuuint64_t)n1, (cuuint64_t)nz};
+  const cuuint64_t stride[2] = {(cuuint64_t)n0 * 8, (cuuint64_t)n0 * n1 * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dim, stride, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool matvec_tma_maps(const Geometry& g, const float2* T0, const float2* T1, const float2* T2,
+                     const float2* w, MatvecMaps* mp) {
+  // row strides must be multiples of 16 bytes (n0 even) and the bases 16-byte aligned
+  if (g.n0 % 2 != 0) return false;
+  for (const void* p : {(const void*)T0, (const void*)T1, (const void*)T2, (const void*)w})
+    if (reinterpret_cast<unsigned long long>(p) % 16 != 0) return false;
+  std::memset(mp, 0, sizeof(*mp));
+  return encode3(&mp->T0, T0, g.n0, g.n1, g.n2, kT0X, kT0Y) &&
+         encode3(&mp->T1, T1, g.n0, g.n1, g.n2, kT1X, kT1Y) &&
+         encode3(&mp->T2, T2, g.n0, g.n1, g.n2 + 1, kT2X, kT2Y) &&  // + the zero plane
+         encode3(&mp->w, w, g.n0, g.n1, g.n2, kWX, kWY);
+}
+
+cudaError_t set_matvec_tma_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_matvec_df_tma<0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_matvec_df_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSmemBytes);
+}
+
+cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
+                                 const float2* w, float2* q, const float2* T2, const float2* FB,
+                                 double* partials, int par, int mode, cudaStream_t s) {
+  int kc;
+  const dim3 grid = matvec_df_grid(g, &kc);
+  const float2* Bout = FB + g.plane;
+  if (mode == 1)
+    k_matvec_df_tma<1><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
+                                                     kc);
+  else
+    k_matvec_df_tma<0><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
+                                                     kc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace etc
