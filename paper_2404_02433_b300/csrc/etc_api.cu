@@ -64,6 +64,7 @@ struct etc_rve {
   MatvecMaps mv_maps[3];  // bulk-tensor maps of the double-float matvec, per loading frame
   bool mv_tma[3] = {false, false, false};
   int frame_dir = -1;  // loading frame of the last queued face assembly (matvec map choice)
+  unsigned int tma_tx_extra = 0;  // test hook, see tma_tx_extra_env
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
@@ -107,6 +108,14 @@ etc_status fail(etc_rve* h, etc_status s, const std::string& msg) {
 int alloc_budget() {
   const char* s = std::getenv("ETC_FAIL_ALLOC_AFTER");
   return s ? std::atoi(s) : -1;
+}
+
+// Bounded-wait test hook: ETC_TEST_TMA_TX_EXTRA=b (read at create) makes every
+// stage of the bulk-tensor matvec expect b bytes more than its copies deliver,
+// so its waits run out and the solve ends with ETC_ECUDA (no fault involved).
+unsigned int tma_tx_extra_env() {
+  const char* s = std::getenv("ETC_TEST_TMA_TX_EXTRA");
+  return s ? (unsigned int)std::atoi(s) : 0u;
 }
 
 cudaError_t dev_alloc(etc_rve* h, void** p, size_t bytes) {
@@ -615,7 +624,7 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
   }
   if (h->frame_dir >= 0 && h->mv_tma[h->frame_dir])
     CK(launch_matvec_df_tma(g, h->mv_maps[h->frame_dir], h->st, h->wdf, df(h->q), h->Tdf[2],
-                            h->Bdf, h->partials, par, 1, h->stream));
+                            h->Bdf, h->partials, par, 1, h->stream, h->tma_tx_extra));
   else
     CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
                         h->partials, par, 1, h->stream));
@@ -758,6 +767,8 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
   fill_results(h, dir, rhs, o.true_residual, st, ms_setup, ms_solve, kappa_eff, info);
   if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
   if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
+  if (st.status == ETC_ECUDA)
+    return fail(h, ETC_ECUDA, "a bounded device wait ran out (matvec bulk-tensor copies)");
   return ETC_OK;
 }
 
@@ -992,6 +1003,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(set_smem_attrs<double>());
   CKC(set_smem_attrs<float>());
   CKC(set_matvec_tma_attrs());
+  h->tma_tx_extra = tma_tx_extra_env();
   for (int d = 0; d < 3; ++d)
     h->mv_tma[d] = matvec_tma_maps(geom_of(h, d), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->wdf,
                                    &h->mv_maps[d]);

@@ -56,7 +56,8 @@ bool matvec_tma_maps(const Geometry& g, const float2* T0, const float2* T1, cons
 cudaError_t set_matvec_tma_attrs();
 cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
                                  const float2* w, float2* q, const float2* T2, const float2* FB,
-                                 double* partials, int par, int mode, cudaStream_t s);
+                                 double* partials, int par, int mode, cudaStream_t s,
+                                 unsigned int tx_extra = 0);
 // grid and planes per thread of both double-float matvec kernels
 dim3 matvec_df_grid(const Geometry& g, int* kchunk);
 void count_launch();  // one more library kernel launched

@@ -22,7 +22,10 @@
 // plane k+kStages-1: the copies of up to kStages-2 planes are in flight while
 // a plane is summed, without holding registers.  Every wait is bounded: a
 // wait that runs out sets status ETC_ECUDA and done in the solver state,
-// drains this block's copies (bounded again) and returns.
+// drains this block's copies (bounded again) and returns.  tx_extra (0 in
+// use) adds bytes that no copy delivers to every stage's expected count: a
+// test sets it (ETC_TEST_TMA_TX_EXTRA, read at create) so that the waits run
+// out and the error path runs without any fault.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -53,8 +56,10 @@ constexpr int kOffW = kOffT2 + align128(kT2Bytes);
 constexpr int kStageBytes = kOffW + align128(kWBytes);
 // + the mbarriers, + slack to align the stages to 128 bytes at run time
 constexpr int kSmemBytes = kStages * kStageBytes + 128 + 128;
-// about 2^22 polls with a short sleep each: far beyond any copy's latency
-constexpr unsigned int kWaitPolls = 1u << 22;
+// A wait gives up after 0.5 s of wall time (a plane's copies take
+// microseconds), with an iteration cap as a second bound.
+constexpr unsigned long long kWaitNs = 500000000ull;
+constexpr unsigned int kWaitPolls = 1u << 24;
 
 __device__ __forceinline__ unsigned int smem_addr(const void* p) {
   return (unsigned int)__cvta_generic_to_shared(p);
@@ -68,22 +73,30 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                "r"(bytes)
                : "memory");
 }
+// one test of the phase; the thread may be suspended up to ~2 us meanwhile
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
   unsigned int ok;
   asm volatile(
       "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(2000u)
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long wall_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // bounded wait for the phase of the given parity; false when it ran out
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = wall_ns();
   for (unsigned int it = 0; it < kWaitPolls; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it >= 16) __nanosleep(64);
+    if (wall_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }
@@ -125,12 +138,15 @@ __device__ __forceinline__ void prod_acc_(float2 x, float2 y, float& s, float& e
   acc_(p, pe, s, e);
 }
 
+}  // namespace
+
 template <int MODE>
 __global__ void __launch_bounds__(256, 4)
     k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
                     const float2* __restrict__ w, float2* __restrict__ q,
                     const float2* __restrict__ T2, const float2* __restrict__ Bin,
-                    const float2* __restrict__ Bout, double* partials, int par, int kchunk) {
+                    const float2* __restrict__ Bout, double* partials, int par, int kchunk,
+                    unsigned int tx_extra) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double sh[32];
   __shared__ int flag, failed;
@@ -149,7 +165,7 @@ __global__ void __launch_bounds__(256, 4)
   auto issue = [&](int k, unsigned int sidx_) {
     unsigned char* sg = smem + sidx_ * kStageBytes;
     unsigned long long* b = bars + sidx_;
-    mbar_expect_tx(b, kTx);
+    mbar_expect_tx(b, kTx + tx_extra);
     tma_load3(sg, &mp.T0, i0, j0, k, b);
     tma_load3(sg + kOffT1, &mp.T1, i0, j0, k, b);
     tma_load3(sg + kOffT2, &mp.T2, i0, j0, k + 1, b);
@@ -254,6 +270,8 @@ __global__ void __launch_bounds__(256, 4)
   }
 }
 
+namespace {
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -309,16 +327,17 @@ cudaError_t set_matvec_tma_attrs() {
 
 cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
                                  const float2* w, float2* q, const float2* T2, const float2* FB,
-                                 double* partials, int par, int mode, cudaStream_t s) {
+                                 double* partials, int par, int mode, cudaStream_t s,
+                                 unsigned int tx_extra) {
   int kc;
   const dim3 grid = matvec_df_grid(g, &kc);
   const float2* Bout = FB + g.plane;
   if (mode == 1)
     k_matvec_df_tma<1><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
-                                                     kc);
+                                                     kc, tx_extra);
   else
     k_matvec_df_tma<0><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
-                                                     kc);
+                                                     kc, tx_extra);
   count_launch();
   return cudaGetLastError();
 }

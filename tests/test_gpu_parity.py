@@ -354,6 +354,28 @@ def test_double_float_split_is_exact():
     assert err.max() <= 2.0 ** -47
 
 
+def test_bulk_copy_wait_runs_out_reports_ecuda_and_recovers():
+    # ETC_TEST_TMA_TX_EXTRA=16 (read at create): every stage of the
+    # bulk-tensor matvec expects 16 bytes that no copy delivers, so its bounded
+    # waits (0.5 s) run out; no fault is involved.  The solve must end with
+    # ETC_ECUDA and a message, and a new handle must solve normally.
+    import os
+    k, _ = M.random_spheres((16, 16, 32), (2, 4), 0.3, 5, 1.0, 10.0)
+    os.environ["ETC_TEST_TMA_TX_EXTRA"] = "16"
+    try:
+        rve = make(k)
+    finally:
+        os.environ.pop("ETC_TEST_TMA_TX_EXTRA", None)
+    with pytest.raises(B.EtcError) as e:
+        rve.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
+    assert e.value.status == B.ETC_ECUDA and "wait ran out" in str(e.value)
+    rve.close()
+    rve2 = make(k)
+    kap_m, info = rve2.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
+    kap_d, _ = rve2.solve(2, rtol=1e-10)
+    assert info["status"] == B.ETC_OK and abs(kap_m - kap_d) <= 1e-6 * kap_d
+
+
 def test_allocation_failure_reports_enomem_and_recovers():
     # ETC_FAIL_ALLOC_AFTER=k: the (k+1)-th device allocation of a handle fails;
     # creation must report ETC_ENOMEM and release what it took, and the next
