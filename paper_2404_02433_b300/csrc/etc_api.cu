@@ -65,6 +65,8 @@ struct etc_rve {
   bool mv_tma[3] = {false, false, false};
   int frame_dir = -1;  // loading frame of the last queued face assembly (matvec map choice)
   unsigned int tma_tx_extra = 0;  // test hook, see tma_tx_extra_env
+  CUtensorMap rhat_maps[3][2];    // bulk-tensor maps of rhat32[0..1], per loading frame
+  bool tri_tma[3] = {false, false, false};
   double* xsol[3] = {nullptr, nullptr, nullptr};
   double* lam = nullptr;                          // adjoint field (etc_gradient)
   double *gen_in = nullptr, *gen_out = nullptr;   // face data of etc_solve_general
@@ -531,8 +533,18 @@ etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
     CK(launch_tridiag<R>(g, h->st, t, hp, kref_dev(h), 1.0, h->partials, tri_mode, nullptr,
                          nullptr, h->stream));
   } else {
-    CK(launch_tridiag_otf(g, h->st, t, zt, h->ck32, h->plans[g.n0].lam, h->plans[g.n1].lam,
-                          kref_dev(h), h->partials, tri_mode, rold, h->stream));
+    // the flexible-PCG solves read r^ from one rhat32 buffer (and r_old from
+    // the other): with maps for this frame they take the bulk-tensor kernel
+    const int fd = h->frame_dir;
+    const int ti = t == h->rhat32[0] ? 0 : (t == h->rhat32[1] ? 1 : -1);
+    if ((tri_mode == 2 || tri_mode == 3) && fd >= 0 && h->tri_tma[fd] && ti >= 0 &&
+        (tri_mode == 3 || rold == h->rhat32[ti ^ 1]) && zt != t)
+      CK(launch_tridiag_tma(g, h->rhat_maps[fd][ti], h->rhat_maps[fd][ti ^ 1], h->st, zt,
+                            h->ck32, h->plans[g.n0].lam, h->plans[g.n1].lam, kref_dev(h),
+                            h->partials, tri_mode, h->stream));
+    else
+      CK(launch_tridiag_otf(g, h->st, t, zt, h->ck32, h->plans[g.n0].lam, h->plans[g.n1].lam,
+                            kref_dev(h), h->partials, tri_mode, rold, h->stream));
   }
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   CK(launch_dct_y<R>(g, p1, h->st, zt, 1, check, h->stream, h->tiles[2]));
@@ -1003,7 +1015,13 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   CKC(set_smem_attrs<double>());
   CKC(set_smem_attrs<float>());
   CKC(set_matvec_tma_attrs());
+  CKC(set_tridiag_tma_attrs());
   h->tma_tx_extra = tma_tx_extra_env();
+  for (int d = 0; d < 3; ++d) {
+    const Geometry gd = geom_of(h, d);
+    h->tri_tma[d] = tridiag_tma_map(gd, h->rhat32[0], &h->rhat_maps[d][0]) &&
+                    tridiag_tma_map(gd, h->rhat32[1], &h->rhat_maps[d][1]);
+  }
   for (int d = 0; d < 3; ++d)
     h->mv_tma[d] = matvec_tma_maps(geom_of(h, d), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->wdf,
                                    &h->mv_maps[d]);

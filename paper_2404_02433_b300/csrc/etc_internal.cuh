@@ -407,3 +407,120 @@ template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
 }  // namespace etc
+
+namespace etc {
+
+// ---------------------------------------------------------------- tridiagonal solves
+// (kernels.cu and tridiag_tma.cu)
+
+// End of the tridiagonal kernels: block partials of rho (and of z_new . r_old
+// for MODE 2), summed in block order by the last block, which forms beta.
+template <int MODE>
+__device__ __forceinline__ void tridiag_tail(double acc, double acc2, PcgState* st,
+                                             double* partials, double w4, const double* kd,
+                                             double kz_host, double* sh, int* flag_) {
+  int& flag = *flag_;
+  double v[2];
+  v[0] = block_sum(acc, sh);
+  v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
+  if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
+    const double wscale = w4 / (kd ? kd[2] : kz_host);
+    double rho_new = 0.0, zr_old = 0.0;
+    {
+      // fixed-order sums of both columns
+      const int nb = (int)nblocks();
+      double a0 = 0.0, a1 = 0.0;
+      const int per = (nb + blockDim.x - 1) / blockDim.x;
+      const int b0 = threadIdx.x * per;
+      const int b1 = min(b0 + per, nb);
+      int b = b0;
+      for (; b + 4 <= b1; b += 4) {  // loads ahead of the in-order additions
+        double2 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[u] = __ldcg(reinterpret_cast<const double2*>(partials) + b + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { a0 += t[u].x; a1 += t[u].y; }
+      }
+      for (; b < b1; ++b) {
+        a0 += __ldcg(partials + 2 * (size_t)b);
+        a1 += __ldcg(partials + 2 * (size_t)b + 1);
+      }
+      rho_new = wscale * block_sum(a0, sh);
+      zr_old = wscale * block_sum(a1, sh);
+    }
+    if (threadIdx.x == 0) {
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
+      }
+      if (st->phase == 0 || MODE == 3) {
+        st->beta = 0.0;
+        st->phase = 1;
+      } else if (MODE == 1) {
+        st->beta = rho_new / st->rho;
+      } else {
+        st->beta = (rho_new - zr_old) / st->rho;
+        st->zq = zr_old;
+      }
+      st->rho = rho_new;
+      if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
+      st->cnt[kCntRho] = 0;
+    }
+  }
+}
+
+// FP32 solves with the pivots generated per column (k_tridiag_otf in
+// kernels.cu, k_tridiag_tma in tridiag_tma.cu): the column's constants, one
+// step of the forward recurrence, and the chunk length of the checkpoints.
+constexpr int kTriChunk = 8;
+
+struct TriCol {
+  float sig;     // sigma
+  float first;   // sigma + a_in (n2 = 1: the whole diagonal sigma + a_in + a_out)
+  float last;    // sigma + a_out
+};
+// 1/d for the pivots (d >= 1 away from the corners, always > 0 and finite):
+// the hardware approximation refined by one Newton-Raphson step
+// r <- r + r (1 - d r), which leaves an error within about one ulp.  Both
+// sweeps use this same function, so the regenerated pivots are bit-identical.
+__device__ __forceinline__ float tri_rcp(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+// kappa_ref ratios kx/kz, ky/kz, 2 kin/kz, 2 kout/kz (one thread per block)
+__device__ __forceinline__ void tri_coef(const double* kd, float* coef) {
+  const double kz = kd[2];
+  coef[0] = narrow(kd[0] / kz);
+  coef[1] = narrow(kd[1] / kz);
+  coef[2] = narrow(2.0 * kd[3] / kz);
+  coef[3] = narrow(2.0 * kd[4] / kz);
+}
+// the constants of column (i, j) from the eigenvalue tables and the ratios
+__device__ __forceinline__ TriCol tri_col(int i, int j, int n2, const double* lam0,
+                                          const double* lam1, const float* coef) {
+  TriCol a;
+  a.sig = fmaf(narrow(lam0[i]), coef[0], narrow(lam1[j]) * coef[1]);
+  a.first = a.sig + coef[2];
+  a.last = a.sig + coef[3];
+  if (n2 == 1) a.first = a.first + coef[3];
+  return a;
+}
+// One plane of the forward recurrence: y_k = r_k + h_{k-1} y_{k-1}, then the
+// pivot of plane k.  State before plane 0: e = h = y = 0.
+__device__ __forceinline__ void tri_step(const TriCol& a, int k, int n2, float r, float& e,
+                                         float& h, float& y) {
+  y = fmaf(h, y, r);
+  float d;
+  if (n2 == 1) {
+    d = a.first;
+  } else if (k == n2 - 1) {
+    d = fmaf(e, h, a.last);
+  } else {
+    e = fmaf(e, h, k == 0 ? a.first : a.sig);
+    d = 1.0f + e;
+  }
+  h = tri_rcp(d);
+}
+
+}  // namespace etc

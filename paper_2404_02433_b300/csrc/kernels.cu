@@ -659,62 +659,6 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
   else dct2_run<R>(p, y, a, b, store);
 }
 
-// End of the tridiagonal kernels: block partials of rho (and of z_new . r_old
-// for MODE 2), summed in block order by the last block, which forms beta.
-template <int MODE>
-__device__ __forceinline__ void tridiag_tail(double acc, double acc2, PcgState* st,
-                                             double* partials, double w4, const double* kd,
-                                             double kz_host, double* sh, int* flag_) {
-  int& flag = *flag_;
-  double v[2];
-  v[0] = block_sum(acc, sh);
-  v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
-  if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
-    const double wscale = w4 / (kd ? kd[2] : kz_host);
-    double rho_new = 0.0, zr_old = 0.0;
-    {
-      // fixed-order sums of both columns
-      const int nb = (int)nblocks();
-      double a0 = 0.0, a1 = 0.0;
-      const int per = (nb + blockDim.x - 1) / blockDim.x;
-      const int b0 = threadIdx.x * per;
-      const int b1 = min(b0 + per, nb);
-      int b = b0;
-      for (; b + 4 <= b1; b += 4) {  // loads ahead of the in-order additions
-        double2 t[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          t[u] = __ldcg(reinterpret_cast<const double2*>(partials) + b + u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { a0 += t[u].x; a1 += t[u].y; }
-      }
-      for (; b < b1; ++b) {
-        a0 += __ldcg(partials + 2 * (size_t)b);
-        a1 += __ldcg(partials + 2 * (size_t)b + 1);
-      }
-      rho_new = wscale * block_sum(a0, sh);
-      zr_old = wscale * block_sum(a1, sh);
-    }
-    if (threadIdx.x == 0) {
-      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-        if (st->phase == 0 || !(rho_new == 0.0)) { st->status = kEBREAKDOWN; st->done = 1; }
-      }
-      if (st->phase == 0 || MODE == 3) {
-        st->beta = 0.0;
-        st->phase = 1;
-      } else if (MODE == 1) {
-        st->beta = rho_new / st->rho;
-      } else {
-        st->beta = (rho_new - zr_old) / st->rho;
-        st->zq = zr_old;
-      }
-      st->rho = rho_new;
-      if (!isfinite(st->beta)) { st->status = kEBREAKDOWN; st->done = 1; }
-      st->cnt[kCntRho] = 0;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ tridiagonal along axis 2
 // Forward sweep y_k = r^_k + h_{k-1} y_{k-1}, backward z_k = h_k (y_k + z_{k+1})
 // solves (T_{i'j'}/kappa_ref^z) z = r^.  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
@@ -823,39 +767,6 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 // ck holds (ceil(n2 / kTriChunk) - 1) * plane pairs.
 // MODE as k_tridiag; MODE 2 reads r_old (the previous iteration's r^, kept by
 // the caller) for z_new . r_old.
-constexpr int kTriChunk = 8;
-
-struct TriCol {
-  float sig;     // sigma
-  float first;   // sigma + a_in (n2 = 1: the whole diagonal sigma + a_in + a_out)
-  float last;    // sigma + a_out
-};
-// 1/d for the pivots (d >= 1 away from the corners, always > 0 and finite):
-// the hardware approximation refined by one Newton-Raphson step
-// r <- r + r (1 - d r), which leaves an error within about one ulp.  Both
-// sweeps use this same function, so the regenerated pivots are bit-identical.
-__device__ __forceinline__ float tri_rcp(float d) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-  return fmaf(r, fmaf(-d, r, 1.0f), r);
-}
-// One plane of the forward recurrence: y_k = r_k + h_{k-1} y_{k-1}, then the
-// pivot of plane k.  State before plane 0: e = h = y = 0.
-__device__ __forceinline__ void tri_step(const TriCol& a, int k, int n2, float r, float& e,
-                                         float& h, float& y) {
-  y = fmaf(h, y, r);
-  float d;
-  if (n2 == 1) {
-    d = a.first;
-  } else if (k == n2 - 1) {
-    d = fmaf(e, h, a.last);
-  } else {
-    e = fmaf(e, h, k == 0 ? a.first : a.sig);
-    d = 1.0f + e;
-  }
-  h = tri_rcp(d);
-}
-
 // MINB 8 caps the registers at 64 so that 8 blocks fit on an SM (for planes
 // with more columns than 6 blocks of 128 threads on every SM; measured 0.55 ->
 // 0.49 ms at 512^3); smaller planes are latency-bound and keep the
@@ -872,24 +783,13 @@ __global__ void __launch_bounds__(128, MINB) k_tridiag_otf(Geometry g, PcgState*
   __shared__ float coef[4];
   __shared__ int flag;
   if (MODE != 0 && st->done) return;
-  if (threadIdx.x == 0) {
-    // kappa_ref ratios, once per block
-    const double kz = kd[2];
-    coef[0] = narrow(kd[0] / kz);
-    coef[1] = narrow(kd[1] / kz);
-    coef[2] = narrow(2.0 * kd[3] / kz);
-    coef[3] = narrow(2.0 * kd[4] / kz);
-  }
+  if (threadIdx.x == 0) tri_coef(kd, coef);  // kappa_ref ratios, once per block
   __syncthreads();
   const long long s = gidx();
   double acc = 0.0, acc2 = 0.0;
   if (s < g.plane) {
     const int i = (int)(s % g.n0), j = (int)(s / g.n0);
-    TriCol a;
-    a.sig = fmaf(narrow(lam0[i]), coef[0], narrow(lam1[j]) * coef[1]);
-    a.first = a.sig + coef[2];
-    a.last = a.sig + coef[3];
-    if (g.n2 == 1) a.first = a.first + coef[3];
+    const TriCol a = tri_col(i, j, g.n2, lam0, lam1, coef);
     const int n2 = g.n2;
     const int nch = (n2 + kTriChunk - 1) / kTriChunk;
     const long long pl = g.plane;

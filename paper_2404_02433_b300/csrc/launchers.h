@@ -58,6 +58,16 @@ cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgSta
                                  const float2* w, float2* q, const float2* T2, const float2* FB,
                                  double* partials, int par, int mode, cudaStream_t s,
                                  unsigned int tx_extra = 0);
+// FP32 tridiagonal solves of the flexible PCG (modes 2 and 3 of
+// launch_tridiag_otf) with r^ and r_old staged by tiled bulk-tensor copies
+// (tridiag_tma.cu).  The maps view an FP32 field as [n2][plane]; they exist
+// when plane is a multiple of 4 and the base 16-byte aligned.
+bool tridiag_tma_map(const Geometry& g, const float* buf, CUtensorMap* m);
+cudaError_t set_tridiag_tma_attrs();
+cudaError_t launch_tridiag_tma(const Geometry& g, const CUtensorMap& min_,
+                               const CUtensorMap& mold, PcgState* st, float* out, float2* ck,
+                               const double* lam0, const double* lam1, const double* kd,
+                               double* partials, int mode, cudaStream_t s);
 // grid and planes per thread of both double-float matvec kernels
 dim3 matvec_df_grid(const Geometry& g, int* kchunk);
 void count_launch();  // one more library kernel launched

@@ -33,6 +33,7 @@
 
 #include "etc_internal.cuh"
 #include "launchers.h"
+#include "tma.cuh"
 
 namespace etc {
 
@@ -56,60 +57,6 @@ constexpr int kOffW = kOffT2 + align128(kT2Bytes);
 constexpr int kStageBytes = kOffW + align128(kWBytes);
 // + the mbarriers, + slack to align the stages to 128 bytes at run time
 constexpr int kSmemBytes = kStages * kStageBytes + 128 + 128;
-// A wait gives up after 0.5 s of wall time (a plane's copies take
-// microseconds), with an iteration cap as a second bound.
-constexpr unsigned long long kWaitNs = 500000000ull;
-constexpr unsigned int kWaitPolls = 1u << 24;
-
-__device__ __forceinline__ unsigned int smem_addr(const void* p) {
-  return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-// one test of the phase; the thread may be suspended up to ~2 us meanwhile
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
-  unsigned int ok;
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity), "r"(2000u)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long wall_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// bounded wait for the phase of the given parity; false when it ran out
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = wall_ns();
-  for (unsigned int it = 0; it < kWaitPolls; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (wall_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z,
-                                          unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
-      "r"(smem_addr(bar))
-      : "memory");
-}
-
 // p + pe ~ T (a - b) and the Sum2 step, as in kernels.cu
 __device__ __forceinline__ void two_sum_(float a, float b, float& s, float& t) {
   s = a + b;
@@ -272,34 +219,13 @@ __global__ void __launch_bounds__(256, 4)
 
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encoder() {
-  static EncodeTiled fn = [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      p = nullptr;
-    return reinterpret_cast<EncodeTiled>(p);
-  }();
-  return fn;
-}
-
 bool encode3(CUtensorMap* m, const void* base, int n0, int n1, int nz, int bx, int by) {
-  const EncodeTiled enc = encoder();
-  if (!enc) return false;
-  const cuuint64_t dim[3] = {(cuuint64_t)n0, (cuuint64_t)n1, (cuuint64_t)nz};
-  const cuuint64_t stride[2] = {(cuuint64_t)n0 * 8, (cuuint64_t)n0 * n1 * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-  const cuuint32_t es[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<void*>(base), dim, stride, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  const unsigned long long dim[3] = {(unsigned long long)n0, (unsigned long long)n1,
+                                     (unsigned long long)nz};
+  const unsigned long long stride[2] = {(unsigned long long)n0 * 8,
+                                        (unsigned long long)n0 * n1 * 8};
+  const unsigned int box[3] = {(unsigned int)bx, (unsigned int)by, 1};
+  return tma_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dim, stride, box);
 }
 
 }  // namespace
