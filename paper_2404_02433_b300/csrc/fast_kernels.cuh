@@ -63,14 +63,16 @@ template <int N, int NT> struct FastX {
   static_assert(L * Fast<N>::P == NT, "rows per block");
 };
 
-template <typename R> struct FastCols {  // columns per block of the axis-1 passes
-  static constexpr int C = sizeof(R) == 4 ? 32 : 16;
+template <typename R, int N> struct FastCols {  // columns per block of the axis-1 passes
+  // FP32: 16 columns from n = 512 on (measured at 512^3: backward pass 0.274 ->
+  // 0.248 ms), 32 below (16 was 5-10 % slower at 192^3 and 256^3); FP64: 16
+  static constexpr int C = sizeof(R) == 4 ? (N >= 512 ? 16 : 32) : 16;
   // resident blocks per SM asked of the compiler: 1024 (FP32) or 512 (FP64)
   // threads, i.e. at most 64 or 128 registers per thread; half that for
   // Q > 16 values per thread
-  static constexpr int MinBlocks(int n) {
-    return ((sizeof(R) == 4 ? 1024 : 512) >> ((n / 2) / fast_p(n / 2) > 16 ? 1 : 0)) /
-           (C * fast_p(n / 2));
+  static constexpr int MinBlocks() {
+    return ((sizeof(R) == 4 ? 1024 : 512) >> ((N / 2) / fast_p(N / 2) > 16 ? 1 : 0)) /
+           (C * fast_p(N / 2));
   }
 };
 
@@ -148,10 +150,10 @@ __device__ __forceinline__ int vrow(int a) {
 // ---------------------------------------------------------------- axis 1
 // In place on t: every block owns C adjacent columns of one plane k.
 template <typename R, int N, int INV>
-__global__ void __launch_bounds__(FastCols<R>::C * Fast<N>::P, FastCols<R>::MinBlocks(N))
+__global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>::MinBlocks())
     k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check) {
   using F = Fast<N>;
-  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = FastCols<R>::C;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = FastCols<R, N>::C;
   constexpr int SIGN = INV ? 1 : -1;
   extern __shared__ __align__(16) unsigned char smraw[];
   c2<R>* sm = reinterpret_cast<c2<R>*>(smraw);  // C * M complex
@@ -480,7 +482,7 @@ size_t fast_x_smem() {
 }
 template <typename R, int N>
 size_t fast_y_smem() {
-  return (size_t)FastCols<R>::C * Fast<N>::M * sizeof(c2<R>);
+  return (size_t)FastCols<R, N>::C * Fast<N>::M * sizeof(c2<R>);
 }
 
 
@@ -544,7 +546,7 @@ cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, con
 template <typename R, int N>
 cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R* t,
                 int inverse, int check, cudaStream_t s) {
-  constexpr int C = FastCols<R>::C;
+  constexpr int C = FastCols<R, N>::C;
   dim3 grid((g.n0 + C - 1) / C, g.n2);
   const size_t sm = fast_y_smem<R, N>();
   if (inverse)
