@@ -205,9 +205,16 @@ def test_series_laminate_harmonic_mean():
     assert kap == pytest.approx(20 / sum(1 / v for v in layer), rel=1e-10)
 
 
+@pytest.mark.parametrize("shape", [
+    (40, 36, 48),  # loading axis 40 planes: whole chunks of the tridiagonal copies
+    (37, 20, 22),  # 37 planes (a partial last chunk), plane 440 (a partial block of columns)
+    (9, 12, 14),   # fewer planes than one chunk plus one, small tiles
+])
 @pytest.mark.parametrize("precision", [B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64])
-def test_mixed_precision_matches_fp64_oracle(precision):
-    k, _ = M.random_spheres((40, 36, 48), (3, 6), 0.3, 77, 1.0, 100.0)
+def test_mixed_precision_matches_fp64_oracle(precision, shape):
+    # arrays are [z][y][x]: loading along z puts x (even here) on axis 0, so
+    # both bulk-tensor kernels (matvec and tridiagonal) run
+    k, _ = M.random_spheres(shape, (3, 6), 0.3, 77, 1.0, 100.0)
     ref = O.solve_direction(k, k, k, 2, rtol=1e-10)
     rve = make(k)
     kap, inf = rve.solve(2, rtol=1e-8, precision=precision)
