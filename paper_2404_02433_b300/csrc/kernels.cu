@@ -114,7 +114,25 @@ __global__ void k_permute_tile(const double* __restrict__ in, double* __restrict
 }
 
 // ------------------------------------------------------------------ setup: faces
-__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * (a * b) / (a + b); }
+// 2ab/(a+b).  The reciprocal of s = a+b comes from the FP32 hardware
+// approximation refined by two Newton-Raphson steps r <- r + r (1 - s r) in
+// FP64 (each roughly doubles the correct bits: 2^-22 -> 2^-44 -> the FP64
+// rounding), so the face is within about two units in the last place of the
+// correctly rounded quotient, at 7 FP64 instructions per face instead of a
+// full division: the face assembly is FP64-bound on this part (about 45 FP64
+// instructions per cell with three divisions).  Sums outside the binary32
+// normal range keep the division.
+__device__ __forceinline__ double harmonic(double a, double b) {
+  const double s = a + b;
+  const float sf = narrow(s);
+  if (!(sf > 1e-30f && sf < 1e30f)) return 2.0 * (a * b) / s;
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(sf));
+  double r = widen(rf);
+  r = fma(r, fma(-s, r, 1.0), r);
+  r = fma(r, fma(-s, r, 1.0), r);
+  return 2.0 * (a * b) * r;
+}
 
 // Face conductances of Eq. (scaled bilinear forms) in the loading frame, the
 // diagonal D of A, the Dirichlet planes and the group extrema of
@@ -127,8 +145,18 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
                         double* __restrict__ Bin, double* __restrict__ Bout, double* partials,
                         PcgState* st) {
   __shared__ int flag;
-  double ext[10];
-  for (int e = 0; e < 10; e += 2) { ext[e] = INFINITY; ext[e + 1] = -INFINITY; }
+  // Extrema of positive doubles (faces and kappa~ are > 0) kept as their bit
+  // patterns: for non-negative IEEE values the unsigned-integer order is the
+  // numeric order, so the integer pipe does the min/max (the FP64 pipe is
+  // this kernel's bound).  Empty: lo = +inf bits, hi = 0.
+  constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+  unsigned long long lo[5], hi[5];
+  for (int e = 0; e < 5; ++e) { lo[e] = kInfBits; hi[e] = 0ull; }
+  auto note = [&](int e, double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    lo[e] = min(lo[e], b);
+    hi[e] = max(hi[e], b);
+  };
   // threads stride over the cells of a plane and blocks over the planes
   // (k = blockIdx.y + m gridDim.y): the three "minus" faces of each cell (each
   // face once; the diagonal follows in k_diag_split from the neighbours' faces)
@@ -141,15 +169,17 @@ __global__ void k_faces(Geometry g, double ih0, double ih1, double ih2,
     const double t0 = (i > 0) ? harmonic(k0[c - 1] * ih0, s0) : 0.0;
     const double t1 = (j > 0) ? harmonic(k1[c - g.n0] * ih1, s1) : 0.0;
     const double t2 = (k > 0) ? harmonic(k2[c - g.plane] * ih2, s2) : 0.0;
-    if (k == 0) { Bin[sidx] = 2.0 * s2; ext[6] = fmin(ext[6], s2); ext[7] = fmax(ext[7], s2); }
-    if (k == g.n2 - 1) {
-      Bout[sidx] = 2.0 * s2;
-      ext[8] = fmin(ext[8], s2); ext[9] = fmax(ext[9], s2);
-    }
+    if (k == 0) { Bin[sidx] = 2.0 * s2; note(3, s2); }
+    if (k == g.n2 - 1) { Bout[sidx] = 2.0 * s2; note(4, s2); }
     T0[c] = t0; T1[c] = t1; T2[c] = t2;
-    if (i > 0) { ext[0] = fmin(ext[0], t0); ext[1] = fmax(ext[1], t0); }
-    if (j > 0) { ext[2] = fmin(ext[2], t1); ext[3] = fmax(ext[3], t1); }
-    if (k > 0) { ext[4] = fmin(ext[4], t2); ext[5] = fmax(ext[5], t2); }
+    if (i > 0) note(0, t0);
+    if (j > 0) note(1, t1);
+    if (k > 0) note(2, t2);
+  }
+  double ext[10];
+  for (int e = 0; e < 5; ++e) {
+    ext[2 * e] = __longlong_as_double((long long)lo[e]);
+    ext[2 * e + 1] = lo[e] == kInfBits ? -INFINITY : __longlong_as_double((long long)hi[e]);
   }
   __shared__ double we[32][10];
   for (int o = 16; o > 0; o >>= 1)
