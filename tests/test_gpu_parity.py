@@ -273,12 +273,17 @@ def test_maxit_reports_noconv_with_info():
     assert np.isfinite(kap) and kap > 0 and info.relres > 1e-12
 
 
-def test_deterministic_bitwise():
+@pytest.mark.parametrize("precision", [B.ETC_PREC_FP64, B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64])
+def test_deterministic_bitwise(precision):
+    # fixed-order reductions, no float atomics: repeated solves are identical
+    # (the mixed forms run the bulk-tensor matvec and tridiagonal kernels)
     k, _ = M.random_spheres((32, 32, 32), (3, 5), 0.3, 1001, 1.0, 10.0)
     rve = make(k)
-    a, ia = rve.solve(1, rtol=1e-10)
+    rtol = 1e-10 if precision == B.ETC_PREC_FP64 else 1e-8
+    a, ia = rve.solve(1, rtol=rtol, precision=precision)
     pa = host(rve.solution(1)).copy()
-    b, ib = rve.solve(1, rtol=1e-10)
+    rve.solve(2, rtol=rtol, precision=precision)  # another frame in between
+    b, ib = rve.solve(1, rtol=rtol, precision=precision)
     pb = host(rve.solution(1))
     assert a == b and ia["iters"] == ib["iters"]
     assert np.array_equal(pa, pb)
