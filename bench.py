@@ -280,6 +280,27 @@ def run_batch(B, torch, media, precision):
             dof_iters / (ms / 1e3), "iters": sum(i["iters"] for i in infos), "status": st}
 
 
+# ------------------------------------------------------------------ ranks
+def over_ranks(dist, device, v, op):
+    """v reduced over the ranks ("max" or "sum"); v itself without a group.
+
+    Timing takes the max over ranks, work the sum: the job's throughput is the
+    units all ranks processed divided by the slowest rank's time.
+    """
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(dist, device, units, seconds):
+    """(units of all ranks / slowest rank's seconds, slowest seconds)."""
+    tmax = over_ranks(dist, device, seconds, "max")
+    return over_ranks(dist, device, units, "sum") / tmax, tmax
+
+
 # ------------------------------------------------------------------ main arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -308,18 +329,10 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     def maxr(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return over_ranks(dist, dev, v, "max")
 
     def sumr(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return over_ranks(dist, dev, v, "sum")
 
     def step(precision):
         Ks, iters = [], 0
