@@ -40,6 +40,8 @@ namespace etc {
 namespace {
 
 constexpr int kStages = 5;
+constexpr int kConsumers = 8;                     // warps, one tile row each
+constexpr int kThreads = (kConsumers + 1) * 32;   // + one producer warp
 // box extents (elements of 8 bytes)
 constexpr int kT0X = 34, kT0Y = 8;
 constexpr int kT1X = 32, kT1Y = 9;
@@ -57,6 +59,7 @@ constexpr int kOffW = kOffT2 + align128(kT2Bytes);
 constexpr int kStageBytes = kOffW + align128(kWBytes);
 // + the mbarriers, + slack to align the stages to 128 bytes at run time
 constexpr int kSmemBytes = kStages * kStageBytes + 128 + 128;
+static_assert(2 * kStages * 8 <= 128, "full and empty barriers fit behind the stages");
 // p + pe ~ T (a - b) and the Sum2 step, as in kernels.cu
 __device__ __forceinline__ void two_sum_(float a, float b, float& s, float& t) {
   s = a + b;
@@ -88,7 +91,7 @@ __device__ __forceinline__ void prod_acc_(float2 x, float2 y, float& s, float& e
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(kThreads, 4)
     k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
                     const float2* __restrict__ w, float2* __restrict__ q,
                     const float2* __restrict__ T2, const float2* __restrict__ Bin,
@@ -100,102 +103,117 @@ __global__ void __launch_bounds__(256, 4)
   if (MODE == 1 && st->done) return;
   // the copies' destinations start on 128-byte boundaries
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + kStages * kStageBytes);
-  const int l = threadIdx.x & 31, r = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
-  const int i = i0 + l, j = j0 + r;
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + kStages * kStageBytes);
+  unsigned long long* empty = full + kStages;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kConsumers;
   const int k0 = blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, g.n2);
   const int kend = min(k1, g.n2 - 1);  // last plane loaded (k1 supplies w above k1-1)
-  const bool own = i < g.n0 && j < g.n1;
-  // plane k lives in stage (k - k0) mod kStages; its u-th use has parity u & 1
-  auto issue = [&](int k, unsigned int sidx_) {
-    unsigned char* sg = smem + sidx_ * kStageBytes;
-    unsigned long long* b = bars + sidx_;
-    mbar_expect_tx(b, kTx + tx_extra);
-    tma_load3(sg, &mp.T0, i0, j0, k, b);
-    tma_load3(sg + kOffT1, &mp.T1, i0, j0, k, b);
-    tma_load3(sg + kOffT2, &mp.T2, i0, j0, k + 1, b);
-    tma_load3(sg + kOffW, &mp.w, i0 - 2, j0 - 1, k, b);
-  };
   if (threadIdx.x == 0) {
     failed = 0;
-    for (int s = 0; s < kStages; ++s) mbar_init(bars + s, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int k = k0; k <= kend && k < k0 + kStages - 1; ++k) issue(k, (unsigned int)(k - k0));
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, kConsumers);
+    }
+    mbar_init_fence();
   }
+  __syncthreads();
+  volatile int* vfailed = &failed;
   float ds = 0.f, dc = 0.f;
-  const long long pl = g.plane;
-  const long long sidx = (long long)j * g.n0 + i;
-  // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
-  float fz = 0.f, fze = 0.f;
-  if (own && k0 > 0) {
-    const long long c = (long long)k0 * pl + sidx;
-    flux_(T2[c], w[c - pl], w[c], fz, fze);
-  }
-  // this thread's element offsets inside a stage (float2 units)
-  const int oT0 = r * kT0X + l, oT1 = r * kT1X + l, oT2 = r * kT2X + l;
-  const int oW = (r + 1) * kWX + l + 2;
-  float2* pq = q + (long long)k0 * pl + sidx;
-  unsigned int sc = 0, pc = 0;  // stage and parity of plane k
-  int k = k0;
-  for (; k < k1; ++k) {
-    const unsigned int sn = sc + 1 == kStages ? 0u : sc + 1;
-    const unsigned int pn = sn == 0 ? pc ^ 1u : pc;
-    // thread 0 waits (bounded) for planes k and k+1; the barrier then hands
-    // their stages to every thread, and frees the stage of plane k-1
-    if (threadIdx.x == 0) {
-      bool ok = mbar_wait(bars + sc, pc);
-      if (ok && k + 1 <= kend) ok = mbar_wait(bars + sn, pn);
-      if (!ok) failed = 1;
-    }
-    __syncthreads();
-    if (failed) break;
-    if (threadIdx.x == 0 && k + kStages - 1 <= kend) {
-      const unsigned int sf = sc == 0 ? kStages - 1 : sc - 1;  // the stage of plane k-1
-      issue(k + kStages - 1, sf);
-    }
-    if (own) {
-      const float2* sT0 = reinterpret_cast<const float2*>(smem + sc * kStageBytes) + oT0;
-      const float2* sT1 = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffT1) + oT1;
-      const float2* sT2 = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffT2) + oT2;
-      const float2* sW = reinterpret_cast<const float2*>(smem + sc * kStageBytes + kOffW) + oW;
-      const float2 wc = sW[0];
-      const float2 wp =
-          k + 1 <= kend ? reinterpret_cast<const float2*>(smem + sn * kStageBytes + kOffW)[oW]
-                        : wc;
-      float sv, ev, p, pe;
-      flux_(sT0[0], wc, sW[-1], sv, ev);
-      flux_(sT0[1], wc, sW[1], p, pe);
-      acc_(p, pe, sv, ev);
-      flux_(sT1[0], wc, sW[-kWX], p, pe);
-      acc_(p, pe, sv, ev);
-      flux_(sT1[kT1X], wc, sW[kWX], p, pe);
-      acc_(p, pe, sv, ev);
-      acc_(-fz, -fze, sv, ev);
-      flux_(sT2[0], wc, wp, fz, fze);
-      acc_(fz, fze, sv, ev);
-      if (k == 0) prod_acc_(Bin[sidx], wc, sv, ev);
-      if (k == g.n2 - 1) prod_acc_(Bout[sidx], wc, sv, ev);
-      float qh, ql;
-      two_sum_(sv, ev, qh, ql);
-      *pq = make_float2(qh, ql);
-      if (MODE == 1) prod_acc_(wc, make_float2(qh, ql), ds, dc);
-    }
-    pq += pl;
-    sc = sn;
-    pc = pn;
-  }
-  if (failed) {
-    // drain this block's copies still in flight (bounded), then report
-    if (threadIdx.x == 0) {
-      unsigned int s2 = sc, p2 = pc;
-      for (int kk = k; kk <= kend && kk < k + kStages - 1; ++kk) {
-        (void)mbar_wait(bars + s2, p2);
-        s2 = s2 + 1 == kStages ? 0u : s2 + 1;
-        if (s2 == 0) p2 ^= 1u;
+  if (warp == kConsumers) {
+    // producer: plane k goes to stage (k - k0) mod kStages once the consumer
+    // warps have released that stage's previous plane
+    if (lane == 0) {
+      int issued = 0;
+      for (int k = k0; k <= kend; ++k) {
+        const int u = k - k0;
+        const unsigned int s = (unsigned int)(u % kStages);
+        if (u >= kStages && !mbar_wait(empty + s, (unsigned int)(((u / kStages) - 1) & 1))) {
+          *vfailed = 1;
+          break;
+        }
+        if (*vfailed) break;
+        unsigned char* sg = smem + s * kStageBytes;
+        mbar_expect_tx(full + s, kTx + tx_extra);
+        tma_load3(sg, &mp.T0, i0, j0, k, full + s);
+        tma_load3(sg + kOffT1, &mp.T1, i0, j0, k, full + s);
+        tma_load3(sg + kOffT2, &mp.T2, i0, j0, k + 1, full + s);
+        tma_load3(sg + kOffW, &mp.w, i0 - 2, j0 - 1, k, full + s);
+        ++issued;
       }
+      // no copy may still be landing when the block exits (bounded)
+      for (int u = max(0, issued - kStages); u < issued; ++u)
+        (void)mbar_wait(full + u % kStages, (unsigned int)((u / kStages) & 1));
+    }
+    __syncwarp();
+  } else {
+    // consumer warp: tile row r, one column per lane
+    const int r = warp, l = lane;
+    const int i = i0 + l, j = j0 + r;
+    const bool own = i < g.n0 && j < g.n1;
+    const long long pl = g.plane;
+    const long long sidx = (long long)j * g.n0 + i;
+    // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
+    float fz = 0.f, fze = 0.f;
+    if (own && k0 > 0) {
+      const long long c = (long long)k0 * pl + sidx;
+      flux_(T2[c], w[c - pl], w[c], fz, fze);
+    }
+    // this thread's element offsets inside a stage (float2 units)
+    const int oT0 = r * kT0X + l, oT1 = r * kT1X + l, oT2 = r * kT2X + l;
+    const int oW = (r + 1) * kWX + l + 2;
+    float2* pq = q + (long long)k0 * pl + sidx;
+    unsigned int sc = 0, pc = 0;  // stage and parity of plane k
+    for (int k = k0; k < k1; ++k) {
+      const unsigned int sn = sc + 1 == kStages ? 0u : sc + 1;
+      const unsigned int pn = sn == 0 ? pc ^ 1u : pc;
+      // every lane waits (bounded) for planes k and k+1 (the z neighbour)
+      bool ok = mbar_wait(full + sc, pc);
+      if (ok && k + 1 <= kend) ok = mbar_wait(full + sn, pn);
+      if (!__all_sync(0xffffffffu, ok) || *vfailed) {
+        *vfailed = 1;
+        break;
+      }
+      if (own) {
+        const unsigned char* sg = smem + sc * kStageBytes;
+        const float2* sT0 = reinterpret_cast<const float2*>(sg) + oT0;
+        const float2* sT1 = reinterpret_cast<const float2*>(sg + kOffT1) + oT1;
+        const float2* sT2 = reinterpret_cast<const float2*>(sg + kOffT2) + oT2;
+        const float2* sW = reinterpret_cast<const float2*>(sg + kOffW) + oW;
+        const float2 wc = sW[0];
+        const float2 wp =
+            k + 1 <= kend ? reinterpret_cast<const float2*>(smem + sn * kStageBytes + kOffW)[oW]
+                          : wc;
+        float sv, ev, p, pe;
+        flux_(sT0[0], wc, sW[-1], sv, ev);
+        flux_(sT0[1], wc, sW[1], p, pe);
+        acc_(p, pe, sv, ev);
+        flux_(sT1[0], wc, sW[-kWX], p, pe);
+        acc_(p, pe, sv, ev);
+        flux_(sT1[kT1X], wc, sW[kWX], p, pe);
+        acc_(p, pe, sv, ev);
+        acc_(-fz, -fze, sv, ev);
+        flux_(sT2[0], wc, wp, fz, fze);
+        acc_(fz, fze, sv, ev);
+        if (k == 0) prod_acc_(Bin[sidx], wc, sv, ev);
+        if (k == g.n2 - 1) prod_acc_(Bout[sidx], wc, sv, ev);
+        float qh, ql;
+        two_sum_(sv, ev, qh, ql);
+        *pq = make_float2(qh, ql);
+        if (MODE == 1) prod_acc_(wc, make_float2(qh, ql), ds, dc);
+      }
+      // the warp is done with plane k's stage (plane k-1 no longer reads it)
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + sc);
+      pq += pl;
+      sc = sn;
+      pc = pn;
+    }
+  }
+  __syncthreads();
+  if (failed) {
+    if (threadIdx.x == 0) {
       st->status = kECUDA;
       st->done = 1;
     }
@@ -259,10 +277,10 @@ cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgSta
   const dim3 grid = matvec_df_grid(g, &kc);
   const float2* Bout = FB + g.plane;
   if (mode == 1)
-    k_matvec_df_tma<1><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
+    k_matvec_df_tma<1><<<grid, kThreads, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
                                                      kc, tx_extra);
   else
-    k_matvec_df_tma<0><<<grid, 256, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
+    k_matvec_df_tma<0><<<grid, kThreads, kSmemBytes, s>>>(mp, g, st, w, q, T2, FB, Bout, partials, par,
                                                      kc, tx_extra);
   count_launch();
   return cudaGetLastError();
