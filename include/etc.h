@@ -28,6 +28,11 @@
  *     Arguments are validated on the host before any GPU work; a rejected call
  *     returns ETC_EINVAL and changes nothing.  After ETC_ECUDA the handle should
  *     be destroyed.  etc_last_error() gives a one-line reason.
+ *   - Test hooks read at etc_create_rve from the environment (both unset in
+ *     use): ETC_FAIL_ALLOC_AFTER=k fails the handle's (k+1)-th device allocation
+ *     (ETC_ENOMEM, clean teardown); ETC_TEST_TMA_TX_EXTRA=b makes the
+ *     bulk-tensor matvec's waits expect b bytes that no copy delivers, so they
+ *     run out and the mixed solve ends with ETC_ECUDA, without any fault.
  *   - A handle is used from one host thread at a time.  All its GPU work is
  *     ordered on the stream given to etc_create_rve; calls that return numbers
  *     to the host synchronise that stream before returning.
@@ -46,7 +51,8 @@ enum {
   ETC_OK = 0,
   ETC_EINVAL = 1,      /* bad argument (size, length, kappa, p_in == p_out, dir) */
   ETC_ENOMEM = 2,      /* device or pinned-host allocation failed */
-  ETC_ECUDA = 3,       /* a CUDA runtime call failed */
+  ETC_ECUDA = 3,       /* a CUDA runtime call failed, or a bounded device wait for
+                          bulk-tensor copies ran out (0.5 s; the solve stops) */
   ETC_ENOCONV = 4,     /* maxit reached; results hold the last iterate */
   ETC_EBREAKDOWN = 5,  /* non-finite or non-positive PCG scalar */
   ETC_ESTATE = 6       /* call out of order (e.g. solution of an unsolved dir) */
