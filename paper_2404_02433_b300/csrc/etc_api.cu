@@ -60,7 +60,8 @@ struct etc_rve {
   // returns to FP64 at the end of each solve
   float2* Tdf[3] = {nullptr, nullptr, nullptr};
   float2* Bdf = nullptr;  // B_in then B_out, plane_max each
-  float2* wdf = nullptr;  // inside an allocation with zero guards (see create)
+  float* wf = nullptr;  // FP32 search direction of the double-float path, inside an
+                        // allocation with zero guards (see create)
   MatvecMaps mv_maps[3];  // bulk-tensor maps of the double-float matvec, per loading frame
   bool mv_tma[3] = {false, false, false};
   int frame_dir = -1;  // loading frame of the last queued face assembly (matvec map choice)
@@ -525,7 +526,7 @@ template <typename R, typename TZ>
 etc_status precond_tail(etc_rve* h, const Geometry& g, const DctPlan<R>& p0,
                         const DctPlan<R>& p1, R* t, R* zt, const R* hp, TZ* out, int tri_mode,
                         int inv_mode, const R* rold = nullptr, cudaEvent_t* ev = nullptr,
-                        TZ* x = nullptr, int par = 0) {
+                        typename XOf<TZ>::T* x = nullptr, int par = 0) {
   const int check = (tri_mode != 0);
   CK(launch_dct_y<R>(g, p1, h->st, t, 0, check, h->stream, h->tiles[2]));
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
@@ -590,16 +591,17 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
     return precond_tail<float, double>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr,
                                        h->w[0], 3, 2);
   }
-  // mixed: x = 0 and w = 0 have the same bytes in both storages; r = b is split
-  CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x,
-                 reinterpret_cast<double*>(h->wdf), h->stream, rhs.pin_f, rhs.pout_f, rhs.src));
+  // mixed: x = 0 has the same bytes in both storages; r = b is split; w = 0 (FP32)
+  CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, nullptr, h->stream, rhs.pin_f,
+                 rhs.pout_f, rhs.src));
+  CK(cudaMemsetAsync(h->wf, 0, (size_t)h->n * sizeof(float), h->stream));
   CK(launch_split_inplace(h->r, h->n, h->stream));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
   CK((launch_fwd_x<float, float2>(g, P0.p32, h->st, nullptr, nullptr, nullptr, df(h->r),
                                   nullptr, h->rhat32[1], h->partials, 0, rtol2, 0, h->stream,
                                   h->tiles[0])));
-  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr,
-                                     h->wdf, 3, 2);
+  return precond_tail<float, float>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr,
+                                    h->wf, 3, 2);
 }
 
 // One PCG iteration (par = parity of the iteration index).  ev (optional):
@@ -635,10 +637,10 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
                                        ev ? ev + 3 : nullptr);
   }
   if (h->frame_dir >= 0 && h->mv_tma[h->frame_dir])
-    CK(launch_matvec_df_tma(g, h->mv_maps[h->frame_dir], h->st, h->wdf, df(h->q), h->Tdf[2],
+    CK(launch_matvec_df_tma(g, h->mv_maps[h->frame_dir], h->st, h->wf, df(h->q), h->Tdf[2],
                             h->Bdf, h->partials, par, 1, h->stream, h->tma_tx_extra));
   else
-    CK(launch_matvec_df(g, h->st, h->wdf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
+    CK(launch_matvec_df(g, h->st, h->wf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
                         h->partials, par, 1, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
   // double-float storage: x += alpha w moves to the w-update kernel, which
@@ -647,8 +649,8 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
                                   nullptr, h->rhat32[par], h->partials, par, 0.0, 1, h->stream,
                                   h->tiles[0])));
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  return precond_tail<float, float2>(h, g, P0.p32, P1.p32, h->rhat32[par], h->t32, nullptr,
-                                     h->wdf, 2, 2, h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
+  return precond_tail<float, float>(h, g, P0.p32, P1.p32, h->rhat32[par], h->t32, nullptr,
+                                    h->wf, 2, 2, h->rhat32[par ^ 1], ev ? ev + 3 : nullptr,
                                      df(x), par);
 }
 
@@ -657,7 +659,7 @@ etc_status launch_iteration(etc_rve* h, const Geometry& g, double* x, int prec, 
 // and the mixed path's x back to FP64.
 etc_status finish_solve_x(etc_rve* h, const Geometry& g, double* x, int prec) {
   if (prec == ETC_PREC_MIXED)
-    CK(launch_finish_x(g, h->st, x, reinterpret_cast<const double*>(h->wdf), 1, h->stream));
+    CK(launch_finish_x(g, h->st, x, nullptr, h->wf, 1, h->stream));
   return ETC_OK;
 }
 
@@ -985,12 +987,12 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   {
     // w of the mixed path with zero guards of the longest axis on both sides
     // (the double-float matvec reads w[c +- n0] without bounds tests)
-    // (an even count keeps w 16-byte aligned for the bulk-tensor copies)
-    const size_t guard = ((size_t)std::max(nx, std::max(ny, nz)) + 1) / 2 * 2;
-    float2* wbase = nullptr;
+    // (a multiple of 4 keeps w 16-byte aligned for the bulk-tensor copies)
+    const size_t guard = ((size_t)std::max(nx, std::max(ny, nz)) + 3) / 4 * 4;
+    float* wbase = nullptr;
     CKC(dalloc(h, &wbase, (size_t)n + 2 * guard));
-    CKC(cudaMemsetAsync(wbase, 0, ((size_t)n + 2 * guard) * sizeof(float2), h->stream));
-    h->wdf = wbase + guard;
+    CKC(cudaMemsetAsync(wbase, 0, ((size_t)n + 2 * guard) * sizeof(float), h->stream));
+    h->wf = wbase + guard;
   }
   // partials: the largest reduction grid over the three directions
   size_t np = 1024;
@@ -1023,7 +1025,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
                     tridiag_tma_map(gd, h->rhat32[1], &h->rhat_maps[d][1]);
   }
   for (int d = 0; d < 3; ++d)
-    h->mv_tma[d] = matvec_tma_maps(geom_of(h, d), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->wdf,
+    h->mv_tma[d] = matvec_tma_maps(geom_of(h, d), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->wf,
                                    &h->mv_maps[d]);
   for (int ax : {nx, ny, nz}) {
     s = make_plan(h, ax);

@@ -360,6 +360,26 @@ template <> struct Scalar<float2> {
   static __device__ __forceinline__ float2 from(double a) { return split_df(a); }
   static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
 };
+template <> struct Scalar<float> {
+  using T = float;
+  static __device__ __forceinline__ float from(double a) { return narrow(a); }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+
+// FP32 search directions (the double-float path keeps w in FP32: it is only a
+// direction, and x and r are updated with the same rounded w and its exact
+// double-float product A w, so the recursive residual still tracks b - A x).
+__device__ __forceinline__ float vaxpy(float a, float x, float y) { return fmaf(a, x, y); }
+
+// Storage of x that goes with a storage of w: FP32 directions with double-float x.
+template <typename TW> struct XOf { using T = TW; };
+template <> struct XOf<float> { using T = float2; };
+// x + alpha w with w in its own storage
+__device__ __forceinline__ double xaxpy(double a, double w, double x) { return fma(a, w, x); }
+__device__ __forceinline__ float2 xaxpy(float2 a, float2 w, float2 x) { return vaxpy(a, w, x); }
+__device__ __forceinline__ float2 xaxpy(float2 a, float w, float2 x) {
+  return vaxpy(a, make_float2(w, 0.f), x);
+}
 
 // A vector value as the FP64 or FP32 input of the preconditioner's transforms
 // (double-float -> binary32: the high part, which is the nearest binary32).
@@ -381,6 +401,7 @@ template <> __device__ __forceinline__ double vfrom<double, float>(float u) { re
 template <> __device__ __forceinline__ float2 vfrom<float2, float>(float u) {
   return make_float2(u, 0.f);
 }
+template <> __device__ __forceinline__ float vfrom<float, float>(float u) { return u; }
 
 // two consecutive elements, 16 bytes
 template <typename V> struct VPair { V a, b; };
@@ -391,6 +412,13 @@ __device__ __forceinline__ VPair<double> ld_pair(const double* p) {
 __device__ __forceinline__ VPair<float2> ld_pair(const float2* p) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ VPair<float> ld_pair(const float* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st_pair(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
 }
 __device__ __forceinline__ void st_pair(double* p, double a, double b) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
@@ -405,6 +433,7 @@ __device__ __forceinline__ void store_f64(double* p, float2 v) { *p = widen(v.x)
 template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
 
 }  // namespace etc
 

@@ -68,7 +68,7 @@ template cudaError_t launch_fast_fwd_x<float, float2>(const Geometry&, const Dct
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
                               TZ* z, const double* kd, double kz_host, int check, int mode,
-                              cudaStream_t s, TZ* x, int par, int nt) {
+                              cudaStream_t s, typename XOf<TZ>::T* x, int par, int nt) {
 #define INV(N)                                                                      \
   case N:                                                                           \
     return inv_x_n<R, TZ, N>(g, p.t, st, t, z, kd, kz_host, check, mode, s, x, par, nt);
@@ -86,10 +86,10 @@ template cudaError_t launch_fast_inv_x<float, double>(const Geometry&, const Dct
                                                       PcgState*, const float*, double*,
                                                       const double*, double, int, int,
                                                       cudaStream_t, double*, int, int);
-template cudaError_t launch_fast_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                      PcgState*, const float*, float2*,
-                                                      const double*, double, int, int,
-                                                      cudaStream_t, float2*, int, int);
+template cudaError_t launch_fast_inv_x<float, float>(const Geometry&, const DctPlan<float>&,
+                                                     PcgState*, const float*, float*,
+                                                     const double*, double, int, int,
+                                                     cudaStream_t, float2*, int, int);
 
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,

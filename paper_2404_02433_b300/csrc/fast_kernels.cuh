@@ -369,7 +369,8 @@ template <typename R, typename TZ, int N, int MODE, int NT>
 __global__ void __launch_bounds__(NT)
     k_fast_inv_x(Geometry g, DctTables<R> tb, PcgState* st, const R* __restrict__ t,
                  TZ* __restrict__ z, const double* kd, double kz_host, int check,
-                 TZ* __restrict__ x, int par) {
+                 typename XOf<TZ>::T* __restrict__ x, int par) {
+  using TX = typename XOf<TZ>::T;  // x's storage (FP32 directions: double-float x)
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
   constexpr int L = FastX<N, NT>::L;
@@ -433,20 +434,21 @@ __global__ void __launch_bounds__(NT)
   const R scale = (R)(1.0 / (kd ? kd[2] : kz_host));
   const typename Scalar<TZ>::T beta = Scalar<TZ>::from((MODE == 2) ? st->beta : 0.0);
   const bool upd = (MODE == 2) && x != nullptr;
-  const typename Scalar<TZ>::T alpha = Scalar<TZ>::from(upd ? st->alpha[par] : 0.0);
+  const typename Scalar<TX>::T alpha = Scalar<TX>::from(upd ? st->alpha[par] : 0.0);
   if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
   constexpr int NQ = L * M / NT;  // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
   static_assert(NQ % G == 0, "pair groups");
 #pragma unroll 1
   for (int r0 = 0; r0 < NQ; r0 += G) {
-    VPair<TZ> wo[G], xo[G];
+    VPair<TZ> wo[G];
+    VPair<TX> xo[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
       const int p = threadIdx.x + NT * (r0 + u);
       const long long row = row0 + p / M;
       wo[u].a = wo[u].b = vzero<TZ>();
-      xo[u] = wo[u];
+      xo[u].a = xo[u].b = vzero<TX>();
       if (MODE == 2 && row < nrows) {
         wo[u] = ld_pair(z + row * N + 2 * (p % M));
         if (upd) xo[u] = ld_pair(x + row * N + 2 * (p % M));
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(NT)
       const R u0 = Ar[lr * 2 * RS + i2] * scale;          // element 2 i2     <- v_{i2}
       const R u1 = Ar[lr * 2 * RS + N - 1 - i2] * scale;  // element 2 i2 + 1 <- v_{n-1-i2}
       if (MODE == 2) {
-        if (upd) st_pair(x + c, vaxpy(alpha, wo[u].a, xo[u].a), vaxpy(alpha, wo[u].b, xo[u].b));
+        if (upd) st_pair(x + c, xaxpy(alpha, wo[u].a, xo[u].a), xaxpy(alpha, wo[u].b, xo[u].b));
         st_pair(z + c, vaxpy(beta, wo[u].a, vfrom<TZ, R>(u0)),
                 vaxpy(beta, wo[u].b, vfrom<TZ, R>(u1)));
       }
@@ -523,7 +525,7 @@ cudaError_t fwd_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, V* 
 template <typename R, typename TZ, int N, int NT>
 cudaError_t inv_x_nt(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
                      const double* kd, double kz_host, int check, int mode, cudaStream_t s,
-                     TZ* x, int par) {
+                     typename XOf<TZ>::T* x, int par) {
   constexpr int L = FastX<N, NT>::L;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
@@ -537,7 +539,7 @@ cudaError_t inv_x_nt(const Geometry& g, const DctTables<R>& tb, PcgState* st, co
 template <typename R, typename TZ, int N>
 cudaError_t inv_x_n(const Geometry& g, const DctTables<R>& tb, PcgState* st, const R* t, TZ* z,
                     const double* kd, double kz_host, int check, int mode, cudaStream_t s,
-                    TZ* x, int par, int nt) {
+                    typename XOf<TZ>::T* x, int par, int nt) {
   if (nt == 128 || !fast_x_fits<R, N, 256>())
     return inv_x_nt<R, TZ, N, 128>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
   return inv_x_nt<R, TZ, N, 256>(g, tb, st, t, z, kd, kz_host, check, mode, s, x, par);
@@ -571,8 +573,7 @@ cudaError_t attrs_nt() {
   if (sizeof(R) == 4) {
     SETF((k_fast_fwd_x<float, N, 0, float2, NT>), sx);
     SETF((k_fast_fwd_x<float, N, 1, float2, NT>), sx);
-    SETF((k_fast_inv_x<float, float2, N, 0, NT>), sx);
-    SETF((k_fast_inv_x<float, float2, N, 2, NT>), sx);
+    SETF((k_fast_inv_x<float, float, N, 2, NT>), sx);
   }
 #undef SETF
   return e;
@@ -615,8 +616,8 @@ cudaError_t attrs_n() {
   PREFIX cudaError_t inv_x_n<float, double, N>(                                              \
       const Geometry&, const DctTables<float>&, PcgState*, const float*, double*,            \
       const double*, double, int, int, cudaStream_t, double*, int, int);                     \
-  PREFIX cudaError_t inv_x_n<float, float2, N>(                                              \
-      const Geometry&, const DctTables<float>&, PcgState*, const float*, float2*,            \
+  PREFIX cudaError_t inv_x_n<float, float, N>(                                               \
+      const Geometry&, const DctTables<float>&, PcgState*, const float*, float*,             \
       const double*, double, int, int, cudaStream_t, float2*, int, int);                     \
   PREFIX cudaError_t y_n<double, N>(const Geometry&, const DctTables<double>&, const PcgState*, \
                                     double*, int, int, cudaStream_t);                        \

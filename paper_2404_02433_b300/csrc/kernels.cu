@@ -311,7 +311,7 @@ __global__ void k_init(Geometry g, const double* __restrict__ Bin, const double*
     if (k == g.n2 - 1) b += Bout[s] * (pout_f ? pout_f[s] : pout);
     r[c] = b;
     x[c] = 0.0;
-    w0[c] = 0.0;
+    if (w0) w0[c] = 0.0;
   }
 }
 
@@ -412,7 +412,7 @@ __device__ __forceinline__ void df_acc(float p, float pe, float& s, float& e) {
 
 template <int MODE>
 __global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
-                                                     const float2* __restrict__ w,
+                                                     const float* __restrict__ w,
                                                      float2* __restrict__ q,
                                                      const float2* __restrict__ T0,
                                                      const float2* __restrict__ T1,
@@ -434,15 +434,18 @@ __global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
     const long long sidx = (long long)j * n0 + i;
     const long long c0 = (long long)k0 * pl + sidx;
     // per-thread pointers, advanced by one plane per step
-    const float2* pw = w + c0;
+    const float* pw = w + c0;
     const float2* p0 = T0 + c0;
     const float2* p1 = T1 + c0;
     const float2* p2 = T2 + c0;
     float2* pq = q + c0;
     // Operands of plane k+1 are loaded during plane k (software pipelining):
     // every thread keeps a full plane's worth of loads in flight while it sums.
-    struct Ops { float2 x0, x1, y0, y1, wx0, wx1, wy0, wy1, wp, zp; };
-    auto load = [&](bool last, float2 wself) {
+    struct Ops {
+      float2 x0, x1, y0, y1, zp;
+      float wx0, wx1, wy0, wy1, wp;
+    };
+    auto load = [&](bool last, float wself) {
       Ops o;
       o.x0 = p0[0];
       o.x1 = p0[1];
@@ -456,32 +459,35 @@ __global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
       o.zp = p2[pl];  // the extra zero plane covers k = n2 - 1
       return o;
     };
-    float2 wc = pw[0];
+    // the FP32 direction as double-float values (low part 0)
+    auto d2 = [](float v) { return make_float2(v, 0.f); };
+    float wc = pw[0];
     float fz, fze;  // flux T2 (w_{k-1} - w_k) through the face below plane k
-    df_flux(p2[0], k0 > 0 ? pw[-pl] : wc, wc, fz, fze);
+    df_flux(p2[0], d2(k0 > 0 ? pw[-pl] : wc), d2(wc), fz, fze);
     Ops cur = load(k0 == g.n2 - 1, wc);
     for (int k = k0; k < k1; ++k) {
       Ops nxt;
       pw += pl; p0 += pl; p1 += pl; p2 += pl;
       if (k + 1 < k1) nxt = load(k + 1 == g.n2 - 1, cur.wp);
       float sv, ev, p, pe;
-      df_flux(cur.x0, wc, cur.wx0, sv, ev);
-      df_flux(cur.x1, wc, cur.wx1, p, pe);
+      const float2 w2 = d2(wc);
+      df_flux(cur.x0, w2, d2(cur.wx0), sv, ev);
+      df_flux(cur.x1, w2, d2(cur.wx1), p, pe);
       df_acc(p, pe, sv, ev);
-      df_flux(cur.y0, wc, cur.wy0, p, pe);
+      df_flux(cur.y0, w2, d2(cur.wy0), p, pe);
       df_acc(p, pe, sv, ev);
-      df_flux(cur.y1, wc, cur.wy1, p, pe);
+      df_flux(cur.y1, w2, d2(cur.wy1), p, pe);
       df_acc(p, pe, sv, ev);
       df_acc(-fz, -fze, sv, ev);
-      df_flux(cur.zp, wc, cur.wp, fz, fze);
+      df_flux(cur.zp, w2, d2(cur.wp), fz, fze);
       df_acc(fz, fze, sv, ev);
-      if (k == 0) df_fma_acc<1>(Bin[sidx], wc, sv, ev);
-      if (k == g.n2 - 1) df_fma_acc<1>(Bout[sidx], wc, sv, ev);
+      if (k == 0) df_fma_acc<1>(Bin[sidx], w2, sv, ev);
+      if (k == g.n2 - 1) df_fma_acc<1>(Bout[sidx], w2, sv, ev);
       float qh, ql;
       two_sum(sv, ev, qh, ql);
       *pq = make_float2(qh, ql);
       pq += pl;
-      if (MODE == 1) df_fma_acc<1>(wc, make_float2(qh, ql), ds, dc);
+      if (MODE == 1) df_fma_acc<1>(w2, make_float2(qh, ql), ds, dc);
       wc = cur.wp;
       cur = nxt;
     }
@@ -514,14 +520,14 @@ __global__ void k_f64_to_df_inplace(double* a, long long n) {
 
 // End of a solve (see PcgState::xpend): x += alpha w if the last residual
 // update's step is still due, then, for double-float storage, x to FP64 in
-// place.  The element arrays are viewed as V.
-template <typename V>
-__global__ void k_finish_x(Geometry g, const PcgState* st, V* x, const V* w) {
+// place.  x is viewed as V, w as W (FP32 directions with double-float x).
+template <typename V, typename W>
+__global__ void k_finish_x(Geometry g, const PcgState* st, V* x, const W* w) {
   const int pend = st->xpend;
   const typename Scalar<V>::T alpha = Scalar<V>::from(pend ? st->alpha[pend - 1] : 0.0);
   for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
     V v = x[c];
-    if (pend) v = vaxpy(alpha, w[c], v);
+    if (pend) v = xaxpy(alpha, w[c], v);
     store_f64(reinterpret_cast<double*>(x) + c, v);
   }
 }
@@ -918,7 +924,8 @@ template <typename R, typename TZ, int MODE>
 __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgState* st,
                                               const R* __restrict__ t, TZ* __restrict__ z,
                                               const double* kd, double kz_host, int L,
-                                              int check, TZ* __restrict__ x, int par) {
+                                              int check, typename XOf<TZ>::T* __restrict__ x, int par) {
+  using TX = typename XOf<TZ>::T;  // x's storage (FP32 directions: double-float x)
   extern __shared__ __align__(16) unsigned char smraw[];
   if (check && st->done) return;
   const Lay y = make_lay(L, g.n0, false);
@@ -930,12 +937,13 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgStat
   const long long row0 = (long long)blockIdx.x * L;
   const int tot = L * g.n0;
   const bool upd = (MODE == 2) && x != nullptr;
-  const typename Scalar<TZ>::T alpha = Scalar<TZ>::from(upd ? st->alpha[par] : 0.0);
+  const typename Scalar<TX>::T alpha = Scalar<TX>::from(upd ? st->alpha[par] : 0.0);
   if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
   constexpr int U = 8;
   for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
     R v[U];
-    TZ wv[U], xv[U];
+    TZ wv[U];
+    TX xv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * blockDim.x;
@@ -953,7 +961,7 @@ __global__ void __launch_bounds__(256) k_inv_x(Geometry g, DctPlan<R> p, PcgStat
       dct3_put<R>(y, b, l, k, v[u]);
       if (MODE == 2) wsh[e] = wv[u];
       if (MODE == 2 && upd && row0 + l < nrows)
-        x[(row0 + l) * g.n0 + k] = vaxpy(alpha, wv[u], xv[u]);
+        x[(row0 + l) * g.n0 + k] = xaxpy(alpha, wv[u], xv[u]);
     }
   }
   __syncthreads();
@@ -1254,7 +1262,7 @@ unsigned int matvec_df_blocks(const Geometry& g) {
   return d.x * d.y * d.z;
 }
 
-cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
                              const float2* FB, double* partials, int par, int mode,
                              cudaStream_t s) {
@@ -1270,12 +1278,12 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, f
 }
 
 cudaError_t launch_finish_x(const Geometry& g, const PcgState* st, double* x, const double* w,
-                            int df, cudaStream_t s) {
+                            const float* wf, int df, cudaStream_t s) {
   if (df)
-    k_finish_x<float2><<<grid_for(g.n, 256), 256, 0, s>>>(
-        g, st, reinterpret_cast<float2*>(x), reinterpret_cast<const float2*>(w));
+    k_finish_x<float2, float><<<grid_for(g.n, 256), 256, 0, s>>>(
+        g, st, reinterpret_cast<float2*>(x), wf);
   else
-    k_finish_x<double><<<grid_for(g.n, 256), 256, 0, s>>>(g, st, x, w);
+    k_finish_x<double, double><<<grid_for(g.n, 256), 256, 0, s>>>(g, st, x, w);
   count_launch();
   return cudaGetLastError();
 }
@@ -1347,8 +1355,8 @@ size_t smem_limit() { return kMaxDyn; }
 static cudaError_t set_df_attrs() {
   cudaError_t e = cudaSuccess;
   const void* fns[] = {(const void*)k_fwd_x<float, 0, float2>, (const void*)k_fwd_x<float, 1, float2>,
-                       (const void*)k_fwd_x<float, 2, float2>, (const void*)k_inv_x<float, float2, 0>,
-                       (const void*)k_inv_x<float, float2, 2>};
+                       (const void*)k_fwd_x<float, 2, float2>, (const void*)k_inv_x<float, float, 0>,
+                       (const void*)k_inv_x<float, float, 2>};
   for (const void* f : fns)
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDyn);
@@ -1501,7 +1509,7 @@ size_t tridiag_ck_pairs(const Geometry& g) {
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
                          const double* kd, double kz_host, int check, int mode, cudaStream_t s,
-                         int L, TZ* x, int par) {
+                         int L, typename XOf<TZ>::T* x, int par) {
   if (L <= 0 && fast_x_ok<R>(g, p, t, z, x, z)) {
     const cudaError_t e = launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s,
                                                    x, par, L == -2 ? 128 : 256);
@@ -1529,10 +1537,10 @@ template cudaError_t launch_inv_x<float, double>(const Geometry&, const DctPlan<
                                                  PcgState*, const float*, double*,
                                                  const double*, double, int, int, cudaStream_t,
                                                  int, double*, int);
-template cudaError_t launch_inv_x<float, float2>(const Geometry&, const DctPlan<float>&,
-                                                 PcgState*, const float*, float2*,
-                                                 const double*, double, int, int, cudaStream_t,
-                                                 int, float2*, int);
+template cudaError_t launch_inv_x<float, float>(const Geometry&, const DctPlan<float>&,
+                                                PcgState*, const float*, float*,
+                                                const double*, double, int, int, cudaStream_t,
+                                                int, float2*, int);
 
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,

@@ -37,25 +37,27 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);
-// Mixed-precision matvec on double-float operands (faces, Dirichlet planes FB
-// as in launch_diag_split, w, q); mode 1 as k_matvec.
-cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float2* w, float2* q,
+// Mixed-precision matvec on double-float faces and Dirichlet planes (FB as in
+// launch_diag_split) and q, with the FP32 search direction w (which needs n0
+// zero guard elements on both sides); mode 1 as k_matvec.
+cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float* w, float2* q,
                              const float2* T0, const float2* T1, const float2* T2,
                              const float2* FB, double* partials, int par, int mode,
                              cudaStream_t s);
 // The same matvec with its operands staged by tiled bulk-tensor copies
-// (matvec_tma.cu).  The maps describe T0, T1, T2 (with its zero plane) and w
-// of one loading frame as [n2][n1][n0] arrays of 8-byte pairs; they exist when
-// n0 is even and the bases are 16-byte aligned (matvec_tma_maps returns false
-// otherwise, and launch_matvec_df serves that frame).
+// (matvec_tma.cu).  The maps describe T0, T1, T2 (with its zero plane) of one
+// loading frame as [n2][n1][n0] arrays of 8-byte pairs and w as FP32; they
+// exist when n0 is a multiple of 4 and the bases are 16-byte aligned
+// (matvec_tma_maps returns false otherwise, and launch_matvec_df serves that
+// frame).
 struct MatvecMaps {
   CUtensorMap T0, T1, T2, w;
 };
 bool matvec_tma_maps(const Geometry& g, const float2* T0, const float2* T1, const float2* T2,
-                     const float2* w, MatvecMaps* mp);
+                     const float* w, MatvecMaps* mp);
 cudaError_t set_matvec_tma_attrs();
 cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
-                                 const float2* w, float2* q, const float2* T2, const float2* FB,
+                                 const float* w, float2* q, const float2* T2, const float2* FB,
                                  double* partials, int par, int mode, cudaStream_t s,
                                  unsigned int tx_extra = 0);
 // FP32 tridiagonal solves of the flexible PCG (modes 2 and 3 of
@@ -97,15 +99,17 @@ cudaError_t launch_tridiag_otf(const Geometry& g, PcgState* st, const float* in,
                                const double* kd, double* partials, int mode, const float* rold,
                                cudaStream_t s);
 size_t tridiag_ck_pairs(const Geometry& g);
-// mode 2 with x: also x += alpha[par] w (old w) before w is replaced.
+// mode 2 with x: also x += alpha[par] w (old w) before w is replaced.  x is
+// stored as XOf<TZ> (double-float when the directions w are FP32).
 template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
                          const double* kd, double kz_host, int check, int mode, cudaStream_t s,
-                         int L = 0, TZ* x = nullptr, int par = 0);
+                         int L = 0, typename XOf<TZ>::T* x = nullptr, int par = 0);
 // End of a solve: the x += alpha w still due (see PcgState::xpend), then for
-// double-float storage (df = 1) x back to FP64 in place.
+// double-float storage (df = 1: w is the FP32 direction wf) x back to FP64 in
+// place; df = 0: FP64 x and w.
 cudaError_t launch_finish_x(const Geometry& g, const PcgState* st, double* x, const double* w,
-                            int df, cudaStream_t s);
+                            const float* wf, int df, cudaStream_t s);
 cudaError_t launch_flux(const Geometry& g, const double* x, const double* T0, const double* T1,
                         const double* T2, const double* Bin, const double* Bout, double pin,
                         double pout, double* partials, PcgState* st, cudaStream_t s);
@@ -145,7 +149,7 @@ cudaError_t launch_fast_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* 
 template <typename R, typename TZ>
 cudaError_t launch_fast_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t,
                               TZ* z, const double* kd, double kz_host, int check, int mode,
-                              cudaStream_t s, TZ* x, int par, int nt);
+                              cudaStream_t s, typename XOf<TZ>::T* x, int par, int nt);
 template <typename R>
 cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                           int inverse, int check, cudaStream_t s);

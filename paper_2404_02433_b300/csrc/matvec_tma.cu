@@ -11,9 +11,10 @@
 //   T0 (x i0 .. i0+33, 8 rows)      the minus x faces and the plus face of the last column
 //   T1 (32 columns, y j0 .. j0+8)   the minus y faces and the plus faces of the last row
 //   T2 of plane k+1 (32 x 8)        the faces above the plane
-//   w (x i0-2 .. i0+33, y j0-1 .. j0+8) the plane with a one-cell halo (x rounded
-//                                   down to an even coordinate: a copy's first
-//                                   x times 8 bytes must be 16-byte aligned)
+//   w (x i0-4 .. i0+35, y j0-1 .. j0+8) the plane with a one-cell halo (FP32
+//                                   search direction; x rounded down to a multiple
+//                                   of 4: a copy's first x times 4 bytes must be
+//                                   16-byte aligned)
 // Copies that reach outside the box are filled with zeros by the hardware,
 // which are exactly the Neumann faces (T = 0) and harmless finite neighbours.
 // Each stage completes an mbarrier (transaction bytes).  Thread 0 waits for
@@ -46,11 +47,11 @@ constexpr int kThreads = (kConsumers + 1) * 32;   // + one producer warp
 constexpr int kT0X = 34, kT0Y = 8;
 constexpr int kT1X = 32, kT1Y = 9;
 constexpr int kT2X = 32, kT2Y = 8;
-constexpr int kWX = 36, kWY = 10;
+constexpr int kWX = 40, kWY = 10;  // w is FP32: x from i0-4 (16-byte aligned)
 constexpr int kT0Bytes = kT0X * kT0Y * 8;   // 2176
 constexpr int kT1Bytes = kT1X * kT1Y * 8;   // 2304
 constexpr int kT2Bytes = kT2X * kT2Y * 8;   // 2048
-constexpr int kWBytes = kWX * kWY * 8;      // 2880
+constexpr int kWBytes = kWX * kWY * 4;      // 1600
 constexpr int kTx = kT0Bytes + kT1Bytes + kT2Bytes + kWBytes;
 constexpr int align128(int b) { return (b + 127) / 128 * 128; }
 constexpr int kOffT1 = align128(kT0Bytes);
@@ -60,31 +61,32 @@ constexpr int kStageBytes = kOffW + align128(kWBytes);
 // + the mbarriers, + slack to align the stages to 128 bytes at run time
 constexpr int kSmemBytes = kStages * kStageBytes + 128 + 128;
 static_assert(2 * kStages * 8 <= 128, "full and empty barriers fit behind the stages");
-// p + pe ~ T (a - b) and the Sum2 step, as in kernels.cu
+// The Sum2 step and the products of the double-float matvec, as in kernels.cu
 __device__ __forceinline__ void two_sum_(float a, float b, float& s, float& t) {
   s = a + b;
   const float bb = s - a;
   t = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void flux_(float2 T, float2 a, float2 b, float& p, float& pe) {
-  float dh, dl;
-  two_sum_(a.x, -b.x, dh, dl);
-  dl += a.y - b.y;
-  p = T.x * dh;
-  pe = fma(T.x, dh, -p);
-  pe = fma(T.x, dl, pe);
-  pe = fma(T.y, dh, pe);
 }
 __device__ __forceinline__ void acc_(float p, float pe, float& s, float& e) {
   float t;
   two_sum_(s, p, s, t);
   e += t + pe;
 }
-__device__ __forceinline__ void prod_acc_(float2 x, float2 y, float& s, float& e) {
-  const float p = x.x * y.x;
-  float pe = fma(x.x, y.x, -p);
-  pe = fma(x.x, y.y, pe);
-  pe = fma(x.y, y.x, pe);
+// p + pe ~ T (a - b) for FP32 a, b (the search direction): TwoSum gives the
+// difference exactly as dh + dl
+__device__ __forceinline__ void flux_f(float2 T, float a, float b, float& p, float& pe) {
+  float dh, dl;
+  two_sum_(a, -b, dh, dl);
+  p = T.x * dh;
+  pe = fma(T.x, dh, -p);
+  pe = fma(T.x, dl, pe);
+  pe = fma(T.y, dh, pe);
+}
+// (s, e) += x w for double-float x and FP32 w
+__device__ __forceinline__ void prod_acc_f(float2 x, float w, float& s, float& e) {
+  const float p = x.x * w;
+  float pe = fma(x.x, w, -p);
+  pe = fma(x.y, w, pe);
   acc_(p, pe, s, e);
 }
 
@@ -93,7 +95,7 @@ __device__ __forceinline__ void prod_acc_(float2 x, float2 y, float& s, float& e
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 4)
     k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
-                    const float2* __restrict__ w, float2* __restrict__ q,
+                    const float* __restrict__ w, float2* __restrict__ q,
                     const float2* __restrict__ T2, const float2* __restrict__ Bin,
                     const float2* __restrict__ Bout, double* partials, int par, int kchunk,
                     unsigned int tx_extra) {
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, 4)
         tma_load3(sg, &mp.T0, i0, j0, k, full + s);
         tma_load3(sg + kOffT1, &mp.T1, i0, j0, k, full + s);
         tma_load3(sg + kOffT2, &mp.T2, i0, j0, k + 1, full + s);
-        tma_load3(sg + kOffW, &mp.w, i0 - 2, j0 - 1, k, full + s);
+        tma_load3(sg + kOffW, &mp.w, i0 - 4, j0 - 1, k, full + s);
         ++issued;
       }
       // no copy may still be landing when the block exits (bounded)
@@ -158,11 +160,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     float fz = 0.f, fze = 0.f;
     if (own && k0 > 0) {
       const long long c = (long long)k0 * pl + sidx;
-      flux_(T2[c], w[c - pl], w[c], fz, fze);
+      flux_f(T2[c], w[c - pl], w[c], fz, fze);
     }
-    // this thread's element offsets inside a stage (float2 units)
+    // this thread's element offsets inside a stage (float2 units; w: float)
     const int oT0 = r * kT0X + l, oT1 = r * kT1X + l, oT2 = r * kT2X + l;
-    const int oW = (r + 1) * kWX + l + 2;
+    const int oW = (r + 1) * kWX + l + 4;
     float2* pq = q + (long long)k0 * pl + sidx;
     unsigned int sc = 0, pc = 0;  // stage and parity of plane k
     for (int k = k0; k < k1; ++k) {
@@ -180,28 +182,28 @@ __global__ void __launch_bounds__(kThreads, 4)
         const float2* sT0 = reinterpret_cast<const float2*>(sg) + oT0;
         const float2* sT1 = reinterpret_cast<const float2*>(sg + kOffT1) + oT1;
         const float2* sT2 = reinterpret_cast<const float2*>(sg + kOffT2) + oT2;
-        const float2* sW = reinterpret_cast<const float2*>(sg + kOffW) + oW;
-        const float2 wc = sW[0];
-        const float2 wp =
-            k + 1 <= kend ? reinterpret_cast<const float2*>(smem + sn * kStageBytes + kOffW)[oW]
+        const float* sW = reinterpret_cast<const float*>(sg + kOffW) + oW;
+        const float wc = sW[0];
+        const float wp =
+            k + 1 <= kend ? reinterpret_cast<const float*>(smem + sn * kStageBytes + kOffW)[oW]
                           : wc;
         float sv, ev, p, pe;
-        flux_(sT0[0], wc, sW[-1], sv, ev);
-        flux_(sT0[1], wc, sW[1], p, pe);
+        flux_f(sT0[0], wc, sW[-1], sv, ev);
+        flux_f(sT0[1], wc, sW[1], p, pe);
         acc_(p, pe, sv, ev);
-        flux_(sT1[0], wc, sW[-kWX], p, pe);
+        flux_f(sT1[0], wc, sW[-kWX], p, pe);
         acc_(p, pe, sv, ev);
-        flux_(sT1[kT1X], wc, sW[kWX], p, pe);
+        flux_f(sT1[kT1X], wc, sW[kWX], p, pe);
         acc_(p, pe, sv, ev);
         acc_(-fz, -fze, sv, ev);
-        flux_(sT2[0], wc, wp, fz, fze);
+        flux_f(sT2[0], wc, wp, fz, fze);
         acc_(fz, fze, sv, ev);
-        if (k == 0) prod_acc_(Bin[sidx], wc, sv, ev);
-        if (k == g.n2 - 1) prod_acc_(Bout[sidx], wc, sv, ev);
+        if (k == 0) prod_acc_f(Bin[sidx], wc, sv, ev);
+        if (k == g.n2 - 1) prod_acc_f(Bout[sidx], wc, sv, ev);
         float qh, ql;
         two_sum_(sv, ev, qh, ql);
         *pq = make_float2(qh, ql);
-        if (MODE == 1) prod_acc_(wc, make_float2(qh, ql), ds, dc);
+        if (MODE == 1) prod_acc_f(make_float2(qh, ql), wc, ds, dc);
       }
       // the warp is done with plane k's stage (plane k-1 no longer reads it)
       __syncwarp();
@@ -237,28 +239,32 @@ __global__ void __launch_bounds__(kThreads, 4)
 
 namespace {
 
-bool encode3(CUtensorMap* m, const void* base, int n0, int n1, int nz, int bx, int by) {
+// esize 8: double-float pairs, 4: FP32
+bool encode3(CUtensorMap* m, const void* base, int esize, int n0, int n1, int nz, int bx,
+             int by) {
   const unsigned long long dim[3] = {(unsigned long long)n0, (unsigned long long)n1,
                                      (unsigned long long)nz};
-  const unsigned long long stride[2] = {(unsigned long long)n0 * 8,
-                                        (unsigned long long)n0 * n1 * 8};
+  const unsigned long long stride[2] = {(unsigned long long)n0 * esize,
+                                        (unsigned long long)n0 * n1 * esize};
   const unsigned int box[3] = {(unsigned int)bx, (unsigned int)by, 1};
-  return tma_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dim, stride, box);
+  return tma_encode(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    3, base, dim, stride, box);
 }
 
 }  // namespace
 
 bool matvec_tma_maps(const Geometry& g, const float2* T0, const float2* T1, const float2* T2,
-                     const float2* w, MatvecMaps* mp) {
-  // row strides must be multiples of 16 bytes (n0 even) and the bases 16-byte aligned
-  if (g.n0 % 2 != 0) return false;
+                     const float* w, MatvecMaps* mp) {
+  // row strides must be multiples of 16 bytes (n0 a multiple of 4 for the FP32
+  // w) and the bases 16-byte aligned
+  if (g.n0 % 4 != 0) return false;
   for (const void* p : {(const void*)T0, (const void*)T1, (const void*)T2, (const void*)w})
     if (reinterpret_cast<unsigned long long>(p) % 16 != 0) return false;
   std::memset(mp, 0, sizeof(*mp));
-  return encode3(&mp->T0, T0, g.n0, g.n1, g.n2, kT0X, kT0Y) &&
-         encode3(&mp->T1, T1, g.n0, g.n1, g.n2, kT1X, kT1Y) &&
-         encode3(&mp->T2, T2, g.n0, g.n1, g.n2 + 1, kT2X, kT2Y) &&  // + the zero plane
-         encode3(&mp->w, w, g.n0, g.n1, g.n2, kWX, kWY);
+  return encode3(&mp->T0, T0, 8, g.n0, g.n1, g.n2, kT0X, kT0Y) &&
+         encode3(&mp->T1, T1, 8, g.n0, g.n1, g.n2, kT1X, kT1Y) &&
+         encode3(&mp->T2, T2, 8, g.n0, g.n1, g.n2 + 1, kT2X, kT2Y) &&  // + the zero plane
+         encode3(&mp->w, w, 4, g.n0, g.n1, g.n2, kWX, kWY);
 }
 
 cudaError_t set_matvec_tma_attrs() {
@@ -270,7 +276,7 @@ cudaError_t set_matvec_tma_attrs() {
 }
 
 cudaError_t launch_matvec_df_tma(const Geometry& g, const MatvecMaps& mp, PcgState* st,
-                                 const float2* w, float2* q, const float2* T2, const float2* FB,
+                                 const float* w, float2* q, const float2* T2, const float2* FB,
                                  double* partials, int par, int mode, cudaStream_t s,
                                  unsigned int tx_extra) {
   int kc;
