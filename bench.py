@@ -98,11 +98,11 @@ def kernel_model(n0, n1, mixed=False, f64_vectors=False):
     work); the FP32 tridiagonal kernel generates its pivots per column and
     reads r^ and last iteration's r^ (flexible beta) and writes z^: 12 bytes (its
     second read of r^ and the chunk checkpoints, 6 more, are not counted).  Its
-    x, r, w and q are double-float
-    pairs (same bytes as FP64) updated on the FP32 pipe; the matvec reads
-    double-float faces and w and writes q (face-difference form, no diagonal:
-    40 bytes); x += alpha w moves from fwd_x (r, q in, r and the FP32
-    transform out) to inv_x (t, w and x in, w and x out).
+    x, r and q are double-float pairs (same bytes as FP64) updated on the FP32
+    pipe and its search direction w is FP32; the matvec reads double-float
+    faces and the FP32 w and writes q (face-difference form, no diagonal:
+    36 bytes); x += alpha w moves from fwd_x (r, q in, r and the FP32
+    transform out) to inv_x (t, w and x in, w and x out: 28 bytes).
     """
     fx, fy = dct_flops_per_point(n0, False), dct_flops_per_point(n1, False)
     ix, iy = dct_flops_per_point(n0, True), dct_flops_per_point(n1, True)
@@ -112,8 +112,8 @@ def kernel_model(n0, n1, mixed=False, f64_vectors=False):
     if not mixed:
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
                 "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
-    return {"matvec": (0.0, 40.0), "fwd_x": (0.0, 28.0), "fwd_y": (0.0, 8.0),
-            "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (0.0, 36.0)}
+    return {"matvec": (0.0, 36.0), "fwd_x": (0.0, 28.0), "fwd_y": (0.0, 8.0),
+            "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (0.0, 28.0)}
 
 
 # ------------------------------------------------------------------ helpers

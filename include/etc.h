@@ -62,8 +62,9 @@ enum {
  * flexible (Polak-Ribiere) PCG; their scalars and reductions are FP64. */
 enum {
   ETC_PREC_FP64 = 0,      /* everything in FP64: plain PCG (Algorithm 1) */
-  ETC_PREC_MIXED = 1,     /* x, r, w, q and the operator in double-float (pairs of
-                             FP32 values, 48-bit significand) on the FP32 pipe */
+  ETC_PREC_MIXED = 1,     /* x, r, q and the operator in double-float (pairs of
+                             FP32 values, 48-bit significand) on the FP32 pipe; the
+                             search direction w in FP32 */
   ETC_PREC_MIXED_F64 = 2  /* x, r, w, q and the operator in FP64 */
 };
 
