@@ -782,7 +782,7 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
   if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
   if (st.status == ETC_EBREAKDOWN) return fail(h, ETC_EBREAKDOWN, "PCG breakdown");
   if (st.status == ETC_ECUDA)
-    return fail(h, ETC_ECUDA, "a bounded device wait ran out (matvec bulk-tensor copies)");
+    return fail(h, ETC_ECUDA, "a bounded device wait for bulk-tensor copies ran out");
   return ETC_OK;
 }
 
