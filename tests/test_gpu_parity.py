@@ -380,7 +380,7 @@ def test_bulk_copy_wait_runs_out_reports_ecuda_and_recovers():
         os.environ.pop("ETC_TEST_TMA_TX_EXTRA", None)
     with pytest.raises(B.EtcError) as e:
         rve.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
-    assert e.value.status == B.ETC_ECUDA and "wait ran out" in str(e.value)
+    assert e.value.status == B.ETC_ECUDA and "wait for bulk-tensor copies ran out" in str(e.value)
     rve.close()
     rve2 = make(k)
     kap_m, info = rve2.solve(2, rtol=1e-8, precision=B.ETC_PREC_MIXED)
