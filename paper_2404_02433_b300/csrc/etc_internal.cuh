@@ -330,9 +330,9 @@ __device__ __forceinline__ void df_fma_acc(float2 x, float2 y, float& s, float& 
 namespace etc {
 
 // ---------------------------------------------------------------- PCG vector storage
-// The outer PCG vectors (x, r, w, q) are FP64 in the FP64 path and
-// double-float pairs (float2) in the mixed path; these overloads give the
-// kernels one source for both.
+// The outer PCG vectors (x, r, w, q) are FP64 in the FP64 path; the mixed
+// path keeps x, r, q as double-float pairs (float2) and the search direction w
+// in FP32.  These overloads give the kernels one source for all of them.
 
 // y + a x.  For double-float: TwoProduct of the high parts by FMA plus the
 // cross terms, TwoSum with y's high part, then renormalisation.

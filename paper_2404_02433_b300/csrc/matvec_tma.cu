@@ -6,8 +6,8 @@
 // in double-float pairs on the FP32 pipe, summed by Sum2, with the partial
 // w.q of Algorithm 1 (alpha = rho / w.q) in MODE 1.  Only the way the
 // operands reach the threads differs.  A block owns a 32 x 8 column tile and
-// marches over kchunk planes; one thread issues, for each plane, four tiled
-// bulk-tensor copies into a ring of kStages shared-memory stages:
+// marches over kchunk planes; for each plane, four tiled bulk-tensor copies
+// land in a ring of kStages shared-memory stages:
 //   T0 (x i0 .. i0+33, 8 rows)      the minus x faces and the plus face of the last column
 //   T1 (32 columns, y j0 .. j0+8)   the minus y faces and the plus faces of the last row
 //   T2 of plane k+1 (32 x 8)        the faces above the plane
@@ -17,13 +17,16 @@
 //                                   16-byte aligned)
 // Copies that reach outside the box are filled with zeros by the hardware,
 // which are exactly the Neumann faces (T = 0) and harmless finite neighbours.
-// Each stage completes an mbarrier (transaction bytes).  Thread 0 waits for
-// planes k and k+1 (the z neighbour), a block barrier hands them to all
-// threads and frees the stage of plane k-1, into which thread 0 then issues
-// plane k+kStages-1: the copies of up to kStages-2 planes are in flight while
-// a plane is summed, without holding registers.  Every wait is bounded: a
-// wait that runs out sets status ETC_ECUDA and done in the solver state,
-// drains this block's copies (bounded again) and returns.  tx_extra (0 in
+// The block is warp-specialised: 8 consumer warps (one tile row each) and one
+// producer warp.  Each stage has a "full" mbarrier (completed by the copies'
+// transaction bytes) and an "empty" one (one arrival per consumer warp).  The
+// producer issues plane k into its stage once the consumers have released the
+// stage's previous plane; each consumer warp waits for planes k and k+1 (the
+// z neighbour), sums its row of plane k and releases that stage.  There is no
+// block barrier in the loop; the copies of up to kStages-1 planes are in
+// flight without holding registers.  Every wait is bounded: a wait that runs
+// out sets status ETC_ECUDA and done in the solver state, the producer drains
+// the block's copies (bounded again) and the block returns.  tx_extra (0 in
 // use) adds bytes that no copy delivers to every stage's expected count: a
 // test sets it (ETC_TEST_TMA_TX_EXTRA, read at create) so that the waits run
 // out and the error path runs without any fault.
