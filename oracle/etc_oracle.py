@@ -31,8 +31,10 @@ places where the paper is garbled or silent:
   * Off-diagonal tensor entries are not defined by the paper (Sec. 2.1 defers
     to a citation); ``effective_tensor`` defines K[a][b] = L^b <v_a> / dp under
     load b, <v_a> the volume average of the cell-averaged a-face fluxes.
-    This entry is "parity unpinned" beyond its invariants (zero for mirror
-    symmetric media, equal to the diagonal formula for a == b).
+    The definition is a reading; the code that evaluates it is pinned by a
+    hand-solved 2 x 2 checkerboard (nonzero K[x][z], non-cubic boxes), by
+    zero entries for mirror-symmetric media and by the diagonal formula for
+    a == b.
 """
 from __future__ import annotations
 
