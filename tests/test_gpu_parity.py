@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 from oracle import etc_oracle as O
 from paper_2404_02433_b300 import binding as B
 from paper_2404_02433_b300 import microstructure as M
+from closed_forms import checkerboard_closed_form
 
 pytestmark = pytest.mark.gpu
 
@@ -184,6 +185,25 @@ def test_tensor_matches_oracle(shape):
     for d in range(3):
         assert abs(infos[d]["iters"] - res_o[d].iters) <= 1
         assert abs(infos[d]["kappa_in"] - res_o[d].kappa_eff) <= 1e-8 * res_o[d].kappa_eff
+
+
+@pytest.mark.parametrize("ny,lengths", [(1, (1.0, 1.0, 1.0)), (3, (2.0, 0.5, 1.0))])
+def test_checkerboard_off_diagonal_closed_form(ny, lengths):
+    # 2 x 2 checkerboard [[a, b], [b, a]] in the x-z plane: nonzero K[x][z]
+    # and K[z][x], solved by hand (half-turn symmetry, 2 x 2 system)
+    a, b = 3.0, 0.7
+    k = np.empty((2, ny, 2))
+    k[0, :, 0], k[0, :, 1], k[1, :, 0], k[1, :, 1] = a, b, b, a
+    lx, _, lz = lengths
+    rve = make(k, lengths=lengths)
+    K, _, st = rve.tensor(rtol=1e-12)
+    K = np.array(K).reshape(3, 3)
+    assert st == B.ETC_OK
+    kxz, kzz = checkerboard_closed_form(a, b, lx, lz)
+    kzx, kxx = checkerboard_closed_form(a, b, lz, lx)
+    np.testing.assert_allclose([K[0, 2], K[2, 2], K[2, 0], K[0, 0], K[1, 1]],
+                               [kxz, kzz, kzx, kxx, 0.5 * (a + b)], rtol=1e-10)
+    assert max(abs(K[0, 1]), abs(K[1, 0]), abs(K[1, 2]), abs(K[2, 1])) < 1e-12
 
 
 def test_homogeneous_one_iteration_exact():

@@ -13,6 +13,7 @@ import scipy.fft
 
 from oracle import etc_oracle as O
 from paper_2404_02433_b300 import microstructure as M
+from closed_forms import checkerboard_closed_form
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -228,32 +229,6 @@ def test_mirror_symmetric_medium_has_zero_off_diagonals():
     np.testing.assert_allclose(np.diag(K), K[0, 0], rtol=1e-10)
 
 
-def _checkerboard_closed_form(a, b, lx, lz):
-    """Load along z of the 2 x 2 checkerboard [[a, b], [b, a]] in the x-z plane.
-
-    Hand solution of the four-cell network of Sec. 2.2 (A = (0,0) kappa a,
-    B = (1,0) kappa b, C = (0,1) kappa b, D = (1,1) kappa a; p_in = 1 at
-    k = -1/2, p_out = 0).  A half-turn about y maps the medium to itself and
-    swaps the two Dirichlet faces, so p_C = 1 - p_B and p_D = 1 - p_A; the
-    balances at A and B are then a 2 x 2 system, solved by Cramer's rule.
-    Returns (K[x][z], K[z][z]) of the off-diagonal definition (mean x-face
-    flux times L^z / dp) and of the outflow formula.
-    """
-    hx, hz = lx / 2.0, lz / 2.0
-    m = 2.0 * a * b / (a + b)
-    tx, tz = m / hx ** 2, m / hz ** 2            # harmonic faces of kappa~
-    ba, bb = 2.0 * a / hz ** 2, 2.0 * b / hz ** 2  # Dirichlet faces 2 kappa~^z
-    a11, a12, r1 = tx + tz + ba, tz - tx, tz + ba
-    a21, a22, r2 = tz - tx, tx + tz + bb, tz + bb
-    det = a11 * a22 - a12 * a21
-    pa = (r1 * a22 - a12 * r2) / det
-    pb = (a11 * r2 - a21 * r1) / det
-    mean_vx = 2.0 * tx * hx * (pa - pb) / 4.0     # two x faces, four cells
-    kxz = lz * mean_vx
-    kzz = lz * hz * (bb * (1.0 - pb) + ba * (1.0 - pa)) / 2.0
-    return kxz, kzz
-
-
 @pytest.mark.parametrize("ny,lengths", [(1, (1.0, 1.0, 1.0)), (3, (2.0, 0.5, 1.0)),
                                         (2, (0.5, 1.0, 3.0))])
 def test_checkerboard_off_diagonal_closed_form(ny, lengths):
@@ -261,7 +236,7 @@ def test_checkerboard_off_diagonal_closed_form(ny, lengths):
 
     The medium has no mirror symmetry in x alone, so K[x][z] != 0.  Its value
     and sign, the h factors of a non-cubic box and the loading-frame
-    permutation are all fixed by ``_checkerboard_closed_form``; load x is the
+    permutation are all fixed by ``checkerboard_closed_form``; load x is the
     same checkerboard with the roles of x and z (and of L^x, L^z) swapped, and
     load y sees four identical parallel columns (arithmetic mean).
     """
@@ -270,8 +245,8 @@ def test_checkerboard_off_diagonal_closed_form(ny, lengths):
     k[0, :, 0], k[0, :, 1], k[1, :, 0], k[1, :, 1] = a, b, b, a
     lx, ly, lz = lengths
     K, _ = O.effective_tensor(k, lengths=lengths, rtol=1e-13)
-    kxz, kzz = _checkerboard_closed_form(a, b, lx, lz)
-    kzx, kxx = _checkerboard_closed_form(a, b, lz, lx)
+    kxz, kzz = checkerboard_closed_form(a, b, lx, lz)
+    kzx, kxx = checkerboard_closed_form(a, b, lz, lx)
     assert abs(kxz) > 0.05
     np.testing.assert_allclose(K[0, 2], kxz, rtol=1e-10)
     np.testing.assert_allclose(K[2, 2], kzz, rtol=1e-10)
