@@ -68,7 +68,7 @@ def test_gradient_identities_and_autograd():
     y = effective_conductivity(logk, direction=1, rtol=1e-12)
     y.backward()
     g = logk.grad.cpu().numpy()
-    assert g.sum() == pytest.approx(float(y), rel=1e-9)
+    assert g.sum() == pytest.approx(float(y.detach()), rel=1e-9)
     assert g.min() >= -1e-12 * float(y)
     # directional derivative against central differences through the Function
     v = np.random.default_rng(1).standard_normal(k.shape)
@@ -77,6 +77,21 @@ def test_gradient_identities_and_autograd():
         up = effective_conductivity(logk + eps * dev(v), direction=1, rtol=1e-13)
         dn = effective_conductivity(logk - eps * dev(v), direction=1, rtol=1e-13)
     assert float((up - dn) / (2 * eps)) == pytest.approx(float((g * v).sum()), rel=1e-5)
+
+
+def test_autograd_forward_without_gradient_skips_the_adjoint():
+    # without requires_grad (or under no_grad) the Function runs one PCG solve
+    k = M.lognormal_field((20, 24, 16), 6.0, 1.0, 11)
+    logk = dev(np.log(k))
+    n0 = B.etc_kernel_launches()
+    with torch.no_grad():
+        y0 = effective_conductivity(logk.clone().requires_grad_(True), direction=0, rtol=1e-12)
+    n1 = B.etc_kernel_launches()
+    y1 = effective_conductivity(logk.clone().requires_grad_(True), direction=0, rtol=1e-12)
+    n2 = B.etc_kernel_launches()
+    assert float(y0) == pytest.approx(float(y1), rel=1e-12)
+    assert (n1 - n0) < (n2 - n1)
+    assert float(effective_conductivity(logk, direction=0, rtol=1e-12)) == float(y0)
 
 
 def test_gradient_full_size_adjoint_config():
