@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -192,12 +193,26 @@ def gpu_index(local_rank):
     return str(local_rank)
 
 
+_COMMENT_OR_LITERAL = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'',
+                                 re.S)
+
+
+def code_only(text):
+    """C++/CUDA source with comments, trailing blanks and empty lines removed
+    (string and character literals kept)."""
+    text = _COMMENT_OR_LITERAL.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+
+
 def src_hash():
+    """First 16 hex digits of the sha256 of the library's code (csrc/, file
+    names and code without comments).  Recorded counters stay valid across
+    edits of comments and are dropped after any change of code."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2404_02433_b300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(name.encode()); h.update(fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            h.update(name.encode()); h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

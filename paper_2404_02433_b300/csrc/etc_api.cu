@@ -3,10 +3,15 @@
 // A handle owns the voxel conductivities, the per-direction face arrays, the
 // PCG vectors, the cosine-transform tables and a small device state block.  A
 // solve (Sec. 2.2 "complete routine") is: permute to the loading frame, face
-// assembly with group extrema (K-setup), reference parameters on the host
-// (Algorithm 2), pivot tables of the tridiagonal systems, then PCG
-// (Algorithm 1 with Algorithm 3) on the handle's stream, then the outflow
-// formula (Eq. effective formula dis).
+// assembly with group extrema, reference parameters from the closed-form
+// optimum of Algorithm 2 (evaluated on the device from the extrema), pivot
+// tables of the tridiagonal systems, then PCG (Algorithm 1 with Algorithm 3)
+// on the handle's stream, then the outflow formula (Eq. effective formula dis).
+//
+// Host-side phases are marked with NVTX ranges ("etc_create_rve",
+// "etc_solve dir=x|y|z", "etc_setup", "etc_pcg", "etc_post", "etc_gradient",
+// "etc_batch_run") for profilers that filter by range; without a profiler
+// attached they cost one predictable branch each.
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -19,6 +24,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/etc.h"
 #include "dct_device.cuh"
 #include "etc_internal.cuh"
@@ -27,6 +34,27 @@
 using namespace etc;
 
 namespace {
+
+// An NVTX range for the lifetime of the object (every return path pops it).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
+// CUDA events destroyed with the object (every return path).
+template <int N>
+struct EventSet {
+  cudaEvent_t e[N] = {};
+  EventSet() = default;
+  EventSet(const EventSet&) = delete;
+  EventSet& operator=(const EventSet&) = delete;
+  ~EventSet() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+};
 
 struct PlanStore {
   DctPlan<double> p64;
@@ -723,23 +751,29 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
   etc_status s = ETC_OK;
   const int prec = o.precision;
   const Geometry g = geom_of(h, dir);
-  cudaEvent_t e[3];
+  EventSet<3> te;
+  cudaEvent_t* e = te.e;
   for (int i = 0; i < 3; ++i) CK(cudaEventCreate(&e[i]));
   CK(cudaEventRecord(e[0], h->stream));
-  CK(launch_state_reset(h->st, o.maxit, h->stream));
-  s = setup_faces(h, dir);
-  if (s != ETC_OK) return s;
-  s = autotune(h, dir, prec);
-  if (s != ETC_OK) return s;
-  s = launch_reference(h, dir, prec);
-  if (s != ETC_OK) return s;
+  {
+    Range r("etc_setup");
+    CK(launch_state_reset(h->st, o.maxit, h->stream));
+    s = setup_faces(h, dir);
+    if (s != ETC_OK) return s;
+    s = autotune(h, dir, prec);
+    if (s != ETC_OK) return s;
+    s = launch_reference(h, dir, prec);
+    if (s != ETC_OK) return s;
+  }
   CK(cudaEventRecord(e[1], h->stream));
+  Range rpcg("etc_pcg");
   s = launch_start(h, g, x, prec, rhs, o.rtol * o.rtol);
   if (s != ETC_OK) return s;
 
   int launched = 0, slot = 1, prev_slot = 2, chunk = 2;
   bool have_prev = false;
-  cudaEvent_t ev[3];
+  EventSet<3> tev;
+  cudaEvent_t* ev = tev.e;
   for (int i = 0; i < 3; ++i) CK(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
   const long long hard_cap = (long long)o.maxit + 64;
   for (;;) {
@@ -765,18 +799,19 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
       return fail(h, ETC_ECUDA, "PCG did not report completion within maxit iterations");
     }
   }
-  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   s = finish_solve_x(h, g, x, prec);
   if (s != ETC_OK) return s;
-  s = launch_post(h, g, x, rhs, o.true_residual);
-  if (s != ETC_OK) return s;
-  CK(cudaEventRecord(e[2], h->stream));
-  s = read_state(h, 1);
-  if (s != ETC_OK) return s;
+  {
+    Range r("etc_post");
+    s = launch_post(h, g, x, rhs, o.true_residual);
+    if (s != ETC_OK) return s;
+    CK(cudaEventRecord(e[2], h->stream));
+    s = read_state(h, 1);
+    if (s != ETC_OK) return s;
+  }
   float ms_setup = 0, ms_solve = 0;
   cudaEventElapsedTime(&ms_setup, e[0], e[1]);
   cudaEventElapsedTime(&ms_solve, e[1], e[2]);
-  for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
   const PcgState& st = h->st_host[1];
   fill_results(h, dir, rhs, o.true_residual, st, ms_setup, ms_solve, kappa_eff, info);
   if (st.status == ETC_ENOCONV) return fail(h, ETC_ENOCONV, "maxit reached");
@@ -939,6 +974,7 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   if (!kx) return ETC_EINVAL;
   const long long n = (long long)nx * ny * nz;
   if (n > (1LL << 34)) return ETC_EINVAL;
+  Range range("etc_create_rve");
   h = new etc_rve();
   h->nx = nx; h->ny = ny; h->nz = nz;
   h->L[0] = lx; h->L[1] = ly; h->L[2] = lz;
@@ -1089,6 +1125,8 @@ etc_status etc_set_reference_params(etc_rve* h, int dir, int mode, const double*
 etc_status etc_solve_direction(etc_rve* h, int dir, double p_in, double p_out,
                                const etc_opts* opts_in, double* kappa_eff, etc_info* info) {
   if (!h) return ETC_EINVAL;
+  static const char* const names[3] = {"etc_solve dir=x", "etc_solve dir=y", "etc_solve dir=z"};
+  Range r(dir >= 0 && dir < 3 ? names[dir] : "etc_solve");
   etc_opts o;
   etc_status s = check_solve_args(h, dir, p_in, p_out, opts_in, &o);
   if (s != ETC_OK) return s;
@@ -1148,6 +1186,7 @@ etc_status etc_solve_general(etc_rve* h, int dir, const double* p_in_face, const
 etc_status etc_gradient(etc_rve* h, int dir, double p_in, double p_out, const etc_opts* opts_in,
                         int per_component, double* grad, double* kappa_eff, etc_info* info) {
   if (!h || !grad) return ETC_EINVAL;
+  Range range("etc_gradient");
   etc_opts o;
   etc_status s = check_solve_args(h, dir, p_in, p_out, opts_in, &o);
   if (s != ETC_OK) return s;
@@ -1432,6 +1471,7 @@ etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opt
 
 etc_status etc_batch_run(etc_batch* b, double* K, etc_info* info, double* ms) {
   if (!b || !K) return ETC_EINVAL;
+  Range range("etc_batch_run");
   for (etc_rve* h : b->rves)
     if ((h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize()) != cudaSuccess)
       return ETC_ECUDA;
