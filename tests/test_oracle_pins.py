@@ -283,6 +283,66 @@ def test_lp_brute_force_tiny():
             assert O.condition_bound(ext, kref) >= best * (1 - 1e-12)
 
 
+def _brute_extrema(kx, ky, kz, lengths):
+    # face by face: harmonic mean of kappa~ = kappa / h^2 of the two cells, over
+    # internal faces of each axis; kappa~^z on the first and last z plane
+    nz, ny, nx = kx.shape
+    h = (lengths[0] / nx, lengths[1] / ny, lengths[2] / nz)
+    groups = [[], [], [], [], []]
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for g, (comp, nb) in enumerate(((kx, (k, j, i + 1)), (ky, (k, j + 1, i)),
+                                                (kz, (k + 1, j, i)))):
+                    if nb[0] < nz and nb[1] < ny and nb[2] < nx:
+                        a = comp[k, j, i] / h[g] ** 2
+                        b = comp[nb] / h[g] ** 2
+                        groups[g].append(2.0 / (1.0 / a + 1.0 / b))
+                if k == 0:
+                    groups[3].append(kz[k, j, i] / h[2] ** 2)
+                if k == nz - 1:
+                    groups[4].append(kz[k, j, i] / h[2] ** 2)
+    return [(min(v), max(v)) if v else None for v in groups]
+
+
+def _dense_of(f, shape):
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for c in range(n):
+        e = np.zeros(n); e[c] = 1.0
+        A[:, c] = O.apply_operator(f, e.reshape(shape)).ravel()
+    return A
+
+
+@pytest.mark.parametrize("seed", [3, 11, 20, 38])
+def test_lemma_3_1_spectral_bounds(seed):
+    # Lemma 3.1: Lambda' <= p.Ap / p.A_ref p <= Lambda'' for every p, with
+    # Lambda' = min_g min_g/kappa_ref^g and Lambda'' = max_g max_g/kappa_ref^g,
+    # so every generalised eigenvalue of (A, A_ref) lies in [Lambda', Lambda''].
+    import scipy.linalg
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(v) for v in rng.integers(2, 5, 3))
+    kx, ky, kz = (np.exp(rng.uniform(-2.0, 2.0, shape)) for _ in range(3))
+    lengths = tuple(rng.uniform(0.5, 2.0, 3))
+    f = O.face_conductances(kx, ky, kz, lengths)
+    ext = O.group_extrema(f)
+    np.testing.assert_allclose(np.array(ext), np.array(_brute_extrema(kx, ky, kz, lengths)),
+                               rtol=1e-14)
+    A = _dense_of(f, shape)
+    for method in ("centred", "linprog"):
+        kref = O.reference_parameters(ext, method)
+        ev = scipy.linalg.eigh(A, _dense_of(O.reference_operator_faces(kref, shape), shape),
+                               eigvals_only=True)
+        lo = min(e[0] / k for e, k in zip(ext, kref))
+        hi = max(e[1] / k for e, k in zip(ext, kref))
+        assert ev.min() >= lo * (1 - 1e-10) and ev.max() <= hi * (1 + 1e-10)
+        assert O.condition_bound(ext, kref) == pytest.approx(hi / lo, rel=1e-14)
+        if seed == 20 and method == "centred":
+            # the bound as printed (out group divided by kappa_ref^in) does not hold
+            lo_p = min([e[0] / k for e, k in zip(ext[:4], kref[:4])] + [ext[4][0] / kref[3]])
+            assert ev.min() < lo_p * (1 - 1e-6)
+
+
 # ---------------------------------------------------------------- the paper's numbers
 def _table3():
     rows = []
