@@ -27,7 +27,10 @@
  *   - Every function returns an etc_status, never throws and never exits.
  *     Arguments are validated on the host before any GPU work; a rejected call
  *     returns ETC_EINVAL and changes nothing.  After ETC_ECUDA the handle should
- *     be destroyed.  etc_last_error() gives a one-line reason.
+ *     be destroyed.  etc_last_error(handle) gives a one-line reason;
+ *     etc_last_error(NULL) gives the reason for the calling thread's last call
+ *     of etc_create_rve, etc_batch_create or etc_apply_reference_inverse_static
+ *     ("" if it succeeded).
  *   - Test hooks read at etc_create_rve from the environment (both unset in
  *     use): ETC_FAIL_ALLOC_AFTER=k fails the handle's (k+1)-th device allocation
  *     (ETC_ENOMEM, clean teardown); ETC_TEST_TMA_TX_EXTRA=b makes the
@@ -278,7 +281,7 @@ unsigned long long etc_kernel_launches(void);
  * Same operation as etc_apply_preconditioner in FP64, but without a handle:
  *   n0, n1, n2  loading-frame sizes, r and z in that layout ([n2][n1][n0]);
  *               limits: n0, n1 <= 2048 and n0*n1*n2 <= 2^20 cells, else
- *               ETC_EINVAL.
+ *               ETC_EINVAL, with the limits in etc_last_error(NULL).
  *   kref        5 reference parameters (x, y, z, in, out; finite, > 0), host.
  *   r, z        device pointers, n0*n1*n2 doubles each, not overlapping.
  *   stream      cudaStream_t the work is queued on; the call does not wait.

@@ -121,11 +121,14 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def _check(status, handle=None, ok=(ETC_OK,)):
+def _check(status, handle=None, ok=(ETC_OK,), thread_reason=False):
+    """Raise EtcError unless status is in ok.  The message is the handle's last
+    error, or with thread_reason the reason etc_last_error(NULL) keeps for the
+    handle-less calls (create, batch create, the allocation-free apply)."""
     if status in ok:
         return status
     lib = load_library()
-    msg = lib.etc_last_error(handle).decode() if handle else ""
+    msg = lib.etc_last_error(handle if handle else None).decode() if (handle or thread_reason) else ""
     if not msg:
         msg = lib.etc_status_string(status).decode()
     raise EtcError(status, msg)
@@ -144,7 +147,7 @@ def etc_create_rve(nx, ny, nz, lx, ly, lz, kx, ky=None, kz=None, stream=None):
     h = c_void_p()
     st = lib.etc_create_rve(nx, ny, nz, lx, ly, lz, _ptr(kx), _ptr(ky), _ptr(kz),
                             c_void_p(stream) if stream else None, byref(h))
-    _check(st)
+    _check(st, thread_reason=True)
     return h
 
 
@@ -246,7 +249,8 @@ class Batch:
         hs = (c_void_p * self.count)(*[r.h.value for r in self.rves])
         self.opts = make_opts(rtol, maxit, precision, true_residual)
         self.b = c_void_p()
-        _check(lib.etc_batch_create(self.count, hs, byref(self.opts), byref(self.b)))
+        _check(lib.etc_batch_create(self.count, hs, byref(self.opts), byref(self.b)),
+               thread_reason=True)
 
     def run(self):
         """Returns (K as a list of 9-lists, info dicts per solve, batch ms, status)."""

@@ -33,6 +33,13 @@
 
 using namespace etc;
 
+namespace etc {
+namespace {
+thread_local std::string g_thread_err;
+}  // namespace
+void set_thread_error(const char* msg) { g_thread_err = msg; }
+}  // namespace etc
+
 namespace {
 
 // An NVTX range for the lifetime of the object (every return path pops it).
@@ -960,20 +967,26 @@ const char* etc_status_string(etc_status s) {
   }
 }
 
-const char* etc_last_error(const etc_rve* h) { return h ? h->err.c_str() : ""; }
+// A handle's last error; for NULL, the reason of this thread's last failed
+// call that has no handle (etc_create_rve, batch creation, the
+// allocation-free apply).
+const char* etc_last_error(const etc_rve* h) { return h ? h->err.c_str() : g_thread_err.c_str(); }
 
 etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double lz,
                           const double* kx, const double* ky, const double* kz, void* stream,
                           etc_rve** out) {
   etc_rve* h = nullptr;
-  if (!out) return ETC_EINVAL;
-  if (nx < 1 || ny < 1 || nz < 1 || nx > 8192 || ny > 8192 || nz > 8192) return ETC_EINVAL;
+  set_thread_error("");
+  auto reject = [](const char* msg) { set_thread_error(msg); return ETC_EINVAL; };
+  if (!out) return reject("etc_create_rve: out is NULL");
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 8192 || ny > 8192 || nz > 8192)
+    return reject("etc_create_rve: nx, ny, nz must be in 1..8192");
   if (!(lx > 0) || !(ly > 0) || !(lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) ||
       !std::isfinite(lz))
-    return ETC_EINVAL;
-  if (!kx) return ETC_EINVAL;
+    return reject("etc_create_rve: lx, ly, lz must be finite and > 0");
+  if (!kx) return reject("etc_create_rve: kx is NULL");
   const long long n = (long long)nx * ny * nz;
-  if (n > (1LL << 34)) return ETC_EINVAL;
+  if (n > (1LL << 34)) return reject("etc_create_rve: more than 2^34 voxels");
   Range range("etc_create_rve");
   h = new etc_rve();
   h->nx = nx; h->ny = ny; h->nz = nz;
@@ -1074,7 +1087,10 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
                       h->stream));
   CKC(cudaStreamSynchronize(h->stream));
   for (int c = 0; c < ncomp; ++c)
-    if (h->st_host[1].ext[3 * c + 2] != 0.0) return bail(ETC_EINVAL);
+    if (h->st_host[1].ext[3 * c + 2] != 0.0) {
+      set_thread_error("etc_create_rve: every kappa must be finite and > 0 (Sec. 2.1)");
+      return bail(ETC_EINVAL);
+    }
 #undef CKC
   *out = h;
   return ETC_OK;
@@ -1402,16 +1418,20 @@ etc_status etc_split_check(const double* d, float* hilo, long long n, void* stre
 // ------------------------------------------------------------------ batches
 etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opts_in,
                             etc_batch** out) {
-  if (!out || count < 1 || !rves) return ETC_EINVAL;
+  set_thread_error("");
+  auto reject = [](const char* msg) { set_thread_error(msg); return ETC_EINVAL; };
+  if (!out || count < 1 || !rves)
+    return reject("etc_batch_create: out and rves must be given and count >= 1");
   for (int i = 0; i < count; ++i) {
-    if (!rves[i]) return ETC_EINVAL;
+    if (!rves[i]) return reject("etc_batch_create: a handle is NULL");
     for (int j = 0; j < i; ++j)
-      if (rves[j] == rves[i]) return ETC_EINVAL;
+      if (rves[j] == rves[i]) return reject("etc_batch_create: the handles must be distinct");
   }
   etc_opts o;
   etc_default_opts(&o);
   if (opts_in) o = *opts_in;
-  if (validate_opts(nullptr, &o) != ETC_OK) return ETC_EINVAL;
+  if (validate_opts(nullptr, &o) != ETC_OK)
+    return reject("etc_batch_create: invalid options (rtol > 0, maxit >= 1, known precision)");
   etc_batch* b = new etc_batch();
   b->count = count;
   b->rves.assign(rves, rves + count);

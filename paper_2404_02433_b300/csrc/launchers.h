@@ -8,6 +8,10 @@
 
 namespace etc {
 
+// Reason of the calling thread's last failed call that has no handle (what
+// etc_last_error(NULL) returns); defined with the C ABI.
+void set_thread_error(const char* msg);
+
 cudaError_t launch_kappa_stats(const double* a, long long n, double* partials, PcgState* st,
                                int slot, cudaStream_t s);
 cudaError_t launch_permute(const double* in, double* out, int d0, int d1, int d2, long long s0,

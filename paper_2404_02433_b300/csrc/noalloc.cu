@@ -144,17 +144,26 @@ using namespace etc;
 extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
                                                          const double* kref, const double* r,
                                                          double* z, void* stream) {
-  if (n0 < 1 || n1 < 1 || n2 < 1 || n0 > kStaticMaxAxis || n1 > kStaticMaxAxis)
-    return ETC_EINVAL;
+  set_thread_error("");
+  auto reject = [](const char* msg) { set_thread_error(msg); return ETC_EINVAL; };
+  if (n0 < 1 || n1 < 1 || n2 < 1)
+    return reject("etc_apply_reference_inverse_static: n0, n1, n2 must be >= 1");
   const long long n = (long long)n0 * n1 * n2;
-  if (n > kStaticMaxCells) return ETC_EINVAL;
-  if (!kref || !r || !z) return ETC_EINVAL;
+  if (n0 > kStaticMaxAxis || n1 > kStaticMaxAxis || n > kStaticMaxCells)
+    return reject("etc_apply_reference_inverse_static: beyond the fixed scratch "
+                  "(n0, n1 <= 2048 and n0*n1*n2 <= 2^20 cells)");
+  if (!kref || !r || !z) return reject("etc_apply_reference_inverse_static: NULL argument");
   for (int i = 0; i < 5; ++i)
-    if (!(kref[i] > 0.0) || !std::isfinite(kref[i])) return ETC_EINVAL;
-  if (z < r + n && r < z + n) return ETC_EINVAL;  // input and output overlap
+    if (!(kref[i] > 0.0) || !std::isfinite(kref[i]))
+      return reject("etc_apply_reference_inverse_static: kref values must be finite and > 0");
+  if (z < r + n && r < z + n)
+    return reject("etc_apply_reference_inverse_static: r and z overlap");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return ETC_ECUDA;
+  if (scratch_address(&base) != cudaSuccess) {
+    set_thread_error("etc_apply_reference_inverse_static: device set-up of the scratch failed");
+    return ETC_ECUDA;
+  }
   double* t = base;
   double* h = base + kStaticMaxCells;
   double* tab0 = base + 2 * kStaticMaxCells;

@@ -84,6 +84,32 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.etc_loading_dims(None, 0, d) == B.ETC_EINVAL
 
 
+def test_handle_less_calls_give_a_reason(lib):
+    # calls without a handle report why they were refused through etc_last_error(NULL)
+    lib.etc_last_error.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    dummy = (ctypes.c_double * 8)(*([1.0] * 8))
+    assert lib.etc_create_rve(0, 2, 2, 1.0, 1.0, 1.0, ctypes.cast(dummy, ctypes.c_void_p), None,
+                              None, None, ctypes.byref(h)) == B.ETC_EINVAL
+    assert b"1..8192" in lib.etc_last_error(None)
+    assert lib.etc_create_rve(2, 2, 2, 1.0, 0.0, 1.0, ctypes.cast(dummy, ctypes.c_void_p), None,
+                              None, None, ctypes.byref(h)) == B.ETC_EINVAL
+    assert b"lx, ly, lz" in lib.etc_last_error(None)
+
+
+@pytest.mark.parametrize("dims", [(4096, 2, 2), (2, 4096, 2), (1024, 1024, 2)])
+def test_static_apply_refuses_sizes_beyond_its_scratch(lib, dims):
+    # the allocation-free apply checks its fixed limits before any CUDA call
+    lib.etc_last_error.restype = ctypes.c_char_p
+    kref = (ctypes.c_double * 5)(*([1.0] * 5))
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert B.load_library().etc_apply_reference_inverse_static(
+        *dims, kref, p, p, None) == B.ETC_EINVAL
+    msg = lib.etc_last_error(None)
+    assert b"n0, n1 <= 2048" in msg and b"2^20" in msg
+
+
 def test_status_strings(lib):
     for s in range(7):
         assert lib.etc_status_string(s)
