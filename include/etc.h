@@ -36,6 +36,13 @@
  *     (ETC_ENOMEM, clean teardown); ETC_TEST_TMA_TX_EXTRA=b makes the
  *     bulk-tensor matvec's waits expect b bytes that no copy delivers, so they
  *     run out and the mixed solve ends with ETC_ECUDA, without any fault.
+ *     ETC_FORCE_TILES="fx,ix,y" (read whenever the transform tiles are chosen)
+ *     replaces the tuned tiles by these candidates: rows per block of the
+ *     axis-0 forward and backward transforms (1..64, or -1 / -2 for the
+ *     register-resident kernels in blocks of 256 / 128 threads) and columns
+ *     per block of the axis-1 transforms (1..32, or -1); a candidate the shape
+ *     does not allow gives ETC_EINVAL.  It lets a test run every kernel the
+ *     tuner may pick.
  *   - A handle is used from one host thread at a time.  All its GPU work is
  *     ordered on the stream given to etc_create_rve; calls that return numbers
  *     to the host synchronise that stream before returning.
@@ -236,13 +243,15 @@ etc_status etc_apply_operator(etc_rve* rve, int dir, const double* w, double* q)
 
 /* z = A_ref^{-1} r by Algorithm 3 with the kref that the next solve of dir uses;
  * precision = ETC_PREC_FP64, or one of the mixed forms (FP32 transforms and
- * solves). */
+ * solves: the kernels of the flexible PCG's initial apply, including the
+ * bulk-tensor tridiagonal solves where the plane is a multiple of 4).  The
+ * transform tiles are those a solve of dir in that precision uses. */
 etc_status etc_apply_preconditioner(etc_rve* rve, int dir, int precision, const double* r,
                                     double* z);
 
 /* Per plane k, the 2-D transform over axes 0 and 1 of the loading frame:
  * inverse == 0 applies Eq. (forward DCT) along both axes, inverse == 1 applies
- * Eq. (backward DCT) along both axes (FP64). */
+ * Eq. (backward DCT) along both axes (FP64, with the tiles of an FP64 solve). */
 etc_status etc_dct_planes(etc_rve* rve, int dir, int inverse, const double* in, double* out);
 
 /*
@@ -290,7 +299,9 @@ unsigned long long etc_kernel_launches(void);
  * cudaMalloc, cudaFree or allocating library routine is called.  The first
  * call on each device looks up that array's device address (and sets kernel
  * attributes) with the device current; make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
+ * capture.  The address and attributes are kept for the life of the process:
+ * resetting a device (cudaDeviceReset) after its first call is not supported.
+ * ETC_ECUDA names the failed step and the CUDA error in etc_last_error(NULL).  All calls share the array and it keeps the last call's contents
  * (each call writes every element it reads), so calls that overlap on the GPU
  * -- on different streams, or from different host threads -- race.
  */

@@ -352,11 +352,14 @@ class PcgResult:
     history: list = field(default_factory=list)
 
 
-def pcg(f: Faces, b, kref, rtol=1e-10, maxit=5000, p0=None):
+def pcg(f: Faces, b, kref, rtol=1e-10, maxit=5000, p0=None, on_iterate=None):
     """Algorithm 1 with exit criterion ||r||_2 / ||b||_2 <= rtol (Eq. exit).
 
     The criterion is tested before each pass of the loop, so ``iters`` is the
-    number of products with A after the initial residual.
+    number of products with A after the initial residual.  ``on_iterate``, if
+    given, is called as on_iterate(it, p, relres) after every pass; it only
+    observes the iterate (the iterates are those of a run without it), so one
+    run can report the solution at several exit thresholds.
     """
     p = np.zeros_like(b) if p0 is None else p0.copy()
     r = b - apply_operator(f, p)
@@ -377,6 +380,8 @@ def pcg(f: Faces, b, kref, rtol=1e-10, maxit=5000, p0=None):
         rho = rho_new
         it += 1
         hist.append(float(np.linalg.norm(r)) / bnorm)
+        if on_iterate is not None:
+            on_iterate(it, p, hist[-1])
     return PcgResult(p, it, hist[-1], hist[-1] <= rtol, hist)
 
 

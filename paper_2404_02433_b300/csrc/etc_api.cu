@@ -504,10 +504,48 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   return best;
 }
 
+// Test hook ETC_FORCE_TILES="fx,ix,y": use these tiles (axis-0 forward,
+// axis-0 backward, axis-1; the values the tuner chooses among) instead of the
+// tuned ones, without recording them, so that a test can run every candidate
+// kernel.  A candidate the shape does not allow is refused with ETC_EINVAL,
+// by the same conditions the tuner applies.
+etc_status forced_tiles(etc_rve* h, const Geometry& g, int prec, const char* spec) {
+  int v[3];
+  if (std::sscanf(spec, "%d,%d,%d", &v[0], &v[1], &v[2]) != 3)
+    return fail(h, ETC_EINVAL, "ETC_FORCE_TILES must be \"fx,ix,y\"");
+  const int eb = prec == ETC_PREC_FP64 ? 8 : 4;
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  const bool fx_fast = prec == ETC_PREC_FP64
+                           ? fast_x_ok<double>(g, P0.p64, h->r, h->z64, nullptr, nullptr)
+                           : fast_x_ok<float>(g, P0.p32, h->r, h->z64, nullptr, nullptr);
+  const bool y_fast = prec == ETC_PREC_FP64 ? fast_y_ok<double>(g, P1.p64)
+                                            : fast_y_ok<float>(g, P1.p32);
+  auto pow2 = [](int x, int hi) { return x >= 1 && x <= hi && (x & (x - 1)) == 0; };
+  const long long nrows = (long long)g.n1 * g.n2;
+  bool ok = true;
+  for (int a = 0; a < 2; ++a) {
+    const int L = v[a];
+    if (L == -1 || L == -2) ok = ok && fx_fast;
+    else ok = ok && pow2(L, 64) && L <= nrows && smem_x_bytes(g.n0, L, eb) <= smem_limit() &&
+              (a == 0 || smem_x_bytes(g.n0, L, eb) + (size_t)L * g.n0 * sizeof(double) <=
+                             smem_limit());
+  }
+  if (g.n1 > 1) {
+    if (v[2] == -1) ok = ok && y_fast;
+    else ok = ok && pow2(v[2], 32) && v[2] <= g.n0 && smem_y_bytes(g.n1, v[2], eb) <= smem_limit();
+  }
+  if (!ok) return fail(h, ETC_EINVAL, "ETC_FORCE_TILES: tile not available for this shape");
+  h->tiles[0] = v[0]; h->tiles[1] = v[1]; h->tiles[2] = v[2];
+  return ETC_OK;
+}
+
 // Choose (or recall) the tiles of dir / prec and make them current.  Uses r, t
 // and z64 as scratch: call it before the initial residual is formed.
 etc_status autotune(etc_rve* h, int dir, int prec) {
   const Geometry g = geom_of(h, dir);
+  if (const char* ft = std::getenv("ETC_FORCE_TILES"); ft && ft[0])
+    return forced_tiles(h, g, prec, ft);
   const std::array<int, 4> key = {g.n0, g.n1, g.n2, prec};
   {
     std::lock_guard<std::mutex> lock(g_tiles_mutex);
@@ -1321,9 +1359,16 @@ etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double*
                                      h->t64, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
     s = precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->t64, h->h64, z, 0, 0);
   } else {
+    // the chain of the flexible PCG's initial apply: r^ in rhat32[1], z^ in
+    // t32, tridiagonal mode 3 -- the bulk-tensor kernel where the frame has
+    // its maps.  Those kernels return at entry once `done` is set, so the
+    // state is cleared first (rho of this apply is left in it).
+    CK(launch_state_reset(h->st, 1, h->stream));
     CK((launch_fwd_x<float, double>(g, P0.p32, h->st, nullptr, nullptr, nullptr, nullptr, r,
-                                    h->t32, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
-    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->t32, h->t32, nullptr, z, 0, 0);
+                                    h->rhat32[1], h->partials, 0, 0.0, 2, h->stream,
+                                    h->tiles[0])));
+    s = precond_tail<float, double>(h, g, P0.p32, P1.p32, h->rhat32[1], h->t32, nullptr, z, 3,
+                                    0);
   }
   if (s != ETC_OK) return s;
   CK(cudaStreamSynchronize(h->stream));
@@ -1334,19 +1379,22 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
   if (!h || !in || !out) return ETC_EINVAL;
   etc_status s = check_dir(h, dir);
   if (s != ETC_OK) return s;
+  // the FP64 tiles the solve uses (tuned, or forced by the test hook)
+  s = autotune(h, dir, ETC_PREC_FP64);
+  if (s != ETC_OK) return s;
   const Geometry g = geom_of(h, dir);
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
   if (!inverse) {
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, nullptr, nullptr, nullptr, nullptr, in,
-                                     h->t64, h->partials, 0, 0.0, 2, h->stream)));
-    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 0, h->stream));
+                                     h->t64, h->partials, 0, 0.0, 2, h->stream, h->tiles[0])));
+    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 0, 0, h->stream, h->tiles[2]));
     CK(cudaMemcpyAsync(out, h->t64, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   } else {
     CK(cudaMemcpyAsync(h->t64, in, g.n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 0, h->stream));
+    CK(launch_dct_y<double>(g, P1.p64, h->st, h->t64, 1, 0, h->stream, h->tiles[2]));
     CK((launch_inv_x<double, double>(g, P0.p64, h->st, h->t64, out, nullptr, 1.0, 0, 0,
-                                     h->stream)));
+                                     h->stream, h->tiles[1])));
   }
   CK(cudaStreamSynchronize(h->stream));
   return ETC_OK;

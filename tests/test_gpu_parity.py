@@ -124,6 +124,50 @@ def test_preconditioner_register_resident_lengths(shape):
     assert relmax(host(z), zo) < 2e-5
 
 
+# the benchmark's transform length (512) on axis 0, on axis 1, and on both;
+# every tile the autotuner may pick is forced in turn (ETC_FORCE_TILES), so the
+# kernels a 512^3 solve runs are compared with the oracle element by element
+TILES_X = [-1, -2, 1, 2, 4, 8, 16, 32, 64]
+TILES_Y = [-1, 1, 2, 4, 8, 16, 32]
+
+
+@pytest.mark.parametrize("shape", [(4, 512, 512), (3, 96, 512), (3, 512, 96)])
+def test_length_512_every_tile_matches_oracle(shape, monkeypatch):
+    rng = np.random.default_rng(512 + sum(shape))
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
+    rve.set_reference(2, B.ETC_REF_USER, ku)
+    r = rng.standard_normal(shape)
+    zo = O.apply_reference_inverse(r, ku)
+    rhat = O.dct_forward(O.dct_forward(r, 2), 1)
+    z = torch.empty(shape, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(z)
+    cands = [(t, t, -1) for t in TILES_X] + [(-1, -1, t) for t in TILES_Y[1:]]
+    ran = {B.ETC_PREC_FP64: 0, B.ETC_PREC_MIXED: 0, B.ETC_PREC_MIXED_F64: 0}
+    for tiles in cands:
+        monkeypatch.setenv("ETC_FORCE_TILES", ",".join(map(str, tiles)))
+        for prec, tol in ((B.ETC_PREC_FP64, 1e-11), (B.ETC_PREC_MIXED, 2e-5),
+                          (B.ETC_PREC_MIXED_F64, 2e-5)):
+            try:
+                B.etc_apply_preconditioner(rve.h, 2, prec, dev(r), z)
+            except B.EtcError as e:  # this tile is not available for the shape
+                assert e.status == B.ETC_EINVAL and "ETC_FORCE_TILES" in str(e)
+                continue
+            assert relmax(host(z), zo) < tol, (tiles, prec)
+            ran[prec] += 1
+        try:
+            B.etc_dct_planes(rve.h, 2, 0, dev(r), out)
+        except B.EtcError as e:
+            assert e.status == B.ETC_EINVAL
+            continue
+        assert relmax(host(out), rhat) < 1e-12, tiles
+        B.etc_dct_planes(rve.h, 2, 1, dev(rhat), out)
+        assert relmax(host(out), r) < 1e-12, tiles
+    # the register-resident kernels and at least the small tiles ran everywhere
+    assert min(ran.values()) >= 6, ran
+
+
 @pytest.mark.parametrize("shape,ku", [
     ((129, 5, 7), [0.7, 1.9, 3.1, 0.4, 2.2]),
     ((200, 6, 10), [0.7, 1.9, 3.1, 0.4, 2.2]),
