@@ -281,6 +281,16 @@ etc_status etc_split_check(const double* d, float* hilo, long long n, void* stre
 /* Kernels launched by this library since the process started (all handles). */
 unsigned long long etc_kernel_launches(void);
 
+/* Measurement support (not in the paper): the FP64 fused multiply-add rate of
+ * the current device on the clock it runs at, in TFLOP/s (an FMA counts 2).
+ * 148 x 8 blocks of 256 threads each keep eight independent FMA chains for
+ * `iters` steps; one warm-up launch, then one launch timed with CUDA events on
+ * `stream`.  This is the measured peak the FP64 kernels' roofline fractions
+ * are quoted against, next to the figure derived from unit counts and the
+ * maximum clock.  Synchronises the stream; ETC_EINVAL for iters < 1 or a NULL
+ * tflops. */
+etc_status etc_fp64_fma_rate(int iters, double* tflops, void* stream);
+
 /*
  * z = A_ref^{-1} r without allocating anything (the paper has no counterpart;
  * it is a service for callers that cannot allocate device memory: those whose

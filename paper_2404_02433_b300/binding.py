@@ -26,7 +26,7 @@ EXPORTED = (
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
-    "etc_solve_general", "etc_split_check",
+    "etc_solve_general", "etc_split_check", "etc_fp64_fma_rate",
 )
 
 
@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
         "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
         "etc_split_check": ([vp, vp, ctypes.c_longlong, vp], c_int),
+        "etc_fp64_fma_rate": ([c_int, dp, vp], c_int),
         "etc_gradient": ([vp, c_int, c_double, c_double, POINTER(EtcOpts), c_int, vp, dp,
                           POINTER(EtcInfo)], c_int),
         "etc_batch_create": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), POINTER(c_void_p)],
@@ -216,6 +217,13 @@ def etc_apply_reference_inverse_static(n0, n1, n2, kref, r, z, stream=None):
     k = (c_double * 5)(*kref)
     return load_library().etc_apply_reference_inverse_static(
         n0, n1, n2, k, _ptr(r), _ptr(z), c_void_p(stream) if stream else None)
+
+
+def etc_fp64_fma_rate(iters=20000, stream=None):
+    """Measured FP64 FMA rate of the current device in TFLOP/s."""
+    v = c_double()
+    _check(load_library().etc_fp64_fma_rate(iters, byref(v), c_void_p(stream) if stream else None))
+    return v.value
 
 
 def etc_convert_check(f_in, d_out, d_in, f_out, stream=None):

@@ -9,6 +9,7 @@
 // the library until the process exits; the caller passes only the input and
 // the output.
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/etc.h"
@@ -160,8 +161,12 @@ extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
     return reject("etc_apply_reference_inverse_static: r and z overlap");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) {
-    set_thread_error("etc_apply_reference_inverse_static: device set-up of the scratch failed");
+  if (const cudaError_t se = scratch_address(&base); se != cudaSuccess) {
+    char msg[192];
+    std::snprintf(msg, sizeof msg,
+                  "etc_apply_reference_inverse_static: device set-up of the scratch failed: %s",
+                  cudaGetErrorString(se));
+    set_thread_error(msg);
     return ETC_ECUDA;
   }
   double* t = base;
@@ -174,21 +179,35 @@ extern "C" etc_status etc_apply_reference_inverse_static(int n0, int n1, int n2,
   g.n = n;
   DctPlan<double> p0, p1;
   const double *lam0 = nullptr, *lam1 = nullptr;
+  // A failed step reports itself and the CUDA error in etc_last_error(NULL).
+  auto cuda_fail = [](const char* step, cudaError_t e) {
+    char msg[192];
+    std::snprintf(msg, sizeof msg, "etc_apply_reference_inverse_static: %s failed: %s", step,
+                  cudaGetErrorString(e));
+    set_thread_error(msg);
+    return ETC_ECUDA;
+  };
+  cudaError_t e;
   // Every scratch element read below is written earlier in this same call:
   // the tables and pivots fully, the transform buffer by the first pass.
-  if (static_plan(n0, tab0, &p0, &lam0, s) != cudaSuccess) return ETC_ECUDA;
-  if (static_plan(n1, tab1, &p1, &lam1, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_pivots<double>(g, lam0, lam1, nullptr, kref, h, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_fwd_x<double, double>(g, p0, nullptr, nullptr, nullptr, nullptr, nullptr, r, t,
-                                   nullptr, 0, 0.0, 2, s) != cudaSuccess)
-    return ETC_ECUDA;
-  if (launch_dct_y<double>(g, p1, nullptr, t, 0, 0, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_tridiag<double>(g, nullptr, t, h, nullptr, kref[2], nullptr, 0, nullptr, nullptr,
-                             s) != cudaSuccess)
-    return ETC_ECUDA;
-  if (launch_dct_y<double>(g, p1, nullptr, t, 1, 0, s) != cudaSuccess) return ETC_ECUDA;
-  if (launch_inv_x<double, double>(g, p0, nullptr, t, z, nullptr, kref[2], 0, 0, s) !=
+  if ((e = static_plan(n0, tab0, &p0, &lam0, s)) != cudaSuccess)
+    return cuda_fail("axis-0 cosine tables", e);
+  if ((e = static_plan(n1, tab1, &p1, &lam1, s)) != cudaSuccess)
+    return cuda_fail("axis-1 cosine tables", e);
+  if ((e = launch_pivots<double>(g, lam0, lam1, nullptr, kref, h, s)) != cudaSuccess)
+    return cuda_fail("pivot table", e);
+  if ((e = launch_fwd_x<double, double>(g, p0, nullptr, nullptr, nullptr, nullptr, nullptr, r, t,
+                                        nullptr, 0, 0.0, 2, s)) != cudaSuccess)
+    return cuda_fail("forward transform, axis 0", e);
+  if ((e = launch_dct_y<double>(g, p1, nullptr, t, 0, 0, s)) != cudaSuccess)
+    return cuda_fail("forward transform, axis 1", e);
+  if ((e = launch_tridiag<double>(g, nullptr, t, h, nullptr, kref[2], nullptr, 0, nullptr,
+                                  nullptr, s)) != cudaSuccess)
+    return cuda_fail("tridiagonal solves", e);
+  if ((e = launch_dct_y<double>(g, p1, nullptr, t, 1, 0, s)) != cudaSuccess)
+    return cuda_fail("backward transform, axis 1", e);
+  if ((e = launch_inv_x<double, double>(g, p0, nullptr, t, z, nullptr, kref[2], 0, 0, s)) !=
       cudaSuccess)
-    return ETC_ECUDA;
+    return cuda_fail("backward transform, axis 0", e);
   return ETC_OK;
 }
