@@ -90,6 +90,9 @@ typedef struct {
   int maxit;           /* iteration cap; default 5000 */
   int precision;       /* ETC_PREC_*; default ETC_PREC_FP64 */
   int true_residual;   /* 1: also compute ||b - A p|| / ||b|| at exit; default 1 */
+  int batch_queue;     /* etc_batch_create only: 1 = work-queue loops per class of
+                          equal sizes (persistent kernels), 0 = a device-driven loop
+                          per solve; default 0 (see etc_batch_create) */
 } etc_opts;
 
 typedef struct {
@@ -205,16 +208,28 @@ etc_status etc_gradient(etc_rve* rve, int dir, double p_in, double p_out, const 
                         int per_component, double* grad, double* kappa_eff, etc_info* info);
 
 /*
- * Batches: the full tensors of many RVEs in one CUDA graph.
- * etc_batch_create captures, for every handle, a branch that runs its three
- * loading directions (p_in = 1, p_out = 0) one after the other, each as a
- * device-driven solve: face assembly, LP optimum and pivots on the device, the
- * initial apply, a graph WHILE node whose body runs two PCG iterations and
- * ends the loop once the device `done` flag is set (or after maxit/2 + 4
- * passes), then the flux sums.  Branches of different handles run
- * concurrently.  The handles must be distinct, must outlive the batch, and
- * must not be used by other calls while a run is in progress; their reference
- * modes are read at creation.
+ * Batches: the full tensors of many RVEs in one CUDA graph (the three loading
+ * directions of Sec. 2.1 for every RVE, p_in = 1, p_out = 0).
+ * By default (opts->batch_queue == 0) every handle gets a branch that runs
+ * its three directions in turn, each as a device-driven solve: face
+ * assembly, LP optimum and pivots on the device, the initial apply, a graph
+ * WHILE node whose body runs two PCG iterations and ends the loop once the
+ * device `done` flag is set (or after maxit/2 + 4 passes), then the flux
+ * sums.  Branches of different handles run concurrently.
+ * With opts->batch_queue == 1 the handles are grouped into classes of equal
+ * sizes.  A class whose loading frames all have register-resident transform
+ * lengths (32, 64, 96, 128, 160, 192, 256, 384, 512, 1024 on axes 0 and 1),
+ * in FP64 or ETC_PREC_MIXED, runs per direction: every member's start in
+ * parallel branches, then ONE graph WHILE loop for the whole class whose body
+ * runs two PCG iterations of every member still iterating -- each kernel of
+ * the iteration one persistent launch whose blocks take (solve, block) items
+ * from a device work queue, finished solves dropped from the queue by the
+ * loop control -- and ends when no member is left (or each after maxit/2 + 4
+ * passes), then every member's flux sums.  Other handles get per-solve
+ * branches.  (Measured on B300 the per-solve branches are faster: see the
+ * design notes.)  The handles must be distinct, must outlive the batch, and
+ * must not be used by other calls while a run is in progress; their
+ * reference modes are read at creation.
  *   etc_batch_run launches the graph, waits, and fills K (count * 9 doubles,
  *   handle i's tensor at K + 9 i, layout as etc_effective_tensor) and, if not
  *   NULL, info (count * 3 records; t_solve_ms is the whole batch) and ms (the
@@ -225,9 +240,24 @@ etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opt
                             etc_batch** out);
 etc_status etc_batch_run(etc_batch* batch, double* K, etc_info* info, double* ms);
 etc_status etc_batch_destroy(etc_batch* batch);
+/* Number of the batch's handles whose solves run in work-queue loops (0 for
+ * NULL). */
+int etc_batch_queued(const etc_batch* batch);
 /* create + run + destroy. */
 etc_status etc_effective_tensor_batch(int count, etc_rve* const* rves, const etc_opts* opts,
                                       double* K, etc_info* info);
+
+/*
+ * Convergence history of the last solve on the handle (any direction or
+ * call): the relative residual ||r_i||_2 / ||b||_2 of Eq. (exit) after
+ * iteration i, i = 0 (the initial residual, 1) .. iters, as the paper plots
+ * it (Sec. 4.2).  The residual-update kernel writes ||r_i||^2 into a device
+ * ring of the last 8192 iterations; this call copies the last min(cap,
+ * iters + 1, 8192) values into out (host memory, cap doubles), sets *first to
+ * the iteration of out[0] and *count to the number written.  Synchronises the
+ * handle's stream.  ETC_ESTATE if no solve has run.
+ */
+etc_status etc_residual_history(etc_rve* rve, double* out, int cap, int* first, int* count);
 
 /* Loading-frame sizes (n0, n1, n2) of direction dir. */
 etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);

@@ -26,13 +26,14 @@ EXPORTED = (
     "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
-    "etc_solve_general", "etc_split_check", "etc_fp64_fma_rate",
+    "etc_solve_general", "etc_split_check", "etc_fp64_fma_rate", "etc_batch_queued",
+    "etc_residual_history",
 )
 
 
 class EtcOpts(ctypes.Structure):
     _fields_ = [("rtol", c_double), ("maxit", c_int), ("precision", c_int),
-                ("true_residual", c_int)]
+                ("true_residual", c_int), ("batch_queue", c_int)]
 
 
 class EtcInfo(ctypes.Structure):
@@ -96,6 +97,8 @@ def load_library(path: str | None = None):
                              c_int),
         "etc_batch_run": ([vp, dp, POINTER(EtcInfo), dp], c_int),
         "etc_batch_destroy": ([vp], c_int),
+        "etc_batch_queued": ([vp], c_int),
+        "etc_residual_history": ([vp, dp, c_int, ip, ip], c_int),
         "etc_solve_general": ([vp, c_int, vp, vp, vp, POINTER(EtcOpts), POINTER(EtcInfo)], c_int),
         "etc_effective_tensor_batch": ([c_int, POINTER(c_void_p), POINTER(EtcOpts), dp,
                                         POINTER(EtcInfo)], c_int),
@@ -135,10 +138,11 @@ def _check(status, handle=None, ok=(ETC_OK,), thread_reason=False):
     raise EtcError(status, msg)
 
 
-def make_opts(rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1):
+def make_opts(rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1, batch_queue=0):
     o = EtcOpts()
     _check(load_library().etc_default_opts(byref(o)))
     o.rtol, o.maxit, o.precision, o.true_residual = rtol, maxit, precision, true_residual
+    o.batch_queue = batch_queue
     return o
 
 
@@ -250,12 +254,13 @@ def etc_gradient(h, direction, grad, p_in=1.0, p_out=0.0, opts=None, per_compone
 class Batch:
     """Full tensors of several RVEs in one CUDA graph (etc_batch_*)."""
 
-    def __init__(self, rves, rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1):
+    def __init__(self, rves, rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1,
+                 queue=False):
         lib = load_library()
         self.rves = list(rves)
         self.count = len(self.rves)
         hs = (c_void_p * self.count)(*[r.h.value for r in self.rves])
-        self.opts = make_opts(rtol, maxit, precision, true_residual)
+        self.opts = make_opts(rtol, maxit, precision, true_residual, int(bool(queue)))
         self.b = c_void_p()
         _check(lib.etc_batch_create(self.count, hs, byref(self.opts), byref(self.b)),
                thread_reason=True)
@@ -270,6 +275,10 @@ class Batch:
         _check(st, ok=(ETC_OK, ETC_ENOCONV, ETC_EBREAKDOWN))
         Ks = [[K[9 * i + j] for j in range(9)] for i in range(self.count)]
         return Ks, [info[i].as_dict() for i in range(3 * self.count)], ms.value, st
+
+    def queued(self):
+        """Handles whose solves run in work-queue loops."""
+        return int(load_library().etc_batch_queued(self.b))
 
     def close(self):
         if getattr(self, "b", None) and self.b.value:
@@ -354,6 +363,14 @@ class RVE:
 
     def loading_dims(self, direction):
         return etc_loading_dims(self.h, direction)
+
+    def history(self, cap=8192):
+        """(first iteration, relative residuals) of the last solve (etc_residual_history)."""
+        out = (c_double * cap)()
+        first, count = c_int(), c_int()
+        _check(load_library().etc_residual_history(self.h, out, cap, byref(first), byref(count)),
+               self.h)
+        return first.value, [out[i] for i in range(count.value)]
 
     def set_reference(self, direction, mode=ETC_REF_LP, kref=None):
         return etc_set_reference_params(self.h, direction, mode, kref)

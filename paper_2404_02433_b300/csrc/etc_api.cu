@@ -73,6 +73,9 @@ struct PlanStore {
 
 }  // namespace
 
+// Entries of the device ring of the convergence history (one per iteration).
+constexpr int kHistCap = 8192;
+
 struct etc_rve {
   int nx = 0, ny = 0, nz = 0;
   double L[3] = {1, 1, 1};
@@ -110,6 +113,7 @@ struct etc_rve {
   double* gbuf[3] = {nullptr, nullptr, nullptr};  // loading-frame gradient components
   double* partials = nullptr;
   size_t npartials = 0;
+  double* hist = nullptr;        // device ring of ||r_i||^2 (kHistCap entries)
   PcgState* st = nullptr;        // device
   PcgState* st_host = nullptr;   // pinned, 3 slots used for read-backs
   std::map<int, PlanStore> plans;
@@ -885,17 +889,12 @@ struct StreamSwap {
   ~StreamSwap() { h->stream = saved; }
 };
 
-// Queue one complete device-driven solve of dir on capture stream cs: state
-// reset, setup, reference parameters, initial apply, a WHILE graph node whose
-// body runs two PCG iterations and the loop control, post-processing, and a
-// copy of the final state block into slot.  bs is the stream used to capture
-// the loop body.
-etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs,
-                         cudaStream_t bs, PcgState* slot) {
+// Queue the start of a device-driven solve of dir on capture stream cs: state
+// reset, setup, reference parameters and the initial apply.
+etc_status capture_solve_start(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs) {
   StreamSwap guard(h, cs);
   const int prec = o.precision;
   const Geometry g = geom_of(h, dir);
-  double* x = h->xsol[dir];
   {
     std::lock_guard<std::mutex> lock(g_tiles_mutex);
     const Tiles& tl = g_tiles[{g.n0, g.n1, g.n2, prec}];
@@ -907,8 +906,29 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Rhs unit;  // p_in = 1, p_out = 0
-  s = launch_start(h, g, x, prec, unit, o.rtol * o.rtol);
+  return launch_start(h, g, h->xsol[dir], prec, unit, o.rtol * o.rtol);
+}
+
+// Queue the end of a device-driven solve: the last x step, post-processing,
+// and a copy of the final state block into slot.
+etc_status capture_solve_end(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs,
+                             PcgState* slot) {
+  StreamSwap guard(h, cs);
+  const Geometry g = geom_of(h, dir);
+  double* x = h->xsol[dir];
+  etc_status s = finish_solve_x(h, g, x, o.precision);
   if (s != ETC_OK) return s;
+  const Rhs unit;
+  s = launch_post(h, g, x, unit, o.true_residual);
+  if (s != ETC_OK) return s;
+  CK(cudaMemcpyAsync(slot, h->st, sizeof(PcgState), cudaMemcpyDeviceToDevice, cs));
+  return ETC_OK;
+}
+
+// Add a WHILE graph node at the capture position of cs (its condition starts
+// true) and capture its body on bs with body(cond, bs).
+template <class Body>
+etc_status capture_while(etc_rve* h, cudaStream_t cs, cudaStream_t bs, Body body) {
   cudaStreamCaptureStatus cst;
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -923,28 +943,116 @@ etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs
   np.conditional.size = 1;
   cudaGraphNode_t node;
   CK(cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaGraph_t bgraph = np.conditional.phGraph_out[0];
   CK(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
                                          cudaStreamSetCaptureDependencies));
-  CK(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  {
-    StreamSwap inner(h, bs);
-    for (int par = 0; par < 2 && s == ETC_OK; ++par) s = launch_iteration(h, g, x, prec, par);
-    if (s == ETC_OK && launch_loop_control(h->st, cond, bs) != cudaSuccess) s = ETC_ECUDA;
-  }
+  CK(cudaStreamBeginCaptureToGraph(bs, bgraph, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  const etc_status s = body(cond, bs);
   cudaGraph_t ended = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(bs, &ended);
   if (s != ETC_OK) return s;
   CK(ee);
-  s = finish_solve_x(h, g, x, prec);
+  return ETC_OK;
+}
+
+// Queue one complete device-driven solve of dir on capture stream cs: the
+// start, a WHILE graph node whose body (captured on bs) runs two PCG
+// iterations and the loop control, and the end.
+etc_status capture_solve(etc_rve* h, int dir, const etc_opts& o, cudaStream_t cs,
+                         cudaStream_t bs, PcgState* slot) {
+  etc_status s = capture_solve_start(h, dir, o, cs);
   if (s != ETC_OK) return s;
-  s = launch_post(h, g, x, unit, o.true_residual);
+  const Geometry g = geom_of(h, dir);
+  double* x = h->xsol[dir];
+  s = capture_while(h, cs, bs, [&](cudaGraphConditionalHandle cond, cudaStream_t b) {
+    StreamSwap inner(h, b);
+    etc_status r = ETC_OK;
+    for (int par = 0; par < 2 && r == ETC_OK; ++par)
+      r = launch_iteration(h, g, x, o.precision, par);
+    if (r == ETC_OK && launch_loop_control(h->st, cond, b) != cudaSuccess) r = ETC_ECUDA;
+    return r;
+  });
   if (s != ETC_OK) return s;
-  CK(cudaMemcpyAsync(slot, h->st, sizeof(PcgState), cudaMemcpyDeviceToDevice, cs));
+  return capture_solve_end(h, dir, o, cs, slot);
+}
+
+// Whether the solves of handle h can run in a persistent class loop: every
+// loading frame has register-resident transform lengths on axes 0 and 1
+// (axis 1 may be a single voxel), and the precision is FP64 or the
+// double-float mixed form.
+bool queue_eligible(etc_rve* h, int prec) {
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED) return false;
+  for (int d = 0; d < 3; ++d) {
+    const Geometry g = geom_of(h, d);
+    const PlanStore& P0 = h->plans[g.n0];
+    const PlanStore& P1 = h->plans[g.n1];
+    const bool x_ok = prec == ETC_PREC_FP64
+                          ? fast_x_ok<double>(g, P0.p64, h->r, h->q, h->xsol[d], h->w[0])
+                          : fast_x_ok<float>(g, P0.p32, h->r, h->q, h->xsol[d], h->wf);
+    const bool y_ok = g.n1 == 1 || (prec == ETC_PREC_FP64 ? fast_y_ok<double>(g, P1.p64)
+                                                          : fast_y_ok<float>(g, P1.p32));
+    if (!x_ok || !y_ok) return false;
+  }
+  return true;
+}
+
+// Device addresses of handle h's solve of direction dir (BatchSolve).
+BatchSolve batch_solve_of(etc_rve* h, int dir) {
+  BatchSolve a = {};
+  a.st = h->st;
+  a.partials = h->partials;
+  a.x = h->xsol[dir];
+  a.r = h->r;
+  a.q = h->q;
+  a.w = h->w[0];
+  a.wf = h->wf;
+  a.T0 = h->T0; a.T1 = h->T1; a.T2 = h->T2; a.D = h->D;
+  a.F0 = h->Tdf[0]; a.F1 = h->Tdf[1]; a.F2 = h->Tdf[2]; a.FB = h->Bdf;
+  a.t64 = h->t64;
+  a.h64 = h->h64;
+  a.t32 = h->t32;
+  a.rhat[0] = h->rhat32[0];
+  a.rhat[1] = h->rhat32[1];
+  a.ck = h->ck32;
+  return a;
+}
+
+// One pass of a class's loop body: two PCG iterations of every solve still
+// listed in the queue, each kernel one persistent launch over the class
+// (slots 6 par + k), then the class's loop control.
+etc_status queue_pass(etc_rve* h, const Geometry& g, int prec, BatchQueue* q,
+                      const BatchSolve* bs, int nm, cudaGraphConditionalHandle cond,
+                      cudaStream_t s) {
+  // the class's tables (equal for all members) and axis-0 block size
+  const PlanStore& P0 = h->plans[g.n0];
+  const PlanStore& P1 = h->plans[g.n1];
+  const int nt = h->tiles[0] == -2 ? 128 : 256;
+  for (int par = 0; par < 2; ++par) {
+    QueueLaunch ql = {q, bs, 6 * par, nm, s};
+    if (prec == ETC_PREC_FP64) {
+      CK(launch_q_matvec(g, ql, par));
+      ql.slot++; CK(launch_q_fast_fwd_x<double>(g, P0.p64.t, ql, par, nt));
+      ql.slot++; CK(launch_q_fast_y<double>(g, P1.p64.t, ql, 0, 0, par));
+      ql.slot++; CK(launch_q_tridiag(g, ql));
+      ql.slot++; CK(launch_q_fast_y<double>(g, P1.p64.t, ql, 1, 0, par));
+      ql.slot++; CK(launch_q_fast_inv_x<double>(g, P0.p64.t, ql, par, nt));
+    } else {
+      CK(launch_q_matvec_df(g, ql, par));
+      ql.slot++; CK(launch_q_fast_fwd_x<float>(g, P0.p32.t, ql, par, nt));
+      ql.slot++; CK(launch_q_fast_y<float>(g, P1.p32.t, ql, 0, 1, par));
+      ql.slot++; CK(launch_q_tridiag_otf(g, ql, P0.lam, P1.lam, par));
+      ql.slot++; CK(launch_q_fast_y<float>(g, P1.p32.t, ql, 1, 2, par));
+      ql.slot++; CK(launch_q_fast_inv_x<float>(g, P0.p32.t, ql, par, nt));
+    }
+  }
+  CK(launch_queue_control(q, bs, cond, 0, s));
   return ETC_OK;
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ batch object}  // namespace
 
 // ------------------------------------------------------------------ batch object
 struct etc_batch {
@@ -952,13 +1060,17 @@ struct etc_batch {
   std::vector<etc_rve*> rves;
   etc_opts o;
   cudaStream_t main = nullptr, body = nullptr;
-  std::vector<cudaStream_t> branch;
-  std::vector<cudaEvent_t> join;
+  std::vector<cudaStream_t> branch;  // one per handle
+  std::vector<cudaEvent_t> join;     // one per handle
+  std::vector<cudaStream_t> cls;     // one per class of the work-queue loops
+  std::vector<cudaEvent_t> cls_ev;   // two per class
+  std::vector<void*> dev;            // queues and solve tables
   cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   PcgState* slots = nullptr;       // device, count * 3
   PcgState* slots_host = nullptr;  // pinned copy
+  int queued = 0;                  // handles whose solves run in work-queue loops
   std::string err;
 };
 
@@ -969,6 +1081,9 @@ void batch_release(etc_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaStream_t s : b->branch) if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->join) if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : b->cls) if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->cls_ev) if (e) cudaEventDestroy(e);
+  for (void* p : b->dev) if (p) cudaFree(p);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->t0) cudaEventDestroy(b->t0);
   if (b->t1) cudaEventDestroy(b->t1);
@@ -989,6 +1104,7 @@ etc_status etc_default_opts(etc_opts* o) {
   o->maxit = 5000;
   o->precision = ETC_PREC_FP64;
   o->true_residual = 1;
+  o->batch_queue = 0;
   return ETC_OK;
 }
 
@@ -1096,7 +1212,18 @@ etc_status etc_create_rve(int nx, int ny, int nz, double lx, double ly, double l
   h->npartials = np * 10;
   CKC(dalloc(h, &h->partials, h->npartials));
   CKC(dalloc(h, &h->st, 1));
+  CKC(dalloc(h, &h->hist, kHistCap));
   CKC(cudaMemsetAsync(h->st, 0, sizeof(PcgState), h->stream));
+  {
+    // the ring of the convergence history, addressed from the state block
+    double* hp = h->hist;
+    const int cap = kHistCap;
+    CKC(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offsetof(PcgState, hist), &hp,
+                        sizeof(hp), cudaMemcpyHostToDevice, h->stream));
+    CKC(cudaMemcpyAsync(reinterpret_cast<char*>(h->st) + offsetof(PcgState, hist_cap), &cap,
+                        sizeof(cap), cudaMemcpyHostToDevice, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+  }
   {
     cudaError_t e = cudaMallocHost(&h->st_host, 3 * sizeof(PcgState));
     if (e != cudaSuccess) { h->st_host = nullptr; return bail(ETC_ENOMEM); }
@@ -1514,11 +1641,107 @@ etc_status etc_batch_create(int count, etc_rve* const* rves, const etc_opts* opt
   CKB(cudaEventCreate(&b->t1));
   CKB(cudaMalloc(&b->slots, sizeof(PcgState) * 3 * (size_t)count));
   CKB(cudaMallocHost(&b->slots_host, sizeof(PcgState) * 3 * (size_t)count));
-  // capture: one branch per RVE, its three directions in sequence
+  // Classes for the work-queue loops: handles of equal sizes whose frames all
+  // have register-resident transform lengths (ETC_BATCH_PER_SOLVE=1 keeps
+  // every handle on its own device-driven loops, for comparison).  Every
+  // other handle gets its own branch of per-solve loops.
+  std::vector<std::vector<int>> classes;
+  std::vector<int> single;
+  {
+    std::map<std::array<int, 3>, int> index;
+    for (int i = 0; i < count; ++i) {
+      etc_rve* h = rves[i];
+      if (!o.batch_queue || !queue_eligible(h, o.precision)) {
+        single.push_back(i);
+        continue;
+      }
+      const std::array<int, 3> key = {h->nx, h->ny, h->nz};
+      auto it = index.find(key);
+      if (it == index.end()) {
+        index[key] = (int)classes.size();
+        classes.push_back({i});
+      } else {
+        classes[it->second].push_back(i);
+      }
+    }
+
+  }
+  // per class: the queue (with its active list) and the solve tables of the
+  // three directions, [dir][member]
+  std::vector<BatchQueue*> queues(classes.size(), nullptr);
+  std::vector<BatchSolve*> tables(classes.size(), nullptr);
+  for (size_t c = 0; c < classes.size(); ++c) {
+    const int nm = (int)classes[c].size();
+    void* p = nullptr;
+    CKB(cudaMalloc(&p, sizeof(BatchQueue) + sizeof(int) * (size_t)nm));
+    b->dev.push_back(p);
+    queues[c] = static_cast<BatchQueue*>(p);
+    BatchQueue hq = {};
+    hq.nsolves = nm;
+    hq.active = reinterpret_cast<int*>(static_cast<char*>(p) + sizeof(BatchQueue));
+    CKB(cudaMemcpy(p, &hq, sizeof(BatchQueue), cudaMemcpyHostToDevice));
+    std::vector<BatchSolve> tab(3 * (size_t)nm);
+    for (int d = 0; d < 3; ++d)
+      for (int m = 0; m < nm; ++m) tab[(size_t)d * nm + m] = batch_solve_of(rves[classes[c][m]], d);
+    CKB(cudaMalloc(&p, sizeof(BatchSolve) * tab.size()));
+    b->dev.push_back(p);
+    tables[c] = static_cast<BatchSolve*>(p);
+    CKB(cudaMemcpy(p, tab.data(), sizeof(BatchSolve) * tab.size(), cudaMemcpyHostToDevice));
+    cudaStream_t cs = nullptr;
+    CKB(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    b->cls.push_back(cs);
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t ev = nullptr;
+      CKB(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      b->cls_ev.push_back(ev);
+    }
+    b->queued += nm;
+  }
+  // capture: one branch per class, its three directions in sequence (each:
+  // the members' starts in parallel branches, one work-queue loop, the
+  // members' ends in parallel branches), and one branch per other handle
   CKB(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeRelaxed));
   etc_status s = ETC_OK;
   cudaError_t e = cudaEventRecord(b->fork, b->main);
-  for (int i = 0; i < count && s == ETC_OK && e == cudaSuccess; ++i) {
+  auto fan = [&](size_t c, auto per_member) {
+    // run per_member(i, stream) for every member of class c in its own
+    // branch, between an event on the class stream and a join back into it
+    cudaStream_t cs = b->cls[c];
+    if (e == cudaSuccess) e = cudaEventRecord(b->cls_ev[2 * c], cs);
+    for (int i : classes[c]) {
+      if (s != ETC_OK || e != cudaSuccess) return;
+      e = cudaStreamWaitEvent(b->branch[i], b->cls_ev[2 * c], 0);
+      if (e == cudaSuccess) s = per_member(i, b->branch[i]);
+      if (s == ETC_OK && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
+      if (s == ETC_OK && e == cudaSuccess) e = cudaStreamWaitEvent(cs, b->join[i], 0);
+    }
+  };
+  for (size_t c = 0; c < classes.size() && s == ETC_OK && e == cudaSuccess; ++c) {
+    cudaStream_t cs = b->cls[c];
+    e = cudaStreamWaitEvent(cs, b->fork, 0);
+    const int nm = (int)classes[c].size();
+    etc_rve* h0 = rves[classes[c][0]];
+    for (int d = 0; d < 3 && s == ETC_OK && e == cudaSuccess; ++d) {
+      fan(c, [&](int i, cudaStream_t bs) { return capture_solve_start(rves[i], d, o, bs); });
+      if (s != ETC_OK || e != cudaSuccess) break;
+      const BatchSolve* tab = tables[c] + (size_t)d * nm;
+      e = launch_queue_control(queues[c], tab, 0, 1, cs);
+      if (e != cudaSuccess) break;
+      const Geometry g = geom_of(h0, d);
+      s = capture_while(nullptr, cs, b->body, [&](cudaGraphConditionalHandle cond,
+                                                  cudaStream_t bs) {
+        return queue_pass(h0, g, o.precision, queues[c], tab, nm, cond, bs);
+      });
+      if (s != ETC_OK) break;
+      fan(c, [&](int i, cudaStream_t bs) {
+        return capture_solve_end(rves[i], d, o, bs, b->slots + 3 * i + d);
+      });
+    }
+    if (s == ETC_OK && e == cudaSuccess) e = cudaEventRecord(b->cls_ev[2 * c + 1], cs);
+    if (s == ETC_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->main, b->cls_ev[2 * c + 1], 0);
+  }
+  for (int i : single) {
+    if (s != ETC_OK || e != cudaSuccess) break;
     e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
     for (int d = 0; d < 3 && s == ETC_OK && e == cudaSuccess; ++d)
       s = capture_solve(rves[i], d, o, b->branch[i], b->body, b->slots + 3 * i + d);
@@ -1571,6 +1794,29 @@ etc_status etc_batch_run(etc_batch* b, double* K, etc_info* info, double* ms) {
     h->setup_dir = 2;  // the last direction captured left its faces in place
   }
   return worst;
+}
+
+int etc_batch_queued(const etc_batch* b) { return b ? b->queued : 0; }
+
+etc_status etc_residual_history(etc_rve* h, double* out, int cap, int* first, int* count) {
+  if (!h || !out || cap < 1 || !first || !count) return ETC_EINVAL;
+  PcgState st;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(&st, h->st, sizeof(PcgState), cudaMemcpyDeviceToHost));
+  if (!(st.bb > 0.0)) return fail(h, ETC_ESTATE, "no solve has run on this handle");
+  // iterations 0 .. st.iter; the ring keeps the last kHistCap of them
+  const long long last = st.iter;
+  long long lo = last - (long long)kHistCap + 1;
+  if (lo < 0) lo = 0;
+  if (last - lo + 1 > cap) lo = last - cap + 1;
+  const int n = (int)(last - lo + 1);
+  std::vector<double> ring(kHistCap);
+  CK(cudaMemcpy(ring.data(), h->hist, sizeof(double) * kHistCap, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i)
+    out[i] = std::sqrt(ring[(size_t)((lo + i) % kHistCap)] / st.bb);
+  *first = (int)lo;
+  *count = n;
+  return ETC_OK;
 }
 
 etc_status etc_batch_destroy(etc_batch* b) {

@@ -62,6 +62,8 @@ struct PcgState {
   int xpend;         // 1 + parity of an iteration whose x += alpha w is still due
                      // (r was updated, the w update that carries x has not run)
   unsigned int cnt[8];  // arrival counters of the last-block reductions
+  double* hist;      // ring of ||r_i||^2 by iteration i (i = 0: ||b||^2), hist_cap entries
+  int hist_cap;
 };
 
 enum CounterSlot { kCntDot = 0, kCntRes = 1, kCntRho = 2, kCntAux = 3, kCntFlux = 4,
@@ -90,6 +92,19 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   if (threadIdx.x == 0)
     for (int w = 0; w < nw; ++w) t += sh[w];
   return t;
+}
+
+// Coordinates of one unit of work of a kernel: the hardware block of an
+// ordinary launch, or an item that a persistent block took from a batch work
+// queue (batch.cu), which stands for block (x, y, z) of the launch of one
+// solve that the item replaces.  The reductions below count arrivals and
+// index partials by these coordinates, so a kernel body written against them
+// runs unchanged in both forms.
+struct Blk {
+  unsigned int x, y, z, nx, ny, nz;
+};
+__device__ __forceinline__ Blk hw_blk() {
+  return {blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
 }
 
 // Publish one partial per block; returns true in the block that arrives last.
@@ -147,9 +162,10 @@ __device__ __forceinline__ double sum_partials(const double* partials, int nb, i
 
 // Each block writes nv values, the last block to arrive gets true.
 __device__ __forceinline__ bool publish_values(double* partials, int stride, const double* vals,
-                                               int nv, unsigned int* counter, int* flag) {
-  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+                                               int nv, unsigned int* counter, int* flag,
+                                               const Blk& b = hw_blk()) {
+  const unsigned int bid = b.x + b.nx * (b.y + b.ny * b.z);
+  const unsigned int nb = b.nx * b.ny * b.nz;
   if (threadIdx.x == 0) {
     for (int v = 0; v < nv; ++v) partials[(size_t)bid * stride + v] = vals[v];
     __threadfence();
@@ -162,7 +178,9 @@ __device__ __forceinline__ bool publish_values(double* partials, int stride, con
   return last;
 }
 
-__device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
+__device__ __forceinline__ unsigned int nblocks(const Blk& b = hw_blk()) {
+  return b.nx * b.ny * b.nz;
+}
 
 // End of the residual-update kernels (Algorithm 1, exit test): block partials
 // of ||r||^2, summed in block order by the last block, which records ||r||^2
@@ -172,11 +190,12 @@ __device__ __forceinline__ unsigned int nblocks() { return gridDim.x * gridDim.y
 template <int MODE>
 __device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, double* partials,
                                                     double rtol2, double* sh, int* flag,
-                                                    int par, bool defer) {
+                                                    int par, bool defer,
+                                                    const Blk& b = hw_blk()) {
   const double bs = block_sum(acc, sh);
   double v[1] = {bs};
-  if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], flag)) {
-    const double rr = sum_partials(partials, (int)nblocks(), 1, sh);
+  if (publish_values(partials, 1, v, 1, &st->cnt[kCntRes], flag, b)) {
+    const double rr = sum_partials(partials, (int)nblocks(b), 1, sh);
     if (threadIdx.x == 0) {
       st->rr = rr;
       if (MODE == 0) {
@@ -190,6 +209,8 @@ __device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, do
         else if (rr <= st->thresh2) { st->status = kOK; st->done = 1; }
         else if (st->iter >= st->maxit) { st->status = kENOCONV; st->done = 1; }
       }
+      // convergence history: ||r||^2 of iteration st->iter (0 after the start)
+      if (st->hist) st->hist[st->iter % st->hist_cap] = rr;
       st->cnt[kCntRes] = 0;
     }
   }
@@ -201,6 +222,71 @@ struct Geometry {
   long long n;        // n0 * n1 * n2
   long long plane;    // n0 * n1
 };
+
+// ---------------------------------------------------------------- batch work queue
+// The iterations of a batch run as persistent launches, one per kernel of the
+// PCG iteration and per class of solves (the same loading-frame sizes and
+// precision).  Each block of such a launch takes items from the class's queue
+// with one atomic add per item; item i stands for block i % per of the
+// one-solve launch of solve active[i / per], and the kernel body runs with
+// those block coordinates (Blk).  Only solves still iterating are listed, so
+// finished solves cost nothing; the loop control of each pass rebuilds the
+// list and rewinds the counters.
+constexpr int kQueueSlots = 12;  // launches per pass of the loop body: 2 iterations x 6 kernels
+struct BatchQueue {
+  unsigned int next[kQueueSlots];  // items taken, per launch of the pass
+  int nactive;                     // solves still iterating (entries of active)
+  int nsolves;
+  int* active;                     // nsolves entries, ascending solve index
+};
+
+// Device addresses of one solve of a batch (one RVE, one loading direction).
+// The mixed path views x, r and q as double-float pairs (same 8 bytes).
+struct BatchSolve {
+  PcgState* st;
+  double* partials;
+  double *x, *r, *q, *w;          // solution, residual, A w, search direction (FP64 path)
+  float* wf;                      // FP32 search direction (mixed path)
+  const double *T0, *T1, *T2, *D; // FP64 faces (with the zero plane) and diagonal
+  const float2 *F0, *F1, *F2, *FB;  // double-float faces and Dirichlet planes (mixed path)
+  double* t64;                    // FP64 transform buffer
+  const double* h64;              // FP64 reciprocal pivots
+  float* t32;                     // FP32 transform buffer (z^, z)
+  float* rhat[2];                 // FP32 r^ of the last two iterations
+  float2* ck;                     // checkpoints of the FP32 tridiagonal sweeps
+};
+
+// The item loop of a persistent launch on slot `slot` (every thread of the
+// block runs it): body(solve, local) for each item the block takes, items
+// numbered solve-major over the active solves, `per` (blocks of one solve)
+// each.  Thread 0 requests the next item with one atomic add as the current
+// one starts and reads the answer only when it ends, so the round trip to
+// the counter overlaps the item's work.
+template <class Body>
+__device__ __forceinline__ void queue_loop(BatchQueue* q, int slot, unsigned int per,
+                                           Body body) {
+  __shared__ unsigned int next_sh;
+  const unsigned int total = (unsigned int)q->nactive * per;
+  if (threadIdx.x == 0) next_sh = atomicAdd(&q->next[slot], 1u);
+  __syncthreads();
+  unsigned int cur = next_sh;
+#pragma unroll 1
+  while (cur < total) {
+    __syncthreads();  // every thread holds cur before next_sh is rewritten
+    unsigned int pre = 0u;
+    if (threadIdx.x == 0) pre = atomicAdd(&q->next[slot], 1u);
+    body(q->active[cur / per], cur % per);
+    if (threadIdx.x == 0) next_sh = pre;
+    __syncthreads();
+    cur = next_sh;
+  }
+}
+
+// Block coordinates of item `local` of a launch of nx x ny x nz blocks.
+__device__ __forceinline__ Blk item_blk(unsigned int local, unsigned int nx, unsigned int ny,
+                                        unsigned int nz) {
+  return {local % nx, (local / nx) % ny, local / (nx * ny), nx, ny, nz};
+}
 
 }  // namespace etc
 
@@ -447,17 +533,18 @@ namespace etc {
 template <int MODE>
 __device__ __forceinline__ void tridiag_tail(double acc, double acc2, PcgState* st,
                                              double* partials, double w4, const double* kd,
-                                             double kz_host, double* sh, int* flag_) {
+                                             double kz_host, double* sh, int* flag_,
+                                             const Blk& blk = hw_blk()) {
   int& flag = *flag_;
   double v[2];
   v[0] = block_sum(acc, sh);
   v[1] = (MODE == 2) ? block_sum(acc2, sh) : 0.0;
-  if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag)) {
+  if (publish_values(partials, 2, v, 2, &st->cnt[kCntRho], &flag, blk)) {
     const double wscale = w4 / (kd ? kd[2] : kz_host);
     double rho_new = 0.0, zr_old = 0.0;
     {
       // fixed-order sums of both columns
-      const int nb = (int)nblocks();
+      const int nb = (int)nblocks(blk);
       double a0 = 0.0, a1 = 0.0;
       const int per = (nb + blockDim.x - 1) / blockDim.x;
       const int b0 = threadIdx.x * per;

@@ -108,6 +108,62 @@ template cudaError_t launch_fast_y<float>(const Geometry&, const DctPlan<float>&
                                           const PcgState*, float*, int, int, cudaStream_t);
 
 template <typename R>
+cudaError_t launch_q_fast_fwd_x(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql,
+                                int par, int nt) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define QX(N) \
+  case N: e = q_x_n<R, N>(g, tb, ql, par, 0, nt); break;
+  switch (g.n0) {
+    QX(32) QX(64) QX(96) QX(128) QX(160) QX(192) QX(256) QX(384) QX(512) QX(1024)
+    default: return e;
+  }
+#undef QX
+  count_launch();
+  return e;
+}
+template <typename R>
+cudaError_t launch_q_fast_inv_x(const Geometry& g, const DctTables<R>& tb,
+                                const QueueLaunch& ql, int par, int nt) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define QX(N) \
+  case N: e = q_x_n<R, N>(g, tb, ql, par, 1, nt); break;
+  switch (g.n0) {
+    QX(32) QX(64) QX(96) QX(128) QX(160) QX(192) QX(256) QX(384) QX(512) QX(1024)
+    default: return e;
+  }
+#undef QX
+  count_launch();
+  return e;
+}
+template <typename R>
+cudaError_t launch_q_fast_y(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql,
+                            int inverse, int buf, int par) {
+  if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
+  cudaError_t e = cudaErrorInvalidValue;
+#define QY(N) \
+  case N: e = q_y_n<R, N>(g, tb, ql, inverse, buf, par); break;
+  switch (g.n1) {
+    QY(32) QY(64) QY(96) QY(128) QY(160) QY(192) QY(256) QY(384) QY(512) QY(1024)
+    default: return e;
+  }
+#undef QY
+  count_launch();
+  return e;
+}
+template cudaError_t launch_q_fast_fwd_x<double>(const Geometry&, const DctTables<double>&,
+                                                 const QueueLaunch&, int, int);
+template cudaError_t launch_q_fast_fwd_x<float>(const Geometry&, const DctTables<float>&,
+                                                const QueueLaunch&, int, int);
+template cudaError_t launch_q_fast_inv_x<double>(const Geometry&, const DctTables<double>&,
+                                                 const QueueLaunch&, int, int);
+template cudaError_t launch_q_fast_inv_x<float>(const Geometry&, const DctTables<float>&,
+                                                const QueueLaunch&, int, int);
+template cudaError_t launch_q_fast_y<double>(const Geometry&, const DctTables<double>&,
+                                             const QueueLaunch&, int, int, int);
+template cudaError_t launch_q_fast_y<float>(const Geometry&, const DctTables<float>&,
+                                            const QueueLaunch&, int, int, int);
+
+template <typename R>
 cudaError_t set_fast_attrs() {
   cudaError_t e = cudaSuccess;
 #define AT(N) \

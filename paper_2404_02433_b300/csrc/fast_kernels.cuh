@@ -149,9 +149,12 @@ __device__ __forceinline__ int vrow(int a) {
 
 // ---------------------------------------------------------------- axis 1
 // In place on t: every block owns C adjacent columns of one plane k.
+// The bodies take the block coordinates b (the hardware block, or a batch
+// queue item standing for one block of this solve's launch).
 template <typename R, int N, int INV>
-__global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>::MinBlocks())
-    k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check) {
+__device__ __forceinline__ void fast_y_body(const Blk& b, Geometry g,
+                                            DctTables<R> tb, const PcgState* st,
+                                            R* __restrict__ t, int check) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = FastCols<R, N>::C;
   constexpr int SIGN = INV ? 1 : -1;
@@ -159,10 +162,10 @@ __global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>
   c2<R>* sm = reinterpret_cast<c2<R>*>(smraw);  // C * M complex
   if (check && st->done) return;
   const int c = threadIdx.x % C, tau = threadIdx.x / C;
-  const int i = blockIdx.x * C + c;
+  const int i = b.x * C + c;
   const bool ok = i < g.n0;
   const long long n0 = g.n0;
-  R* col = t + (long long)blockIdx.y * g.plane + (ok ? i : 0);
+  R* col = t + (long long)b.y * g.plane + (ok ? i : 0);
   c2<R> v[Q];
   if (!INV) {
 #pragma unroll
@@ -235,6 +238,11 @@ __global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>
       }
   }
 }
+template <typename R, int N, int INV>
+__global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>::MinBlocks())
+    k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check) {
+  fast_y_body<R, N, INV>(hw_blk(), g, tb, st, t, check);
+}
 
 // ---------------------------------------------------------------- axis 0, forward
 // Same contract as k_fwd_x (MODE 0 initial residual, 1 PCG update, 2 transform
@@ -242,11 +250,13 @@ __global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>
 // Rows [row0, row0 + L) are contiguous in memory: the vector phase walks them
 // as pairs of elements with 16-byte loads.
 template <typename R, int N, int MODE, typename V, int NT>
-__global__ void __launch_bounds__(NT)
-    k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, V* __restrict__ x,
-                 const V* __restrict__ w, const V* __restrict__ q, V* __restrict__ r,
-                 const double* __restrict__ rin, R* __restrict__ t, double* partials, int par,
-                 double rtol2) {
+__device__ __forceinline__ void fast_fwd_x_body(const Blk& b, Geometry g,
+                                                DctTables<R> tb, PcgState* st,
+                                                V* __restrict__ x, const V* __restrict__ w,
+                                                const V* __restrict__ q, V* __restrict__ r,
+                                                const double* __restrict__ rin,
+                                                R* __restrict__ t, double* partials, int par,
+                                                double rtol2) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
   constexpr int L = FastX<N, NT>::L;
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(NT)
   c2<R>* A = reinterpret_cast<c2<R>*>(smraw);  // rows of RS complex: staging, transpose, Z
   R* Ar = reinterpret_cast<R*>(A);
   const long long nrows = (long long)g.n1 * g.n2;
-  const long long row0 = (long long)blockIdx.x * L;
+  const long long row0 = (long long)b.x * L;
   using S = Scalar<V>;
   constexpr bool XHERE = (MODE == 1) && std::is_same<V, double>::value;
   const typename S::T alpha = S::from((MODE == 1) ? st->alpha[par] : 0.0);
@@ -358,7 +368,17 @@ __global__ void __launch_bounds__(NT)
       }
     }
   if (MODE != 2)
-    fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag, par, !XHERE);
+    fwd_x_residual_tail<MODE>(acc + widen(accf), st, partials, rtol2, sh, &flag, par, !XHERE,
+                              b);
+}
+template <typename R, int N, int MODE, typename V, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fast_fwd_x(Geometry g, DctTables<R> tb, PcgState* st, V* __restrict__ x,
+                 const V* __restrict__ w, const V* __restrict__ q, V* __restrict__ r,
+                 const double* __restrict__ rin, R* __restrict__ t, double* partials, int par,
+                 double rtol2) {
+  fast_fwd_x_body<R, N, MODE, V, NT>(hw_blk(), g, tb, st, x, w, q, r, rin, t, partials, par,
+                                     rtol2);
 }
 
 // ---------------------------------------------------------------- axis 0, backward
@@ -366,10 +386,11 @@ __global__ void __launch_bounds__(NT)
 // MODE 0: z = u; MODE 2: w = u + beta w in place (z points at w), after
 // x += alpha w with the old w when x is given.
 template <typename R, typename TZ, int N, int MODE, int NT>
-__global__ void __launch_bounds__(NT)
-    k_fast_inv_x(Geometry g, DctTables<R> tb, PcgState* st, const R* __restrict__ t,
-                 TZ* __restrict__ z, const double* kd, double kz_host, int check,
-                 typename XOf<TZ>::T* __restrict__ x, int par) {
+__device__ __forceinline__ void fast_inv_x_body(const Blk& b, Geometry g,
+                                                DctTables<R> tb, PcgState* st,
+                                                const R* __restrict__ t, TZ* __restrict__ z,
+                                                const double* kd, double kz_host, int check,
+                                                typename XOf<TZ>::T* __restrict__ x, int par) {
   using TX = typename XOf<TZ>::T;  // x's storage (FP32 directions: double-float x)
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
@@ -380,7 +401,7 @@ __global__ void __launch_bounds__(NT)
   c2<R>* A = reinterpret_cast<c2<R>*>(smraw);  // rows of RS complex: staging, transpose, z
   R* Ar = reinterpret_cast<R*>(A);
   const long long nrows = (long long)g.n1 * g.n2;
-  const long long row0 = (long long)blockIdx.x * L;
+  const long long row0 = (long long)b.x * L;
   // stage the block's rows in natural order, 16 bytes per access, all of a
   // thread's loads issued before the first shared-memory store
   using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
@@ -435,7 +456,7 @@ __global__ void __launch_bounds__(NT)
   const typename Scalar<TZ>::T beta = Scalar<TZ>::from((MODE == 2) ? st->beta : 0.0);
   const bool upd = (MODE == 2) && x != nullptr;
   const typename Scalar<TX>::T alpha = Scalar<TX>::from(upd ? st->alpha[par] : 0.0);
-  if (upd && blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
+  if (upd && b.x == 0 && threadIdx.x == 0) st->xpend = 0;
   constexpr int NQ = L * M / NT;  // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
   static_assert(NQ % G == 0, "pair groups");
@@ -472,6 +493,66 @@ __global__ void __launch_bounds__(NT)
         st_pair(z + c, vfrom<TZ, R>(u0), vfrom<TZ, R>(u1));
     }
   }
+}
+template <typename R, typename TZ, int N, int MODE, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fast_inv_x(Geometry g, DctTables<R> tb, PcgState* st, const R* __restrict__ t,
+                 TZ* __restrict__ z, const double* kd, double kz_host, int check,
+                 typename XOf<TZ>::T* __restrict__ x, int par) {
+  fast_inv_x_body<R, TZ, N, MODE, NT>(hw_blk(), g, tb, st, t, z, kd, kz_host, check, x, par);
+}
+
+// ---------------------------------------------------------------- batch work queue
+// Persistent forms of the three transforms over the solves of a batch class
+// (BatchQueue in etc_internal.cuh), with the operands of the PCG iteration:
+// FP64 (R = double) on the FP64 vectors, mixed (R = float) on the
+// double-float vectors and the FP32 search direction.
+template <typename R, int N, int NT>
+__global__ void __launch_bounds__(NT)
+    kq_fast_fwd_x(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g, DctTables<R> tb,
+                  unsigned int nb, int par) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    if constexpr (sizeof(R) == 8)
+      fast_fwd_x_body<R, N, 1, double, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.x, a.w, a.q,
+                                           a.r, nullptr, a.t64, a.partials, par, 0.0);
+    else
+      fast_fwd_x_body<R, N, 1, float2, NT>(
+          item_blk(l, nb, 1, 1), g, tb, a.st, nullptr, nullptr,
+          reinterpret_cast<const float2*>(a.q), reinterpret_cast<float2*>(a.r), nullptr,
+          a.rhat[par], a.partials, par, 0.0);
+  });
+}
+
+// buf: 0 = t64, 1 = rhat[par], 2 = t32
+template <typename R, int N, int INV>
+__global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>::MinBlocks())
+    kq_fast_y(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g, DctTables<R> tb,
+              unsigned int nbx, int buf, int par) {
+  const unsigned int per = nbx * (unsigned int)g.n2;
+  queue_loop(q, slot, per, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    R* t;
+    if constexpr (sizeof(R) == 8) t = a.t64;
+    else t = buf == 1 ? a.rhat[par] : a.t32;
+    fast_y_body<R, N, INV>(item_blk(l, nbx, (unsigned int)g.n2, 1), g, tb, a.st, t, 1);
+  });
+}
+
+template <typename R, int N, int NT>
+__global__ void __launch_bounds__(NT)
+    kq_fast_inv_x(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g, DctTables<R> tb,
+                  unsigned int nb, int par) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    if constexpr (sizeof(R) == 8)
+      fast_inv_x_body<R, double, N, 2, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.t64, a.w,
+                                           a.st->kref, 1.0, 1, nullptr, par);
+    else
+      fast_inv_x_body<R, float, N, 2, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.t32, a.wf,
+                                          a.st->kref, 1.0, 1, reinterpret_cast<float2*>(a.x),
+                                          par);
+  });
 }
 
 // ---------------------------------------------------------------- per-size launchers
@@ -559,6 +640,47 @@ cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R
 }
 
 template <typename R, int N, int NT>
+cudaError_t q_x_nt(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql, int par,
+                   int inverse) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<R, N, NT>();
+  const long long items = (long long)nb * ql.nsolves;
+  if (inverse) {
+    const unsigned int grid = persistent_grid(kq_fast_inv_x<R, N, NT>, NT, sm, items);
+    kq_fast_inv_x<R, N, NT><<<grid, NT, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nb, par);
+  } else {
+    const unsigned int grid = persistent_grid(kq_fast_fwd_x<R, N, NT>, NT, sm, items);
+    kq_fast_fwd_x<R, N, NT><<<grid, NT, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nb, par);
+  }
+  return cudaGetLastError();
+}
+template <typename R, int N>
+cudaError_t q_x_n(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql, int par,
+                  int inverse, int nt) {
+  if (nt == 128 || !fast_x_fits<R, N, 256>()) return q_x_nt<R, N, 128>(g, tb, ql, par, inverse);
+  return q_x_nt<R, N, 256>(g, tb, ql, par, inverse);
+}
+template <typename R, int N>
+cudaError_t q_y_n(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql, int inverse,
+                  int buf, int par) {
+  constexpr int C = FastCols<R, N>::C;
+  constexpr int NTY = C * Fast<N>::P;
+  const unsigned int nbx = (unsigned int)((g.n0 + C - 1) / C);
+  const size_t sm = fast_y_smem<R, N>();
+  const long long items = (long long)nbx * g.n2 * ql.nsolves;
+  if (inverse) {
+    const unsigned int grid = persistent_grid(kq_fast_y<R, N, 1>, NTY, sm, items);
+    kq_fast_y<R, N, 1><<<grid, NTY, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nbx, buf, par);
+  } else {
+    const unsigned int grid = persistent_grid(kq_fast_y<R, N, 0>, NTY, sm, items);
+    kq_fast_y<R, N, 0><<<grid, NTY, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nbx, buf, par);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R, int N, int NT>
 cudaError_t attrs_nt() {
   cudaError_t e = cudaSuccess;
   if (!fast_x_fits<R, N, NT>()) return e;  // never launched
@@ -570,6 +692,8 @@ cudaError_t attrs_nt() {
   SETF((k_fast_fwd_x<R, N, 2, double, NT>), sx);
   SETF((k_fast_inv_x<R, double, N, 0, NT>), sx);
   SETF((k_fast_inv_x<R, double, N, 2, NT>), sx);
+  SETF((kq_fast_fwd_x<R, N, NT>), sx);
+  SETF((kq_fast_inv_x<R, N, NT>), sx);
   if (sizeof(R) == 4) {
     SETF((k_fast_fwd_x<float, N, 0, float2, NT>), sx);
     SETF((k_fast_fwd_x<float, N, 1, float2, NT>), sx);
@@ -588,6 +712,10 @@ cudaError_t attrs_n() {
     e = cudaFuncSetAttribute(k_fast_y<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fast_y<R, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kq_fast_y<R, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kq_fast_y<R, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
   return e;
 }
 
@@ -623,6 +751,14 @@ cudaError_t attrs_n() {
                                     double*, int, int, cudaStream_t);                        \
   PREFIX cudaError_t y_n<float, N>(const Geometry&, const DctTables<float>&, const PcgState*, \
                                    float*, int, int, cudaStream_t);                          \
+  PREFIX cudaError_t q_x_n<double, N>(const Geometry&, const DctTables<double>&,              \
+                                      const QueueLaunch&, int, int, int);                    \
+  PREFIX cudaError_t q_x_n<float, N>(const Geometry&, const DctTables<float>&,                \
+                                     const QueueLaunch&, int, int, int);                     \
+  PREFIX cudaError_t q_y_n<double, N>(const Geometry&, const DctTables<double>&,              \
+                                      const QueueLaunch&, int, int, int);                    \
+  PREFIX cudaError_t q_y_n<float, N>(const Geometry&, const DctTables<float>&,                \
+                                     const QueueLaunch&, int, int, int);                     \
   PREFIX cudaError_t attrs_n<double, N>();                                                   \
   PREFIX cudaError_t attrs_n<float, N>();
 #define ETC_FAST_EXTERN(N) ETC_FAST_LAUNCHERS(extern template, N)

@@ -324,21 +324,23 @@ __global__ void k_init(Geometry g, const double* __restrict__ Bin, const double*
 // T1[c+n0], T2[c+plane] are read from arrays that carry one zero plane of
 // padding.
 // MODE 0: q = A w.  MODE 1: PCG step, also w.q -> alpha (last block).
+// The body takes the block coordinates b (the hardware block, or a batch
+// queue item standing for one block of this solve's launch).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
-                                               const double* __restrict__ w,
-                                               double* __restrict__ q,
-                                               const double* __restrict__ T0,
-                                               const double* __restrict__ T1,
-                                               const double* __restrict__ T2,
-                                               const double* __restrict__ D, double* partials,
-                                               int par) {
+__device__ __forceinline__ void matvec_body(const Blk& b, Geometry g, PcgState* st,
+                                            const double* __restrict__ w,
+                                            double* __restrict__ q,
+                                            const double* __restrict__ T0,
+                                            const double* __restrict__ T1,
+                                            const double* __restrict__ T2,
+                                            const double* __restrict__ D, double* partials,
+                                            int par) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE == 1 && st->done) return;
   double dot = 0.0;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c = gidx(); c < g.n; c += stride) {
+  const long long stride = (long long)b.nx * blockDim.x;
+  for (long long c = (long long)b.x * blockDim.x + threadIdx.x; c < g.n; c += stride) {
     const int i = (int)(c % g.n0);
     const long long rem = c / g.n0;
     const int j = (int)(rem % g.n1);
@@ -360,8 +362,8 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
   if (MODE == 1) {
     const double bs = block_sum(dot, sh);
     double v[1] = {bs};
-    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag)) {
-      const double dq = sum_partials(partials, (int)nblocks(), 1, sh);
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag, b)) {
+      const double dq = sum_partials(partials, (int)nblocks(b), 1, sh);
       if (threadIdx.x == 0) {
         const double alpha = st->rho / dq;
         st->dq = dq;
@@ -371,6 +373,17 @@ __global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
       }
     }
   }
+}
+template <int MODE>
+__global__ void __launch_bounds__(256) k_matvec(Geometry g, PcgState* st,
+                                               const double* __restrict__ w,
+                                               double* __restrict__ q,
+                                               const double* __restrict__ T0,
+                                               const double* __restrict__ T1,
+                                               const double* __restrict__ T2,
+                                               const double* __restrict__ D, double* partials,
+                                               int par) {
+  matvec_body<MODE>(hw_blk(), g, st, w, q, T0, T1, T2, D, partials, par);
 }
 
 // ------------------------------------------------------------------ double-float matvec
@@ -411,21 +424,21 @@ __device__ __forceinline__ void df_acc(float p, float pe, float& s, float& e) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
-                                                     const float* __restrict__ w,
-                                                     float2* __restrict__ q,
-                                                     const float2* __restrict__ T0,
-                                                     const float2* __restrict__ T1,
-                                                     const float2* __restrict__ T2,
-                                                     const float2* __restrict__ Bin,
-                                                     const float2* __restrict__ Bout,
-                                                     double* partials, int par, int kchunk) {
+__device__ __forceinline__ void matvec_df_body(const Blk& b, Geometry g, PcgState* st,
+                                               const float* __restrict__ w,
+                                               float2* __restrict__ q,
+                                               const float2* __restrict__ T0,
+                                               const float2* __restrict__ T1,
+                                               const float2* __restrict__ T2,
+                                               const float2* __restrict__ Bin,
+                                               const float2* __restrict__ Bout,
+                                               double* partials, int par, int kchunk) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE == 1 && st->done) return;
-  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-  const int k0 = blockIdx.z * kchunk;
+  const int i = b.x * 32 + (threadIdx.x & 31);
+  const int j = b.y * 8 + (threadIdx.x >> 5);
+  const int k0 = b.z * kchunk;
   const int k1 = min(k0 + kchunk, g.n2);
   float ds = 0.f, dc = 0.f;
   if (i < g.n0 && j < g.n1 && k0 < k1) {
@@ -495,8 +508,8 @@ __global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
   if (MODE == 1) {
     const double bs = block_sum(widen(ds) + widen(dc), sh);
     double v[1] = {bs};
-    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag)) {
-      const double dq = sum_partials(partials, (int)nblocks(), 1, sh);
+    if (publish_values(partials, 1, v, 1, &st->cnt[kCntDot], &flag, b)) {
+      const double dq = sum_partials(partials, (int)nblocks(b), 1, sh);
       if (threadIdx.x == 0) {
         const double alpha = st->rho / dq;
         st->dq = dq;
@@ -506,6 +519,18 @@ __global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
       }
     }
   }
+}
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_matvec_df(Geometry g, PcgState* st,
+                                                     const float* __restrict__ w,
+                                                     float2* __restrict__ q,
+                                                     const float2* __restrict__ T0,
+                                                     const float2* __restrict__ T1,
+                                                     const float2* __restrict__ T2,
+                                                     const float2* __restrict__ Bin,
+                                                     const float2* __restrict__ Bout,
+                                                     double* partials, int par, int kchunk) {
+  matvec_df_body<MODE>(hw_blk(), g, st, w, q, T0, T1, T2, Bin, Bout, partials, par, kchunk);
 }
 
 // FP64 to double-float storage in place (8 bytes either way): the mixed
@@ -707,15 +732,15 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
 //         gives the Polak-Ribiere beta = (rho_new - z_new . r_old) / rho.
 // MODE 3: flexible PCG, initial apply: stores r^ in rnew, beta = 0.
 template <typename R, int MODE>
-__global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __restrict__ t,
-                                                const R* __restrict__ h, double w4,
-                                                const double* kd, double kz_host,
-                                                double* partials, R* __restrict__ rnew,
-                                                const R* __restrict__ rold) {
+__device__ __forceinline__ void tridiag_body(const Blk& b, Geometry g, PcgState* st,
+                                             R* __restrict__ t, const R* __restrict__ h,
+                                             double w4, const double* kd, double kz_host,
+                                             double* partials, R* __restrict__ rnew,
+                                             const R* __restrict__ rold) {
   __shared__ double sh[32];
   __shared__ int flag;
   if (MODE != 0 && st->done) return;
-  const long long s = gidx();
+  const long long s = (long long)b.x * blockDim.x + threadIdx.x;
   double acc = 0.0, acc2 = 0.0;
   if (s < g.plane) {
     // P planes per round (4 in FP64, 8 in FP32, the faster depths measured):
@@ -774,7 +799,15 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
     acc = wgt * to_f64<R>(part);
     if (MODE == 2) acc2 = wgt * to_f64<R>(zr);
   }
-  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, kz_host, sh, &flag);
+  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, kz_host, sh, &flag, b);
+}
+template <typename R, int MODE>
+__global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __restrict__ t,
+                                                const R* __restrict__ h, double w4,
+                                                const double* kd, double kz_host,
+                                                double* partials, R* __restrict__ rnew,
+                                                const R* __restrict__ rold) {
+  tridiag_body<R, MODE>(hw_blk(), g, st, t, h, w4, kd, kz_host, partials, rnew, rold);
 }
 
 // ------------------------------------------------------------------ tridiagonal, FP32, pivots on the fly
@@ -807,21 +840,22 @@ __global__ void __launch_bounds__(128) k_tridiag(Geometry g, PcgState* st, R* __
 // with more columns than 6 blocks of 128 threads on every SM; measured 0.55 ->
 // 0.49 ms at 512^3); smaller planes are latency-bound and keep the
 // unconstrained allocation (a few spilled registers cost 5-10 % there).
-template <int MODE, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_tridiag_otf(Geometry g, PcgState* st, const float* in,
-                                                    float* out, float2* __restrict__ ck,
-                                                    const double* __restrict__ lam0,
-                                                    const double* __restrict__ lam1,
-                                                    const double* __restrict__ kd, double w4,
-                                                    double* partials,
-                                                    const float* __restrict__ rold) {
+template <int MODE>
+__device__ __forceinline__ void tridiag_otf_body(const Blk& b, Geometry g, PcgState* st,
+                                                 const float* in, float* out,
+                                                 float2* __restrict__ ck,
+                                                 const double* __restrict__ lam0,
+                                                 const double* __restrict__ lam1,
+                                                 const double* __restrict__ kd, double w4,
+                                                 double* partials,
+                                                 const float* __restrict__ rold) {
   __shared__ double sh[32];
   __shared__ float coef[4];
   __shared__ int flag;
   if (MODE != 0 && st->done) return;
   if (threadIdx.x == 0) tri_coef(kd, coef);  // kappa_ref ratios, once per block
   __syncthreads();
-  const long long s = gidx();
+  const long long s = (long long)b.x * blockDim.x + threadIdx.x;
   double acc = 0.0, acc2 = 0.0;
   if (s < g.plane) {
     const int i = (int)(s % g.n0), j = (int)(s / g.n0);
@@ -910,7 +944,17 @@ __global__ void __launch_bounds__(128, MINB) k_tridiag_otf(Geometry g, PcgState*
     acc = wgt * widen(part);
     if (MODE == 2) acc2 = wgt * widen(zr);
   }
-  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, 1.0, sh, &flag);
+  if (MODE != 0) tridiag_tail<MODE>(acc, acc2, st, partials, w4, kd, 1.0, sh, &flag, b);
+}
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_tridiag_otf(Geometry g, PcgState* st, const float* in,
+                                                    float* out, float2* __restrict__ ck,
+                                                    const double* __restrict__ lam0,
+                                                    const double* __restrict__ lam1,
+                                                    const double* __restrict__ kd, double w4,
+                                                    double* partials,
+                                                    const float* __restrict__ rold) {
+  tridiag_otf_body<MODE>(hw_blk(), g, st, in, out, ck, lam0, lam1, kd, w4, partials, rold);
 }
 
 // ------------------------------------------------------------------ backward DCT along axis 0
@@ -1307,6 +1351,130 @@ cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, doub
   const unsigned int nb = matvec_blocks(g);
   if (mode == 0) k_matvec<0><<<nb, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par);
   else k_matvec<1><<<nb, 256, 0, s>>>(g, st, w, q, T0, T1, T2, D, partials, par);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ batch work queue
+// Persistent forms of the loop kernels above for the solves of one batch class
+// (BatchQueue in etc_internal.cuh): every block takes (solve, block) items
+// until the queue is empty and runs the kernel body on the solve's buffers
+// with the block coordinates the one-solve launch would have given it.
+
+template <int MODE>
+__global__ void __launch_bounds__(256) kq_matvec(BatchQueue* q, int slot, const BatchSolve* bs,
+                                                Geometry g, unsigned int nb, int par) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    matvec_body<MODE>(item_blk(l, nb, 1, 1), g, a.st, a.w, a.q, a.T0, a.T1, a.T2, a.D,
+                      a.partials, par);
+  });
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) kq_matvec_df(BatchQueue* q, int slot,
+                                                      const BatchSolve* bs, Geometry g,
+                                                      dim3 grid, int kchunk, int par) {
+  const unsigned int per = grid.x * grid.y * grid.z;
+  queue_loop(q, slot, per, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    matvec_df_body<MODE>(item_blk(l, grid.x, grid.y, grid.z), g, a.st, a.wf,
+                         reinterpret_cast<float2*>(a.q), a.F0, a.F1, a.F2, a.FB,
+                         a.FB + g.plane, a.partials, par, kchunk);
+  });
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) kq_tridiag(BatchQueue* q, int slot, const BatchSolve* bs,
+                                                 Geometry g, unsigned int nb, double w4) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    tridiag_body<double, MODE>(item_blk(l, nb, 1, 1), g, a.st, a.t64, a.h64, w4, a.st->kref,
+                               1.0, a.partials, nullptr, nullptr);
+  });
+}
+
+template <int MODE, int MINB>
+__global__ void __launch_bounds__(128, MINB) kq_tridiag_otf(BatchQueue* q, int slot,
+                                                           const BatchSolve* bs, Geometry g,
+                                                           unsigned int nb,
+                                                           const double* __restrict__ lam0,
+                                                           const double* __restrict__ lam1,
+                                                           double w4, int par) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    tridiag_otf_body<MODE>(item_blk(l, nb, 1, 1), g, a.st, a.rhat[par], a.t32, a.ck, lam0,
+                           lam1, a.st->kref, w4, a.partials, a.rhat[par ^ 1]);
+  });
+}
+
+// End of one pass of a class's loop (and, with init, its start): the pass
+// count and iteration cap of every solve as in k_loop_control, then the list
+// of solves still iterating and the rewound item counters; the loop ends when
+// no solve is left.
+__global__ void k_queue_control(BatchQueue* q, const BatchSolve* bs,
+                                cudaGraphConditionalHandle handle, int init) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int na = 0;
+  for (int s = 0; s < q->nsolves; ++s) {
+    PcgState* st = bs[s].st;
+    if (!init) {
+      st->passes += 1;
+      if (!st->done && st->passes >= st->max_passes) {
+        st->status = kENOCONV;
+        st->done = 1;
+      }
+    }
+    if (!st->done) q->active[na++] = s;
+  }
+  q->nactive = na;
+  for (int k = 0; k < kQueueSlots; ++k) q->next[k] = 0u;
+  if (!init && na == 0) cudaGraphSetConditional(handle, 0u);
+}
+
+cudaError_t launch_queue_control(BatchQueue* q, const BatchSolve* bs,
+                                 cudaGraphConditionalHandle handle, int init, cudaStream_t s) {
+  k_queue_control<<<1, 32, 0, s>>>(q, bs, handle, init);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_matvec(const Geometry& g, const QueueLaunch& ql, int par) {
+  const unsigned int nb = matvec_blocks(g);
+  const unsigned int grid =
+      persistent_grid(kq_matvec<1>, 256, 0, (long long)nb * ql.nsolves);
+  kq_matvec<1><<<grid, 256, 0, ql.s>>>(ql.q, ql.slot, ql.bs, g, nb, par);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_matvec_df(const Geometry& g, const QueueLaunch& ql, int par) {
+  int kc;
+  const dim3 d = matvec_df_grid(g, &kc);
+  const long long per = (long long)d.x * d.y * d.z;
+  const unsigned int grid = persistent_grid(kq_matvec_df<1>, 256, 0, per * ql.nsolves);
+  kq_matvec_df<1><<<grid, 256, 0, ql.s>>>(ql.q, ql.slot, ql.bs, g, d, kc, par);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_tridiag(const Geometry& g, const QueueLaunch& ql) {
+  const unsigned int nb = tridiag_blocks(g);
+  const double w4 = 4.0 / ((double)g.n0 * g.n1);
+  const unsigned int grid = persistent_grid(kq_tridiag<1>, 128, 0, (long long)nb * ql.nsolves);
+  kq_tridiag<1><<<grid, 128, 0, ql.s>>>(ql.q, ql.slot, ql.bs, g, nb, w4);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q_tridiag_otf(const Geometry& g, const QueueLaunch& ql, const double* lam0,
+                                 const double* lam1, int par) {
+  const unsigned int nb = tridiag_blocks(g);
+  const double w4 = 4.0 / ((double)g.n0 * g.n1);
+  const long long items = (long long)nb * ql.nsolves;
+  // (no 64-register cap as in the one-solve launcher: in the item loop it spills)
+  const unsigned int grid = persistent_grid(kq_tridiag_otf<2, 1>, 128, 0, items);
+  kq_tridiag_otf<2, 1><<<grid, 128, 0, ql.s>>>(ql.q, ql.slot, ql.bs, g, nb, lam0, lam1, w4, par);
   count_launch();
   return cudaGetLastError();
 }

@@ -162,6 +162,61 @@ cudaError_t set_fast_attrs();
 
 unsigned long long launch_count();
 
+// ---------------------------------------------------------------- batch work queue
+// Persistent launches over the solves of one batch class (BatchQueue): the
+// queue, the per-solve addresses, the launch slot of the loop-body pass, the
+// number of solves of the class (bounds the grid) and the stream.
+struct QueueLaunch {
+  BatchQueue* q;
+  const BatchSolve* bs;
+  int slot;
+  int nsolves;
+  cudaStream_t s;
+};
+
+// Blocks of a persistent launch: as many as the SMs hold at once, at most one
+// per item.
+template <typename K>
+unsigned int persistent_grid(K kernel, int threads, size_t smem, long long items) {
+  int occ = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) !=
+          cudaSuccess || occ < 1)
+    occ = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    sms = 148;
+  long long g = (long long)sms * occ;
+  if (g > items) g = items;
+  return (unsigned int)(g < 1 ? 1 : g);
+}
+
+// Loop control of a class (init: the initial list before the loop).
+cudaError_t launch_queue_control(BatchQueue* q, const BatchSolve* bs,
+                                 cudaGraphConditionalHandle handle, int init, cudaStream_t s);
+// The iteration's kernels over the class: FP64 matvec (mode 1), double-float
+// matvec (mode 1), FP64 tridiagonal solves (mode 1), FP32 tridiagonal solves
+// of the flexible PCG (mode 2, r^ in rhat[par], r_old in rhat[par ^ 1]).
+cudaError_t launch_q_matvec(const Geometry& g, const QueueLaunch& ql, int par);
+cudaError_t launch_q_matvec_df(const Geometry& g, const QueueLaunch& ql, int par);
+cudaError_t launch_q_tridiag(const Geometry& g, const QueueLaunch& ql);
+cudaError_t launch_q_tridiag_otf(const Geometry& g, const QueueLaunch& ql, const double* lam0,
+                                 const double* lam1, int par);
+// Register-resident transforms over the class (lengths with fast_len):
+// axis-0 forward with the residual update (FP64: x, w, q, r and t64; mixed:
+// the double-float q, r and rhat[par]), axis 1 in place (buf 0: t64, 1:
+// rhat[par], 2: t32), axis-0 backward with w <- z + beta w (FP64: t64 into w;
+// mixed: t32 into wf, with x += alpha w).  nt: 256 or 128 threads (axis 0).
+template <typename R>
+cudaError_t launch_q_fast_fwd_x(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql,
+                                int par, int nt);
+template <typename R>
+cudaError_t launch_q_fast_y(const Geometry& g, const DctTables<R>& tb, const QueueLaunch& ql,
+                            int inverse, int buf, int par);
+template <typename R>
+cudaError_t launch_q_fast_inv_x(const Geometry& g, const DctTables<R>& tb,
+                                const QueueLaunch& ql, int par, int nt);
+
 // Grid sizes of the reduction kernels (to size the partials buffer).
 unsigned int matvec_blocks(const Geometry& g);
 unsigned int matvec_df_blocks(const Geometry& g);

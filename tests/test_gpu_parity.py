@@ -210,6 +210,30 @@ def test_config_32_spheres_direction_x():
     assert relmax(p, ref.p) < 1e-8
 
 
+def test_residual_history_matches_oracle():
+    # ||r_i|| / ||b|| after every iteration (the convergence histories of
+    # Sec. 4.2) against the oracle's Algorithm 1 on the same input
+    k, _ = M.random_spheres((32, 32, 32), (3, 5), 0.3, 1001, 1.0, 10.0)
+    (k0, k1, k2), lens = O.permute_medium(k, k, k, (1.0, 1.0, 1.0), 0)
+    f = O.face_conductances(k0, k1, k2, lens)
+    res = O.pcg(f, O.right_hand_side(f, 1.0, 0.0), O.reference_parameters(O.group_extrema(f)),
+                rtol=1e-10)
+    rve = make(k)
+    kap, inf = rve.solve(0, rtol=1e-10)
+    first, hist = rve.history()
+    assert first == 0 and len(hist) == inf["iters"] + 1 == len(res.history)
+    assert hist[0] == 1.0 and hist[-1] == pytest.approx(inf["relres"], rel=1e-14)
+    np.testing.assert_allclose(hist, res.history, rtol=1e-6)
+    # a short window: the last five iterations
+    first5, hist5 = rve.history(cap=5)
+    assert first5 == inf["iters"] - 4 and hist5 == hist[-5:]
+    # the mixed path records its own iterations
+    _, inf_m = rve.solve(0, rtol=1e-8, precision=B.ETC_PREC_MIXED)
+    first_m, hist_m = rve.history()
+    assert first_m == 0 and len(hist_m) == inf_m["iters"] + 1
+    assert hist_m[-1] == pytest.approx(inf_m["relres"], rel=1e-14) and hist_m[-1] <= 1e-8
+
+
 @pytest.mark.parametrize("shape", [(18, 20, 24), (11, 13, 17), (1, 6, 4), (7, 1, 9), (1, 1, 5),
                                    (6, 1, 1), (1, 1, 1)])
 def test_tensor_matches_oracle(shape):
