@@ -85,6 +85,17 @@ enum {
   ETC_REF_USER = 2     /* values given to etc_set_reference_params */
 };
 
+/* Initial guess of PCG (Algorithm 1 leaves it open). */
+enum {
+  ETC_INIT_ZERO = 0,   /* x0 = 0 (r0 = b) */
+  ETC_INIT_LINEAR = 1  /* x0 = p_in + (p_out - p_in) (k + 1/2) / n along the loading axis:
+                          the exact TPFA solution of a homogeneous medium; costs one
+                          product with A.  Solves with per-face data or a source
+                          (etc_solve_general) start from 0. */
+};
+
+/* Options of a solve.  Fill with etc_default_opts before setting fields
+ * (fields may be added at the end). */
 typedef struct {
   double rtol;         /* exit when ||r||_2 <= rtol ||b||_2 (Eq. exit); default 1e-8 */
   int maxit;           /* iteration cap; default 5000 */
@@ -93,6 +104,8 @@ typedef struct {
   int batch_queue;     /* etc_batch_create only: 1 = work-queue loops per class of
                           equal sizes (persistent kernels), 0 = a device-driven loop
                           per solve; default 0 (see etc_batch_create) */
+  int init;            /* ETC_INIT_ZERO (default) or ETC_INIT_LINEAR; a guess that
+                          already meets the exit test ends with 0 iterations */
 } etc_opts;
 
 typedef struct {
@@ -144,8 +157,9 @@ etc_status etc_set_reference_params(etc_rve* rve, int dir, int mode, const doubl
 
 /*
  * Solve the TPFA system for loading direction dir with p = p_in on the low face
- * and p_out on the high face of that axis (Sec. 2.1), by PCG with initial guess
- * 0, and return the effective conductivity kappa_eff (Eq. effective formula dis,
+ * and p_out on the high face of that axis (Sec. 2.1), by PCG from the initial
+ * guess opts->init (default 0), and return the effective conductivity
+ * kappa_eff (Eq. effective formula dis,
  * outflow side).  opts may be NULL (defaults).  info may be NULL.
  * p_in == p_out is rejected (Sec. 2.1).  ETC_ENOCONV still fills kappa_eff and
  * info from the last iterate.

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libetc.so")
 ETC_OK, ETC_EINVAL, ETC_ENOMEM, ETC_ECUDA, ETC_ENOCONV, ETC_EBREAKDOWN, ETC_ESTATE = range(7)
 ETC_PREC_FP64, ETC_PREC_MIXED, ETC_PREC_MIXED_F64 = 0, 1, 2
 ETC_REF_LP, ETC_REF_ONES, ETC_REF_USER = 0, 1, 2
+ETC_INIT_ZERO, ETC_INIT_LINEAR = 0, 1
 
 EXPORTED = (
     "etc_default_opts", "etc_create_rve", "etc_destroy_rve", "etc_set_reference_params",
@@ -33,7 +34,7 @@ EXPORTED = (
 
 class EtcOpts(ctypes.Structure):
     _fields_ = [("rtol", c_double), ("maxit", c_int), ("precision", c_int),
-                ("true_residual", c_int), ("batch_queue", c_int)]
+                ("true_residual", c_int), ("batch_queue", c_int), ("init", c_int)]
 
 
 class EtcInfo(ctypes.Structure):
@@ -138,11 +139,12 @@ def _check(status, handle=None, ok=(ETC_OK,), thread_reason=False):
     raise EtcError(status, msg)
 
 
-def make_opts(rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1, batch_queue=0):
+def make_opts(rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1, batch_queue=0,
+              init=ETC_INIT_ZERO):
     o = EtcOpts()
     _check(load_library().etc_default_opts(byref(o)))
     o.rtol, o.maxit, o.precision, o.true_residual = rtol, maxit, precision, true_residual
-    o.batch_queue = batch_queue
+    o.batch_queue, o.init = batch_queue, init
     return o
 
 
@@ -324,8 +326,8 @@ class RVE:
             pass
 
     def solve(self, direction, p_in=1.0, p_out=0.0, rtol=1e-8, maxit=5000,
-              precision=ETC_PREC_FP64, true_residual=1):
-        opts = make_opts(rtol, maxit, precision, true_residual)
+              precision=ETC_PREC_FP64, true_residual=1, init=ETC_INIT_ZERO):
+        opts = make_opts(rtol, maxit, precision, true_residual, init=init)
         st, k, info = etc_solve_direction(self.h, direction, p_in, p_out, opts)
         return k, info.as_dict()
 

@@ -640,19 +640,36 @@ etc_status validate_opts(etc_rve* h, const etc_opts* o) {
   if (o->precision != ETC_PREC_FP64 && o->precision != ETC_PREC_MIXED &&
       o->precision != ETC_PREC_MIXED_F64)
     return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64, _MIXED or _MIXED_F64");
+  if (o->init != ETC_INIT_ZERO && o->init != ETC_INIT_LINEAR)
+    return fail(h, ETC_EINVAL, "init must be ETC_INIT_ZERO or ETC_INIT_LINEAR");
   return ETC_OK;
 }
 
 // Initial residual and preconditioner apply (Algorithm 1, first line): r = b,
 // x = 0, z0 = A_ref^{-1} r, rho = r.z0, w = z0 (written over w = 0 by the
 // last inverse pass with beta = 0).
+// x0 = the linear profile (init ETC_INIT_LINEAR, constant Dirichlet data only):
+// r = b - A x0 in FP64 after launch_init has set r = b, with ||b||^2 recorded.
+etc_status start_linear(etc_rve* h, const Geometry& g, double* x, const Rhs& rhs) {
+  CK(launch_init_linear(g, rhs.pin, rhs.pout, h->r, x, h->partials, h->st, h->stream));
+  CK(launch_matvec(g, h->st, x, h->q, h->T0, h->T1, h->T2, h->D, h->partials, 0, 0,
+                   h->stream));
+  CK(launch_sub(g.n, h->r, h->q, h->stream));
+  return ETC_OK;
+}
+
 etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, const Rhs& rhs,
-                        double rtol2) {
+                        double rtol2, int init = ETC_INIT_ZERO) {
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
+  const bool lin = init == ETC_INIT_LINEAR && !rhs.general();
   if (prec == ETC_PREC_FP64) {
     CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream,
                    rhs.pin_f, rhs.pout_f, rhs.src));
+    if (lin) {
+      const etc_status s = start_linear(h, g, x, rhs);
+      if (s != ETC_OK) return s;
+    }
     CK((launch_fwd_x<double, double>(g, P0.p64, h->st, x, nullptr, nullptr, h->r, nullptr,
                                      h->t64, h->partials, 0, rtol2, 0, h->stream, h->tiles[0])));
     return precond_tail<double, double>(h, g, P0.p64, P1.p64, h->t64, h->t64, h->h64, h->w[0],
@@ -661,6 +678,10 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
   if (prec == ETC_PREC_MIXED_F64) {
     CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, h->w[0], h->stream,
                    rhs.pin_f, rhs.pout_f, rhs.src));
+    if (lin) {
+      const etc_status s = start_linear(h, g, x, rhs);
+      if (s != ETC_OK) return s;
+    }
     // iteration 0 reads the transformed residual of this apply from rhat32[1]
     CK((launch_fwd_x<float, double>(g, P0.p32, h->st, x, nullptr, nullptr, h->r, nullptr,
                                     h->rhat32[1], h->partials, 0, rtol2, 0, h->stream,
@@ -671,6 +692,11 @@ etc_status launch_start(etc_rve* h, const Geometry& g, double* x, int prec, cons
   // mixed: x = 0 has the same bytes in both storages; r = b is split; w = 0 (FP32)
   CK(launch_init(g, h->Bin, h->Bout, rhs.pin, rhs.pout, h->r, x, nullptr, h->stream, rhs.pin_f,
                  rhs.pout_f, rhs.src));
+  if (lin) {
+    const etc_status s = start_linear(h, g, x, rhs);
+    if (s != ETC_OK) return s;
+    CK(launch_split_inplace(x, h->n, h->stream));  // x0 as double-float pairs
+  }
   CK(cudaMemsetAsync(h->wf, 0, (size_t)h->n * sizeof(float), h->stream));
   CK(launch_split_inplace(h->r, h->n, h->stream));
   // iteration 0 reads the transformed residual of this apply from rhat32[1]
@@ -816,7 +842,7 @@ etc_status solve_impl(etc_rve* h, int dir, const Rhs& rhs, const etc_opts& o, do
   }
   CK(cudaEventRecord(e[1], h->stream));
   Range rpcg("etc_pcg");
-  s = launch_start(h, g, x, prec, rhs, o.rtol * o.rtol);
+  s = launch_start(h, g, x, prec, rhs, o.rtol * o.rtol, o.init);
   if (s != ETC_OK) return s;
 
   int launched = 0, slot = 1, prev_slot = 2, chunk = 2;
@@ -906,7 +932,7 @@ etc_status capture_solve_start(etc_rve* h, int dir, const etc_opts& o, cudaStrea
   s = launch_reference(h, dir, prec);
   if (s != ETC_OK) return s;
   const Rhs unit;  // p_in = 1, p_out = 0
-  return launch_start(h, g, h->xsol[dir], prec, unit, o.rtol * o.rtol);
+  return launch_start(h, g, h->xsol[dir], prec, unit, o.rtol * o.rtol, o.init);
 }
 
 // Queue the end of a device-driven solve: the last x step, post-processing,
@@ -1105,6 +1131,7 @@ etc_status etc_default_opts(etc_opts* o) {
   o->precision = ETC_PREC_FP64;
   o->true_residual = 1;
   o->batch_queue = 0;
+  o->init = ETC_INIT_ZERO;
   return ETC_OK;
 }
 

@@ -62,8 +62,9 @@ struct PcgState {
   int xpend;         // 1 + parity of an iteration whose x += alpha w is still due
                      // (r was updated, the w update that carries x has not run)
   unsigned int cnt[8];  // arrival counters of the last-block reductions
-  double* hist;      // ring of ||r_i||^2 by iteration i (i = 0: ||b||^2), hist_cap entries
+  double* hist;      // ring of ||r_i||^2 by iteration i (i = 0: ||r_0||^2), hist_cap entries
   int hist_cap;
+  double bb_given;   // ||b||^2 when the initial guess is not 0 (else 0: ||b|| = ||r_0||)
 };
 
 enum CounterSlot { kCntDot = 0, kCntRes = 1, kCntRho = 2, kCntAux = 3, kCntFlux = 4,
@@ -199,9 +200,12 @@ __device__ __forceinline__ void fwd_x_residual_tail(double acc, PcgState* st, do
     if (threadIdx.x == 0) {
       st->rr = rr;
       if (MODE == 0) {
-        st->bb = rr;
-        st->thresh2 = rtol2 * rr;
-        if (!(rr > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+        // the exit test is relative to ||b|| (Eq. exit): r_0 = b for x0 = 0
+        const double bb = st->bb_given > 0.0 ? st->bb_given : rr;
+        st->bb = bb;
+        st->thresh2 = rtol2 * bb;
+        if (!(bb > 0.0) || !isfinite(rr)) { st->status = kEBREAKDOWN; st->done = 1; }
+        else if (st->bb_given > 0.0 && rr <= st->thresh2) { st->status = kOK; st->done = 1; }
       } else {
         st->iter += 1;
         st->xpend = defer ? par + 1 : 0;

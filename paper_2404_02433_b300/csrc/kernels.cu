@@ -282,6 +282,7 @@ __global__ void k_state_reset(PcgState* st, int maxit) {
   st->passes = 0;
   st->max_passes = maxit / 2 + 4;  // the loop body runs two iterations
   st->xpend = 0;
+  st->bb_given = 0.0;
 }
 
 // End of one pass of a device-driven PCG loop (graph WHILE node): stop when
@@ -313,6 +314,37 @@ __global__ void k_init(Geometry g, const double* __restrict__ Bin, const double*
     x[c] = 0.0;
     if (w0) w0[c] = 0.0;
   }
+}
+
+// Initial guess x0 of a homogeneous medium: the TPFA solution with constant
+// conductivity is linear in k, half a cell from each Dirichlet face,
+// x_c = p_in + (p_out - p_in) (k + 1/2) / n2.  Also ||b||^2 of r = b (last
+// block: st->bb_given), for the exit test of Eq. (exit), which stays relative
+// to ||b|| when r_0 = b - A x0 differs from b.
+__global__ void k_init_linear(Geometry g, double pin, double pout, const double* __restrict__ r,
+                              double* __restrict__ x, double* partials, PcgState* st) {
+  __shared__ double sh[32];
+  __shared__ int flag;
+  double acc = 0.0;
+  for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
+    const long long k = c / g.plane;
+    x[c] = pin + (pout - pin) * (((double)k + 0.5) / (double)g.n2);
+    acc = fma(r[c], r[c], acc);
+  }
+  const double bs = block_sum(acc, sh);
+  double v[1] = {bs};
+  if (publish_values(partials, 1, v, 1, &st->cnt[kCntAux], &flag)) {
+    const double bb = sum_partials(partials, (int)nblocks(), 1, sh);
+    if (threadIdx.x == 0) {
+      st->bb_given = bb;
+      st->cnt[kCntAux] = 0;
+    }
+  }
+}
+
+// r <- r - q
+__global__ void k_sub(long long n, double* __restrict__ r, const double* __restrict__ q) {
+  for (long long c = gidx(); c < n; c += (long long)gridDim.x * blockDim.x) r[c] -= q[c];
 }
 
 // ------------------------------------------------------------------ matvec
@@ -1317,6 +1349,19 @@ cudaError_t launch_matvec_df(const Geometry& g, PcgState* st, const float* w, fl
     k_matvec_df<1><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, FB, Bout, partials, par, kc);
   else
     k_matvec_df<0><<<grid, 256, 0, s>>>(g, st, w, q, T0, T1, T2, FB, Bout, partials, par, kc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_linear(const Geometry& g, double pin, double pout, const double* r,
+                               double* x, double* partials, PcgState* st, cudaStream_t s) {
+  k_init_linear<<<grid_for(g.n, 256), 256, 0, s>>>(g, pin, pout, r, x, partials, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(long long n, double* r, const double* q, cudaStream_t s) {
+  k_sub<<<grid_for(n, 256), 256, 0, s>>>(n, r, q);
   count_launch();
   return cudaGetLastError();
 }

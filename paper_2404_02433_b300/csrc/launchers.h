@@ -38,6 +38,10 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
                         double pout, double* r, double* x, double* w0, cudaStream_t s,
                         const double* pin_f = nullptr, const double* pout_f = nullptr,
                         const double* src = nullptr);
+// x0 of a homogeneous medium (linear in k) and ||b||^2 of r = b into st->bb_given.
+cudaError_t launch_init_linear(const Geometry& g, double pin, double pout, const double* r,
+                               double* x, double* partials, PcgState* st, cudaStream_t s);
+cudaError_t launch_sub(long long n, double* r, const double* q, cudaStream_t s);  // r -= q
 cudaError_t launch_matvec(const Geometry& g, PcgState* st, const double* w, double* q,
                           const double* T0, const double* T1, const double* T2, const double* D,
                           double* partials, int par, int mode, cudaStream_t s);

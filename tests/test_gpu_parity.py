@@ -210,6 +210,49 @@ def test_config_32_spheres_direction_x():
     assert relmax(p, ref.p) < 1e-8
 
 
+@pytest.mark.parametrize("direction", [0, 2])
+def test_linear_initial_guess_matches_oracle(direction):
+    # x0 = p_in + (p_out - p_in)(k + 1/2)/n2 along the loading axis: the
+    # oracle's Algorithm 1 started from the same guess (the exit test stays
+    # relative to ||b||, Eq. exit)
+    k, _ = M.random_spheres((24, 20, 28), (3, 5), 0.3, 1001, 1.0, 10.0)
+    (k0, k1, k2), lens = O.permute_medium(k, k, k, (1.0, 1.0, 1.0), direction)
+    f = O.face_conductances(k0, k1, k2, lens)
+    kref = O.reference_parameters(O.group_extrema(f))
+    b = O.right_hand_side(f, 2.0, -1.0)
+    nz = k0.shape[0]
+    prof = 2.0 + (-1.0 - 2.0) * (np.arange(nz) + 0.5) / nz
+    p0 = np.ascontiguousarray(np.broadcast_to(prof[:, None, None], k0.shape))
+    res = O.pcg(f, b, kref, rtol=1e-10, p0=p0)
+    kap_o = O.outflow_etc(f, res.p, lens, 2.0, -1.0)
+    rve = make(k)
+    kap, inf = rve.solve(direction, p_in=2.0, p_out=-1.0, rtol=1e-10, init=B.ETC_INIT_LINEAR)
+    assert inf["status"] == B.ETC_OK
+    assert abs(kap - kap_o) <= 1e-9 * kap_o
+    assert abs(inf["iters"] - res.iters) <= 1
+    _, hist = rve.history()
+    assert hist[0] == pytest.approx(res.history[0], rel=1e-12) and hist[0] < 1.0
+    assert relmax(host(rve.solution(direction)), O.unpermute_field(res.p, direction)) < 1e-8
+    # the mixed forms start from the same guess
+    for prec in (B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64):
+        km, im = rve.solve(direction, p_in=2.0, p_out=-1.0, rtol=1e-9, precision=prec,
+                           init=B.ETC_INIT_LINEAR)
+        assert im["status"] == B.ETC_OK and abs(km - kap_o) <= 1e-6 * kap_o
+
+
+def test_linear_initial_guess_homogeneous_zero_iterations():
+    # the guess is the solution of a homogeneous medium: no iteration at all
+    shape = (10, 12, 14)
+    comps = (np.full(shape, 2.0), np.full(shape, 3.5), np.full(shape, 0.7))
+    rve = make(*comps)
+    for prec in (B.ETC_PREC_FP64, B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64):
+        for d in range(3):
+            kap, inf = rve.solve(d, p_in=2.0, p_out=-1.0, rtol=1e-12, precision=prec,
+                                 init=B.ETC_INIT_LINEAR)
+            assert inf["status"] == B.ETC_OK and inf["iters"] == 0
+            assert kap == pytest.approx(comps[d][0, 0, 0], rel=1e-12)
+
+
 def test_residual_history_matches_oracle():
     # ||r_i|| / ||b|| after every iteration (the convergence histories of
     # Sec. 4.2) against the oracle's Algorithm 1 on the same input
