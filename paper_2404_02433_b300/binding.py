@@ -257,12 +257,12 @@ class Batch:
     """Full tensors of several RVEs in one CUDA graph (etc_batch_*)."""
 
     def __init__(self, rves, rtol=1e-8, maxit=5000, precision=ETC_PREC_FP64, true_residual=1,
-                 queue=False):
+                 queue=False, init=ETC_INIT_ZERO):
         lib = load_library()
         self.rves = list(rves)
         self.count = len(self.rves)
         hs = (c_void_p * self.count)(*[r.h.value for r in self.rves])
-        self.opts = make_opts(rtol, maxit, precision, true_residual, int(bool(queue)))
+        self.opts = make_opts(rtol, maxit, precision, true_residual, int(bool(queue)), init)
         self.b = c_void_p()
         _check(lib.etc_batch_create(self.count, hs, byref(self.opts), byref(self.b)),
                thread_reason=True)

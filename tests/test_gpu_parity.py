@@ -210,6 +210,37 @@ def test_config_32_spheres_direction_x():
     assert relmax(p, ref.p) < 1e-8
 
 
+def test_residual_history_of_a_capped_solve():
+    # ETC_ENOCONV after maxit iterations: the history holds iterations 0..maxit,
+    # its last value is the reported relres
+    k, _ = M.random_spheres((24, 24, 24), (3, 5), 0.3, 9, 1.0, 1000.0)
+    rve = make(k)
+    st, kap, info = B.etc_solve_direction(rve.h, 2, 1.0, 0.0, B.make_opts(rtol=1e-12, maxit=7))
+    assert st == B.ETC_ENOCONV and info.iters == 7
+    first, hist = rve.history()
+    assert first == 0 and len(hist) == 8 and hist[0] == 1.0
+    assert hist[-1] == pytest.approx(info.relres, rel=1e-14) and hist[-1] > 1e-12
+
+
+def test_linear_initial_guess_in_batches():
+    # the batch forms honour the initial guess: homogeneous media end with 0
+    # iterations, a random medium matches the one-solve value
+    media = [np.full((32, 32, 32), 2.5), M.random_spheres((32, 32, 32), (2, 5), 0.3, 21, 1.0, 30.0)[0]]
+    rves = [make(k) for k in media]
+    for queue in (False, True):
+        b = B.Batch(rves, rtol=1e-10, queue=queue, init=B.ETC_INIT_LINEAR)
+        assert b.queued() == (2 if queue else 0)
+        Ks, infos, _, st = b.run()
+        b.close()
+        assert st == B.ETC_OK
+        assert all(infos[d]["iters"] == 0 for d in range(3))
+        assert all(Ks[0][4 * d] == pytest.approx(2.5, rel=1e-12) for d in range(3))
+        for d in range(3):
+            kap, inf = rves[1].solve(d, rtol=1e-10, init=B.ETC_INIT_LINEAR)
+            assert abs(Ks[1][4 * d] - kap) <= 1e-9 * kap
+            assert abs(infos[3 + d]["iters"] - inf["iters"]) <= 1
+
+
 @pytest.mark.parametrize("direction", [0, 2])
 def test_linear_initial_guess_matches_oracle(direction):
     # x0 = p_in + (p_out - p_in)(k + 1/2)/n2 along the loading axis: the
