@@ -270,7 +270,7 @@ ACC_BAR = 1e-6        # kappa_eff error bar of the mixed path at rtol 1e-8
 ACC_REF_RTOL = 1e-11  # the converged reference: FP64 PCG to this rtol
 
 
-def accuracy(B, rves, K64, Km, Kf):
+def accuracy(B, rves, K64, Km, Kf, energies):
     """kappa_eff errors of the three paths against a converged FP64 solve.
 
     Outside every timed region.  The reference solves the same handles in FP64
@@ -280,7 +280,8 @@ def accuracy(B, rves, K64, Km, Kf):
     the 1e-6 bar is found by solving again.  Two pass flags: the bar itself,
     and the bar read as "no less accurate than FP64 at the same rtol" (FP64
     stopped at rtol 1e-8 is itself about 1e-6 away from convergence at this
-    contrast).
+    contrast).  The energy form of kappa_eff of the same rtol-1e-8 solves
+    (error quadratic in the solve error) is reported beside each path.
     """
     conv = []
     for rv in rves:
@@ -292,11 +293,15 @@ def accuracy(B, rves, K64, Km, Kf):
     def err(Ks):
         return max(abs(K[4 * d] - c[d]) / c[d] for K, c in zip(Ks, conv) for d in range(3))
 
+    def err_energy(Es):
+        return max(abs(E[d] - c[d]) / c[d] for E, c in zip(Es, conv) for d in range(3))
+
     e64 = err(K64)
     out = {"reference": f"FP64 PCG to rtol {ACC_REF_RTOL:g} on the same RVEs (6 diagonal entries)",
-           "bar": ACC_BAR, "fp64": {"err_at_rtol_1e-8": e64}}
-    for label, prec, K8 in (("mixed", B.ETC_PREC_MIXED, Km),
-                            ("mixed_f64", B.ETC_PREC_MIXED_F64, Kf)):
+           "bar": ACC_BAR, "fp64": {"err_at_rtol_1e-8": e64,
+                                    "energy_form_err_at_rtol_1e-8": err_energy(energies[0])}}
+    for label, prec, K8, E8 in (("mixed", B.ETC_PREC_MIXED, Km, energies[1]),
+                                ("mixed_f64", B.ETC_PREC_MIXED_F64, Kf, energies[2])):
         errs = {"1e-08": err(K8)}
         reach = 1e-8 if errs["1e-08"] <= ACC_BAR else None
         for rt in (1e-9, 1e-10):
@@ -312,6 +317,7 @@ def accuracy(B, rves, K64, Km, Kf):
             if errs[f"{rt:g}"] <= ACC_BAR:
                 reach = rt
         out[label] = {"err_by_rtol": errs, "loosest_rtol_meeting_bar": reach,
+                      "energy_form_err_at_rtol_1e-8": err_energy(E8),
                       "meets_bar_at_rtol_1e-8": errs["1e-08"] <= ACC_BAR,
                       "no_less_accurate_than_fp64_at_rtol_1e-8":
                           errs["1e-08"] <= max(ACC_BAR, e64)}
@@ -399,14 +405,18 @@ def run_ours(args, rank, world, local_rank):
     def sumr(v):
         return over_ranks(dist, dev, v, "sum")
 
+    energy = {}  # energy form of kappa_eff of the last step, per precision
+
     def step(precision):
-        Ks, iters = [], 0
+        Ks, iters, Es = [], 0, []
         for rv in rves:
             K, infos, st = rv.tensor(rtol=RTOL, precision=precision)
             if st != B.ETC_OK:
                 raise RuntimeError(f"solve status {st}")
             Ks.append(K)
+            Es.append([i["kappa_energy"] for i in infos])
             iters += sum(i["iters"] for i in infos)
+        energy[precision] = Es
         return Ks, iters
 
     def timed(precision, steps, warmup, clocks=False):
@@ -489,7 +499,9 @@ def run_ours(args, rank, world, local_rank):
         if rf["bound"] == "alu":
             rf["peak_probed"] = fp64_probed
             rf["frac_probed"] = rf["achieved"] / fp64_probed
-    acc = None if args.no_accuracy else accuracy(B, rves, K64, Km, Kf)
+    acc = None if args.no_accuracy else accuracy(
+        B, rves, K64, Km, Kf,
+        [energy[p] for p in (B.ETC_PREC_FP64, B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64)])
 
     # ---- end to end through the C ABI from pinned host memory
     pinned = [torch.from_numpy(k).pin_memory() for k in kap_host]

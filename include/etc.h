@@ -120,6 +120,12 @@ typedef struct {
   double column[3];    /* K[:, dir] in physical axes x, y, z (see etc_effective_tensor) */
   double t_setup_ms;   /* faces, LP, pivot tables */
   double t_solve_ms;   /* PCG loop and post-processing */
+  double kappa_energy; /* effective conductivity from the energy of the solution,
+                          L h E / (n0 n1 (p_in - p_out)^2) with E = p.Ap - 2 b.p +
+                          sum B_in p_in^2 + sum B_out p_out^2 summed as its positive
+                          face terms; equal to kappa_eff at the exact solution, with
+                          an error quadratic in the solve error; -1 unless the true
+                          residual is computed (opts->true_residual) */
 } etc_info;
 
 /* Fill *opts with the defaults listed in etc_opts. */

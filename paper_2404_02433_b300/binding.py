@@ -41,14 +41,14 @@ class EtcInfo(ctypes.Structure):
     _fields_ = [("iters", c_int), ("status", c_int), ("relres", c_double),
                 ("true_relres", c_double), ("kref", c_double * 5), ("cond_bound", c_double),
                 ("kappa_in", c_double), ("column", c_double * 3), ("t_setup_ms", c_double),
-                ("t_solve_ms", c_double)]
+                ("t_solve_ms", c_double), ("kappa_energy", c_double)]
 
     def as_dict(self):
         return {"iters": self.iters, "status": self.status, "relres": self.relres,
                 "true_relres": self.true_relres, "kref": list(self.kref),
                 "cond_bound": self.cond_bound, "kappa_in": self.kappa_in,
                 "column": list(self.column), "t_setup_ms": self.t_setup_ms,
-                "t_solve_ms": self.t_solve_ms}
+                "t_solve_ms": self.t_solve_ms, "kappa_energy": self.kappa_energy}
 
 
 class EtcError(RuntimeError):

@@ -807,6 +807,8 @@ void fill_results(const etc_rve* h, int dir, const Rhs& rhs, int true_residual,
     std::memcpy(info->kref, st.kref, sizeof(info->kref));
     info->cond_bound = cond_bound_of(st.ext, st.kref);
     info->kappa_in = flux ? L2 * hh[2] * st.res[4] / ((double)g.plane * dp) : 0.0;
+    info->kappa_energy =
+        (flux && true_residual) ? L2 * hh[2] * st.res[6] / ((double)g.plane * dp * dp) : -1.0;
     for (int l = 0; l < 3; ++l) info->column[f[l]] = flux ? h->L[dir] * vbar[l] / dp : 0.0;
     info->t_setup_ms = ms_setup;
     info->t_solve_ms = ms_solve;

@@ -1098,16 +1098,19 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
                                 const double* __restrict__ src, double* partials, PcgState* st) {
   __shared__ double sh[32];
   __shared__ int flag;
-  double acc = 0.0;
+  double acc = 0.0, en = 0.0;
   for (long long c = gidx(); c < g.n; c += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(c % g.n0);
     const long long rem = c / g.n0;
     const int j = (int)(rem % g.n1), k = (int)(rem / g.n1);
     const long long s = c - (long long)k * g.plane;
+    const double xc = x[c];
+    const double ein = k == 0 ? xc - (pin_f ? pin_f[s] : pin) : 0.0;
+    const double eout = k == g.n2 - 1 ? xc - (pout_f ? pout_f[s] : pout) : 0.0;
     double b = src ? src[c] : 0.0;
     if (k == 0) b += Bin[s] * (pin_f ? pin_f[s] : pin);
     if (k == g.n2 - 1) b += Bout[s] * (pout_f ? pout_f[s] : pout);
-    double ax = D[c] * x[c];
+    double ax = D[c] * xc;
     if (i > 0) ax -= T0[c] * x[c - 1];
     if (i < g.n0 - 1) ax -= T0[c + 1] * x[c + 1];
     if (j > 0) ax -= T1[c] * x[c - g.n0];
@@ -1116,13 +1119,24 @@ __global__ void k_true_residual(Geometry g, const double* __restrict__ x,
     if (k < g.n2 - 1) ax -= T2[c + g.plane] * x[c + g.plane];
     const double d = b - ax;
     acc = fma(d, d, acc);
+    // the energy x.Ax - 2 b.x + sum B p^2 as its sum of positive face terms:
+    // every internal face once (the minus face of each cell) and the
+    // Dirichlet faces, T (x_c - x_nb)^2 and B (x - p)^2
+    if (i > 0) { const double t = xc - x[c - 1]; en = fma(T0[c] * t, t, en); }
+    if (j > 0) { const double t = xc - x[c - g.n0]; en = fma(T1[c] * t, t, en); }
+    if (k > 0) { const double t = xc - x[c - g.plane]; en = fma(T2[c] * t, t, en); }
+    if (k == 0) en = fma(Bin[s] * ein, ein, en);
+    if (k == g.n2 - 1) en = fma(Bout[s] * eout, eout, en);
   }
-  const double bs = block_sum(acc, sh);
-  double v[1] = {bs};
-  if (publish_values(partials, 1, v, 1, &st->cnt[kCntAux], &flag)) {
-    const double tot = sum_partials(partials, (int)nblocks(), 1, sh);
+  double v[2];
+  v[0] = block_sum(acc, sh);
+  v[1] = block_sum(en, sh);
+  if (publish_values(partials, 2, v, 2, &st->cnt[kCntAux], &flag)) {
+    const double tot = sum_partials(partials, (int)nblocks(), 2, sh);
+    const double etot = sum_partials(partials + 1, (int)nblocks(), 2, sh);
     if (threadIdx.x == 0) {
       st->res[5] = tot;
+      st->res[6] = etot;
       st->cnt[kCntAux] = 0;
     }
   }

@@ -210,6 +210,33 @@ def test_config_32_spheres_direction_x():
     assert relmax(p, ref.p) < 1e-8
 
 
+@pytest.mark.parametrize("precision", [B.ETC_PREC_FP64, B.ETC_PREC_MIXED, B.ETC_PREC_MIXED_F64])
+def test_energy_form_of_kappa_eff(precision):
+    # the energy identity (outflow = inflow = energy value at the exact
+    # solution): at convergence it equals the oracle's outflow value; its
+    # error is quadratic in the solve error, so early iterates are far closer
+    # to the converged value than the outflow value; the energy is minimal at
+    # the solution, so it never falls below the converged value
+    k, _ = M.random_spheres((40, 36, 48), (3, 6), 0.3, 5, 1.0, 1000.0)
+    ref = O.solve_direction(k, k, k, 2, rtol=1e-12)
+    rve = make(k)
+    kc, ic = rve.solve(2, rtol=1e-12)
+    assert abs(kc - ref.kappa_eff) <= 1e-10 * ref.kappa_eff
+    assert abs(ic["kappa_energy"] - ref.kappa_eff) <= 1e-10 * ref.kappa_eff
+    rtol = 1e-6 if precision == B.ETC_PREC_FP64 else 1e-5
+    kr, ir = rve.solve(2, rtol=rtol, precision=precision)
+    err_out = abs(kr - kc) / kc
+    err_en = abs(ir["kappa_energy"] - kc) / kc
+    assert err_out > 1e-9
+    # quadratic in the error: at least 20 times closer (measured 84 times for
+    # the mixed forms at rtol 1e-5, more for FP64)
+    assert err_en <= max(1e-10, 0.05 * err_out), (err_out, err_en)
+    # E(x) - E(x*) = ||x - x*||_A^2 >= 0 (against the converged energy value)
+    assert ir["kappa_energy"] >= ic["kappa_energy"] * (1.0 - 1e-13)
+    _, i0 = rve.solve(2, rtol=1e-8, precision=precision, true_residual=0)
+    assert i0["kappa_energy"] == -1.0
+
+
 def test_residual_history_of_a_capped_solve():
     # ETC_ENOCONV after maxit iterations: the history holds iterations 0..maxit,
     # its last value is the reported relres
