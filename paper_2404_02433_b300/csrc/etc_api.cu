@@ -260,6 +260,43 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
   t->cosq = d + ntw + 2 * npost;
   t->tw4 = fast ? d + off4 : nullptr;
   *mem = d;
+  if (sizeof(R) == 8 && s.fft && fx_len(n)) {
+    // the same constants in 62-bit fixed point (fixed_point.cuh): C = c 2^62
+    // rounded, |C| <= 2^62 - 1, as (C >> 31, C mod 2^31)
+    const int P = fast_threads_per_line(n), Q = m / P;
+    std::vector<int> fx(4 * (size_t)(m + 4 * (m + 1)));
+    auto put = [&](size_t slot, long double c) {
+      long long C = llroundl(c * 4611686018427387904.0L);
+      const long long lim = 4611686018427387903LL;
+      C = C > lim ? lim : (C < -lim ? -lim : C);
+      fx[2 * slot] = (int)(C >> 31);
+      fx[2 * slot + 1] = (int)(C & 0x7fffffffLL);
+    };
+    for (int tau = 0; tau < P; ++tau)
+      for (int k1 = 0; k1 < Q; ++k1) {
+        const long double a = -2.0L * pi * (long double)((tau * k1) % m) / m;
+        put(2 * (size_t)(tau * Q + k1), cosl(a));
+        put(2 * (size_t)(tau * Q + k1) + 1, sinl(a));
+      }
+    const size_t post = 2 * (size_t)m, pre = 2 * (size_t)(m + 2 * (m + 1));
+    for (int k = 0; k <= m; ++k) {
+      const long double th = pi * k / (2.0L * n);
+      put(post + 4 * k + 0, cosl(th) / 2);
+      put(post + 4 * k + 1, sinl(th) / 2);
+      put(post + 4 * k + 2, cosl(5 * th) / 2);
+      put(post + 4 * k + 3, sinl(5 * th) / 2);
+      put(pre + 4 * k + 0, cosl(th));
+      put(pre + 4 * k + 1, sinl(th));
+      put(pre + 4 * k + 2, cosl(4 * th));
+      put(pre + 4 * k + 3, sinl(4 * th));
+    }
+    int4* dq = nullptr;
+    e = dalloc(h, &dq, fx.size() / 4);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(dq, fx.data(), fx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    t->fxq = dq;
+  }
   return cudaSuccess;
 }
 
@@ -484,6 +521,30 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
     });
     best.y = -1;
   }
+  if constexpr (sizeof(R) == 8) {
+    // tiles -3 and -4 (axis 0) and -3 (axis 1): the block-floating-point
+    // kernels of the FP64 path, where the line length allows them
+    if (fx_x_ok(g, p0, h->r, h->z64, h->z64, h->z64)) {
+      for (int T = -3; T >= -4; --T) {
+        const double tx = time_launch(h->stream, e0, e1, [&] {
+          return launch_fwd_x<R, double>(g, p0, h->st, nullptr, nullptr, nullptr, nullptr,
+                                         h->r, t, h->partials, 0, 0.0, 2, h->stream, T);
+        });
+        if (tx < bx) { bx = tx; best.fx = T; }
+        const double ti = time_launch(h->stream, e0, e1, [&] {
+          return launch_inv_x<R, double>(g, p0, h->st, t, h->z64, nullptr, 1.0, 0, 2,
+                                         h->stream, T);
+        });
+        if (ti < bi) { bi = ti; best.ix = T; }
+      }
+    }
+    if (g.n1 > 1 && fx_y_ok(g, p1)) {
+      const double ty = time_launch(h->stream, e0, e1, [&] {
+        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -3);
+      });
+      if (ty < by) { by = ty; best.y = -3; }
+    }
+  }
   for (int L = 1; L <= 64; L *= 2) {
     if (L > nrows || smem_x_bytes(g.n0, L, eb) > smem_limit()) break;
     const double tx = time_launch(h->stream, e0, e1, [&] {
@@ -528,15 +589,20 @@ etc_status forced_tiles(etc_rve* h, const Geometry& g, int prec, const char* spe
   auto pow2 = [](int x, int hi) { return x >= 1 && x <= hi && (x & (x - 1)) == 0; };
   const long long nrows = (long long)g.n1 * g.n2;
   bool ok = true;
+  const bool fx_x = prec == ETC_PREC_FP64 &&
+                    fx_x_ok(g, P0.p64, h->r, h->z64, h->z64, h->z64);
+  const bool fx_y = prec == ETC_PREC_FP64 && fx_y_ok(g, P1.p64);
   for (int a = 0; a < 2; ++a) {
     const int L = v[a];
     if (L == -1 || L == -2) ok = ok && fx_fast;
+    else if (L == -3 || L == -4) ok = ok && fx_x;
     else ok = ok && pow2(L, 64) && L <= nrows && smem_x_bytes(g.n0, L, eb) <= smem_limit() &&
               (a == 0 || smem_x_bytes(g.n0, L, eb) + (size_t)L * g.n0 * sizeof(double) <=
                              smem_limit());
   }
   if (g.n1 > 1) {
     if (v[2] == -1) ok = ok && y_fast;
+    else if (v[2] == -3) ok = ok && fx_y;
     else ok = ok && pow2(v[2], 32) && v[2] <= g.n0 && smem_y_bytes(g.n1, v[2], eb) <= smem_limit();
   }
   if (!ok) return fail(h, ETC_EINVAL, "ETC_FORCE_TILES: tile not available for this shape");
@@ -1055,7 +1121,7 @@ etc_status queue_pass(etc_rve* h, const Geometry& g, int prec, BatchQueue* q,
   // the class's tables (equal for all members) and axis-0 block size
   const PlanStore& P0 = h->plans[g.n0];
   const PlanStore& P1 = h->plans[g.n1];
-  const int nt = h->tiles[0] == -2 ? 128 : 256;
+  const int nt = (h->tiles[0] == -2 || h->tiles[0] == -4) ? 128 : 256;
   for (int par = 0; par < 2; ++par) {
     QueueLaunch ql = {q, bs, 6 * par, nm, s};
     if (prec == ETC_PREC_FP64) {

@@ -24,6 +24,9 @@ struct DctTables {
   const R* cosq;   // 4n: cos(pi q / (2n))
   const R* tw4 = nullptr;  // P x Q complex exp(-2 pi i tau k1 / m), [tau][k1], for the
                            // register-resident transforms (n = 32..512); NULL: not built
+  const int4* fxq = nullptr;  // the same constants in 62-bit fixed point for the
+                              // block-floating-point transforms (fixed_point.cuh);
+                              // FP64 tables of n = 32..512, powers of two
 };
 
 struct DctShape {

@@ -1,0 +1,70 @@
+// Dispatch of the block-floating-point transforms of the FP64 path
+// (fixed_kernels.cuh) by line length; the per-length launchers are
+// instantiated in fixed_sizes_*.cu.
+#include "fixed_kernels.cuh"
+
+namespace etc {
+
+bool fx_len(int n) { return fx_len_c(n); }
+
+ETC_FX_SIZES(ETC_FX_EXTERN)
+
+namespace {
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+bool fx_x_ok(const Geometry& g, const DctPlan<double>& p, const void* a, const void* b,
+             const void* c, const void* d) {
+  return p.t.fxq != nullptr && fx_len(g.n0) && p.s.n == g.n0 && aligned16(a) && aligned16(b) &&
+         aligned16(c) && aligned16(d);
+}
+bool fx_y_ok(const Geometry& g, const DctPlan<double>& p) {
+  return p.t.fxq != nullptr && fx_len(g.n1) && p.s.n == g.n1;
+}
+
+cudaError_t launch_fx_fwd_x(const Geometry& g, const DctPlan<double>& p, PcgState* st, double* x,
+                            const double* w, const double* q, double* r, const double* rin,
+                            double* t, double* partials, int par, double rtol2, int mode,
+                            cudaStream_t s, int nt) {
+#define FWD(N) \
+  case N: return fx_fwd_x_n<N>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s, nt);
+  switch (g.n0) {
+    FWD(32) FWD(64) FWD(128) FWD(256) FWD(512)
+    default: return cudaErrorInvalidValue;
+  }
+#undef FWD
+}
+
+cudaError_t launch_fx_inv_x(const Geometry& g, const DctPlan<double>& p, PcgState* st,
+                            const double* t, double* z, const double* kd, double kz_host,
+                            int check, int mode, cudaStream_t s, int nt) {
+#define INV(N) \
+  case N: return fx_inv_x_n<N>(g, p.t, st, t, z, kd, kz_host, check, mode, s, nt);
+  switch (g.n0) {
+    INV(32) INV(64) INV(128) INV(256) INV(512)
+    default: return cudaErrorInvalidValue;
+  }
+#undef INV
+}
+
+cudaError_t launch_fx_y(const Geometry& g, const DctPlan<double>& p, const PcgState* st,
+                        double* t, int inverse, int check, cudaStream_t s) {
+#define YN(N) \
+  case N: return fx_y_n<N>(g, p.t, st, t, inverse, check, s);
+  switch (g.n1) {
+    YN(32) YN(64) YN(128) YN(256) YN(512)
+    default: return cudaErrorInvalidValue;
+  }
+#undef YN
+}
+
+cudaError_t set_fx_attrs() {
+  cudaError_t e = cudaSuccess;
+#define AT(N) \
+  if (e == cudaSuccess) e = fx_attrs_n<N>();
+  ETC_FX_SIZES(AT)
+#undef AT
+  return e;
+}
+
+}  // namespace etc

@@ -1,0 +1,589 @@
+// Register-resident cosine transforms of the FP64 path in block floating point
+// (fixed_point.cuh): the same four-step layout and data movement as the
+// floating-point kernels of fast_kernels.cuh (Eq. (forward DCT) and Eq.
+// (backward DCT) through the half-length complex FFT, Sec. 3.2), for the
+// power-of-two lengths n = 32 .. 512, on FP64 vectors.  Each line (a row of
+// axis 0, a column of axis 1) is converted to 64-bit integers with its own
+// exponent after its largest exponent is known (a shuffle over the line's P
+// threads on axis 0, a shared-memory maximum over its P warps on axis 1),
+// transformed with integer arithmetic, and converted back to binary64.
+#pragma once
+
+#include "fast_kernels.cuh"
+#include "fixed_point.cuh"
+
+namespace etc {
+
+constexpr bool fx_len_c(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+
+// First four-step stage of thread tau: DFT of length Q, then the twiddle
+// exp(SIGN 2 pi i tau k1 / M) (forward sign stored).
+template <int N, int SIGN>
+__device__ __forceinline__ void fx_four_step_a(fxp::cx* v, const int4* __restrict__ tw4,
+                                               int tau) {
+  using F = Fast<N>;
+  fxp::Fb<F::Q, SIGN>::run(v);
+  const int4* tw = tw4 + tau * F::Q;
+#pragma unroll
+  for (int k1 = 1; k1 < F::Q; ++k1) {
+    const fxp::Kc2 w = fxp::ld_k2(tw + k1);
+    v[k1] = SIGN < 0 ? fxp::crot(v[k1], w.a, w.b) : fxp::crotc(v[k1], w.a, w.b);
+  }
+}
+
+// Largest exponent field over the P consecutive lanes of a line.
+template <int P>
+__device__ __forceinline__ int fx_lane_max(int e) {
+#pragma unroll
+  for (int o = 1; o < P; o *= 2) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  return e;
+}
+
+__device__ __forceinline__ fxp::cx ld_cx(const fxp::cx* p) {
+  const longlong2 v = *reinterpret_cast<const longlong2*>(p);
+  return fxp::mk(v.x, v.y);
+}
+__device__ __forceinline__ void st_cx(fxp::cx* p, fxp::cx v) {
+  *reinterpret_cast<longlong2*>(p) = make_longlong2(v.x, v.y);
+}
+
+// ---------------------------------------------------------------- axis 1
+// In place on t: every block owns C = 16 adjacent columns of one plane.
+template <int N>
+constexpr size_t fx_y_smem() {
+  return (size_t)16 * (N / 2 + 1) * sizeof(fxp::cx) + 16 * sizeof(int);
+}
+template <int N, int INV>
+__device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<double> tb,
+                                          const PcgState* st, double* __restrict__ t,
+                                          int check) {
+  using F = Fast<N>;
+  using fxp::cx;
+  using fxp::i64;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = 16;
+  constexpr int SIGN = INV ? 1 : -1;
+  constexpr int B = INV ? fxp::FxBits<M>::I : fxp::FxBits<M>::F;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx* sm = reinterpret_cast<cx*>(smraw);                 // C (M + 1) complex
+  int* emx = reinterpret_cast<int*>(smraw + (size_t)C * (M + 1) * sizeof(cx));
+  if (check && st->done) return;
+  const int4* tw4 = tb.fxq;
+  const int4* post = tb.fxq + fxp::fx_off_post(M);
+  const int4* pre = tb.fxq + fxp::fx_off_pre(M);
+  const int c = threadIdx.x % C, tau = threadIdx.x / C;
+  const int i = b.x * C + c;
+  const bool ok = i < g.n0;
+  const long long n0 = g.n0;
+  double* col = t + (long long)b.y * g.plane + (ok ? i : 0);
+  if (tau == 0) emx[c] = 1;
+  __syncthreads();
+  cx v[Q];
+  int emax;
+  if (!INV) {
+    double d0[Q], d1[Q];
+    int em = 1;
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int q = tau + P * s;  // z_q = (v_{2q}, v_{2q+1})
+      d0[s] = ok ? col[vrow<N>(2 * q) * n0] : 0.0;
+      d1[s] = ok ? col[vrow<N>(2 * q + 1) * n0] : 0.0;
+      em = max(em, max(fxp::bexp(d0[s]), fxp::bexp(d1[s])));
+    }
+    atomicMax(&emx[c], em);
+    __syncthreads();
+    emax = emx[c];
+#pragma unroll
+    for (int s = 0; s < Q; ++s)
+      v[s] = fxp::mk(fxp::to_fx<B>(d0[s], emax), fxp::to_fx<B>(d1[s], emax));
+  } else {
+    // the pre-twiddle of input j needs X_j, X_{n-j}, X_{m-j} and X_{m+j}:
+    // stage the tile's columns as integers, form every V_k once, then a_j
+    i64* sr = reinterpret_cast<i64*>(smraw);  // real rows of C integers
+    double xs[2 * Q];
+    int em = 1;
+#pragma unroll
+    for (int s = 0; s < 2 * Q; ++s) {
+      xs[s] = ok ? col[(tau + P * s) * n0] : 0.0;
+      em = max(em, fxp::bexp(xs[s]));
+    }
+    atomicMax(&emx[c], em);
+    __syncthreads();
+    emax = emx[c];
+#pragma unroll
+    for (int s = 0; s < 2 * Q; ++s) sr[(tau + P * s) * C + c] = fxp::to_fx<B>(xs[s], emax);
+    __syncthreads();
+    cx vv[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      vv[s] = fxp::inv_v(pre, j, sr[j * C + c], j ? sr[(N - j) * C + c] : 0);
+    }
+    cx vm = fxp::mk(0, 0);
+    if (tau == 0) vm = fxp::inv_v(pre, M, sr[M * C + c], sr[M * C + c]);
+    __syncthreads();  // the staged columns are read before V overwrites them
+#pragma unroll
+    for (int s = 0; s < Q; ++s) st_cx(sm + (tau + P * s) * C + c, vv[s]);
+    if (tau == 0) st_cx(sm + M * C + c, vm);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      v[s] = fxp::inv_a(pre, j, vv[s], ld_cx(sm + (M - j) * C + c));
+    }
+    __syncthreads();  // V is read before the transpose reuses the buffer
+  }
+  fx_four_step_a<N, SIGN>(v, tw4, tau);
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) st_cx(sm + (k1 * P + tau) * C + c, v[k1]);
+  __syncthreads();
+  cx u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(sm + ((tau + P * e) * P + tt) * C + c);
+    fxp::Fb<P, SIGN>::run(u + e * P);
+  }
+  const bool bad = emax == 2047;  // an infinity or NaN in the line
+  if (!INV) {
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) st_cx(sm + (tau + P * e + Q * k2) * C + c, u[e * P + k2]);
+    __syncthreads();
+    const int e2 = emax - 1022 - B;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        const int k = tau + P * e + Q * k2;
+        i64 xa, xb;
+        fxp::untangle(u[e * P + k2], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
+        if (ok) {
+          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx(xa, e2);
+          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(xb, e2);
+        }
+      }
+  } else {
+    // the pre-twiddle omitted 1 / (2m): a power of two in the exponent
+    const int e2 = emax - 1022 - B - fxp::ilog2c(2 * M);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) {
+        const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
+        if (ok) {
+          col[vrow<N>(2 * j) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(u[e * P + k2].x, e2);
+          col[vrow<N>(2 * j + 1) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(u[e * P + k2].y, e2);
+        }
+      }
+  }
+}
+template <int N, int INV>
+__global__ void __launch_bounds__(16 * Fast<N>::P, FastCols<double, N>::MinBlocks())
+    k_fx_y(Geometry g, DctTables<double> tb, const PcgState* st, double* __restrict__ t,
+           int check) {
+  fx_y_body<N, INV>(hw_blk(), g, tb, st, t, check);
+}
+
+// ---------------------------------------------------------------- axis 0, forward
+// Same contract as k_fast_fwd_x on FP64 vectors (MODE 0 initial residual, 1 PCG
+// update with x moved here, 2 transform only).
+template <int N, int MODE, int NT>
+__device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTables<double> tb,
+                                              PcgState* st, double* __restrict__ x,
+                                              const double* __restrict__ w,
+                                              const double* __restrict__ q,
+                                              double* __restrict__ r,
+                                              const double* __restrict__ rin,
+                                              double* __restrict__ t, double* partials, int par,
+                                              double rtol2) {
+  using F = Fast<N>;
+  using fxp::cx;
+  using fxp::i64;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
+  constexpr int L = FastX<N, NT>::L;
+  constexpr int B = fxp::FxBits<M>::F;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sh[32];
+  __shared__ int flag;
+  if (MODE != 2 && st->done) return;
+  cx* A = reinterpret_cast<cx*>(smraw);  // rows of RS complex: staging, transpose, Z
+  double* Ar = reinterpret_cast<double*>(smraw);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)b.x * L;
+  const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  double acc = 0.0;
+  constexpr int NP = L * M;  // element pairs of the block
+  constexpr int U = 2;       // pairs per thread whose loads are in flight together
+  static_assert(NP % (NT * U) == 0, "pair rounds");
+  for (int p0 = threadIdx.x; p0 < NP; p0 += NT * U) {
+    VPair<double> rv[U], qv[U], xv[U], wv[U];
+    double2 dv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + NT * u;
+      const int l = p / M, i2 = p % M;
+      const long long row = row0 + l;
+      rv[u].a = rv[u].b = 0.0;
+      qv[u] = rv[u]; xv[u] = rv[u]; wv[u] = rv[u];
+      dv[u] = make_double2(0.0, 0.0);
+      if (row < nrows) {
+        const long long c = row * N + 2 * i2;
+        if (MODE == 2) dv[u] = *reinterpret_cast<const double2*>(rin + c);
+        else rv[u] = ld_pair(r + c);
+        if (MODE == 1) {
+          qv[u] = ld_pair(q + c);
+          xv[u] = ld_pair(x + c);
+          wv[u] = ld_pair(w + c);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + NT * u;
+      const int l = p / M, i2 = p % M;
+      const long long row = row0 + l;
+      double in0, in1;
+      if (MODE == 2) {
+        in0 = dv[u].x;
+        in1 = dv[u].y;
+      } else {
+        double v0 = rv[u].a, v1 = rv[u].b;
+        if (row < nrows) {
+          const long long c = row * N + 2 * i2;
+          if (MODE == 1) {
+            st_pair(x + c, fma(alpha, wv[u].a, xv[u].a), fma(alpha, wv[u].b, xv[u].b));
+            v0 = fma(-alpha, qv[u].a, v0);
+            v1 = fma(-alpha, qv[u].b, v1);
+            st_pair(r + c, v0, v1);
+          }
+          acc = fma(v0, v0, acc);
+          acc = fma(v1, v1, acc);
+        }
+        in0 = v0;
+        in1 = v1;
+      }
+      // element 2 i2 -> v_{i2}; element 2 i2 + 1 -> v_{n-1-i2}
+      Ar[l * 2 * RS + i2] = in0;
+      Ar[l * 2 * RS + N - 1 - i2] = in1;
+    }
+  }
+  __syncthreads();
+  const int l = threadIdx.x / P, tau = threadIdx.x % P;
+  cx v[Q];
+  int emax;
+  {
+    double2 dv[Q];
+    int em = 1;
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      dv[s] = *reinterpret_cast<const double2*>(A + l * RS + tau + P * s);
+      em = max(em, max(fxp::bexp(dv[s].x), fxp::bexp(dv[s].y)));
+    }
+    emax = fx_lane_max<P>(em);
+#pragma unroll
+    for (int s = 0; s < Q; ++s)
+      v[s] = fxp::mk(fxp::to_fx<B>(dv[s].x, emax), fxp::to_fx<B>(dv[s].y, emax));
+  }
+  fx_four_step_a<N, -1>(v, tb.fxq, tau);
+  __syncthreads();  // the row is read before the transpose overwrites it
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) st_cx(A + l * RS + k1 * (P + 1) + tau, v[k1]);
+  __syncthreads();
+  cx u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(A + l * RS + (tau + P * e) * (P + 1) + tt);
+    fxp::Fb<P, -1>::run(u + e * P);
+  }
+  __syncthreads();  // the transpose is read before Z overwrites it
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
+  __syncthreads();
+  const long long row = row0 + l;
+  const int4* post = tb.fxq + fxp::fx_off_post(M);
+  const bool bad = emax == 2047;  // an infinity or NaN in the row
+  const int e2 = emax - 1022 - B;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) {
+      const int k = tau + P * e + Q * k2;
+      i64 xa, xb;
+      fxp::untangle(u[e * P + k2], ld_cx(A + l * RS + (k ? M - k : 0)), post, k, M, xa, xb);
+      if (row < nrows) {
+        t[row * N + k] = bad ? fxp::nan_f64() : fxp::from_fx(xa, e2);
+        t[row * N + (k ? N - k : M)] = bad ? fxp::nan_f64() : fxp::from_fx(xb, e2);
+      }
+    }
+  if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag, par, false, b);
+}
+template <int N, int MODE, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fx_fwd_x(Geometry g, DctTables<double> tb, PcgState* st, double* __restrict__ x,
+               const double* __restrict__ w, const double* __restrict__ q,
+               double* __restrict__ r, const double* __restrict__ rin, double* __restrict__ t,
+               double* partials, int par, double rtol2) {
+  fx_fwd_x_body<N, MODE, NT>(hw_blk(), g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+}
+
+// ---------------------------------------------------------------- axis 0, backward
+// Same contract as k_fast_inv_x on FP64 vectors: u = scale * (backward DCT of
+// t along axis 0), then MODE 0: z = u; MODE 2: w = u + beta w in place (z
+// points at w).  scale = 1 / kappa_ref^z = f 2^Es with f in [1/2, 1) is applied
+// as one more product by the constant f and the exponent Es.
+template <int N, int MODE, int NT>
+__device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTables<double> tb,
+                                              PcgState* st, const double* __restrict__ t,
+                                              double* __restrict__ z, const double* kd,
+                                              double kz_host, int check) {
+  using F = Fast<N>;
+  using fxp::cx;
+  using fxp::i64;
+  constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
+  constexpr int L = FastX<N, NT>::L;
+  constexpr int SR = N + P;  // real stride of the staged input rows
+  constexpr int B = fxp::FxBits<M>::I;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (check && st->done) return;
+  cx* A = reinterpret_cast<cx*>(smraw);  // rows of RS complex: V, transpose, z
+  double* Ar = reinterpret_cast<double*>(smraw);
+  i64* Ai = reinterpret_cast<i64*>(smraw);
+  const long long nrows = (long long)g.n1 * g.n2;
+  const long long row0 = (long long)b.x * L;
+  // stage the block's rows in natural order, 16 bytes per access, all of a
+  // thread's loads issued before the first shared-memory store
+  constexpr int NR = L * N / 2 / NT;
+  static_assert(NR * NT * 2 == L * N, "staging rounds");
+  {
+    double2 val[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int e = threadIdx.x + NT * r;
+      const int l = (e * 2) / N, i = (e * 2) % N;
+      const long long row = row0 + l;
+      val[r] = row < nrows ? *reinterpret_cast<const double2*>(t + row * N + i)
+                           : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int e = threadIdx.x + NT * r;
+      const int l = (e * 2) / N, i = (e * 2) % N;
+      *reinterpret_cast<double2*>(Ar + l * SR + i) = val[r];
+    }
+  }
+  __syncthreads();
+  const int l = threadIdx.x / P, tau = threadIdx.x % P;
+  const double* X = Ar + l * SR;
+  int em = 1;
+#pragma unroll
+  for (int r = 0; r < 2 * Q; ++r) em = max(em, fxp::bexp(X[tau + P * r]));
+  const int emax = fx_lane_max<P>(em);
+  const int4* pre = tb.fxq + fxp::fx_off_pre(M);
+  // V_k = e^{i t_k} (X_k - i X_{n-k}) for the thread's own k = tau + P s, and V_m
+  cx vv[Q];
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    const int j = tau + P * s;
+    vv[s] = fxp::inv_v(pre, j, fxp::to_fx<B>(X[j], emax),
+                       j ? fxp::to_fx<B>(X[N - j], emax) : 0);
+  }
+  cx vm = fxp::mk(0, 0);
+  if (tau == 0) {
+    const i64 xm = fxp::to_fx<B>(X[M], emax);
+    vm = fxp::inv_v(pre, M, xm, xm);
+  }
+  __syncthreads();  // the staged rows are read before V overwrites them
+#pragma unroll
+  for (int s = 0; s < Q; ++s) st_cx(A + l * RS + tau + P * s, vv[s]);
+  if (tau == 0) st_cx(A + l * RS + M, vm);
+  __syncthreads();
+  cx v[Q];
+#pragma unroll
+  for (int s = 0; s < Q; ++s) {
+    const int j = tau + P * s;
+    v[s] = fxp::inv_a(pre, j, vv[s], ld_cx(A + l * RS + M - j));
+  }
+  fx_four_step_a<N, 1>(v, tb.fxq, tau);
+  __syncthreads();  // V is read before the transpose overwrites it
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) st_cx(A + l * RS + k1 * (P + 1) + tau, v[k1]);
+  __syncthreads();
+  cx u[Q];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+#pragma unroll
+    for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(A + l * RS + (tau + P * e) * (P + 1) + tt);
+    fxp::Fb<P, 1>::run(u + e * P);
+  }
+  __syncthreads();  // the transpose is read before z overwrites it
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
+  // the row's exponent for the output pass, which walks other rows
+  __shared__ int erow[NT / P];
+  if (tau == 0) erow[l] = emax;
+  __syncthreads();
+  // scale = f 2^Es from its binary64 fields (a positive normal number)
+  const double scale = 1.0 / (kd ? kd[2] : kz_host);
+  const unsigned long long sb = (unsigned long long)__double_as_longlong(scale);
+  const fxp::Kc kf = fxp::kc_split((i64)(((sb & 0xfffffffffffffull) | (1ull << 52)) << 9));
+  const int es = (int)((sb >> 52) & 0x7ff) - 1022;
+  // the pre-twiddle omitted 1 / (2m)
+  constexpr int EOFF = -1022 - B - fxp::ilog2c(2 * M);
+  const double beta = (MODE == 2) ? st->beta : 0.0;
+  constexpr int NQ = L * M / NT;      // element pairs per thread
+  constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
+  static_assert(NQ % G == 0, "pair groups");
+#pragma unroll 1
+  for (int r0 = 0; r0 < NQ; r0 += G) {
+    VPair<double> wo[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int p = threadIdx.x + NT * (r0 + u);
+      const long long row = row0 + p / M;
+      wo[u].a = wo[u].b = 0.0;
+      if (MODE == 2 && row < nrows) wo[u] = ld_pair(z + row * N + 2 * (p % M));
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int p = threadIdx.x + NT * (r0 + u);
+      const int lr = p / M, i2 = p % M;
+      const long long row = row0 + lr;
+      if (row >= nrows) continue;
+      const long long c = row * N + 2 * i2;
+      const int er = erow[lr];
+      const int e2 = er + EOFF + es;
+      // element 2 i2 <- v_{i2}; element 2 i2 + 1 <- v_{n-1-i2}
+      // halved first: the FFT output may reach 2^62, a product's operand may not
+      double u0 = fxp::from_fx(fxp::mulk(Ai[lr * 2 * RS + i2] >> 1, kf), e2 + 1);
+      double u1 = fxp::from_fx(fxp::mulk(Ai[lr * 2 * RS + N - 1 - i2] >> 1, kf), e2 + 1);
+      if (er == 2047) u0 = u1 = fxp::nan_f64();
+      if (MODE == 2) st_pair(z + c, fma(beta, wo[u].a, u0), fma(beta, wo[u].b, u1));
+      else st_pair(z + c, u0, u1);
+    }
+  }
+}
+template <int N, int MODE, int NT>
+__global__ void __launch_bounds__(NT)
+    k_fx_inv_x(Geometry g, DctTables<double> tb, PcgState* st, const double* __restrict__ t,
+               double* __restrict__ z, const double* kd, double kz_host, int check) {
+  fx_inv_x_body<N, MODE, NT>(hw_blk(), g, tb, st, t, z, kd, kz_host, check);
+}
+
+// ---------------------------------------------------------------- per-size launchers
+// Defined here, instantiated per length in fixed_sizes_*.cu, called by
+// fixed_dispatch.cu.  The shared-memory layouts of the axis-0 kernels are
+// those of the floating-point kernels (16-byte complex values).
+template <int N, int NT>
+cudaError_t fx_fwd_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState* st, double* x,
+                        const double* w, const double* q, double* r, const double* rin,
+                        double* t, double* partials, int par, double rtol2, int mode,
+                        cudaStream_t s) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<double, N, NT>();
+  if (mode == 0)
+    k_fx_fwd_x<N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+  else if (mode == 1)
+    k_fx_fwd_x<N, 1, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+  else
+    k_fx_fwd_x<N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+  return cudaGetLastError();
+}
+template <int N>
+cudaError_t fx_fwd_x_n(const Geometry& g, const DctTables<double>& tb, PcgState* st, double* x,
+                       const double* w, const double* q, double* r, const double* rin, double* t,
+                       double* partials, int par, double rtol2, int mode, cudaStream_t s,
+                       int nt) {
+  if (nt == 128 || !fast_x_fits<double, N, 256>())
+    return fx_fwd_x_nt<N, 128>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+  return fx_fwd_x_nt<N, 256>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
+}
+
+template <int N, int NT>
+cudaError_t fx_inv_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState* st,
+                        const double* t, double* z, const double* kd, double kz_host, int check,
+                        int mode, cudaStream_t s) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<double, N, NT>();
+  if (mode == 2)
+    k_fx_inv_x<N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
+  else
+    k_fx_inv_x<N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
+  return cudaGetLastError();
+}
+template <int N>
+cudaError_t fx_inv_x_n(const Geometry& g, const DctTables<double>& tb, PcgState* st,
+                       const double* t, double* z, const double* kd, double kz_host, int check,
+                       int mode, cudaStream_t s, int nt) {
+  if (nt == 128 || !fast_x_fits<double, N, 256>())
+    return fx_inv_x_nt<N, 128>(g, tb, st, t, z, kd, kz_host, check, mode, s);
+  return fx_inv_x_nt<N, 256>(g, tb, st, t, z, kd, kz_host, check, mode, s);
+}
+
+template <int N>
+cudaError_t fx_y_n(const Geometry& g, const DctTables<double>& tb, const PcgState* st, double* t,
+                   int inverse, int check, cudaStream_t s) {
+  dim3 grid((g.n0 + 15) / 16, g.n2);
+  const size_t sm = fx_y_smem<N>();
+  if (inverse)
+    k_fx_y<N, 1><<<grid, 16 * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+  else
+    k_fx_y<N, 0><<<grid, 16 * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+  return cudaGetLastError();
+}
+
+template <int N, int NT>
+cudaError_t fx_attrs_nt() {
+  cudaError_t e = cudaSuccess;
+  if (!fast_x_fits<double, N, NT>()) return e;  // never launched
+  const int sx = (int)fast_x_smem<double, N, NT>();
+#define SETF(fn, b) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  SETF((k_fx_fwd_x<N, 0, NT>), sx);
+  SETF((k_fx_fwd_x<N, 1, NT>), sx);
+  SETF((k_fx_fwd_x<N, 2, NT>), sx);
+  SETF((k_fx_inv_x<N, 0, NT>), sx);
+  SETF((k_fx_inv_x<N, 2, NT>), sx);
+#undef SETF
+  return e;
+}
+template <int N>
+cudaError_t fx_attrs_n() {
+  cudaError_t e = fx_attrs_nt<N, 256>();
+  if (e == cudaSuccess) e = fx_attrs_nt<N, 128>();
+  const int sy = (int)fx_y_smem<N>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fx_y<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fx_y<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  return e;
+}
+
+// The lengths with block-floating-point transforms, and the per-length
+// launchers each instantiates (PREFIX as for ETC_FAST_LAUNCHERS).
+#define ETC_FX_SIZES(X) X(32) X(64) X(128) X(256) X(512)
+#define ETC_FX_LAUNCHERS(PREFIX, N)                                                            \
+  PREFIX cudaError_t fx_fwd_x_n<N>(const Geometry&, const DctTables<double>&, PcgState*,       \
+                                   double*, const double*, const double*, double*,             \
+                                   const double*, double*, double*, int, double, int,          \
+                                   cudaStream_t, int);                                          \
+  PREFIX cudaError_t fx_inv_x_n<N>(const Geometry&, const DctTables<double>&, PcgState*,       \
+                                   const double*, double*, const double*, double, int, int,    \
+                                   cudaStream_t, int);                                          \
+  PREFIX cudaError_t fx_y_n<N>(const Geometry&, const DctTables<double>&, const PcgState*,     \
+                               double*, int, int, cudaStream_t);                                \
+  PREFIX cudaError_t fx_attrs_n<N>();
+#define ETC_FX_EXTERN(N) ETC_FX_LAUNCHERS(extern template, N)
+#define ETC_FX_INSTANTIATE(N) ETC_FX_LAUNCHERS(template, N)
+
+}  // namespace etc

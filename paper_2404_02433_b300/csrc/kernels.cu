@@ -1606,6 +1606,7 @@ cudaError_t set_smem_attrs() {
 #undef SETA
   if (e == cudaSuccess && sizeof(R) == 4) e = set_df_attrs();
   if (e == cudaSuccess) e = set_fast_attrs<R>();
+  if (e == cudaSuccess && sizeof(R) == 8) e = set_fx_attrs();
   return e;
 }
 template cudaError_t set_smem_attrs<double>();
@@ -1615,6 +1616,16 @@ template <typename R, typename V>
 cudaError_t launch_fwd_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, V* x, const V* w,
                          const V* q, V* r, const double* rin, R* t, double* partials, int par,
                          double rtol2, int mode, cudaStream_t s, int L) {
+  if constexpr (std::is_same<R, double>::value && std::is_same<V, double>::value) {
+    if (L == -3 || L == -4) {
+      if (!fx_x_ok(g, p, mode == 2 ? (const void*)rin : (const void*)r, q, x, w))
+        return cudaErrorInvalidValue;
+      const cudaError_t e = launch_fx_fwd_x(g, p, st, x, w, q, r, rin, t, partials, par, rtol2,
+                                            mode, s, L == -4 ? 128 : 256);
+      count_launch();
+      return e;
+    }
+  }
   if (L <= 0 && fast_x_ok<R>(g, p, mode == 2 ? (const void*)rin : (const void*)r, q, x, w)) {
     const cudaError_t e = launch_fast_fwd_x<R, V>(g, p, st, x, w, q, r, rin, t, partials, par,
                                                   rtol2, mode, s, L == -2 ? 128 : 256);
@@ -1653,6 +1664,14 @@ template <typename R>
 cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState* st, R* t,
                          int inverse, int check, cudaStream_t s, int TI) {
   if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
+  if constexpr (std::is_same<R, double>::value) {
+    if (TI == -3) {
+      if (!fx_y_ok(g, p)) return cudaErrorInvalidValue;
+      const cudaError_t e = launch_fx_y(g, p, st, t, inverse, check, s);
+      count_launch();
+      return e;
+    }
+  }
   if (TI <= 0 && fast_y_ok<R>(g, p)) {
     const cudaError_t e = launch_fast_y<R>(g, p, st, t, inverse, check, s);
     count_launch();
@@ -1737,6 +1756,16 @@ template <typename R, typename TZ>
 cudaError_t launch_inv_x(const Geometry& g, const DctPlan<R>& p, PcgState* st, const R* t, TZ* z,
                          const double* kd, double kz_host, int check, int mode, cudaStream_t s,
                          int L, typename XOf<TZ>::T* x, int par) {
+  if constexpr (std::is_same<R, double>::value && std::is_same<TZ, double>::value) {
+    if (L == -3 || L == -4) {
+      // FP64 storage: x moves in the forward pass, never here
+      if (x != nullptr || !fx_x_ok(g, p, t, z, z, z)) return cudaErrorInvalidValue;
+      const cudaError_t e = launch_fx_inv_x(g, p, st, t, z, kd, kz_host, check, mode, s,
+                                            L == -4 ? 128 : 256);
+      count_launch();
+      return e;
+    }
+  }
   if (L <= 0 && fast_x_ok<R>(g, p, t, z, x, z)) {
     const cudaError_t e = launch_fast_inv_x<R, TZ>(g, p, st, t, z, kd, kz_host, check, mode, s,
                                                    x, par, L == -2 ? 128 : 256);

@@ -164,6 +164,25 @@ cudaError_t launch_fast_y(const Geometry& g, const DctPlan<R>& p, const PcgState
 template <typename R>
 cudaError_t set_fast_attrs();
 
+// Block-floating-point transforms of the FP64 path for the power-of-two line
+// lengths 32..512 (fixed_kernels.cuh): tiles -3 (axis 0, blocks of 256
+// threads), -4 (axis 0, blocks of 128) and -3 (axis 1) of launch_fwd_x /
+// launch_inv_x / launch_dct_y with R = double, where fx_*_ok holds.
+bool fx_len(int n);
+bool fx_x_ok(const Geometry& g, const DctPlan<double>& p, const void* a, const void* b,
+             const void* c, const void* d);
+bool fx_y_ok(const Geometry& g, const DctPlan<double>& p);
+cudaError_t launch_fx_fwd_x(const Geometry& g, const DctPlan<double>& p, PcgState* st, double* x,
+                            const double* w, const double* q, double* r, const double* rin,
+                            double* t, double* partials, int par, double rtol2, int mode,
+                            cudaStream_t s, int nt);
+cudaError_t launch_fx_inv_x(const Geometry& g, const DctPlan<double>& p, PcgState* st,
+                            const double* t, double* z, const double* kd, double kz_host,
+                            int check, int mode, cudaStream_t s, int nt);
+cudaError_t launch_fx_y(const Geometry& g, const DctPlan<double>& p, const PcgState* st,
+                        double* t, int inverse, int check, cudaStream_t s);
+cudaError_t set_fx_attrs();
+
 unsigned long long launch_count();
 
 // ---------------------------------------------------------------- batch work queue

@@ -1,0 +1,142 @@
+"""Block-floating-point transforms of the FP64 path against the oracle.
+
+The FP64 path may run its cosine transforms (Eq. (forward DCT), Eq. (backward
+DCT), Sec. 3.2) in 64-bit fixed point with one exponent per line, for the
+power-of-two lengths 32..512 (tiles -3/-4 on axis 0, -3 on axis 1, chosen by
+the autotuner or forced through ETC_FORCE_TILES).  These tests force them on
+every such length, on each axis alone and on both, and compare with the
+oracle's direct O(n^2) transforms and its reference inverse (Algorithm 3):
+  * the 2-D transform pair within 1e-14 and the preconditioner within 2e-14
+    (max norm): the error of FP64 transforms (1e-15 and 2e-15 measured at
+    n = 512, fixed point and floating point alike), with margin, and 100 times
+    inside the FP64 kernels' bars;
+  * planes scaled by 10^-300 .. 10^200 in one array, each within 1e-14 of the
+    oracle relative to its own size (one exponent per line, not per array),
+    a zero plane staying zero;
+  * a NaN in one plane turns that plane, and only that plane, into NaN;
+  * a whole solve with the forced tiles reaches the oracle's kappa_eff.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import etc_oracle as O
+from paper_2404_02433_b300 import binding as B
+from paper_2404_02433_b300 import microstructure as M
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def relmax(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# [n2][n1][n0]: every power-of-two length 32..512 on axis 0 and on axis 1,
+# ragged partners, and the benchmark length on both
+SHAPES = [(3, 40, 32), (3, 32, 40), (2, 24, 64), (2, 64, 24), (3, 20, 128), (3, 128, 20),
+          (2, 12, 256), (2, 256, 12), (2, 6, 512), (2, 512, 6), (2, 64, 512), (2, 512, 256)]
+# forced (axis-0 forward, axis-0 backward, axis 1); 1 and 2 are generic
+# floating-point tiles, used where the other axis has no fixed-point kernel
+FIXED = [(-3, -3, -3), (-4, -4, -3), (-3, -4, 1), (-4, -3, 1), (1, 1, -3), (2, 2, -3)]
+
+
+def forced(monkeypatch, tiles):
+    monkeypatch.setenv("ETC_FORCE_TILES", ",".join(map(str, tiles)))
+
+
+def medium(shape, seed):
+    rng = np.random.default_rng(seed)
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    return B.RVE(dev(kx), dev(ky), dev(kz)), rng
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fixed_point_transforms_match_oracle(shape, monkeypatch):
+    rve, rng = medium(shape, 7 * sum(shape))
+    ku = [0.7, 1.9, 3.1, 0.4, 2.2]
+    rve.set_reference(2, B.ETC_REF_USER, ku)
+    r = rng.standard_normal(shape)
+    zo = O.apply_reference_inverse(r, ku)
+    rhat = O.dct_forward(O.dct_forward(r, 2), 1)
+    z = torch.empty(shape, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(z)
+    ran = 0
+    for tiles in FIXED:
+        forced(monkeypatch, tiles)
+        try:
+            B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_FP64, dev(r), z)
+        except B.EtcError as e:  # the other axis has no such kernel
+            assert e.status == B.ETC_EINVAL and "ETC_FORCE_TILES" in str(e)
+            continue
+        ran += 1
+        assert relmax(host(z), zo) < 2e-14, tiles
+        B.etc_dct_planes(rve.h, 2, 0, dev(r), out)
+        assert relmax(host(out), rhat) < 1e-14, tiles
+        B.etc_dct_planes(rve.h, 2, 1, dev(rhat), out)
+        assert relmax(host(out), r) < 1e-14, tiles
+        # the mixed forms have no fixed-point kernels
+        with pytest.raises(B.EtcError):
+            B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_MIXED, dev(r), z)
+    assert ran >= 2
+    rve.close()
+
+
+@pytest.mark.parametrize("tiles", [(-3, -3, -3), (-4, -4, -3)])
+def test_fixed_point_dynamic_range_per_line(tiles, monkeypatch):
+    shape = (6, 64, 128)
+    rve, rng = medium(shape, 11)
+    forced(monkeypatch, tiles)
+    scales = np.array([1e-200, 1.0, 0.0, 3e150, 1e-300, 7e200])
+    u = rng.standard_normal(shape)
+    u[1, :, :5] *= 1e-12  # a line with a wide range inside it
+    u *= scales[:, None, None]
+    ref = O.dct_forward(O.dct_forward(u, 2), 1)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
+    got = host(out)
+    back = torch.empty_like(out)
+    B.etc_dct_planes(rve.h, 2, 1, dev(ref), back)
+    gb = host(back)
+    for k in range(shape[0]):
+        if scales[k] == 0.0:
+            assert not got[k].any() and not gb[k].any()
+            continue
+        assert relmax(got[k], ref[k]) < 1e-14, k
+        assert relmax(gb[k], u[k]) < 1e-14, k
+    rve.close()
+
+
+def test_fixed_point_nan_stays_in_its_plane(monkeypatch):
+    shape = (4, 32, 64)
+    rve, rng = medium(shape, 13)
+    forced(monkeypatch, (-3, -3, -3))
+    u = rng.standard_normal(shape)
+    u[2, 5, 7] = np.nan
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
+    got = host(out)
+    assert np.isnan(got[2]).all()
+    assert np.isfinite(got[[0, 1, 3]]).all()
+    rve.close()
+
+
+@pytest.mark.parametrize("tiles", [(-3, -3, -3), (-4, -4, -3)])
+def test_fixed_point_solve_matches_oracle(tiles, monkeypatch):
+    k, _ = M.random_spheres((32, 64, 64), (3, 6), 0.3, 31, 1.0, 50.0)
+    ref = O.solve_direction(k, k, k, 2, rtol=1e-10)
+    forced(monkeypatch, tiles)
+    rve = B.RVE(torch.from_numpy(k).cuda())
+    kap, inf = rve.solve(2, rtol=1e-10)
+    assert inf["status"] == B.ETC_OK
+    assert abs(kap - ref.kappa_eff) <= 1e-9 * ref.kappa_eff, (kap, ref.kappa_eff)
+    assert abs(inf["iters"] - ref.iters) <= 1, (inf["iters"], ref.iters)
+    rve.close()
