@@ -13,7 +13,8 @@ mixed     = the same with the FP32 preconditioner (flexible PCG).
 e2e       = FP64 through the C ABI from pinned host buffers: create handle
             (H2D of kappa), tensor, K back to the host, destroy -- per step.
 roofline  = dominant kernel of the FP64 iteration (CUDA events on the
-            library's stream), against the derived FP64 ALU peak.
+            library's stream), against its bound: the FP64 ALU peak (derived,
+            and the measured DFMA rate) or the measured HBM copy rate.
 cpu_baseline / --impl reference = the CPU oracle on a bounded slab sample.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -89,8 +90,11 @@ def dct_flops_per_point(n, inverse):
     return fft / 2.0 + (9.0 if inverse else 8.0)
 
 
-def kernel_model(n0, n1, mixed=False, f64_vectors=False):
+def kernel_model(n0, n1, mixed=False, f64_vectors=False, fixed=(False, False, False)):
     """(FP64 flops, algorithmic bytes) per DOF of each kernel of one PCG iteration.
+
+    fixed: whether the FP64 axis-0 forward, axis-0 backward and axis-1
+    transforms run in block floating point (integer arithmetic, no FP64 flops).
 
     matvec: q = D w - sum T w_nb and w.q; fwd_x: x += alpha w, r -= alpha q,
     ||r||^2 and the axis-0 transform; tridiag: the two sweeps and r.z (the y
@@ -111,6 +115,8 @@ def kernel_model(n0, n1, mixed=False, f64_vectors=False):
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0, 52.0), "fwd_y": (0.0, 8.0),
                 "tridiag": (0.0, 12.0), "inv_y": (0.0, 8.0), "inv_x": (2.0, 20.0)}
     if not mixed:
+        fx, ix = (0.0 if fixed[0] else fx), (0.0 if fixed[1] else ix)
+        fy, iy = (0.0, 0.0) if fixed[2] else (fy, iy)
         return {"matvec": (15.0, 48.0), "fwd_x": (6.0 + fx, 56.0), "fwd_y": (fy, 16.0),
                 "tridiag": (7.0, 32.0), "inv_y": (iy, 16.0), "inv_x": (ix + 2.0, 24.0)}
     return {"matvec": (0.0, 36.0), "fwd_x": (0.0, 28.0), "fwd_y": (0.0, 8.0),
@@ -469,10 +475,14 @@ def run_ours(args, rank, world, local_rank):
         ms = B.etc_profile_iteration(rves[-1].h, 2, prec, 4)
         prof[label] = dict(zip(KERNELS, ms))
 
-    def roofline(label, mixed):
-        model = kernel_model(n, n, mixed, label == "mixed_f64")
+    # the FP64 transform kernels in use (block floating point: tiles -3/-4)
+    tiles64 = B.etc_transform_tiles(rves[-1].h, 2, B.ETC_PREC_FP64)
+    fixed64 = (tiles64[0] in (-3, -4), tiles64[1] in (-3, -4), tiles64[2] == -3)
+
+    def roofline(label, mixed, k=None):
+        model = kernel_model(n, n, mixed, label == "mixed_f64", fixed64)
         ms = prof[label]
-        k = max(ms, key=ms.get)
+        k = k or max(ms, key=ms.get)
         flops, byts = model[k]
         dof = float(n) ** 3
         t_alu = flops * dof / (FP64_PEAK_TFLOPS * 1e12)
@@ -578,6 +588,11 @@ def run_ours(args, rank, world, local_rank):
                       "roofline": roof_f, "kernel_ms": prof["mixed_f64"]},
         "roofline": roof,
         "kernel_ms": prof["fp64"],
+        "kernel_roofline": {k: {kk: r[kk] for kk in ("bound", "frac", "unit")}
+                            for k, r in ((k, roofline("fp64", False, k)) for k in KERNELS)},
+        "fp64_transforms": {"tiles": tiles64,
+                            "arithmetic": ["int64 block floating point" if f else "f64"
+                                           for f in fixed64]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                 "note": "create_rve from pinned host kappa + effective_tensor + K to host + "

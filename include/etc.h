@@ -314,6 +314,20 @@ etc_status etc_dct_planes(etc_rve* rve, int dir, int inverse, const double* in, 
  */
 etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters, double* ms);
 
+/*
+ * The transform kernels a solve of dir in `precision` uses, as chosen by the
+ * tile autotuner (or forced by ETC_FORCE_TILES): tiles[0] the axis-0 forward
+ * pass, tiles[1] the axis-0 backward pass, tiles[2] the axis-1 passes.
+ * Values: L > 0 rows (axis 0) or columns (axis 1) per block of the generic
+ * kernels; -1/-2 the register-resident floating-point kernels (axis-0 blocks
+ * of 256/128 threads); -3/-4 the FP64 path's block-floating-point kernels
+ * (integer arithmetic, axis-0 blocks of 256/128 threads; -3 on axis 1); 0 the
+ * default of the generic kernels (no autotuning).  tiles: host array of 3 ints
+ * written on ETC_OK.  May run the autotuner (timed launches on the handle's
+ * stream) when dir/precision has no recorded choice yet in the process.
+ */
+etc_status etc_transform_tiles(etc_rve* rve, int dir, int precision, int* tiles);
+
 /* Test support: the integer-pipe conversions the mixed path uses, element-wise
  * on device arrays of n values: d_out = (double) f_in exactly, f_out = f_in
  * rounded to nearest even.  Synchronises the stream. */

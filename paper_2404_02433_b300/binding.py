@@ -24,7 +24,7 @@ EXPORTED = (
     "etc_default_opts", "etc_create_rve", "etc_destroy_rve", "etc_set_reference_params",
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
     "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
-    "etc_last_error", "etc_profile_iteration", "etc_kernel_launches",
+    "etc_last_error", "etc_profile_iteration", "etc_transform_tiles", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
     "etc_solve_general", "etc_split_check", "etc_fp64_fma_rate", "etc_batch_queued",
@@ -87,6 +87,7 @@ def load_library(path: str | None = None):
         "etc_status_string": ([c_int], ctypes.c_char_p),
         "etc_last_error": ([vp], ctypes.c_char_p),
         "etc_profile_iteration": ([vp, c_int, c_int, c_int, dp], c_int),
+        "etc_transform_tiles": ([vp, c_int, c_int, ip], c_int),
         "etc_kernel_launches": ([], ctypes.c_ulonglong),
         "etc_apply_reference_inverse_static": ([c_int, c_int, c_int, dp, vp, vp, vp], c_int),
         "etc_convert_check": ([vp, vp, vp, vp, ctypes.c_longlong, vp], c_int),
@@ -216,6 +217,12 @@ def etc_profile_iteration(h, direction, precision, iters):
     ms = (c_double * 6)()
     _check(load_library().etc_profile_iteration(h, direction, precision, iters, ms), h)
     return [ms[i] for i in range(6)]
+
+
+def etc_transform_tiles(h, direction, precision):
+    tiles = (c_int * 3)()
+    _check(load_library().etc_transform_tiles(h, direction, precision, tiles), h)
+    return [tiles[i] for i in range(3)]
 
 
 def etc_apply_reference_inverse_static(n0, n1, n2, kref, r, z, stream=None):

@@ -1624,6 +1624,20 @@ etc_status etc_dct_planes(etc_rve* h, int dir, int inverse, const double* in, do
 
 unsigned long long etc_kernel_launches(void) { return launch_count(); }
 
+etc_status etc_transform_tiles(etc_rve* h, int dir, int prec, int* tiles) {
+  if (!h || !tiles) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  if (prec != ETC_PREC_FP64 && prec != ETC_PREC_MIXED && prec != ETC_PREC_MIXED_F64)
+    return fail(h, ETC_EINVAL, "precision must be ETC_PREC_FP64, _MIXED or _MIXED_F64");
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  s = autotune(h, dir, prec);
+  if (s != ETC_OK) return s;
+  for (int a = 0; a < 3; ++a) tiles[a] = h->tiles[a];
+  return ETC_OK;
+}
+
 etc_status etc_profile_iteration(etc_rve* h, int dir, int prec, int iters, double* ms) {
   if (!h || !ms || iters < 1) return ETC_EINVAL;
   etc_status s = check_dir(h, dir);

@@ -29,7 +29,8 @@ cudaError_t launch_fx_fwd_x(const Geometry& g, const DctPlan<double>& p, PcgStat
 #define FWD(N) \
   case N: return fx_fwd_x_n<N>(g, p.t, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s, nt);
   switch (g.n0) {
-    FWD(32) FWD(64) FWD(128) FWD(256) FWD(512)
+    FWD(32) FWD(64) FWD(96) FWD(128) FWD(160) FWD(192) FWD(256) FWD(384) FWD(512)
+    FWD(1024)
     default: return cudaErrorInvalidValue;
   }
 #undef FWD
@@ -41,7 +42,8 @@ cudaError_t launch_fx_inv_x(const Geometry& g, const DctPlan<double>& p, PcgStat
 #define INV(N) \
   case N: return fx_inv_x_n<N>(g, p.t, st, t, z, kd, kz_host, check, mode, s, nt);
   switch (g.n0) {
-    INV(32) INV(64) INV(128) INV(256) INV(512)
+    INV(32) INV(64) INV(96) INV(128) INV(160) INV(192) INV(256) INV(384) INV(512)
+    INV(1024)
     default: return cudaErrorInvalidValue;
   }
 #undef INV
@@ -52,7 +54,7 @@ cudaError_t launch_fx_y(const Geometry& g, const DctPlan<double>& p, const PcgSt
 #define YN(N) \
   case N: return fx_y_n<N>(g, p.t, st, t, inverse, check, s);
   switch (g.n1) {
-    YN(32) YN(64) YN(128) YN(256) YN(512)
+    YN(32) YN(64) YN(96) YN(128) YN(160) YN(192) YN(256) YN(384) YN(512) YN(1024)
     default: return cudaErrorInvalidValue;
   }
 #undef YN

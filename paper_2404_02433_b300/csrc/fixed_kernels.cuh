@@ -1,8 +1,8 @@
 // Register-resident cosine transforms of the FP64 path in block floating point
 // (fixed_point.cuh): the same four-step layout and data movement as the
 // floating-point kernels of fast_kernels.cuh (Eq. (forward DCT) and Eq.
-// (backward DCT) through the half-length complex FFT, Sec. 3.2), for the
-// power-of-two lengths n = 32 .. 512, on FP64 vectors.  Each line (a row of
+// (backward DCT) through the half-length complex FFT, Sec. 3.2), for their
+// lengths n = 32 .. 1024, on FP64 vectors.  Each line (a row of
 // axis 0, a column of axis 1) is converted to 64-bit integers with its own
 // exponent after its largest exponent is known (a shuffle over the line's P
 // threads on axis 0, a shared-memory maximum over its P warps on axis 1),
@@ -14,7 +14,10 @@
 
 namespace etc {
 
-constexpr bool fx_len_c(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+constexpr bool fx_len_c(int n) {
+  return n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 192 || n == 256 ||
+         n == 384 || n == 512 || n == 1024;
+}
 
 // First four-step stage of thread tau: DFT of length Q, then the twiddle
 // exp(SIGN 2 pi i tau k1 / M) (forward sign stored).
@@ -165,16 +168,25 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
         }
       }
   } else {
-    // the pre-twiddle omitted 1 / (2m): a power of two in the exponent
-    const int e2 = emax - 1022 - B - fxp::ilog2c(2 * M);
+    // the pre-twiddle omitted 1 / (2m) = f 2^E0: a power of two goes to the
+    // exponent, otherwise one more product by f (after halving: the FFT output
+    // may reach 2^62, a product's operand may not)
+    using FB = fxp::FxBits<M>;
+    constexpr fxp::Kc kf = fxp::kc(FB::f());
+    const int e2 = emax - 1022 - B + FB::E + (FB::POW2 ? -1 : 1);
+    auto out = [&](i64 y) {
+      if (bad) return fxp::nan_f64();
+      if constexpr (FB::POW2) return fxp::from_fx(y, e2);
+      else return fxp::from_fx(fxp::mulk(y >> 1, kf), e2);
+    };
 #pragma unroll
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int k2 = 0; k2 < P; ++k2) {
         const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
         if (ok) {
-          col[vrow<N>(2 * j) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(u[e * P + k2].x, e2);
-          col[vrow<N>(2 * j + 1) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(u[e * P + k2].y, e2);
+          col[vrow<N>(2 * j) * n0] = out(u[e * P + k2].x);
+          col[vrow<N>(2 * j + 1) * n0] = out(u[e * P + k2].y);
         }
       }
   }
@@ -334,8 +346,9 @@ __global__ void __launch_bounds__(NT)
 // ---------------------------------------------------------------- axis 0, backward
 // Same contract as k_fast_inv_x on FP64 vectors: u = scale * (backward DCT of
 // t along axis 0), then MODE 0: z = u; MODE 2: w = u + beta w in place (z
-// points at w).  scale = 1 / kappa_ref^z = f 2^Es with f in [1/2, 1) is applied
-// as one more product by the constant f and the exponent Es.
+// points at w).  scale = 1 / kappa_ref^z, times the 1 / (2m) the pre-twiddle
+// omitted, = f 2^Es with f in [1/2, 1), is applied as one more product by the
+// constant f and the exponent Es.
 template <int N, int MODE, int NT>
 __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTables<double> tb,
                                               PcgState* st, const double* __restrict__ t,
@@ -429,13 +442,13 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
   __shared__ int erow[NT / P];
   if (tau == 0) erow[l] = emax;
   __syncthreads();
-  // scale = f 2^Es from its binary64 fields (a positive normal number)
-  const double scale = 1.0 / (kd ? kd[2] : kz_host);
+  // scale = 1 / (kappa_ref^z 2m) (the pre-twiddle omitted 1 / (2m)) = f 2^Es
+  // from its binary64 fields (a positive normal number)
+  const double scale = 1.0 / ((kd ? kd[2] : kz_host) * (2.0 * M));
   const unsigned long long sb = (unsigned long long)__double_as_longlong(scale);
   const fxp::Kc kf = fxp::kc_split((i64)(((sb & 0xfffffffffffffull) | (1ull << 52)) << 9));
   const int es = (int)((sb >> 52) & 0x7ff) - 1022;
-  // the pre-twiddle omitted 1 / (2m)
-  constexpr int EOFF = -1022 - B - fxp::ilog2c(2 * M);
+  constexpr int EOFF = -1022 - B;
   const double beta = (MODE == 2) ? st->beta : 0.0;
   constexpr int NQ = L * M / NT;      // element pairs per thread
   constexpr int G = NQ < 4 ? NQ : 4;  // pairs whose loads are in flight together
@@ -571,7 +584,7 @@ cudaError_t fx_attrs_n() {
 
 // The lengths with block-floating-point transforms, and the per-length
 // launchers each instantiates (PREFIX as for ETC_FAST_LAUNCHERS).
-#define ETC_FX_SIZES(X) X(32) X(64) X(128) X(256) X(512)
+#define ETC_FX_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(1024)
 #define ETC_FX_LAUNCHERS(PREFIX, N)                                                            \
   PREFIX cudaError_t fx_fwd_x_n<N>(const Geometry&, const DctTables<double>&, PcgState*,       \
                                    double*, const double*, const double*, double*,             \

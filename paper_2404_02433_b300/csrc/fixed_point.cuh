@@ -21,6 +21,8 @@
 // infinity or NaN comes out as NaN.
 #pragma once
 
+#include "dct_device.cuh"
+
 namespace etc {
 namespace fxp {
 
@@ -183,6 +185,83 @@ template <int SIGN> struct Fb<16, SIGN> {
   }
 };
 
+// t / 2 rounded to nearest, ties to even (no bias: a one-sided rounding of
+// the exact halves would add up coherently in the DFTs' zero-frequency outputs)
+__device__ __forceinline__ i64 half_even(i64 t) { return (t >> 1) + (t & (t >> 1) & 1); }
+
+template <int SIGN> struct Fb<3, SIGN> {
+  static __device__ __forceinline__ void run(cx* v) {
+    constexpr Kc s3 = kc(0.86602540378443864676);  // sqrt(3)/2
+    const cx t1 = add(v[1], v[2]);
+    const cx t2 = mk(v[0].x - half_even(t1.x), v[0].y - half_even(t1.y));
+    const cx d = sub(v[1], v[2]);
+    const cx t3 = rot<SIGN>(mk(mulk(d.x, s3), mulk(d.y, s3)));  // SIGN i sqrt(3)/2 (v1 - v2)
+    v[0] = add(v[0], t1);
+    v[1] = add(t2, t3);
+    v[2] = sub(t2, t3);
+  }
+};
+
+template <int SIGN> struct Fb<5, SIGN> {
+  static __device__ __forceinline__ void run(cx* v) {
+    constexpr Kc c1 = kc(0.30901699437494742410), c2 = kc(-0.80901699437494742410);
+    constexpr Kc n1 = kc(0.95105651629515357212), n2 = kc(0.58778525229247312917);
+    constexpr Kc mn1 = kc(-0.95105651629515357212);
+    const cx b1 = add(v[1], v[4]), b2 = add(v[2], v[3]);
+    const cx d1 = sub(v[1], v[4]), d2 = sub(v[2], v[3]);
+    const cx a = v[0];
+    const Sp b1x = split(b1.x), b1y = split(b1.y), b2x = split(b2.x), b2y = split(b2.y);
+    const Sp d1x = split(d1.x), d1y = split(d1.y), d2x = split(d2.x), d2y = split(d2.y);
+    const cx p1 = mk(a.x + mulk(b1x, c1) + mulk(b2x, c2), a.y + mulk(b1y, c1) + mulk(b2y, c2));
+    const cx p2 = mk(a.x + mulk(b1x, c2) + mulk(b2x, c1), a.y + mulk(b1y, c2) + mulk(b2y, c1));
+    const cx q1 = rot<SIGN>(mk(mulk(d1x, n1) + mulk(d2x, n2), mulk(d1y, n1) + mulk(d2y, n2)));
+    const cx q2 = rot<SIGN>(mk(mulk(d1x, n2) + mulk(d2x, mn1), mulk(d1y, n2) + mulk(d2y, mn1)));
+    v[0] = add(a, add(b1, b2));
+    v[1] = add(p1, q1);
+    v[4] = sub(p1, q1);
+    v[2] = add(p2, q2);
+    v[3] = sub(p2, q2);
+  }
+};
+
+// Length A*B by Cooley-Tukey (as the floating-point composite butterflies):
+// DFT-B over s2 of x[s1 + A s2] for each s1, twiddle exp(SIGN 2 pi i s1 k1 /
+// (A B)) from compile-time constants, DFT-A over s1 for each k1; output
+// X[k1 + B k2] in natural order.
+template <int A, int B, int SIGN> struct FbCT {
+  static __device__ __forceinline__ void run(cx* v) {
+    cx y[A][B];
+#pragma unroll
+    for (int s1 = 0; s1 < A; ++s1) {
+#pragma unroll
+      for (int s2 = 0; s2 < B; ++s2) y[s1][s2] = v[s1 + A * s2];
+      Fb<B, SIGN>::run(y[s1]);
+    }
+    SFor<1, A>::run([&](auto i1) {
+      constexpr int s1 = decltype(i1)::value;
+      SFor<1, B>::run([&](auto j1) {
+        constexpr int k1 = decltype(j1)::value;
+        constexpr CosSin w = cis2pi(s1 * k1, A * B);
+        constexpr Kc wc = kc(w.c), ws = kc(w.s);
+        y[s1][k1] = crot_s<SIGN>(y[s1][k1], wc, ws);
+      });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < B; ++k1) {
+      cx z[A];
+#pragma unroll
+      for (int s1 = 0; s1 < A; ++s1) z[s1] = y[s1][k1];
+      Fb<A, SIGN>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < A; ++k2) v[k1 + B * k2] = z[k2];
+    }
+  }
+};
+template <int SIGN> struct Fb<12, SIGN> : FbCT<4, 3, SIGN> {};
+template <int SIGN> struct Fb<20, SIGN> : FbCT<4, 5, SIGN> {};
+template <int SIGN> struct Fb<24, SIGN> : FbCT<8, 3, SIGN> {};
+template <int SIGN> struct Fb<32, SIGN> : FbCT<8, 4, SIGN> {};
+
 // ---------------------------------------------------------------- conversions
 // Biased exponent field of a binary64 value, 1 for zero and subnormals.
 __device__ __forceinline__ int bexp(double v) {
@@ -228,10 +307,14 @@ __device__ __forceinline__ double nan_f64() { return __longlong_as_double(0x7ff8
 //     |V_{m-j}|^2), so the packed FFT input |a_j| <= |p| + |o| <= 4 max|X| and
 //     its FFT output <= 4 m max|X| (halved before the product by the output
 //     scale).
-constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+constexpr int clog2c(int v) { return v <= 1 ? 0 : 1 + clog2c((v + 1) / 2); }  // ceil(log2 v)
 template <int M> struct FxBits {
-  static constexpr int F = (61 - ilog2c(2 * M)) < 53 ? (61 - ilog2c(2 * M)) : 53;  // 61.5 - log2(2m)
-  static constexpr int I = (60 - ilog2c(M)) < 53 ? (60 - ilog2c(M)) : 53;          // 62 - log2(4m)
+  static constexpr int F = (61 - clog2c(2 * M)) < 53 ? (61 - clog2c(2 * M)) : 53;  // 61.5 - log2(2m)
+  static constexpr int I = (60 - clog2c(M)) < 53 ? (60 - clog2c(M)) : 53;          // 62 - log2(4m)
+  // 1 / (2m) = f 2^E with f in [1/2, 1): the backward scale the pre-twiddle omits
+  static constexpr bool POW2 = (M & (M - 1)) == 0;
+  static constexpr int E = 1 - clog2c(2 * M);
+  static constexpr double f() { return (double)(1LL << clog2c(2 * M)) / (2.0 * M) / 2.0; }
 };
 
 // ---------------------------------------------------------------- tables
@@ -241,7 +324,8 @@ template <int M> struct FxBits {
 //   m + 2k, m + 2k + 1  untangling, t = pi k / (2n): (cos t / 2, sin t / 2), (cos 5t / 2, sin 5t / 2)
 //   3m + 2 + 2k, +1     backward pre-twiddle: (cos t, sin t), (cos 4t, sin 4t)
 // for k = 0..m.  The backward pre-twiddle omits the floating-point tables'
-// factor 1/(2m), a power of two that moves to the output exponent.
+// factor 1/(2m), which the output conversion applies (a power of two in the
+// exponent, otherwise one more product by its significand).
 struct Kc2 {
   Kc a, b;
 };

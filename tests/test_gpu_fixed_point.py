@@ -2,8 +2,8 @@
 
 The FP64 path may run its cosine transforms (Eq. (forward DCT), Eq. (backward
 DCT), Sec. 3.2) in 64-bit fixed point with one exponent per line, for the
-power-of-two lengths 32..512 (tiles -3/-4 on axis 0, -3 on axis 1, chosen by
-the autotuner or forced through ETC_FORCE_TILES).  These tests force them on
+register-resident lengths 32..1024 (tiles -3/-4 on axis 0, -3 on axis 1,
+chosen by the autotuner or forced through ETC_FORCE_TILES).  These tests force them on
 every such length, on each axis alone and on both, and compare with the
 oracle's direct O(n^2) transforms and its reference inverse (Algorithm 3):
   * the 2-D transform pair within 1e-14 and the preconditioner within 2e-14
@@ -40,10 +40,13 @@ def relmax(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-# [n2][n1][n0]: every power-of-two length 32..512 on axis 0 and on axis 1,
-# ragged partners, and the benchmark length on both
-SHAPES = [(3, 40, 32), (3, 32, 40), (2, 24, 64), (2, 64, 24), (3, 20, 128), (3, 128, 20),
-          (2, 12, 256), (2, 256, 12), (2, 6, 512), (2, 512, 6), (2, 64, 512), (2, 512, 256)]
+# [n2][n1][n0]: every length of these kernels (32..1024; radices 2, 3, 5 and
+# the non-power-of-two backward scale) on axis 0 and on axis 1 with ragged
+# partners, and pairs of them on both axes including the benchmark length
+SHAPES = [(3, 40, 32), (3, 32, 40), (2, 24, 64), (2, 64, 24), (2, 20, 96), (2, 96, 20),
+          (3, 20, 128), (3, 128, 20), (2, 12, 160), (2, 160, 12), (2, 10, 192), (2, 192, 10),
+          (2, 12, 256), (2, 256, 12), (2, 6, 384), (2, 384, 6), (2, 6, 512), (2, 512, 6),
+          (2, 3, 1024), (2, 1024, 3), (2, 96, 160), (2, 384, 192), (2, 64, 512), (2, 512, 256)]
 # forced (axis-0 forward, axis-0 backward, axis 1); 1 and 2 are generic
 # floating-point tiles, used where the other axis has no fixed-point kernel
 FIXED = [(-3, -3, -3), (-4, -4, -3), (-3, -4, 1), (-4, -3, 1), (1, 1, -3), (2, 2, -3)]
