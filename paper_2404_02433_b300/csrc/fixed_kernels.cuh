@@ -51,7 +51,9 @@ __device__ __forceinline__ void st_cx(fxp::cx* p, fxp::cx v) {
 }
 
 // ---------------------------------------------------------------- axis 1
-// In place on t: every block owns C = 16 adjacent columns of one plane.
+// In place on t: every block owns C = 16 adjacent columns of one plane.  The
+// conversions use the hardware's (the FP64 pipe is idle here); the axis-0
+// kernels, whose FP64 pipe carries the vector updates, use the integer forms.
 template <int N>
 constexpr size_t fx_y_smem() {
   return (size_t)16 * (N / 2 + 1) * sizeof(fxp::cx) + 16 * sizeof(int);
@@ -97,7 +99,7 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
     emax = emx[c];
 #pragma unroll
     for (int s = 0; s < Q; ++s)
-      v[s] = fxp::mk(fxp::to_fx<B>(d0[s], emax), fxp::to_fx<B>(d1[s], emax));
+      v[s] = fxp::mk(fxp::to_fx_hw<B>(d0[s], emax), fxp::to_fx_hw<B>(d1[s], emax));
   } else {
     // the pre-twiddle of input j needs X_j, X_{n-j}, X_{m-j} and X_{m+j}:
     // stage the tile's columns as integers, form every V_k once, then a_j
@@ -113,7 +115,7 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
     __syncthreads();
     emax = emx[c];
 #pragma unroll
-    for (int s = 0; s < 2 * Q; ++s) sr[(tau + P * s) * C + c] = fxp::to_fx<B>(xs[s], emax);
+    for (int s = 0; s < 2 * Q; ++s) sr[(tau + P * s) * C + c] = fxp::to_fx_hw<B>(xs[s], emax);
     __syncthreads();
     cx vv[Q];
 #pragma unroll
@@ -163,8 +165,8 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
         i64 xa, xb;
         fxp::untangle(u[e * P + k2], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
         if (ok) {
-          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx(xa, e2);
-          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx(xb, e2);
+          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xa, e2);
+          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xb, e2);
         }
       }
   } else {
@@ -176,8 +178,8 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
     const int e2 = emax - 1022 - B + FB::E + (FB::POW2 ? -1 : 1);
     auto out = [&](i64 y) {
       if (bad) return fxp::nan_f64();
-      if constexpr (FB::POW2) return fxp::from_fx(y, e2);
-      else return fxp::from_fx(fxp::mulk(y >> 1, kf), e2);
+      if constexpr (FB::POW2) return fxp::from_fx_hw(y, e2);
+      else return fxp::from_fx_hw(fxp::mulk(y >> 1, kf), e2);
     };
 #pragma unroll
     for (int e = 0; e < E; ++e)

@@ -299,6 +299,27 @@ __device__ __forceinline__ double from_fx(i64 Y, int e2) {
 }
 __device__ __forceinline__ double nan_f64() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+// The same two conversions by the hardware's binary64 <-> 64-bit integer
+// conversions (round to nearest even), with the power-of-two scaling done on
+// the exponent field: one FP64-pipe instruction and a few integer ones each,
+// where the integer forms above take 15 to 25.  The transforms leave the FP64
+// pipe otherwise idle (axis 1) or lightly used (axis 0).
+template <int B>
+__device__ __forceinline__ i64 to_fx_hw(double v, int emax) {
+  const int hi = __double2hiint(v), lo = __double2loint(v);
+  const int e = (hi >> 20) & 0x7ff;
+  const int sc = 1022 - emax + B;  // S
+  // zero, subnormal, or below half a unit of the line: 0
+  if (e == 0 || e + sc <= 0) return 0;
+  return __double2ll_rn(__hiloint2double(hi + (sc << 20), lo));
+}
+__device__ __forceinline__ double from_fx_hw(i64 Y, int e2) {
+  const double d = __ll2double_rn(Y);
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  const int e = (hi >> 20) & 0x7ff;
+  return (e == 0 || e + e2 <= 0) ? 0.0 : __hiloint2double(hi + (e2 << 20), lo);
+}
+
 // Bits kept for the largest element of a line (at most binary64's 53), so that
 // no intermediate value reaches 2^62:
 //   forward, FFT of length m: |Z_k| <= 2 m max|u| / sqrt(2) per component pair,

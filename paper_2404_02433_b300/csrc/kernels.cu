@@ -754,7 +754,9 @@ __global__ void __launch_bounds__(256) k_dct_y(Geometry g, DctPlan<R> p, const P
 
 // ------------------------------------------------------------------ tridiagonal along axis 2
 // Forward sweep y_k = r^_k + h_{k-1} y_{k-1}, backward z_k = h_k (y_k + z_{k+1})
-// solves (T_{i'j'}/kappa_ref^z) z = r^.  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
+// solves (T_{i'j'}/kappa_ref^z) z = r^.  The forward sweep stores g_k = h_k y_k,
+// so that the backward sweep is one FMA per cell, z_k = g_k + h_k z_{k+1}
+// (four FP64 instructions per cell for both sweeps and rho, not five).  r^.T^{-1} r^ = sum_k h_k y_k^2 / kappa_ref^z,
 // so rho = r.z follows from Parseval for the DCT pair of Sec. 3.2 (weight
 // 4 alpha_i' alpha_j' / (n0 n1), applied in the last block through wscale).
 // MODE 0: solve only.
@@ -797,8 +799,9 @@ __device__ __forceinline__ void tridiag_body(const Blk& b, Geometry g, PcgState*
           const long long c = (long long)k * g.plane + s;
           if (MODE >= 2) rnew[c] = tv[u];
           yv = fma(hp, yv, tv[u]);
-          t[c] = yv;
-          part = fma(hv[u] * yv, yv, part);
+          const R gv = hv[u] * yv;  // g_k = h_k y_k, kept for the backward sweep
+          t[c] = gv;
+          part = fma(gv, yv, part);
           hp = hv[u];
         }
       }
@@ -820,7 +823,7 @@ __device__ __forceinline__ void tridiag_body(const Blk& b, Geometry g, PcgState*
       for (int u = 0; u < P; ++u) {
         const int k = kb - u;
         if (k >= 0) {
-          zn = hv[u] * (tv[u] + zn);
+          zn = fma(hv[u], zn, tv[u]);  // z_k = h_k (y_k + z_{k+1}) = g_k + h_k z_{k+1}
           t[(long long)k * g.plane + s] = zn;
           if (MODE == 2) zr = fma(zn, ro[u], zr);
         }
