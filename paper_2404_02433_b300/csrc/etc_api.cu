@@ -1125,12 +1125,22 @@ etc_status queue_pass(etc_rve* h, const Geometry& g, int prec, BatchQueue* q,
   for (int par = 0; par < 2; ++par) {
     QueueLaunch ql = {q, bs, 6 * par, nm, s};
     if (prec == ETC_PREC_FP64) {
+      // the block-floating-point transforms where the tuner chose them (and
+      // the lengths have them), else the register-resident FP64 ones
+      const bool fxx = (h->tiles[0] == -3 || h->tiles[0] == -4) && fx_len(g.n0);
+      const bool fxy = h->tiles[2] == -3 && fx_len(g.n1);
       CK(launch_q_matvec(g, ql, par));
-      ql.slot++; CK(launch_q_fast_fwd_x<double>(g, P0.p64.t, ql, par, nt));
-      ql.slot++; CK(launch_q_fast_y<double>(g, P1.p64.t, ql, 0, 0, par));
+      ql.slot++;
+      CK(fxx ? launch_q_fx_x(g, P0.p64, ql, par, 0, nt)
+             : launch_q_fast_fwd_x<double>(g, P0.p64.t, ql, par, nt));
+      ql.slot++;
+      CK(fxy ? launch_q_fx_y(g, P1.p64, ql, 0) : launch_q_fast_y<double>(g, P1.p64.t, ql, 0, 0, par));
       ql.slot++; CK(launch_q_tridiag(g, ql));
-      ql.slot++; CK(launch_q_fast_y<double>(g, P1.p64.t, ql, 1, 0, par));
-      ql.slot++; CK(launch_q_fast_inv_x<double>(g, P0.p64.t, ql, par, nt));
+      ql.slot++;
+      CK(fxy ? launch_q_fx_y(g, P1.p64, ql, 1) : launch_q_fast_y<double>(g, P1.p64.t, ql, 1, 0, par));
+      ql.slot++;
+      CK(fxx ? launch_q_fx_x(g, P0.p64, ql, par, 1, nt)
+             : launch_q_fast_inv_x<double>(g, P0.p64.t, ql, par, nt));
     } else {
       CK(launch_q_matvec_df(g, ql, par));
       ql.slot++; CK(launch_q_fast_fwd_x<float>(g, P0.p32.t, ql, par, nt));

@@ -60,6 +60,34 @@ cudaError_t launch_fx_y(const Geometry& g, const DctPlan<double>& p, const PcgSt
 #undef YN
 }
 
+cudaError_t launch_q_fx_x(const Geometry& g, const DctPlan<double>& p, const QueueLaunch& ql,
+                          int par, int inverse, int nt) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define QX(N) \
+  case N: e = q_fx_x_n<N>(g, p.t, ql, par, inverse, nt); break;
+  switch (g.n0) {
+    QX(32) QX(64) QX(96) QX(128) QX(160) QX(192) QX(256) QX(384) QX(512) QX(1024)
+    default: return e;
+  }
+#undef QX
+  count_launch();
+  return e;
+}
+cudaError_t launch_q_fx_y(const Geometry& g, const DctPlan<double>& p, const QueueLaunch& ql,
+                          int inverse) {
+  if (g.n1 == 1) return cudaSuccess;  // a length-1 transform is the identity
+  cudaError_t e = cudaErrorInvalidValue;
+#define QY(N) \
+  case N: e = q_fx_y_n<N>(g, p.t, ql, inverse); break;
+  switch (g.n1) {
+    QY(32) QY(64) QY(96) QY(128) QY(160) QY(192) QY(256) QY(384) QY(512) QY(1024)
+    default: return e;
+  }
+#undef QY
+  count_launch();
+  return e;
+}
+
 cudaError_t set_fx_attrs() {
   cudaError_t e = cudaSuccess;
 #define AT(N) \

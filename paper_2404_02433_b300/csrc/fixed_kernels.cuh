@@ -492,6 +492,39 @@ __global__ void __launch_bounds__(NT)
   fx_inv_x_body<N, MODE, NT>(hw_blk(), g, tb, st, t, z, kd, kz_host, check);
 }
 
+// ---------------------------------------------------------------- batch work queue
+// Persistent forms of the three transforms over the FP64 solves of a batch
+// class (BatchQueue in etc_internal.cuh), as kq_fast_* in fast_kernels.cuh.
+template <int N, int NT>
+__global__ void __launch_bounds__(NT)
+    kq_fx_fwd_x(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g,
+                DctTables<double> tb, unsigned int nb, int par) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    fx_fwd_x_body<N, 1, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.x, a.w, a.q, a.r, nullptr,
+                            a.t64, a.partials, par, 0.0);
+  });
+}
+template <int N, int INV>
+__global__ void __launch_bounds__(16 * Fast<N>::P, FastCols<double, N>::MinBlocks())
+    kq_fx_y(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g, DctTables<double> tb,
+            unsigned int nbx) {
+  const unsigned int per = nbx * (unsigned int)g.n2;
+  queue_loop(q, slot, per, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    fx_y_body<N, INV>(item_blk(l, nbx, (unsigned int)g.n2, 1), g, tb, a.st, a.t64, 1);
+  });
+}
+template <int N, int NT>
+__global__ void __launch_bounds__(NT)
+    kq_fx_inv_x(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g,
+                DctTables<double> tb, unsigned int nb) {
+  queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
+    const BatchSolve& a = bs[sv];
+    fx_inv_x_body<N, 2, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.t64, a.w, a.st->kref, 1.0, 1);
+  });
+}
+
 // ---------------------------------------------------------------- per-size launchers
 // Defined here, instantiated per length in fixed_sizes_*.cu, called by
 // fixed_dispatch.cu.  The shared-memory layouts of the axis-0 kernels are
@@ -559,6 +592,46 @@ cudaError_t fx_y_n(const Geometry& g, const DctTables<double>& tb, const PcgStat
 }
 
 template <int N, int NT>
+cudaError_t q_fx_x_nt(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
+                      int par, int inverse) {
+  constexpr int L = FastX<N, NT>::L;
+  const long long nrows = (long long)g.n1 * g.n2;
+  const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
+  const size_t sm = fast_x_smem<double, N, NT>();
+  const long long items = (long long)nb * ql.nsolves;
+  if (inverse) {
+    const unsigned int grid = persistent_grid(kq_fx_inv_x<N, NT>, NT, sm, items);
+    kq_fx_inv_x<N, NT><<<grid, NT, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nb);
+  } else {
+    const unsigned int grid = persistent_grid(kq_fx_fwd_x<N, NT>, NT, sm, items);
+    kq_fx_fwd_x<N, NT><<<grid, NT, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nb, par);
+  }
+  return cudaGetLastError();
+}
+template <int N>
+cudaError_t q_fx_x_n(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
+                     int par, int inverse, int nt) {
+  if (nt == 128 || !fast_x_fits<double, N, 256>()) return q_fx_x_nt<N, 128>(g, tb, ql, par, inverse);
+  return q_fx_x_nt<N, 256>(g, tb, ql, par, inverse);
+}
+template <int N>
+cudaError_t q_fx_y_n(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
+                     int inverse) {
+  constexpr int NTY = 16 * Fast<N>::P;
+  const unsigned int nbx = (unsigned int)((g.n0 + 15) / 16);
+  const size_t sm = fx_y_smem<N>();
+  const long long items = (long long)nbx * g.n2 * ql.nsolves;
+  if (inverse) {
+    const unsigned int grid = persistent_grid(kq_fx_y<N, 1>, NTY, sm, items);
+    kq_fx_y<N, 1><<<grid, NTY, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nbx);
+  } else {
+    const unsigned int grid = persistent_grid(kq_fx_y<N, 0>, NTY, sm, items);
+    kq_fx_y<N, 0><<<grid, NTY, sm, ql.s>>>(ql.q, ql.slot, ql.bs, g, tb, nbx);
+  }
+  return cudaGetLastError();
+}
+
+template <int N, int NT>
 cudaError_t fx_attrs_nt() {
   cudaError_t e = cudaSuccess;
   if (!fast_x_fits<double, N, NT>()) return e;  // never launched
@@ -570,6 +643,8 @@ cudaError_t fx_attrs_nt() {
   SETF((k_fx_fwd_x<N, 2, NT>), sx);
   SETF((k_fx_inv_x<N, 0, NT>), sx);
   SETF((k_fx_inv_x<N, 2, NT>), sx);
+  SETF((kq_fx_fwd_x<N, NT>), sx);
+  SETF((kq_fx_inv_x<N, NT>), sx);
 #undef SETF
   return e;
 }
@@ -582,6 +657,10 @@ cudaError_t fx_attrs_n() {
     e = cudaFuncSetAttribute(k_fx_y<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fx_y<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kq_fx_y<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kq_fx_y<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
   return e;
 }
 
@@ -598,6 +677,10 @@ cudaError_t fx_attrs_n() {
                                    cudaStream_t, int);                                          \
   PREFIX cudaError_t fx_y_n<N>(const Geometry&, const DctTables<double>&, const PcgState*,     \
                                double*, int, int, cudaStream_t);                                \
+  PREFIX cudaError_t q_fx_x_n<N>(const Geometry&, const DctTables<double>&, const QueueLaunch&, \
+                                 int, int, int);                                                \
+  PREFIX cudaError_t q_fx_y_n<N>(const Geometry&, const DctTables<double>&, const QueueLaunch&, \
+                                 int);                                                          \
   PREFIX cudaError_t fx_attrs_n<N>();
 #define ETC_FX_EXTERN(N) ETC_FX_LAUNCHERS(extern template, N)
 #define ETC_FX_INSTANTIATE(N) ETC_FX_LAUNCHERS(template, N)

@@ -240,6 +240,14 @@ template <typename R>
 cudaError_t launch_q_fast_inv_x(const Geometry& g, const DctTables<R>& tb,
                                 const QueueLaunch& ql, int par, int nt);
 
+// The block-floating-point transforms over an FP64 class (fx_len lengths):
+// axis 0 forward (inverse = 0) or backward (1) with blocks of nt threads, and
+// axis 1.
+cudaError_t launch_q_fx_x(const Geometry& g, const DctPlan<double>& p, const QueueLaunch& ql,
+                          int par, int inverse, int nt);
+cudaError_t launch_q_fx_y(const Geometry& g, const DctPlan<double>& p, const QueueLaunch& ql,
+                          int inverse);
+
 // Grid sizes of the reduction kernels (to size the partials buffer).
 unsigned int matvec_blocks(const Geometry& g);
 unsigned int matvec_df_blocks(const Geometry& g);
