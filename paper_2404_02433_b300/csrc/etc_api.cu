@@ -263,7 +263,7 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
   if (sizeof(R) == 8 && s.fft && fx_len(n)) {
     // the same constants in 62-bit fixed point (fixed_point.cuh): C = c 2^62
     // rounded, |C| <= 2^62 - 1, as (C >> 31, C mod 2^31)
-    const int P = fast_threads_per_line(n), Q = m / P;
+    const int P = fx_threads_per_line(n), Q = m / P;
     std::vector<int> fx(4 * (size_t)(m + 4 * (m + 1)));
     auto put = [&](size_t slot, long double c) {
       long long C = llroundl(c * 4611686018427387904.0L);

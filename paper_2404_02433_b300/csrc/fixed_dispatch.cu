@@ -6,6 +6,7 @@
 namespace etc {
 
 bool fx_len(int n) { return fx_len_c(n); }
+int fx_threads_per_line(int n) { return fx_p(n / 2); }
 
 ETC_FX_SIZES(ETC_FX_EXTERN)
 

@@ -19,12 +19,50 @@ constexpr bool fx_len_c(int n) {
          n == 384 || n == 512 || n == 1024;
 }
 
+// Four-step split m = P * Q of these kernels (P threads per line).  A 64-bit
+// complex value takes twice the registers of an FP32 one, so where the
+// floating-point split gives a thread 20 or 24 values (n = 160, 192, 384:
+// up to 254 registers and 8 warps per SM) these kernels take twice the
+// threads per line and half the values.  Q need not then be a multiple of P:
+// the Q length-P DFTs of the second stage go round-robin over the P threads
+// in E = ceil(Q / P) rounds, the last one partly idle.
+constexpr int fx_p(int m) { return (m == 80 || m == 96) ? 8 : m == 192 ? 16 : fast_p(m); }
+template <int N> struct FxFast {
+  static constexpr int M = N / 2;
+  static constexpr int P = fx_p(M);
+  static constexpr int Q = M / P;
+  static constexpr int E = (Q + P - 1) / P;  // second-stage rounds per thread
+  static constexpr bool EXACT = Q % P == 0;
+  static_assert(P * Q == M, "four-step split");
+  // axis-0 shared layout, in complex units per row (as Fast<N>)
+  static constexpr int SA = M + P;
+  static constexpr int BS0 = Q * (P + 1);
+  static constexpr int BS = BS0 + (((P - BS0) % 16) + 16) % 16;
+  static constexpr int RS = SA > BS ? SA : BS;
+  // axis-1 blocks of 16 columns: at most 128 registers a thread (255 for
+  // more than 16 values a thread)
+  static constexpr int YMIN = ((512 >> (Q > 16 ? 1 : 0)) / (16 * P)) > 0
+                                  ? ((512 >> (Q > 16 ? 1 : 0)) / (16 * P)) : 1;
+};
+template <int N, int NT> struct FxX {  // axis-0 blocks of NT threads: L rows
+  static constexpr int L = NT / FxFast<N>::P;
+  static_assert(L * FxFast<N>::P == NT, "rows per block");
+};
+template <int N, int NT>
+constexpr size_t fx_x_smem() {
+  return (size_t)FxX<N, NT>::L * FxFast<N>::RS * sizeof(fxp::cx);
+}
+template <int N, int NT>
+constexpr bool fx_x_fits() {
+  return fx_x_smem<N, NT>() <= kFastSmemMax;
+}
+
 // First four-step stage of thread tau: DFT of length Q, then the twiddle
 // exp(SIGN 2 pi i tau k1 / M) (forward sign stored).
 template <int N, int SIGN>
 __device__ __forceinline__ void fx_four_step_a(fxp::cx* v, const int4* __restrict__ tw4,
                                                int tau) {
-  using F = Fast<N>;
+  using F = FxFast<N>;
   fxp::Fb<F::Q, SIGN>::run(v);
   const int4* tw = tw4 + tau * F::Q;
 #pragma unroll
@@ -63,7 +101,7 @@ template <int N, int INV>
 __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<double> tb,
                                           const PcgState* st, double* __restrict__ t,
                                           int check) {
-  using F = Fast<N>;
+  using F = FxFast<N>;
   using fxp::cx;
   using fxp::i64;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = 16;
@@ -142,9 +180,10 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
 #pragma unroll
   for (int k1 = 0; k1 < Q; ++k1) st_cx(sm + (k1 * P + tau) * C + c, v[k1]);
   __syncthreads();
-  cx u[Q];
+  cx u[E * P];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
+    if (!F::EXACT && tau + P * e >= Q) continue;  // this round's DFT index is past Q
 #pragma unroll
     for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(sm + ((tau + P * e) * P + tt) * C + c);
     fxp::Fb<P, SIGN>::run(u + e * P);
@@ -155,13 +194,15 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
 #pragma unroll
     for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int k2 = 0; k2 < P; ++k2) st_cx(sm + (tau + P * e + Q * k2) * C + c, u[e * P + k2]);
+      for (int k2 = 0; k2 < P; ++k2)
+        if (F::EXACT || tau + P * e < Q) st_cx(sm + (tau + P * e + Q * k2) * C + c, u[e * P + k2]);
     __syncthreads();
     const int e2 = emax - 1022 - B;
 #pragma unroll
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int k2 = 0; k2 < P; ++k2) {
+        if (!F::EXACT && tau + P * e >= Q) continue;
         const int k = tau + P * e + Q * k2;
         i64 xa, xb;
         fxp::untangle(u[e * P + k2], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
@@ -186,6 +227,7 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
     for (int e = 0; e < E; ++e)
 #pragma unroll
       for (int k2 = 0; k2 < P; ++k2) {
+        if (!F::EXACT && tau + P * e >= Q) continue;
         const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
         if (ok) {
           col[vrow<N>(2 * j) * n0] = out(u[e * P + k2].x);
@@ -195,7 +237,7 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
   }
 }
 template <int N, int INV>
-__global__ void __launch_bounds__(16 * Fast<N>::P, FastCols<double, N>::MinBlocks())
+__global__ void __launch_bounds__(16 * FxFast<N>::P, FxFast<N>::YMIN)
     k_fx_y(Geometry g, DctTables<double> tb, const PcgState* st, double* __restrict__ t,
            int check) {
   fx_y_body<N, INV>(hw_blk(), g, tb, st, t, check);
@@ -213,11 +255,11 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
                                               const double* __restrict__ rin,
                                               double* __restrict__ t, double* partials, int par,
                                               double rtol2) {
-  using F = Fast<N>;
+  using F = FxFast<N>;
   using fxp::cx;
   using fxp::i64;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
-  constexpr int L = FastX<N, NT>::L;
+  constexpr int L = FxX<N, NT>::L;
   constexpr int B = fxp::FxBits<M>::F;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sh[32];
@@ -231,8 +273,8 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
   double acc = 0.0;
   constexpr int NP = L * M;  // element pairs of the block
   // pairs per thread whose loads are in flight together (4: 1.95 -> 1.80 ms at
-  // 512^3 against 2)
-  constexpr int U = 4;
+  // 512^3 against 2), or the largest of 2, 1 that divides the block's pairs
+  constexpr int U = (L * M) % (NT * 4) == 0 ? 4 : (L * M) % (NT * 2) == 0 ? 2 : 1;
   static_assert(NP % (NT * U) == 0, "pair rounds");
   for (int p0 = threadIdx.x; p0 < NP; p0 += NT * U) {
     VPair<double> rv[U], qv[U], xv[U], wv[U];
@@ -308,9 +350,10 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
 #pragma unroll
   for (int k1 = 0; k1 < Q; ++k1) st_cx(A + l * RS + k1 * (P + 1) + tau, v[k1]);
   __syncthreads();
-  cx u[Q];
+  cx u[E * P];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
+    if (!F::EXACT && tau + P * e >= Q) continue;  // this round's DFT index is past Q
 #pragma unroll
     for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(A + l * RS + (tau + P * e) * (P + 1) + tt);
     fxp::Fb<P, -1>::run(u + e * P);
@@ -319,7 +362,8 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
 #pragma unroll
   for (int e = 0; e < E; ++e)
 #pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
+    for (int k2 = 0; k2 < P; ++k2)
+      if (F::EXACT || tau + P * e < Q) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
   __syncthreads();
   const long long row = row0 + l;
   const int4* post = tb.fxq + fxp::fx_off_post(M);
@@ -329,6 +373,7 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
   for (int e = 0; e < E; ++e)
 #pragma unroll
     for (int k2 = 0; k2 < P; ++k2) {
+      if (!F::EXACT && tau + P * e >= Q) continue;
       const int k = tau + P * e + Q * k2;
       i64 xa, xb;
       fxp::untangle(u[e * P + k2], ld_cx(A + l * RS + (k ? M - k : 0)), post, k, M, xa, xb);
@@ -360,11 +405,11 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
                                               PcgState* st, const double* __restrict__ t,
                                               double* __restrict__ z, const double* kd,
                                               double kz_host, int check) {
-  using F = Fast<N>;
+  using F = FxFast<N>;
   using fxp::cx;
   using fxp::i64;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, RS = F::RS;
-  constexpr int L = FastX<N, NT>::L;
+  constexpr int L = FxX<N, NT>::L;
   constexpr int SR = N + P;  // real stride of the staged input rows
   constexpr int B = fxp::FxBits<M>::I;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -432,9 +477,10 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
 #pragma unroll
   for (int k1 = 0; k1 < Q; ++k1) st_cx(A + l * RS + k1 * (P + 1) + tau, v[k1]);
   __syncthreads();
-  cx u[Q];
+  cx u[E * P];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
+    if (!F::EXACT && tau + P * e >= Q) continue;  // this round's DFT index is past Q
 #pragma unroll
     for (int tt = 0; tt < P; ++tt) u[e * P + tt] = ld_cx(A + l * RS + (tau + P * e) * (P + 1) + tt);
     fxp::Fb<P, 1>::run(u + e * P);
@@ -443,7 +489,8 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
 #pragma unroll
   for (int e = 0; e < E; ++e)
 #pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
+    for (int k2 = 0; k2 < P; ++k2)
+      if (F::EXACT || tau + P * e < Q) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
   // the row's exponent for the output pass, which walks other rows
   __shared__ int erow[NT / P];
   if (tau == 0) erow[l] = emax;
@@ -506,7 +553,7 @@ __global__ void __launch_bounds__(NT)
   });
 }
 template <int N, int INV>
-__global__ void __launch_bounds__(16 * Fast<N>::P, FastCols<double, N>::MinBlocks())
+__global__ void __launch_bounds__(16 * FxFast<N>::P, FxFast<N>::YMIN)
     kq_fx_y(BatchQueue* q, int slot, const BatchSolve* bs, Geometry g, DctTables<double> tb,
             unsigned int nbx) {
   const unsigned int per = nbx * (unsigned int)g.n2;
@@ -534,10 +581,10 @@ cudaError_t fx_fwd_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState
                         const double* w, const double* q, double* r, const double* rin,
                         double* t, double* partials, int par, double rtol2, int mode,
                         cudaStream_t s) {
-  constexpr int L = FastX<N, NT>::L;
+  constexpr int L = FxX<N, NT>::L;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
-  const size_t sm = fast_x_smem<double, N, NT>();
+  const size_t sm = fx_x_smem<N, NT>();
   if (mode == 0)
     k_fx_fwd_x<N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
   else if (mode == 1)
@@ -551,7 +598,7 @@ cudaError_t fx_fwd_x_n(const Geometry& g, const DctTables<double>& tb, PcgState*
                        const double* w, const double* q, double* r, const double* rin, double* t,
                        double* partials, int par, double rtol2, int mode, cudaStream_t s,
                        int nt) {
-  if (nt == 128 || !fast_x_fits<double, N, 256>())
+  if (nt == 128 || !fx_x_fits<N, 256>())
     return fx_fwd_x_nt<N, 128>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
   return fx_fwd_x_nt<N, 256>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, mode, s);
 }
@@ -560,10 +607,10 @@ template <int N, int NT>
 cudaError_t fx_inv_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState* st,
                         const double* t, double* z, const double* kd, double kz_host, int check,
                         int mode, cudaStream_t s) {
-  constexpr int L = FastX<N, NT>::L;
+  constexpr int L = FxX<N, NT>::L;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
-  const size_t sm = fast_x_smem<double, N, NT>();
+  const size_t sm = fx_x_smem<N, NT>();
   if (mode == 2)
     k_fx_inv_x<N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, t, z, kd, kz_host, check);
   else
@@ -574,7 +621,7 @@ template <int N>
 cudaError_t fx_inv_x_n(const Geometry& g, const DctTables<double>& tb, PcgState* st,
                        const double* t, double* z, const double* kd, double kz_host, int check,
                        int mode, cudaStream_t s, int nt) {
-  if (nt == 128 || !fast_x_fits<double, N, 256>())
+  if (nt == 128 || !fx_x_fits<N, 256>())
     return fx_inv_x_nt<N, 128>(g, tb, st, t, z, kd, kz_host, check, mode, s);
   return fx_inv_x_nt<N, 256>(g, tb, st, t, z, kd, kz_host, check, mode, s);
 }
@@ -585,19 +632,19 @@ cudaError_t fx_y_n(const Geometry& g, const DctTables<double>& tb, const PcgStat
   dim3 grid((g.n0 + 15) / 16, g.n2);
   const size_t sm = fx_y_smem<N>();
   if (inverse)
-    k_fx_y<N, 1><<<grid, 16 * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+    k_fx_y<N, 1><<<grid, 16 * FxFast<N>::P, sm, s>>>(g, tb, st, t, check);
   else
-    k_fx_y<N, 0><<<grid, 16 * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+    k_fx_y<N, 0><<<grid, 16 * FxFast<N>::P, sm, s>>>(g, tb, st, t, check);
   return cudaGetLastError();
 }
 
 template <int N, int NT>
 cudaError_t q_fx_x_nt(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
                       int par, int inverse) {
-  constexpr int L = FastX<N, NT>::L;
+  constexpr int L = FxX<N, NT>::L;
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
-  const size_t sm = fast_x_smem<double, N, NT>();
+  const size_t sm = fx_x_smem<N, NT>();
   const long long items = (long long)nb * ql.nsolves;
   if (inverse) {
     const unsigned int grid = persistent_grid(kq_fx_inv_x<N, NT>, NT, sm, items);
@@ -611,13 +658,13 @@ cudaError_t q_fx_x_nt(const Geometry& g, const DctTables<double>& tb, const Queu
 template <int N>
 cudaError_t q_fx_x_n(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
                      int par, int inverse, int nt) {
-  if (nt == 128 || !fast_x_fits<double, N, 256>()) return q_fx_x_nt<N, 128>(g, tb, ql, par, inverse);
+  if (nt == 128 || !fx_x_fits<N, 256>()) return q_fx_x_nt<N, 128>(g, tb, ql, par, inverse);
   return q_fx_x_nt<N, 256>(g, tb, ql, par, inverse);
 }
 template <int N>
 cudaError_t q_fx_y_n(const Geometry& g, const DctTables<double>& tb, const QueueLaunch& ql,
                      int inverse) {
-  constexpr int NTY = 16 * Fast<N>::P;
+  constexpr int NTY = 16 * FxFast<N>::P;
   const unsigned int nbx = (unsigned int)((g.n0 + 15) / 16);
   const size_t sm = fx_y_smem<N>();
   const long long items = (long long)nbx * g.n2 * ql.nsolves;
@@ -634,8 +681,8 @@ cudaError_t q_fx_y_n(const Geometry& g, const DctTables<double>& tb, const Queue
 template <int N, int NT>
 cudaError_t fx_attrs_nt() {
   cudaError_t e = cudaSuccess;
-  if (!fast_x_fits<double, N, NT>()) return e;  // never launched
-  const int sx = (int)fast_x_smem<double, N, NT>();
+  if (!fx_x_fits<N, NT>()) return e;  // never launched
+  const int sx = (int)fx_x_smem<N, NT>();
 #define SETF(fn, b) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   SETF((k_fx_fwd_x<N, 0, NT>), sx);

@@ -189,6 +189,14 @@ template <int SIGN> struct Fb<16, SIGN> {
 // the exact halves would add up coherently in the DFTs' zero-frequency outputs)
 __device__ __forceinline__ i64 half_even(i64 t) { return (t >> 1) + (t & (t >> 1) & 1); }
 
+template <int SIGN> struct Fb<2, SIGN> {
+  static __device__ __forceinline__ void run(cx* v) {
+    const cx a = v[0];
+    v[0] = add(a, v[1]);
+    v[1] = sub(a, v[1]);
+  }
+};
+
 template <int SIGN> struct Fb<3, SIGN> {
   static __device__ __forceinline__ void run(cx* v) {
     constexpr Kc s3 = kc(0.86602540378443864676);  // sqrt(3)/2
@@ -257,6 +265,7 @@ template <int A, int B, int SIGN> struct FbCT {
     }
   }
 };
+template <int SIGN> struct Fb<10, SIGN> : FbCT<2, 5, SIGN> {};
 template <int SIGN> struct Fb<12, SIGN> : FbCT<4, 3, SIGN> {};
 template <int SIGN> struct Fb<20, SIGN> : FbCT<4, 5, SIGN> {};
 template <int SIGN> struct Fb<24, SIGN> : FbCT<8, 3, SIGN> {};

@@ -169,6 +169,7 @@ cudaError_t set_fast_attrs();
 // threads), -4 (axis 0, blocks of 128) and -3 (axis 1) of launch_fwd_x /
 // launch_inv_x / launch_dct_y with R = double, where fx_*_ok holds.
 bool fx_len(int n);
+int fx_threads_per_line(int n);  // P of their split n/2 = P * Q
 bool fx_x_ok(const Geometry& g, const DctPlan<double>& p, const void* a, const void* b,
              const void* c, const void* d);
 bool fx_y_ok(const Geometry& g, const DctPlan<double>& p);
