@@ -325,6 +325,10 @@ def accuracy(B, rves, K64, Km, Kf, energies):
         out[label] = {"err_by_rtol": errs, "loosest_rtol_meeting_bar": reach,
                       "energy_form_err_at_rtol_1e-8": err_energy(E8),
                       "meets_bar_at_rtol_1e-8": errs["1e-08"] <= ACC_BAR,
+                      # the same solves' kappa_eff from the energy form (the
+                      # quadratic form of the solution): error quadratic in
+                      # the solve error
+                      "meets_bar_at_rtol_1e-8_energy_form": err_energy(E8) <= ACC_BAR,
                       "no_less_accurate_than_fp64_at_rtol_1e-8":
                           errs["1e-08"] <= max(ACC_BAR, e64)}
     return out
@@ -560,7 +564,9 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if not any(fixed64) else "f64; transforms int64 (block floating point)",
+        "data": "synthetic",
         "config": {"workload": f"{n}^3 random spheres r8-20 phi0.25 seed{SEED}, contrasts "
                                f"1:100 and 1:1000, 3 directions each (full 3x3 tensor), "
                                f"PCG rtol {RTOL:g}, FP64",
