@@ -107,3 +107,32 @@ def test_queue_batch_iteration_cap(precision):
     assert st == B.ETC_ENOCONV
     assert all(i["status"] == B.ETC_ENOCONV and i["iters"] == 4 for i in infos)
     assert all(np.all(np.isfinite(K)) for K in Ks)
+
+
+def test_queue_batch_fp64_lengths_160_192():
+    # lengths whose FP64 block-floating-point transforms take eight threads a
+    # line (n = 160, 192: the second-stage DFTs go round-robin): a class of
+    # two 32 x 96 x 160 boxes and a class of one 192 x 32 x 64 box, against
+    # the oracle and the per-solve batch
+    media = [M.random_spheres((32, 96, 160), (3, 7), 0.25, 41, 1.0, 60.0)[0],
+             M.random_spheres((32, 96, 160), (3, 7), 0.3, 42, 1.0, 5.0)[0],
+             M.random_spheres((192, 32, 64), (3, 7), 0.25, 43, 1.0, 200.0)[0]]
+    rves = [B.RVE(dev(k)) for k in media]
+    batch = B.Batch(rves, rtol=1e-10, precision=B.ETC_PREC_FP64, queue=True)
+    assert batch.queued() == 3
+    Ks, infos, _, st = batch.run()
+    batch.close()
+    assert st == B.ETC_OK
+    ref = B.Batch(rves, rtol=1e-10, precision=B.ETC_PREC_FP64)
+    Kp, infp, _, stp = ref.run()
+    ref.close()
+    assert stp == B.ETC_OK
+    for i, k in enumerate(media):
+        K = np.array(Ks[i]).reshape(3, 3)
+        np.testing.assert_allclose(K, np.array(Kp[i]).reshape(3, 3), rtol=1e-9,
+                                   atol=1e-9 * np.abs(K).max())
+        K_o, res_o = O.effective_tensor(k, rtol=1e-10)
+        np.testing.assert_allclose(np.diag(K), np.diag(K_o), rtol=1e-9)
+        for d in range(3):
+            assert infos[3 * i + d]["status"] == B.ETC_OK
+            assert abs(infos[3 * i + d]["iters"] - res_o[d].iters) <= 1
