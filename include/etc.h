@@ -39,10 +39,12 @@
  *     ETC_FORCE_TILES="fx,ix,y" (read whenever the transform tiles are chosen)
  *     replaces the tuned tiles by these candidates: rows per block of the
  *     axis-0 forward and backward transforms (1..64, or -1 / -2 for the
- *     register-resident kernels in blocks of 256 / 128 threads) and columns
- *     per block of the axis-1 transforms (1..32, or -1); a candidate the shape
- *     does not allow gives ETC_EINVAL.  It lets a test run every kernel the
- *     tuner may pick.
+ *     register-resident kernels in blocks of 256 / 128 threads, or, FP64
+ *     only, -3 / -4 for the block-floating-point kernels in blocks of 256 /
+ *     128 threads) and columns per block of the axis-1 transforms (1..32, or
+ *     -1, or, FP64 only, -3); a candidate the shape or precision does not
+ *     allow gives ETC_EINVAL.  It lets a test run every kernel the tuner may
+ *     pick.
  *   - A handle is used from one host thread at a time.  All its GPU work is
  *     ordered on the stream given to etc_create_rve; calls that return numbers
  *     to the host synchronise that stream before returning.
