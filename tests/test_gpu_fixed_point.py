@@ -14,6 +14,9 @@ oracle's direct O(n^2) transforms and its reference inverse (Algorithm 3):
     oracle relative to its own size (one exponent per line, not per array),
     a zero plane staying zero;
   * a NaN in one plane turns that plane, and only that plane, into NaN;
+  * lines at the growth bounds of the arithmetic (constant, alternating, a
+    spike; backward, one dominant coefficient) within tolerances derived from
+    the per-line quantisation;
   * a whole solve with the forced tiles reaches the oracle's kappa_eff.
 """
 import numpy as np
@@ -142,4 +145,59 @@ def test_fixed_point_solve_matches_oracle(tiles, monkeypatch):
     assert inf["status"] == B.ETC_OK
     assert abs(kap - ref.kappa_eff) <= 1e-9 * ref.kappa_eff, (kap, ref.kappa_eff)
     assert abs(inf["iters"] - ref.iters) <= 1, (inf["iters"], ref.iters)
+    rve.close()
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 512), (5, 512, 4), (5, 4, 1024), (5, 4, 192)])
+def test_fixed_point_worst_case_growth(shape, monkeypatch):
+    # lines that drive the transforms to their bounds: all equal (the whole line
+    # lands in the zero-frequency output), alternating signs (the highest
+    # frequency), one spike over a tiny background, and, backward, spectra of
+    # equal coefficients; each within 1e-14 of the oracle relative to its line
+    n2, n1, n0 = shape
+    rve, rng = medium(shape, 17)
+    tiles = (-3, -3, 1) if n1 == 4 else (1, 1, -3)  # the long axis in fixed point
+    forced(monkeypatch, tiles)
+    axis_len = n0 if n1 == 4 else n1
+    idx = np.arange(axis_len)
+    lines = [np.full(axis_len, 1.0), np.where(idx % 2 == 0, 1.0, -1.0),
+             np.where(idx == 7, 1.0, 1e-9 * rng.standard_normal(axis_len)),
+             -np.full(axis_len, 3.5e10)]
+    u = np.zeros(shape)
+    for k in range(n2):
+        line = lines[k % len(lines)] * (1.0 + 0.001 * k)
+        if n1 == 4:
+            u[k, :, :] = line[None, :]
+        else:
+            u[k, :, :] = line[:, None]
+    # bits kept for a line's largest value: forward min(53, 61 - ceil(log2 n)),
+    # backward min(53, 60 - ceil(log2 (n/2))) (the growth bounds of the
+    # arithmetic); a value is quantised to units of 2^-(bits-1) of the line's
+    # largest, and n such roundings add up in each forward output as a random
+    # walk: about sqrt(n) units of the largest output (4 sqrt(n) allowed)
+    lg = int(np.ceil(np.log2(axis_len)))
+    bits_f, bits_b = min(53, 61 - lg), min(53, 61 - lg)
+    tol_f = 4.0 * np.sqrt(axis_len) * 2.0 ** -(bits_f - 1)
+    ref = O.dct_forward(O.dct_forward(u, 2), 1)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
+    got = host(out)
+    for k in range(n2):
+        assert relmax(got[k], ref[k]) < tol_f, (shape, k)
+    # backward of spectra of equal coefficients, and of the forward results:
+    # a constant line's spectrum is one coefficient n max|u| over the oracle's
+    # rounding noise, which block floating point quantises to units of
+    # 2^-(bits-1) of the largest coefficient (FP64 keeps each to 2^-53 of
+    # itself); the output, of size max|X| / n, then carries up to n such units
+    # of itself (3.4e-14 measured at n = 512, against 1e-16 for FP64
+    # transforms: where these transforms trail FP64, inside the 1e-12 bar)
+    spec = np.ones(shape) * (1.0 + np.arange(n2))[:, None, None]
+    tol_b = axis_len * 2.0 ** -(bits_b - 1)
+    for X in (spec, ref):
+        back = torch.empty_like(out)
+        B.etc_dct_planes(rve.h, 2, 1, dev(X), back)
+        want = O.dct_backward(O.dct_backward(X, 1), 2)
+        gb = host(back)
+        for k in range(n2):
+            assert relmax(gb[k], want[k]) < tol_b, (shape, k)
     rve.close()
