@@ -6,19 +6,24 @@
 // constants, so they run here in 64-bit two's complement fixed point with one
 // exponent per line (one transform):
 //   * a line's values v become X = v 2^S with S chosen from the largest
-//     exponent of the line, so that X keeps B = 52..53 bits of the largest
-//     element (the rounding FP64's own first butterfly applies) and no
-//     intermediate value of the transform can reach 2^62;
+//     exponent of the line, so that X keeps B = 51..53 bits of the largest
+//     element (53 up to n = 256, 52 at n = 512, 51 at n = 1024: about the
+//     rounding FP64's own first butterfly applies) and no intermediate value
+//     of the transform can reach 2^62;
 //   * additions and subtractions are exact;
 //   * a product by a constant c in [-1, 1], held as C = c 2^62 rounded, keeps
 //     the top bits of the exact 128-bit product X C, rounded: error about half
 //     a unit, i.e. 2^-62 of the largest intermediate value, where FP64 rounds
 //     every operation at 2^-53 of its result.
-// The transform error is therefore of the order of an FP64 transform's
-// (norm-wise per line; measured at n = 512 against exact transforms: 5e-16 of
-// the largest output forward, 9e-16 backward, where an FP64 transform gives
-// 5e-16), while the FP64 pipe only carries the PCG vector updates around it.  Values below 2^-1022 come out as zero; a line holding an
-// infinity or NaN comes out as NaN.
+// For random lines the transform error is that of an FP64 transform
+// (measured at n = 512 against exact sums, 2-D: 1.05e-15 of the largest output
+// forward and 1.45e-15 backward, where FP64 transforms give 0.97e-15 and
+// 1.27e-15), while the FP64 pipe only carries the PCG vector updates around
+// it.  Being relative to a line's largest value, it can trail FP64's for lines
+// of very uneven values: a spectrum of one dominant coefficient over rounding
+// noise comes back with up to n units of 2^-(B-1) of its output (3.4e-14 at
+// n = 512, against 1e-16).  Values below 2^-1022 come out as zero; a line
+// holding an infinity or NaN comes out as NaN.
 #pragma once
 
 #include "dct_device.cuh"
@@ -335,7 +340,7 @@ __device__ __forceinline__ double from_fx_hw(i64 Y, int e2) {
 //     the untangling sums a1 = Re Z_k + Re Z_{m-k} <= 2 m sqrt(2) max|u|;
 //   backward: |V_k| <= sqrt(2) max|X| and |p|^2 + |o|^2 = 2 (|V_j|^2 +
 //     |V_{m-j}|^2), so the packed FFT input |a_j| <= |p| + |o| <= 4 max|X| and
-//     its FFT output <= 4 m max|X| (halved before the product by the output
+//     its FFT output <= 4 m max|X| (halved before a product by an output
 //     scale).
 constexpr int clog2c(int v) { return v <= 1 ? 0 : 1 + clog2c((v + 1) / 2); }  // ceil(log2 v)
 template <int M> struct FxBits {
