@@ -574,8 +574,8 @@ __global__ void __launch_bounds__(NT)
 
 // ---------------------------------------------------------------- per-size launchers
 // Defined here, instantiated per length in fixed_sizes_*.cu, called by
-// fixed_dispatch.cu.  The shared-memory layouts of the axis-0 kernels are
-// those of the floating-point kernels (16-byte complex values).
+// fixed_dispatch.cu.  The axis-0 kernels' shared memory is laid out as the
+// floating-point kernels' (16-byte complex values), with this split's P and Q.
 template <int N, int NT>
 cudaError_t fx_fwd_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState* st, double* x,
                         const double* w, const double* q, double* r, const double* rin,
