@@ -504,6 +504,11 @@ def run_ours(args, rank, world, local_rank):
                 "frac": ach / hbm, "traffic": traffic, "peak_source": hbm_src,
                 "ms_per_launch": ms[k], "share": ms[k] / sum(ms.values())}
 
+    def kernel_roofs(label, mixed):
+        """Bound and fraction of each of the six kernels of one iteration."""
+        return {k: {kk: r[kk] for kk in ("bound", "frac", "unit")}
+                for k, r in ((k, roofline(label, mixed, k)) for k in KERNELS)}
+
     # measured FP64 FMA rate (the derived figure is an upper bound)
     fp64_probed = B.etc_fp64_fma_rate(20000, stream.cuda_stream)
     roof = roofline("fp64", False)
@@ -583,7 +588,8 @@ def run_ours(args, rank, world, local_rank):
                           "as FP32 pairs (48-bit significand), FP32 search direction",
                   "max_rel_diff_kappa_eff_vs_fp64": etc_err,
                   "time_to_solution_s_per_tensor": msm / args.steps / 2e3,
-                  "roofline": roof_m, "kernel_ms": prof["mixed"]},
+                  "roofline": roof_m, "kernel_ms": prof["mixed"],
+                  "kernel_roofline": kernel_roofs("mixed", True)},
         "mixed_f64": {"value": value_f, "unit": UNIT, "ms_per_step": msf / args.steps,
                       "pcg_iters_per_step": itf / args.steps,
                       "dtype": "f32 preconditioner; f64 vectors, operator and scalars",
@@ -591,11 +597,11 @@ def run_ours(args, rank, world, local_rank):
                               "matvec, residual update and dot products in FP64",
                       "max_rel_diff_kappa_eff_vs_fp64": etc_err_f,
                       "time_to_solution_s_per_tensor": msf / args.steps / 2e3,
-                      "roofline": roof_f, "kernel_ms": prof["mixed_f64"]},
+                      "roofline": roof_f, "kernel_ms": prof["mixed_f64"],
+                      "kernel_roofline": kernel_roofs("mixed_f64", True)},
         "roofline": roof,
         "kernel_ms": prof["fp64"],
-        "kernel_roofline": {k: {kk: r[kk] for kk in ("bound", "frac", "unit")}
-                            for k, r in ((k, roofline("fp64", False, k)) for k in KERNELS)},
+        "kernel_roofline": kernel_roofs("fp64", False),
         "fp64_transforms": {"tiles": tiles64,
                             "arithmetic": ["int64 block floating point" if f else "f64"
                                            for f in fixed64]},
