@@ -201,3 +201,20 @@ def test_fixed_point_worst_case_growth(shape, monkeypatch):
         for k in range(n2):
             assert relmax(gb[k], want[k]) < tol_b, (shape, k)
     rve.close()
+
+
+@pytest.mark.parametrize("tiles", [(-3, -3, 1), (-4, -4, 2)])
+def test_fixed_point_axis0_with_generic_axis1_in_a_solve(tiles, monkeypatch):
+    # load z on a 37 x 100 x 96 box: axis 0 (n0 = 96, the radix-3 length) in
+    # block floating point, axis 1 (n1 = 100, no such kernel) generic, in one
+    # solve; kappa_eff and iterations against the oracle
+    k, _ = M.random_spheres((37, 100, 96), (3, 7), 0.3, 51, 1.0, 80.0)
+    ref = O.solve_direction(k, k, k, 2, rtol=1e-10)
+    forced(monkeypatch, tiles)
+    rve = B.RVE(torch.from_numpy(k).cuda())
+    kap, inf = rve.solve(2, rtol=1e-10)
+    assert B.etc_transform_tiles(rve.h, 2, B.ETC_PREC_FP64) == list(tiles)
+    rve.close()
+    assert inf["status"] == B.ETC_OK
+    assert abs(kap - ref.kappa_eff) <= 1e-9 * ref.kappa_eff, (kap, ref.kappa_eff, tiles)
+    assert abs(inf["iters"] - ref.iters) <= 1, (inf["iters"], ref.iters)
