@@ -22,8 +22,9 @@
 // it.  Being relative to a line's largest value, it can trail FP64's for lines
 // of very uneven values: a spectrum of one dominant coefficient over rounding
 // noise comes back with up to n units of 2^-(B-1) of its output (3.4e-14 at
-// n = 512, against 1e-16).  Values below 2^-1022 come out as zero; a line
-// holding an infinity or NaN comes out as NaN.
+// n = 512, against 1e-16).  Values below 2^-1022 come out as zero, values
+// above the binary64 range as infinities; a line holding an infinity or NaN
+// comes out as NaN.
 #pragma once
 
 #include "dct_device.cuh"
@@ -298,7 +299,7 @@ __device__ __forceinline__ i64 to_fx(double v, int emax) {
   return (int)hi < 0 ? -X : X;
 }
 // Y 2^e2 rounded to the nearest binary64 (ties to even), |Y| < 2^63; 0 below
-// the normal range.
+// the normal range, an infinity above it.
 __device__ __forceinline__ double from_fx(i64 Y, int e2) {
   const u64 sgn = (u64)(Y >> 63);
   u64 a = ((u64)Y ^ sgn) - sgn;
@@ -308,7 +309,8 @@ __device__ __forceinline__ double from_fx(i64 Y, int e2) {
   const int be = 1086 - lz + e2;  // biased exponent of the leading one
   // mant carries the leading one: added onto the field be - 1 it gives be (be + 1
   // when the rounding reached 2^53)
-  const u64 bits = ((u64)(be - 1) << 52) + mant + (sgn << 63);
+  const u64 bits = be >= 2047 ? 0x7ff0000000000000ull + (sgn << 63)
+                               : ((u64)(be - 1) << 52) + mant + (sgn << 63);
   return (lz == 64 || be <= 0) ? 0.0 : __longlong_as_double((i64)bits);
 }
 __device__ __forceinline__ double nan_f64() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -331,7 +333,9 @@ __device__ __forceinline__ double from_fx_hw(i64 Y, int e2) {
   const double d = __ll2double_rn(Y);
   const int hi = __double2hiint(d), lo = __double2loint(d);
   const int e = (hi >> 20) & 0x7ff;
-  return (e == 0 || e + e2 <= 0) ? 0.0 : __hiloint2double(hi + (e2 << 20), lo);
+  if (e == 0 || e + e2 <= 0) return 0.0;
+  if (e + e2 >= 2047) return __hiloint2double((hi & (int)0x80000000) | 0x7ff00000, 0);
+  return __hiloint2double(hi + (e2 << 20), lo);
 }
 
 // Bits kept for the largest element of a line (at most binary64's 53), so that

@@ -13,7 +13,8 @@ oracle's direct O(n^2) transforms and its reference inverse (Algorithm 3):
   * planes scaled by 10^-300 .. 10^200 in one array, each within 1e-14 of the
     oracle relative to its own size (one exponent per line, not per array),
     a zero plane staying zero;
-  * a NaN in one plane turns that plane, and only that plane, into NaN;
+  * a NaN in one plane turns that plane, and only that plane, into NaN, and
+    an output above the binary64 range becomes an infinity;
   * lines at the growth bounds of the arithmetic (constant, alternating, a
     spike; backward, one dominant coefficient) within tolerances derived from
     the per-line quantisation;
@@ -118,6 +119,23 @@ def test_fixed_point_dynamic_range_per_line(tiles, monkeypatch):
             continue
         assert relmax(got[k], ref[k]) < 1e-14, k
         assert relmax(gb[k], u[k]) < 1e-14, k
+    rve.close()
+
+
+def test_fixed_point_overflow_gives_infinities(monkeypatch):
+    # a constant line near the top of the binary64 range: its zero-frequency
+    # output (n times the value) overflows to an infinity of the right sign,
+    # as in floating point; the other outputs stay finite
+    shape = (2, 4, 64)
+    rve, _ = medium(shape, 19)
+    forced(monkeypatch, (-3, -3, 1))
+    u = np.full(shape, 1e307)
+    u[1] *= -1.0
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
+    got = host(out)
+    assert got[0, 0, 0] == np.inf and got[1, 0, 0] == -np.inf
+    assert np.isfinite(got[:, :, 1:]).all()
     rve.close()
 
 
