@@ -42,7 +42,8 @@
  *     register-resident kernels in blocks of 256 / 128 threads, or, FP64
  *     only, -3 / -4 for the block-floating-point kernels in blocks of 256 /
  *     128 threads) and columns per block of the axis-1 transforms (1..32, or
- *     -1, or, FP64 only, -3); a candidate the shape or precision does not
+ *     -1, or, FP64 only, -3, or -4 for the three-stage kernels of lengths
+ *     256, 512, 1024); a candidate the shape or precision does not
  *     allow gives ETC_EINVAL.  It lets a test run every kernel the tuner may
  *     pick.
  *   - A handle is used from one host thread at a time.  All its GPU work is
@@ -323,7 +324,8 @@ etc_status etc_profile_iteration(etc_rve* rve, int dir, int precision, int iters
  * Values: L > 0 rows (axis 0) or columns (axis 1) per block of the generic
  * kernels; -1/-2 the register-resident floating-point kernels (axis-0 blocks
  * of 256/128 threads); -3/-4 the FP64 path's block-floating-point kernels
- * (integer arithmetic, axis-0 blocks of 256/128 threads; -3 on axis 1); 0 the
+ * (integer arithmetic, axis-0 blocks of 256/128 threads; on axis 1, -3 the
+ * two-stage and -4 the three-stage kernels); 0 the
  * default of the generic kernels (no autotuning).  tiles: host array of 3 ints
  * written on ETC_OK.  May run the autotuner (timed launches on the handle's
  * stream) when dir/precision has no recorded choice yet in the process.

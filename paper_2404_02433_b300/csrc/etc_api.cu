@@ -264,7 +264,7 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
     // the same constants in 62-bit fixed point (fixed_point.cuh): C = c 2^62
     // rounded, |C| <= 2^62 - 1, as (C >> 31, C mod 2^31)
     const int P = fx_threads_per_line(n), Q = m / P;
-    std::vector<int> fx(4 * (size_t)(m + 4 * (m + 1)));
+    std::vector<int> fx(4 * (size_t)fxp_table_int4(m));
     auto put = [&](size_t slot, long double c) {
       long long C = llroundl(c * 4611686018427387904.0L);
       const long long lim = 4611686018427387903LL;
@@ -289,6 +289,23 @@ cudaError_t build_tables(etc_rve* h, const DctShape& s, DctTables<R>* t, void** 
       put(pre + 4 * k + 1, sinl(th));
       put(pre + 4 * k + 2, cosl(4 * th));
       put(pre + 4 * k + 3, sinl(4 * th));
+    }
+    if (fxp_has_y3(m)) {
+      // the three-stage axis-1 kernels' twiddles (fixed_kernels.cuh)
+      const size_t y3 = 2 * (size_t)(m + 4 * (m + 1));
+      const int P3 = m / 8, P2 = m / 64;
+      for (int tau = 0; tau < P3; ++tau)
+        for (int k1 = 0; k1 < 8; ++k1) {
+          const long double a = -2.0L * pi * (long double)((tau * k1) % m) / m;
+          put(y3 + 2 * (size_t)(tau * 8 + k1), cosl(a));
+          put(y3 + 2 * (size_t)(tau * 8 + k1) + 1, sinl(a));
+        }
+      for (int tb = 0; tb < P2; ++tb)
+        for (int ka = 0; ka < 8; ++ka) {
+          const long double a = -2.0L * pi * (long double)((tb * ka) % P3) / P3;
+          put(y3 + 2 * (size_t)(m + tb * 8 + ka), cosl(a));
+          put(y3 + 2 * (size_t)(m + tb * 8 + ka) + 1, sinl(a));
+        }
     }
     int4* dq = nullptr;
     e = dalloc(h, &dq, fx.size() / 4);
@@ -544,6 +561,12 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
       });
       if (ty < by) { by = ty; best.y = -3; }
     }
+    if (g.n1 > 1 && fx_y3_ok(g, p1)) {
+      const double ty = time_launch(h->stream, e0, e1, [&] {
+        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -4);
+      });
+      if (ty < by) { by = ty; best.y = -4; }
+    }
   }
   for (int L = 1; L <= 64; L *= 2) {
     if (L > nrows || smem_x_bytes(g.n0, L, eb) > smem_limit()) break;
@@ -592,6 +615,7 @@ etc_status forced_tiles(etc_rve* h, const Geometry& g, int prec, const char* spe
   const bool fx_x = prec == ETC_PREC_FP64 &&
                     fx_x_ok(g, P0.p64, h->r, h->z64, h->z64, h->z64);
   const bool fx_y = prec == ETC_PREC_FP64 && fx_y_ok(g, P1.p64);
+  const bool fx_y3 = prec == ETC_PREC_FP64 && fx_y3_ok(g, P1.p64);
   for (int a = 0; a < 2; ++a) {
     const int L = v[a];
     if (L == -1 || L == -2) ok = ok && fx_fast;
@@ -603,6 +627,7 @@ etc_status forced_tiles(etc_rve* h, const Geometry& g, int prec, const char* spe
   if (g.n1 > 1) {
     if (v[2] == -1) ok = ok && y_fast;
     else if (v[2] == -3) ok = ok && fx_y;
+    else if (v[2] == -4) ok = ok && fx_y3;
     else ok = ok && pow2(v[2], 32) && v[2] <= g.n0 && smem_y_bytes(g.n1, v[2], eb) <= smem_limit();
   }
   if (!ok) return fail(h, ETC_EINVAL, "ETC_FORCE_TILES: tile not available for this shape");

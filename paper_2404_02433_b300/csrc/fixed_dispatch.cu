@@ -7,8 +7,24 @@ namespace etc {
 
 bool fx_len(int n) { return fx_len_c(n); }
 int fx_threads_per_line(int n) { return fx_p(n / 2); }
+int fxp_table_int4(int m) { return fxp::fx_table_int4(m); }
+bool fxp_has_y3(int m) { return fxp::fx_has_y3(m); }
 
 ETC_FX_SIZES(ETC_FX_EXTERN)
+ETC_FX_Y3_SIZES(ETC_FX_Y3_EXTERN)
+
+bool fx_y3_ok(const Geometry& g, const DctPlan<double>& p) {
+  return fx_y_ok(g, p) && fxp::fx_has_y3(g.n1 / 2) && g.n1 % 2 == 0;
+}
+cudaError_t launch_fx_y3(const Geometry& g, const DctPlan<double>& p, const PcgState* st,
+                         double* t, int inverse, int check, cudaStream_t s) {
+  switch (g.n1) {
+    case 256: return fx_y3_n<256>(g, p.t, st, t, inverse, check, s);
+    case 512: return fx_y3_n<512>(g, p.t, st, t, inverse, check, s);
+    case 1024: return fx_y3_n<1024>(g, p.t, st, t, inverse, check, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 namespace {
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -95,6 +111,10 @@ cudaError_t set_fx_attrs() {
   if (e == cudaSuccess) e = fx_attrs_n<N>();
   ETC_FX_SIZES(AT)
 #undef AT
+#define AT3(N) \
+  if (e == cudaSuccess) e = fx_y3_attrs_n<N>();
+  ETC_FX_Y3_SIZES(AT3)
+#undef AT3
   return e;
 }
 

@@ -243,6 +243,190 @@ __global__ void __launch_bounds__(16 * FxFast<N>::P, FxFast<N>::YMIN)
   fx_y_body<N, INV>(hw_blk(), g, tb, st, t, check);
 }
 
+// ---------------------------------------------------------------- axis 1, three stages
+// The axis-1 transforms for m = 8 * 8 * P2 (n = 256, 512, 1024) over P = 8 P2
+// threads per line with 8 values each, half the registers of the two-stage
+// split (16 values), so that more warps hide the latency of the integer
+// products: stage 1, thread tau: DFT-8 of z_{tau + P s} and the twiddle
+// exp(SIGN 2 pi i tau k1 / m); stage 2, thread (k1, tb): DFT-8 over ta of the
+// stage-1 values of tau = tb + P2 ta and the twiddle exp(SIGN 2 pi i tb ka / P);
+// stage 3: DFT-P2 over tb for Q / P2 pairs (k1, ka) a thread, giving
+// Z_{k1 + 8 ka + 64 kb}.  Two shared-memory exchanges instead of one, and the
+// second-stage twiddles, in exchange for the occupancy.
+template <int N> struct FxY3 {
+  static constexpr int M = N / 2, Q = 8, P2 = M / 64, P = Q * P2, R = Q / P2;
+  static constexpr int C = 256 / P;  // columns per block: blocks of 256 threads
+  static constexpr int NT = C * P;
+  static_assert(M == Q * Q * P2 && P2 >= 2 && P2 <= 8, "three-stage split");
+};
+template <int N>
+constexpr size_t fx_y3_smem() {
+  return (size_t)FxY3<N>::C * (N / 2 + 1) * sizeof(fxp::cx) + FxY3<N>::C * sizeof(int);
+}
+template <int N, int INV>
+__device__ __forceinline__ void fx_y3_body(const Blk& b, Geometry g, DctTables<double> tb,
+                                           const PcgState* st, double* __restrict__ t,
+                                           int check) {
+  using Y = FxY3<N>;
+  using fxp::cx;
+  using fxp::i64;
+  constexpr int M = Y::M, Q = Y::Q, P2 = Y::P2, P = Y::P, R = Y::R, C = Y::C;
+  constexpr int SIGN = INV ? 1 : -1;
+  constexpr int B = INV ? fxp::FxBits<M>::I : fxp::FxBits<M>::F;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cx* sm = reinterpret_cast<cx*>(smraw);  // C (M + 1) complex
+  int* emx = reinterpret_cast<int*>(smraw + (size_t)C * (M + 1) * sizeof(cx));
+  if (check && st->done) return;
+  const int4* post = tb.fxq + fxp::fx_off_post(M);
+  const int4* pre = tb.fxq + fxp::fx_off_pre(M);
+  const int4* tw1 = tb.fxq + fxp::fx_off_y3(M);
+  const int4* tw2 = tw1 + M;
+  const int c = threadIdx.x % C, tau = threadIdx.x / C;
+  const int i = b.x * C + c;
+  const bool ok = i < g.n0;
+  const long long n0 = g.n0;
+  double* col = t + (long long)b.y * g.plane + (ok ? i : 0);
+  if (tau == 0) emx[c] = 1;
+  __syncthreads();
+  cx v[Q];
+  int emax;
+  if (!INV) {
+    double d0[Q], d1[Q];
+    int em = 1;
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int q = tau + P * s;  // z_q = (v_{2q}, v_{2q+1})
+      d0[s] = ok ? col[vrow<N>(2 * q) * n0] : 0.0;
+      d1[s] = ok ? col[vrow<N>(2 * q + 1) * n0] : 0.0;
+      em = max(em, max(fxp::bexp(d0[s]), fxp::bexp(d1[s])));
+    }
+    atomicMax(&emx[c], em);
+    __syncthreads();
+    emax = emx[c];
+#pragma unroll
+    for (int s = 0; s < Q; ++s)
+      v[s] = fxp::mk(fxp::to_fx_hw<B>(d0[s], emax), fxp::to_fx_hw<B>(d1[s], emax));
+  } else {
+    i64* sr = reinterpret_cast<i64*>(smraw);  // real rows of C integers
+    double xs[2 * Q];
+    int em = 1;
+#pragma unroll
+    for (int s = 0; s < 2 * Q; ++s) {
+      xs[s] = ok ? col[(tau + P * s) * n0] : 0.0;
+      em = max(em, fxp::bexp(xs[s]));
+    }
+    atomicMax(&emx[c], em);
+    __syncthreads();
+    emax = emx[c];
+#pragma unroll
+    for (int s = 0; s < 2 * Q; ++s) sr[(tau + P * s) * C + c] = fxp::to_fx_hw<B>(xs[s], emax);
+    __syncthreads();
+    cx vv[Q];
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      vv[s] = fxp::inv_v(pre, j, sr[j * C + c], j ? sr[(N - j) * C + c] : 0);
+    }
+    cx vm = fxp::mk(0, 0);
+    if (tau == 0) vm = fxp::inv_v(pre, M, sr[M * C + c], sr[M * C + c]);
+    __syncthreads();  // the staged columns are read before V overwrites them
+#pragma unroll
+    for (int s = 0; s < Q; ++s) st_cx(sm + (tau + P * s) * C + c, vv[s]);
+    if (tau == 0) st_cx(sm + M * C + c, vm);
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      v[s] = fxp::inv_a(pre, j, vv[s], ld_cx(sm + (M - j) * C + c));
+    }
+    __syncthreads();  // V is read before stage 1 reuses the buffer
+  }
+  // stage 1: DFT-8 over s, twiddle exp(SIGN 2 pi i tau k1 / M); values to S1[k1][tau]
+  fxp::Fb<Q, SIGN>::run(v);
+#pragma unroll
+  for (int k1 = 1; k1 < Q; ++k1) {
+    const fxp::Kc2 w = fxp::ld_k2(tw1 + tau * Q + k1);
+    v[k1] = SIGN < 0 ? fxp::crot(v[k1], w.a, w.b) : fxp::crotc(v[k1], w.a, w.b);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) st_cx(sm + (k1 * P + tau) * C + c, v[k1]);
+  __syncthreads();
+  // stage 2, thread (k1, tb): DFT-8 over ta of S1[k1][tb + P2 ta], twiddle
+  // exp(SIGN 2 pi i tb ka / P); values to S2[k1][ka][tb]
+  {
+    const int k1 = tau / P2, tbi = tau % P2;
+#pragma unroll
+    for (int ta = 0; ta < Q; ++ta) v[ta] = ld_cx(sm + (k1 * P + tbi + P2 * ta) * C + c);
+    fxp::Fb<Q, SIGN>::run(v);
+#pragma unroll
+    for (int ka = 1; ka < Q; ++ka) {
+      const fxp::Kc2 w = fxp::ld_k2(tw2 + tbi * Q + ka);
+      v[ka] = SIGN < 0 ? fxp::crot(v[ka], w.a, w.b) : fxp::crotc(v[ka], w.a, w.b);
+    }
+    __syncthreads();  // S1 is read before S2 overwrites it
+#pragma unroll
+    for (int ka = 0; ka < Q; ++ka) st_cx(sm + ((k1 * Q + ka) * P2 + tbi) * C + c, v[ka]);
+  }
+  __syncthreads();
+  // stage 3: pairs pr = k1 Q + ka (R a thread), DFT-P2 over tb; u[r P2 + kb]
+  // holds Z_k, k = k1 + Q ka + Q^2 kb
+  cx u[Q];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int pr = tau + P * r;
+#pragma unroll
+    for (int tt = 0; tt < P2; ++tt) u[r * P2 + tt] = ld_cx(sm + (pr * P2 + tt) * C + c);
+    fxp::Fb<P2, SIGN>::run(u + r * P2);
+  }
+  auto kof = [&](int r, int kb) {
+    const int pr = tau + P * r;
+    return pr / Q + Q * (pr % Q) + Q * Q * kb;
+  };
+  const bool bad = emax == 2047;  // an infinity or NaN in the line
+  if (!INV) {
+    __syncthreads();  // S2 is read before Z overwrites it
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int kb = 0; kb < P2; ++kb) st_cx(sm + kof(r, kb) * C + c, u[r * P2 + kb]);
+    __syncthreads();
+    const int e2 = emax - 1022 - B;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int kb = 0; kb < P2; ++kb) {
+        const int k = kof(r, kb);
+        i64 xa, xb;
+        fxp::untangle(u[r * P2 + kb], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
+        if (ok) {
+          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xa, e2);
+          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xb, e2);
+        }
+      }
+  } else {
+    // the pre-twiddle omitted 1 / (2m), a power of two here
+    static_assert(fxp::FxBits<M>::POW2, "power-of-two lengths");
+    const int e2 = emax - 1022 - B + fxp::FxBits<M>::E - 1;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int kb = 0; kb < P2; ++kb) {
+        const int j = kof(r, kb);  // z_j = (v_{2j}, v_{2j+1})
+        if (ok) {
+          col[vrow<N>(2 * j) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(u[r * P2 + kb].x, e2);
+          col[vrow<N>(2 * j + 1) * n0] =
+              bad ? fxp::nan_f64() : fxp::from_fx_hw(u[r * P2 + kb].y, e2);
+        }
+      }
+  }
+}
+template <int N, int INV>
+__global__ void __launch_bounds__(FxY3<N>::NT, 3)
+    k_fx_y3(Geometry g, DctTables<double> tb, const PcgState* st, double* __restrict__ t,
+            int check) {
+  fx_y3_body<N, INV>(hw_blk(), g, tb, st, t, check);
+}
+
 // ---------------------------------------------------------------- axis 0, forward
 // Same contract as k_fast_fwd_x on FP64 vectors (MODE 0 initial residual, 1 PCG
 // update with x moved here, 2 transform only).
@@ -711,6 +895,28 @@ cudaError_t fx_attrs_n() {
   return e;
 }
 
+template <int N>
+cudaError_t fx_y3_n(const Geometry& g, const DctTables<double>& tb, const PcgState* st, double* t,
+                    int inverse, int check, cudaStream_t s) {
+  using Y = FxY3<N>;
+  dim3 grid((g.n0 + Y::C - 1) / Y::C, g.n2);
+  const size_t sm = fx_y3_smem<N>();
+  if (inverse)
+    k_fx_y3<N, 1><<<grid, Y::NT, sm, s>>>(g, tb, st, t, check);
+  else
+    k_fx_y3<N, 0><<<grid, Y::NT, sm, s>>>(g, tb, st, t, check);
+  return cudaGetLastError();
+}
+template <int N>
+cudaError_t fx_y3_attrs_n() {
+  const int sy = (int)fx_y3_smem<N>();
+  cudaError_t e =
+      cudaFuncSetAttribute(k_fx_y3<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fx_y3<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sy);
+  return e;
+}
+
 // The lengths with block-floating-point transforms, and the per-length
 // launchers each instantiates (PREFIX as for ETC_FAST_LAUNCHERS).
 #define ETC_FX_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(1024)
@@ -731,5 +937,13 @@ cudaError_t fx_attrs_n() {
   PREFIX cudaError_t fx_attrs_n<N>();
 #define ETC_FX_EXTERN(N) ETC_FX_LAUNCHERS(extern template, N)
 #define ETC_FX_INSTANTIATE(N) ETC_FX_LAUNCHERS(template, N)
+// The lengths with three-stage axis-1 kernels and their launchers.
+#define ETC_FX_Y3_SIZES(X) X(256) X(512) X(1024)
+#define ETC_FX_Y3_LAUNCHERS(PREFIX, N)                                                          \
+  PREFIX cudaError_t fx_y3_n<N>(const Geometry&, const DctTables<double>&, const PcgState*,    \
+                                double*, int, int, cudaStream_t);                               \
+  PREFIX cudaError_t fx_y3_attrs_n<N>();
+#define ETC_FX_Y3_EXTERN(N) ETC_FX_Y3_LAUNCHERS(extern template, N)
+#define ETC_FX_Y3_INSTANTIATE(N) ETC_FX_Y3_LAUNCHERS(template, N)
 
 }  // namespace etc

@@ -377,7 +377,14 @@ __device__ __forceinline__ Kc2 ld_k2(const int4* p) {
 }
 __host__ __device__ constexpr int fx_off_post(int m) { return m; }
 __host__ __device__ constexpr int fx_off_pre(int m) { return m + 2 * (m + 1); }
-__host__ __device__ constexpr int fx_table_int4(int m) { return m + 4 * (m + 1); }
+// Three-stage axis-1 kernels (m = 8 * 8 * P2, m = 128 .. 512): their first-stage
+// twiddles exp(-2 pi i tau k1 / m), [tau][k1] for tau < m / 8, k1 < 8, then the
+// second-stage twiddles exp(-2 pi i tb ka / (m / 8)), [tb][ka] for tb < m / 64.
+__host__ __device__ constexpr bool fx_has_y3(int m) { return m == 128 || m == 256 || m == 512; }
+__host__ __device__ constexpr int fx_off_y3(int m) { return m + 4 * (m + 1); }
+__host__ __device__ constexpr int fx_table_int4(int m) {
+  return m + 4 * (m + 1) + (fx_has_y3(m) ? m + m / 8 : 0);
+}
 
 // ---------------------------------------------------------------- transform steps
 // Forward untangling of the pair (k, m - k): X_k and X_{n-k} (X_m for k = 0)

@@ -7,4 +7,5 @@ namespace etc {
 ETC_FX_INSTANTIATE(160)
 ETC_FX_INSTANTIATE(192)
 ETC_FX_INSTANTIATE(256)
+ETC_FX_Y3_INSTANTIATE(256)
 }  // namespace etc

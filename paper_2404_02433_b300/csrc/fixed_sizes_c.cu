@@ -4,4 +4,5 @@
 
 namespace etc {
 ETC_FX_INSTANTIATE(512)
+ETC_FX_Y3_INSTANTIATE(512)
 }  // namespace etc

@@ -6,4 +6,5 @@
 namespace etc {
 ETC_FX_INSTANTIATE(384)
 ETC_FX_INSTANTIATE(1024)
+ETC_FX_Y3_INSTANTIATE(1024)
 }  // namespace etc

@@ -1674,6 +1674,12 @@ cudaError_t launch_dct_y(const Geometry& g, const DctPlan<R>& p, const PcgState*
       count_launch();
       return e;
     }
+    if (TI == -4) {
+      if (!fx_y3_ok(g, p)) return cudaErrorInvalidValue;
+      const cudaError_t e = launch_fx_y3(g, p, st, t, inverse, check, s);
+      count_launch();
+      return e;
+    }
   }
   if (TI <= 0 && fast_y_ok<R>(g, p)) {
     const cudaError_t e = launch_fast_y<R>(g, p, st, t, inverse, check, s);

@@ -170,6 +170,8 @@ cudaError_t set_fast_attrs();
 // launch_inv_x / launch_dct_y with R = double, where fx_*_ok holds.
 bool fx_len(int n);
 int fx_threads_per_line(int n);  // P of their split n/2 = P * Q
+int fxp_table_int4(int m);       // int4 entries of their constant table
+bool fxp_has_y3(int m);          // a three-stage axis-1 kernel for n = 2 m
 bool fx_x_ok(const Geometry& g, const DctPlan<double>& p, const void* a, const void* b,
              const void* c, const void* d);
 bool fx_y_ok(const Geometry& g, const DctPlan<double>& p);
@@ -182,6 +184,10 @@ cudaError_t launch_fx_inv_x(const Geometry& g, const DctPlan<double>& p, PcgStat
                             int check, int mode, cudaStream_t s, int nt);
 cudaError_t launch_fx_y(const Geometry& g, const DctPlan<double>& p, const PcgState* st,
                         double* t, int inverse, int check, cudaStream_t s);
+// The three-stage axis-1 kernels (n1 = 256, 512, 1024): tile -4 of axis 1.
+bool fx_y3_ok(const Geometry& g, const DctPlan<double>& p);
+cudaError_t launch_fx_y3(const Geometry& g, const DctPlan<double>& p, const PcgState* st,
+                         double* t, int inverse, int check, cudaStream_t s);
 cudaError_t set_fx_attrs();
 
 unsigned long long launch_count();

@@ -2,8 +2,9 @@
 
 The FP64 path may run its cosine transforms (Eq. (forward DCT), Eq. (backward
 DCT), Sec. 3.2) in 64-bit fixed point with one exponent per line, for the
-register-resident lengths 32..1024 (tiles -3/-4 on axis 0, -3 on axis 1,
-chosen by the autotuner or forced through ETC_FORCE_TILES).  These tests force them on
+register-resident lengths 32..1024 (tiles -3/-4 on axis 0, -3 on axis 1, and
+-4 on axis 1 for the three-stage kernels of n1 = 256, 512, 1024; chosen by the
+autotuner or forced through ETC_FORCE_TILES).  These tests force them on
 every such length, on each axis alone and on both, and compare with the
 oracle's direct O(n^2) transforms and its reference inverse (Algorithm 3):
   * the 2-D transform pair within 1e-14 and the preconditioner within 2e-14
@@ -53,7 +54,8 @@ SHAPES = [(3, 40, 32), (3, 32, 40), (2, 24, 64), (2, 64, 24), (2, 20, 96), (2, 9
           (2, 3, 1024), (2, 1024, 3), (2, 96, 160), (2, 384, 192), (2, 64, 512), (2, 512, 256)]
 # forced (axis-0 forward, axis-0 backward, axis 1); 1 and 2 are generic
 # floating-point tiles, used where the other axis has no fixed-point kernel
-FIXED = [(-3, -3, -3), (-4, -4, -3), (-3, -4, 1), (-4, -3, 1), (1, 1, -3), (2, 2, -3)]
+FIXED = [(-3, -3, -3), (-4, -4, -3), (-3, -4, 1), (-4, -3, 1), (1, 1, -3), (2, 2, -3),
+         (1, 1, -4), (-3, -3, -4)]  # -4 on axis 1: the three-stage kernels (n1 = 256..1024)
 
 
 def forced(monkeypatch, tiles):
@@ -166,15 +168,17 @@ def test_fixed_point_solve_matches_oracle(tiles, monkeypatch):
     rve.close()
 
 
-@pytest.mark.parametrize("shape", [(5, 4, 512), (5, 512, 4), (5, 4, 1024), (5, 4, 192)])
-def test_fixed_point_worst_case_growth(shape, monkeypatch):
+@pytest.mark.parametrize("shape,ytile", [((5, 4, 512), -3), ((5, 512, 4), -3), ((5, 512, 4), -4),
+                                         ((5, 4, 1024), -3), ((5, 1024, 4), -4),
+                                         ((5, 4, 192), -3)])
+def test_fixed_point_worst_case_growth(shape, ytile, monkeypatch):
     # lines that drive the transforms to their bounds: all equal (the whole line
     # lands in the zero-frequency output), alternating signs (the highest
     # frequency), one spike over a tiny background, and, backward, spectra of
     # equal coefficients; each within 1e-14 of the oracle relative to its line
     n2, n1, n0 = shape
     rve, rng = medium(shape, 17)
-    tiles = (-3, -3, 1) if n1 == 4 else (1, 1, -3)  # the long axis in fixed point
+    tiles = (-3, -3, 1) if n1 == 4 else (1, 1, ytile)  # the long axis in fixed point
     forced(monkeypatch, tiles)
     axis_len = n0 if n1 == 4 else n1
     idx = np.arange(axis_len)

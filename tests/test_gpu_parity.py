@@ -128,7 +128,7 @@ def test_preconditioner_register_resident_lengths(shape):
 # every tile the autotuner may pick is forced in turn (ETC_FORCE_TILES), so the
 # kernels a 512^3 solve runs are compared with the oracle element by element
 TILES_X = [-1, -2, -3, -4, 1, 2, 4, 8, 16, 32, 64]
-TILES_Y = [-1, -3, 1, 2, 4, 8, 16, 32]
+TILES_Y = [-1, -3, -4, 1, 2, 4, 8, 16, 32]
 
 
 @pytest.mark.parametrize("shape", [(4, 512, 512), (3, 96, 512), (3, 512, 96)])
