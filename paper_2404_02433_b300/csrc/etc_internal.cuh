@@ -107,6 +107,24 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 struct Blk {
   unsigned int x, y, z, nx, ny, nz;
 };
+// Bulk prefetch of [p, p + bytes) into L2: nothing is waited on and no
+// register is held (p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned int bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Blocks of kernel k (nt threads, sm bytes of dynamic shared memory) resident
+// on the current device at once; 0 if a query fails.
+template <typename K>
+int resident_blocks(K k, int nt, size_t sm) {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, sm) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
+}
 __device__ __forceinline__ Blk hw_blk() {
   return {blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
 }

@@ -154,13 +154,27 @@ __device__ __forceinline__ int vrow(int a) {
 template <typename R, int N, int INV>
 __device__ __forceinline__ void fast_y_body(const Blk& b, Geometry g,
                                             DctTables<R> tb, const PcgState* st,
-                                            R* __restrict__ t, int check) {
+                                            R* __restrict__ t, int check, int pf) {
   using F = Fast<N>;
   constexpr int M = F::M, P = F::P, Q = F::Q, E = F::E, C = FastCols<R, N>::C;
   constexpr int SIGN = INV ? 1 : -1;
   extern __shared__ __align__(16) unsigned char smraw[];
   c2<R>* sm = reinterpret_cast<c2<R>*>(smraw);  // C * M complex
   if (check && st->done) return;
+  if (pf > 0 && threadIdx.x == 0) {
+    // the share of the buffer of the block pf blocks ahead (a plane's blocks
+    // split it into equal byte ranges) goes to L2 while this block computes
+    const unsigned long long total = (unsigned long long)g.plane * g.n2 * sizeof(R);
+    const unsigned long long share =
+        ((unsigned long long)g.plane * sizeof(R) / b.nx + 15) / 16 * 16;
+    const unsigned long long a0 =
+        ((unsigned long long)b.y * b.nx + b.x + (unsigned long long)pf) * share;
+    if (a0 < total) {
+      const unsigned long long a1 = min(a0 + share, total / 16 * 16);
+      if (a1 > a0)
+        l2_prefetch(reinterpret_cast<const unsigned char*>(t) + a0, (unsigned int)(a1 - a0));
+    }
+  }
   const int c = threadIdx.x % C, tau = threadIdx.x / C;
   const int i = b.x * C + c;
   const bool ok = i < g.n0;
@@ -240,8 +254,9 @@ __device__ __forceinline__ void fast_y_body(const Blk& b, Geometry g,
 }
 template <typename R, int N, int INV>
 __global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>::MinBlocks())
-    k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check) {
-  fast_y_body<R, N, INV>(hw_blk(), g, tb, st, t, check);
+    k_fast_y(Geometry g, DctTables<R> tb, const PcgState* st, R* __restrict__ t, int check,
+             int pf) {
+  fast_y_body<R, N, INV>(hw_blk(), g, tb, st, t, check, pf);
 }
 
 // ---------------------------------------------------------------- axis 0, forward
@@ -535,7 +550,7 @@ __global__ void __launch_bounds__(FastCols<R, N>::C * Fast<N>::P, FastCols<R, N>
     R* t;
     if constexpr (sizeof(R) == 8) t = a.t64;
     else t = buf == 1 ? a.rhat[par] : a.t32;
-    fast_y_body<R, N, INV>(item_blk(l, nbx, (unsigned int)g.n2, 1), g, tb, a.st, t, 1);
+    fast_y_body<R, N, INV>(item_blk(l, nbx, (unsigned int)g.n2, 1), g, tb, a.st, t, 1, 0);
   });
 }
 
@@ -632,10 +647,15 @@ cudaError_t y_n(const Geometry& g, const DctTables<R>& tb, const PcgState* st, R
   constexpr int C = FastCols<R, N>::C;
   dim3 grid((g.n0 + C - 1) / C, g.n2);
   const size_t sm = fast_y_smem<R, N>();
+  // L2 prefetch distance: a quarter of the blocks resident on the GPU (FP32,
+  // 512^3: forward 0.217 -> 0.197 ms, flat from a quarter to all of them;
+  // backward unchanged), when the grid is more than two waves
+  static const int resident = resident_blocks(k_fast_y<R, N, 0>, C * Fast<N>::P, sm);
+  const int pf = resident > 0 && (long long)grid.x * grid.y > 2LL * resident ? resident / 4 : 0;
   if (inverse)
-    k_fast_y<R, N, 1><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+    k_fast_y<R, N, 1><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check, pf);
   else
-    k_fast_y<R, N, 0><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check);
+    k_fast_y<R, N, 0><<<grid, C * Fast<N>::P, sm, s>>>(g, tb, st, t, check, pf);
   return cudaGetLastError();
 }
 
