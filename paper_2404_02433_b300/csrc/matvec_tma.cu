@@ -170,12 +170,15 @@ __global__ void __launch_bounds__(kThreads, 4)
     const int oW = (r + 1) * kWX + l + 4;
     float2* pq = q + (long long)k0 * pl + sidx;
     unsigned int sc = 0, pc = 0;  // stage and parity of plane k
+    bool seen = false;            // plane k's copies were seen complete (as plane k+1)
     for (int k = k0; k < k1; ++k) {
       const unsigned int sn = sc + 1 == kStages ? 0u : sc + 1;
       const unsigned int pn = sn == 0 ? pc ^ 1u : pc;
-      // every lane waits (bounded) for planes k and k+1 (the z neighbour)
-      bool ok = mbar_wait(full + sc, pc);
+      // every lane waits (bounded) for planes k and k+1 (the z neighbour); a
+      // stage seen complete stays so until this warp releases it
+      bool ok = seen || mbar_wait(full + sc, pc);
       if (ok && k + 1 <= kend) ok = mbar_wait(full + sn, pn);
+      seen = k + 1 <= kend;
       if (!__all_sync(0xffffffffu, ok) || *vfailed) {
         *vfailed = 1;
         break;
