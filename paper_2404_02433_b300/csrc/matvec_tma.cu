@@ -17,7 +17,7 @@
 //                                   16-byte aligned)
 // Copies that reach outside the box are filled with zeros by the hardware,
 // which are exactly the Neumann faces (T = 0) and harmless finite neighbours.
-// The block is warp-specialised: 8 consumer warps (one tile row each) and one
+// The block is warp-specialised: 4 consumer warps (two tile rows each) and one
 // producer warp.  Each stage has a "full" mbarrier (completed by the copies'
 // transaction bytes) and an "empty" one (one arrival per consumer warp).  The
 // producer issues plane k into its stage once the consumers have released the
@@ -44,7 +44,9 @@ namespace etc {
 namespace {
 
 constexpr int kStages = 5;
-constexpr int kConsumers = 8;                     // warps, one tile row each
+constexpr int kConsumers = 4;                     // warps
+constexpr int kRowsPerWarp = 2;                   // tile rows r and r + kConsumers
+constexpr int kTileY = kConsumers * kRowsPerWarp; // 8
 constexpr int kThreads = (kConsumers + 1) * 32;   // + one producer warp
 // box extents (elements of 8 bytes)
 constexpr int kT0X = 34, kT0Y = 8;
@@ -96,7 +98,7 @@ __device__ __forceinline__ void prod_acc_f(float2 x, float w, float& s, float& e
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 5)
     k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
                     const float* __restrict__ w, float2* __restrict__ q,
                     const float2* __restrict__ T2, const float2* __restrict__ Bin,
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + kStages * kStageBytes);
   unsigned long long* empty = full + kStages;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kConsumers;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kTileY;
   const int k0 = blockIdx.z * kchunk;
   const int k1 = min(k0 + kchunk, g.n2);
   const int kend = min(k1, g.n2 - 1);  // last plane loaded (k1 supplies w above k1-1)
@@ -153,22 +155,34 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
     __syncwarp();
   } else {
-    // consumer warp: tile row r, one column per lane
-    const int r = warp, l = lane;
-    const int i = i0 + l, j = j0 + r;
-    const bool own = i < g.n0 && j < g.n1;
+    // consumer warp: tile rows r and r + kConsumers, one column per lane
+    const int l = lane;
+    const int i = i0 + l;
     const long long pl = g.plane;
-    const long long sidx = (long long)j * g.n0 + i;
-    // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
-    float fz = 0.f, fze = 0.f;
-    if (own && k0 > 0) {
-      const long long c = (long long)k0 * pl + sidx;
-      flux_f(T2[c], w[c - pl], w[c], fz, fze);
+    bool own[kRowsPerWarp];
+    long long sidx[kRowsPerWarp];
+    float fz[kRowsPerWarp], fze[kRowsPerWarp];
+    float2* pq[kRowsPerWarp];
+    int oT0[kRowsPerWarp], oT1[kRowsPerWarp], oT2[kRowsPerWarp], oW[kRowsPerWarp];
+#pragma unroll
+    for (int h = 0; h < kRowsPerWarp; ++h) {
+      const int r = warp + h * kConsumers, j = j0 + r;
+      own[h] = i < g.n0 && j < g.n1;
+      sidx[h] = (long long)j * g.n0 + i;
+      // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
+      fz[h] = 0.f;
+      fze[h] = 0.f;
+      if (own[h] && k0 > 0) {
+        const long long c = (long long)k0 * pl + sidx[h];
+        flux_f(T2[c], w[c - pl], w[c], fz[h], fze[h]);
+      }
+      // this row's element offsets inside a stage (float2 units; w: float)
+      oT0[h] = r * kT0X + l;
+      oT1[h] = r * kT1X + l;
+      oT2[h] = r * kT2X + l;
+      oW[h] = (r + 1) * kWX + l + 4;
+      pq[h] = q + (long long)k0 * pl + sidx[h];
     }
-    // this thread's element offsets inside a stage (float2 units; w: float)
-    const int oT0 = r * kT0X + l, oT1 = r * kT1X + l, oT2 = r * kT2X + l;
-    const int oW = (r + 1) * kWX + l + 4;
-    float2* pq = q + (long long)k0 * pl + sidx;
     unsigned int sc = 0, pc = 0;  // stage and parity of plane k
     bool seen = false;            // plane k's copies were seen complete (as plane k+1)
     for (int k = k0; k < k1; ++k) {
@@ -183,16 +197,17 @@ __global__ void __launch_bounds__(kThreads, 4)
         *vfailed = 1;
         break;
       }
-      if (own) {
-        const unsigned char* sg = smem + sc * kStageBytes;
-        const float2* sT0 = reinterpret_cast<const float2*>(sg) + oT0;
-        const float2* sT1 = reinterpret_cast<const float2*>(sg + kOffT1) + oT1;
-        const float2* sT2 = reinterpret_cast<const float2*>(sg + kOffT2) + oT2;
-        const float* sW = reinterpret_cast<const float*>(sg + kOffW) + oW;
+      const unsigned char* sg = smem + sc * kStageBytes;
+      const float* sWn = reinterpret_cast<const float*>(smem + sn * kStageBytes + kOffW);
+#pragma unroll
+      for (int h = 0; h < kRowsPerWarp; ++h) {
+        if (!own[h]) continue;
+        const float2* sT0 = reinterpret_cast<const float2*>(sg) + oT0[h];
+        const float2* sT1 = reinterpret_cast<const float2*>(sg + kOffT1) + oT1[h];
+        const float2* sT2 = reinterpret_cast<const float2*>(sg + kOffT2) + oT2[h];
+        const float* sW = reinterpret_cast<const float*>(sg + kOffW) + oW[h];
         const float wc = sW[0];
-        const float wp =
-            k + 1 <= kend ? reinterpret_cast<const float*>(smem + sn * kStageBytes + kOffW)[oW]
-                          : wc;
+        const float wp = k + 1 <= kend ? sWn[oW[h]] : wc;
         float sv, ev, p, pe;
         flux_f(sT0[0], wc, sW[-1], sv, ev);
         flux_f(sT0[1], wc, sW[1], p, pe);
@@ -201,20 +216,20 @@ __global__ void __launch_bounds__(kThreads, 4)
         acc_(p, pe, sv, ev);
         flux_f(sT1[kT1X], wc, sW[kWX], p, pe);
         acc_(p, pe, sv, ev);
-        acc_(-fz, -fze, sv, ev);
-        flux_f(sT2[0], wc, wp, fz, fze);
-        acc_(fz, fze, sv, ev);
-        if (k == 0) prod_acc_f(Bin[sidx], wc, sv, ev);
-        if (k == g.n2 - 1) prod_acc_f(Bout[sidx], wc, sv, ev);
+        acc_(-fz[h], -fze[h], sv, ev);
+        flux_f(sT2[0], wc, wp, fz[h], fze[h]);
+        acc_(fz[h], fze[h], sv, ev);
+        if (k == 0) prod_acc_f(Bin[sidx[h]], wc, sv, ev);
+        if (k == g.n2 - 1) prod_acc_f(Bout[sidx[h]], wc, sv, ev);
         float qh, ql;
         two_sum_(sv, ev, qh, ql);
-        *pq = make_float2(qh, ql);
+        *pq[h] = make_float2(qh, ql);
         if (MODE == 1) prod_acc_f(make_float2(qh, ql), wc, ds, dc);
+        pq[h] += pl;
       }
       // the warp is done with plane k's stage (plane k-1 no longer reads it)
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + sc);
-      pq += pl;
       sc = sn;
       pc = pn;
     }
