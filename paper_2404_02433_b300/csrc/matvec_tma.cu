@@ -43,7 +43,7 @@ namespace etc {
 
 namespace {
 
-constexpr int kStages = 5;
+constexpr int kStages = 4;
 constexpr int kConsumers = 4;                     // warps
 constexpr int kRowsPerWarp = 2;                   // tile rows r and r + kConsumers
 constexpr int kTileY = kConsumers * kRowsPerWarp; // 8
@@ -98,7 +98,7 @@ __device__ __forceinline__ void prod_acc_f(float2 x, float w, float& s, float& e
 }  // namespace
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 6)
     k_matvec_df_tma(const __grid_constant__ MatvecMaps mp, Geometry g, PcgState* st,
                     const float* __restrict__ w, float2* __restrict__ q,
                     const float2* __restrict__ T2, const float2* __restrict__ Bin,
