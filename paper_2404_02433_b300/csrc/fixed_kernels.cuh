@@ -198,19 +198,26 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
         if (F::EXACT || tau + P * e < Q) st_cx(sm + (tau + P * e + Q * k2) * C + c, u[e * P + k2]);
     __syncthreads();
     const int e2 = emax - 1022 - B;
+    // only a line near the top of the range (or holding an infinity or NaN)
+    // takes the tests for the range's top
+    auto out = [&](auto satc) {
+      constexpr bool S = decltype(satc)::value;
 #pragma unroll
-    for (int e = 0; e < E; ++e)
+      for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int k2 = 0; k2 < P; ++k2) {
-        if (!F::EXACT && tau + P * e >= Q) continue;
-        const int k = tau + P * e + Q * k2;
-        i64 xa, xb;
-        fxp::untangle(u[e * P + k2], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
-        if (ok) {
-          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xa, e2);
-          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xb, e2);
+        for (int k2 = 0; k2 < P; ++k2) {
+          if (!F::EXACT && tau + P * e >= Q) continue;
+          const int k = tau + P * e + Q * k2;
+          i64 xa, xb;
+          fxp::untangle(u[e * P + k2], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
+          if (ok) {
+            col[k * n0] = (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(xa, e2);
+            col[(k ? N - k : M) * n0] = (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(xb, e2);
+          }
         }
-      }
+    };
+    if (bad || 1086 + e2 >= 2047) out(std::true_type{});
+    else out(std::false_type{});
   } else {
     // the pre-twiddle omitted 1 / (2m) = f 2^E0: a power of two goes to the
     // exponent, otherwise one more product by f (after halving: the FFT output
@@ -218,22 +225,27 @@ __device__ __forceinline__ void fx_y_body(const Blk& b, Geometry g, DctTables<do
     using FB = fxp::FxBits<M>;
     constexpr fxp::Kc kf = fxp::kc(FB::f());
     const int e2 = emax - 1022 - B + FB::E + (FB::POW2 ? -1 : 1);
-    auto out = [&](i64 y) {
-      if (bad) return fxp::nan_f64();
-      if constexpr (FB::POW2) return fxp::from_fx_hw(y, e2);
-      else return fxp::from_fx_hw(fxp::mulk(y >> 1, kf), e2);
-    };
+    auto outs = [&](auto satc) {
+      constexpr bool S = decltype(satc)::value;
+      auto out = [&](i64 y) {
+        if (S && bad) return fxp::nan_f64();
+        if constexpr (FB::POW2) return fxp::from_fx_hw<S>(y, e2);
+        else return fxp::from_fx_hw<S>(fxp::mulk(y >> 1, kf), e2);
+      };
 #pragma unroll
-    for (int e = 0; e < E; ++e)
+      for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int k2 = 0; k2 < P; ++k2) {
-        if (!F::EXACT && tau + P * e >= Q) continue;
-        const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
-        if (ok) {
-          col[vrow<N>(2 * j) * n0] = out(u[e * P + k2].x);
-          col[vrow<N>(2 * j + 1) * n0] = out(u[e * P + k2].y);
+        for (int k2 = 0; k2 < P; ++k2) {
+          if (!F::EXACT && tau + P * e >= Q) continue;
+          const int j = tau + P * e + Q * k2;  // z_j = (v_{2j}, v_{2j+1})
+          if (ok) {
+            col[vrow<N>(2 * j) * n0] = out(u[e * P + k2].x);
+            col[vrow<N>(2 * j + 1) * n0] = out(u[e * P + k2].y);
+          }
         }
-      }
+    };
+    if (bad || 1086 + e2 >= 2047) outs(std::true_type{});
+    else outs(std::false_type{});
   }
 }
 template <int N, int INV>
@@ -391,33 +403,44 @@ __device__ __forceinline__ void fx_y3_body(const Blk& b, Geometry g, DctTables<d
       for (int kb = 0; kb < P2; ++kb) st_cx(sm + kof(r, kb) * C + c, u[r * P2 + kb]);
     __syncthreads();
     const int e2 = emax - 1022 - B;
+    auto out = [&](auto satc) {  // the tests for the range's top near it only
+      constexpr bool S = decltype(satc)::value;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int kb = 0; kb < P2; ++kb) {
-        const int k = kof(r, kb);
-        i64 xa, xb;
-        fxp::untangle(u[r * P2 + kb], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
-        if (ok) {
-          col[k * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xa, e2);
-          col[(k ? N - k : M) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(xb, e2);
+        for (int kb = 0; kb < P2; ++kb) {
+          const int k = kof(r, kb);
+          i64 xa, xb;
+          fxp::untangle(u[r * P2 + kb], ld_cx(sm + (k ? M - k : 0) * C + c), post, k, M, xa, xb);
+          if (ok) {
+            col[k * n0] = (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(xa, e2);
+            col[(k ? N - k : M) * n0] = (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(xb, e2);
+          }
         }
-      }
+    };
+    if (bad || 1086 + e2 >= 2047) out(std::true_type{});
+    else out(std::false_type{});
   } else {
     // the pre-twiddle omitted 1 / (2m), a power of two here
     static_assert(fxp::FxBits<M>::POW2, "power-of-two lengths");
     const int e2 = emax - 1022 - B + fxp::FxBits<M>::E - 1;
+    auto out = [&](auto satc) {  // the tests for the range's top near it only
+      constexpr bool S = decltype(satc)::value;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int kb = 0; kb < P2; ++kb) {
-        const int j = kof(r, kb);  // z_j = (v_{2j}, v_{2j+1})
-        if (ok) {
-          col[vrow<N>(2 * j) * n0] = bad ? fxp::nan_f64() : fxp::from_fx_hw(u[r * P2 + kb].x, e2);
-          col[vrow<N>(2 * j + 1) * n0] =
-              bad ? fxp::nan_f64() : fxp::from_fx_hw(u[r * P2 + kb].y, e2);
+        for (int kb = 0; kb < P2; ++kb) {
+          const int j = kof(r, kb);  // z_j = (v_{2j}, v_{2j+1})
+          if (ok) {
+            col[vrow<N>(2 * j) * n0] =
+                (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(u[r * P2 + kb].x, e2);
+            col[vrow<N>(2 * j + 1) * n0] =
+                (S && bad) ? fxp::nan_f64() : fxp::from_fx_hw<S>(u[r * P2 + kb].y, e2);
+          }
         }
-      }
+    };
+    if (bad || 1086 + e2 >= 2047) out(std::true_type{});
+    else out(std::false_type{});
   }
 }
 template <int N, int INV>
@@ -553,19 +576,28 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
   const int4* post = tb.fxq + fxp::fx_off_post(M);
   const bool bad = emax == 2047;  // an infinity or NaN in the row
   const int e2 = emax - 1022 - B;
+  // |Y| < 2^63 puts an output's biased exponent at most at 1086 + e2: only a
+  // row whose largest element lies within 2^(64 - B) of the top of the range
+  // (and a row holding an infinity or NaN) takes the tests for the range's top
+  const bool sat = bad || 1086 + e2 >= 2047;
+  auto out = [&](auto satc) {
+    constexpr bool S = decltype(satc)::value;
 #pragma unroll
-  for (int e = 0; e < E; ++e)
+    for (int e = 0; e < E; ++e)
 #pragma unroll
-    for (int k2 = 0; k2 < P; ++k2) {
-      if (!F::EXACT && tau + P * e >= Q) continue;
-      const int k = tau + P * e + Q * k2;
-      i64 xa, xb;
-      fxp::untangle(u[e * P + k2], ld_cx(A + l * RS + (k ? M - k : 0)), post, k, M, xa, xb);
-      if (row < nrows) {
-        t[row * N + k] = bad ? fxp::nan_f64() : fxp::from_fx(xa, e2);
-        t[row * N + (k ? N - k : M)] = bad ? fxp::nan_f64() : fxp::from_fx(xb, e2);
+      for (int k2 = 0; k2 < P; ++k2) {
+        if (!F::EXACT && tau + P * e >= Q) continue;
+        const int k = tau + P * e + Q * k2;
+        i64 xa, xb;
+        fxp::untangle(u[e * P + k2], ld_cx(A + l * RS + (k ? M - k : 0)), post, k, M, xa, xb);
+        if (row < nrows) {
+          t[row * N + k] = (S && bad) ? fxp::nan_f64() : fxp::from_fx<S>(xa, e2);
+          t[row * N + (k ? N - k : M)] = (S && bad) ? fxp::nan_f64() : fxp::from_fx<S>(xb, e2);
+        }
       }
-    }
+  };
+  if (sat) out(std::true_type{});
+  else out(std::false_type{});
   if (MODE != 2) fwd_x_residual_tail<MODE>(acc, st, partials, rtol2, sh, &flag, par, false, b);
 }
 template <int N, int MODE, int NT>
@@ -684,9 +716,17 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
 #pragma unroll
     for (int k2 = 0; k2 < P; ++k2)
       if (F::EXACT || tau + P * e < Q) st_cx(A + l * RS + tau + P * e + Q * k2, u[e * P + k2]);
-  // the row's exponent for the output pass, which walks other rows
+  // the row's exponent for the output pass, which walks other rows; rows near
+  // the top of the range (or holding an infinity or NaN) put the block on the
+  // output path with the tests for the range's top
   __shared__ int erow[NT / P];
-  if (tau == 0) erow[l] = emax;
+  __shared__ int anysat;
+  if (threadIdx.x == 0) anysat = 0;
+  __syncthreads();
+  if (tau == 0) {
+    erow[l] = emax;
+    if (emax == 2047 || 1086 + emax - 1022 - B >= 2047) anysat = 1;
+  }
   __syncthreads();
   // scale = 1 / (kappa_ref^z 2m): the pre-twiddle omitted 1 / (2m)
   const double scale = 1.0 / ((kd ? kd[2] : kz_host) * (2.0 * M));
@@ -697,33 +737,38 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
   // (8 measured slower: 1.47 -> 1.60 ms at 512^3)
   constexpr int G = NQ % 4 == 0 ? 4 : NQ % 2 == 0 ? 2 : 1;
   static_assert(NQ % G == 0, "pair groups");
+  auto out = [&](auto satc) {
+    constexpr bool S = decltype(satc)::value;
 #pragma unroll 1
-  for (int r0 = 0; r0 < NQ; r0 += G) {
-    VPair<double> wo[G];
+    for (int r0 = 0; r0 < NQ; r0 += G) {
+      VPair<double> wo[G];
 #pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int p = threadIdx.x + NT * (r0 + u);
-      const long long row = row0 + p / M;
-      wo[u].a = wo[u].b = 0.0;
-      if (MODE == 2 && row < nrows) wo[u] = ld_pair(z + row * N + 2 * (p % M));
-    }
+      for (int u = 0; u < G; ++u) {
+        const int p = threadIdx.x + NT * (r0 + u);
+        const long long row = row0 + p / M;
+        wo[u].a = wo[u].b = 0.0;
+        if (MODE == 2 && row < nrows) wo[u] = ld_pair(z + row * N + 2 * (p % M));
+      }
 #pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int p = threadIdx.x + NT * (r0 + u);
-      const int lr = p / M, i2 = p % M;
-      const long long row = row0 + lr;
-      if (row >= nrows) continue;
-      const long long c = row * N + 2 * i2;
-      const int er = erow[lr];
-      const int e2 = er + EOFF;
-      // element 2 i2 <- v_{i2}; element 2 i2 + 1 <- v_{n-1-i2}
-      double u0 = fxp::from_fx_hw(Ai[lr * 2 * RS + i2], e2) * scale;
-      double u1 = fxp::from_fx_hw(Ai[lr * 2 * RS + N - 1 - i2], e2) * scale;
-      if (er == 2047) u0 = u1 = fxp::nan_f64();
-      if (MODE == 2) st_pair(z + c, fma(beta, wo[u].a, u0), fma(beta, wo[u].b, u1));
-      else st_pair(z + c, u0, u1);
+      for (int u = 0; u < G; ++u) {
+        const int p = threadIdx.x + NT * (r0 + u);
+        const int lr = p / M, i2 = p % M;
+        const long long row = row0 + lr;
+        if (row >= nrows) continue;
+        const long long c = row * N + 2 * i2;
+        const int er = erow[lr];
+        const int e2 = er + EOFF;
+        // element 2 i2 <- v_{i2}; element 2 i2 + 1 <- v_{n-1-i2}
+        double u0 = fxp::from_fx_hw<S>(Ai[lr * 2 * RS + i2], e2) * scale;
+        double u1 = fxp::from_fx_hw<S>(Ai[lr * 2 * RS + N - 1 - i2], e2) * scale;
+        if (S && er == 2047) u0 = u1 = fxp::nan_f64();
+        if (MODE == 2) st_pair(z + c, fma(beta, wo[u].a, u0), fma(beta, wo[u].b, u1));
+        else st_pair(z + c, u0, u1);
+      }
     }
-  }
+  };
+  if (anysat) out(std::true_type{});
+  else out(std::false_type{});
 }
 template <int N, int MODE, int NT>
 __global__ void __launch_bounds__(NT)

@@ -299,7 +299,10 @@ __device__ __forceinline__ i64 to_fx(double v, int emax) {
   return (int)hi < 0 ? -X : X;
 }
 // Y 2^e2 rounded to the nearest binary64 (ties to even), |Y| < 2^63; 0 below
-// the normal range, an infinity above it.
+// the normal range, an infinity above it.  The exponent field comes out at
+// most 1086 + e2 (leading one at bit 62, plus a rounding carry): SAT false
+// drops the test for the top of the range, for callers with 1086 + e2 < 2047.
+template <bool SAT = true>
 __device__ __forceinline__ double from_fx(i64 Y, int e2) {
   const u64 sgn = (u64)(Y >> 63);
   u64 a = ((u64)Y ^ sgn) - sgn;
@@ -309,8 +312,8 @@ __device__ __forceinline__ double from_fx(i64 Y, int e2) {
   const int be = 1086 - lz + e2;  // biased exponent of the leading one
   // mant carries the leading one: added onto the field be - 1 it gives be (be + 1
   // when the rounding reached 2^53)
-  const u64 bits = be >= 2047 ? 0x7ff0000000000000ull + (sgn << 63)
-                               : ((u64)(be - 1) << 52) + mant + (sgn << 63);
+  const u64 bits = (SAT && be >= 2047) ? 0x7ff0000000000000ull + (sgn << 63)
+                                       : ((u64)(be - 1) << 52) + mant + (sgn << 63);
   return (lz == 64 || be <= 0) ? 0.0 : __longlong_as_double((i64)bits);
 }
 __device__ __forceinline__ double nan_f64() { return __longlong_as_double(0x7ff8000000000000LL); }
@@ -329,12 +332,14 @@ __device__ __forceinline__ i64 to_fx_hw(double v, int emax) {
   if (e == 0 || e + sc <= 0) return 0;
   return __double2ll_rn(__hiloint2double(hi + (sc << 20), lo));
 }
+// (SAT false: without the test for the top of the range, for 1086 + e2 < 2047)
+template <bool SAT = true>
 __device__ __forceinline__ double from_fx_hw(i64 Y, int e2) {
   const double d = __ll2double_rn(Y);
   const int hi = __double2hiint(d), lo = __double2loint(d);
   const int e = (hi >> 20) & 0x7ff;
   if (e == 0 || e + e2 <= 0) return 0.0;
-  if (e + e2 >= 2047) return __hiloint2double((hi & (int)0x80000000) | 0x7ff00000, 0);
+  if (SAT && e + e2 >= 2047) return __hiloint2double((hi & (int)0x80000000) | 0x7ff00000, 0);
   return __hiloint2double(hi + (e2 << 20), lo);
 }
 
