@@ -548,9 +548,15 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
       em = max(em, max(fxp::bexp(dv[s].x), fxp::bexp(dv[s].y)));
     }
     emax = fx_lane_max<P>(em);
+    if (emax >= 10 + B) {  // zeros and subnormals of the row round to 0 anyway
 #pragma unroll
-    for (int s = 0; s < Q; ++s)
-      v[s] = fxp::mk(fxp::to_fx<B>(dv[s].x, emax), fxp::to_fx<B>(dv[s].y, emax));
+      for (int s = 0; s < Q; ++s)
+        v[s] = fxp::mk(fxp::to_fx<B, false>(dv[s].x, emax), fxp::to_fx<B, false>(dv[s].y, emax));
+    } else {
+#pragma unroll
+      for (int s = 0; s < Q; ++s)
+        v[s] = fxp::mk(fxp::to_fx<B>(dv[s].x, emax), fxp::to_fx<B>(dv[s].y, emax));
+    }
   }
   fx_four_step_a<N, -1>(v, tb.fxq, tau);
   __syncthreads();  // the row is read before the transpose overwrites it
@@ -675,17 +681,22 @@ __device__ __forceinline__ void fx_inv_x_body(const Blk& b, Geometry g, DctTable
   const int4* pre = tb.fxq + fxp::fx_off_pre(M);
   // V_k = e^{i t_k} (X_k - i X_{n-k}) for the thread's own k = tau + P s, and V_m
   cx vv[Q];
-#pragma unroll
-  for (int s = 0; s < Q; ++s) {
-    const int j = tau + P * s;
-    vv[s] = fxp::inv_v(pre, j, fxp::to_fx<B>(X[j], emax),
-                       j ? fxp::to_fx<B>(X[N - j], emax) : 0);
-  }
   cx vm = fxp::mk(0, 0);
-  if (tau == 0) {
-    const i64 xm = fxp::to_fx<B>(X[M], emax);
-    vm = fxp::inv_v(pre, M, xm, xm);
-  }
+  auto in = [&](auto lowc) {  // LOW false: zeros and subnormals round to 0 anyway
+    constexpr bool LOW = decltype(lowc)::value;
+#pragma unroll
+    for (int s = 0; s < Q; ++s) {
+      const int j = tau + P * s;
+      vv[s] = fxp::inv_v(pre, j, fxp::to_fx<B, LOW>(X[j], emax),
+                         j ? fxp::to_fx<B, LOW>(X[N - j], emax) : 0);
+    }
+    if (tau == 0) {
+      const i64 xm = fxp::to_fx<B, LOW>(X[M], emax);
+      vm = fxp::inv_v(pre, M, xm, xm);
+    }
+  };
+  if (emax >= 10 + B) in(std::false_type{});
+  else in(std::true_type{});
   __syncthreads();  // the staged rows are read before V overwrites them
 #pragma unroll
   for (int s = 0; s < Q; ++s) st_cx(A + l * RS + tau + P * s, vv[s]);

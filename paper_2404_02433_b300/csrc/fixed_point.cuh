@@ -286,14 +286,16 @@ __device__ __forceinline__ int bexp(double v) {
 // Scale exponent of a line whose largest exponent field is emax, with B bits
 // kept for its largest element: X = v 2^S, S = 1022 - emax + B.  The binary64
 // value +-mant 2^(e - 1075) becomes mant 2^(e - emax - (53 - B)), rounded to
-// nearest (ties up), with integer operations only.
-template <int B>
+// nearest (ties up), with integer operations only.  LOW false drops the cases
+// of zeros and subnormals, for lines with emax >= 10 + B: the shift of such a
+// value is then at least 63 and it comes out 0 either way.
+template <int B, bool LOW = true>
 __device__ __forceinline__ i64 to_fx(double v, int emax) {
   static_assert(B <= 53, "at most the binary64 significand");
   const unsigned int hi = (unsigned int)__double2hiint(v), lo = (unsigned int)__double2loint(v);
   const int e = (int)((hi >> 20) & 0x7ffu);
-  const u64 mant = ((u64)((hi & 0xfffffu) | (e ? 0x100000u : 0u)) << 32) | lo;
-  int sh = emax - (e > 1 ? e : 1) + (53 - B);
+  const u64 mant = ((u64)((hi & 0xfffffu) | ((!LOW || e) ? 0x100000u : 0u)) << 32) | lo;
+  int sh = emax - (LOW ? (e > 1 ? e : 1) : e) + (53 - B);
   sh = sh < 63 ? sh : 63;
   const i64 X = (i64)((((mant << 1) >> sh) + 1ull) >> 1);
   return (int)hi < 0 ? -X : X;
