@@ -516,6 +516,13 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   const int eb = (int)sizeof(R);
   const long long nrows = (long long)g.n1 * g.n2;
   double bx = INFINITY, bi = INFINITY, by = INFINITY;
+  // an axis-1 tile serves the forward and the backward pass: both are timed
+  auto time_y = [&](int T) {
+    return time_launch(h->stream, e0, e1,
+                       [&] { return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, T); }) +
+           time_launch(h->stream, e0, e1,
+                       [&] { return launch_dct_y<R>(g, p1, h->st, t, 1, 0, h->stream, T); });
+  };
   // tiles -1 and -2: the register-resident kernels (blocks of 256 and 128
   // threads), where the line length allows them
   if (fast_x_ok<R>(g, p0, h->r, h->z64, nullptr, nullptr)) {
@@ -533,9 +540,7 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
     }
   }
   if (g.n1 > 1 && fast_y_ok<R>(g, p1)) {
-    by = time_launch(h->stream, e0, e1, [&] {
-      return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -1);
-    });
+    by = time_y(-1);
     best.y = -1;
   }
   if constexpr (sizeof(R) == 8) {
@@ -556,15 +561,11 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
       }
     }
     if (g.n1 > 1 && fx_y_ok(g, p1)) {
-      const double ty = time_launch(h->stream, e0, e1, [&] {
-        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -3);
-      });
+      const double ty = time_y(-3);
       if (ty < by) { by = ty; best.y = -3; }
     }
     if (g.n1 > 1 && fx_y3_ok(g, p1)) {
-      const double ty = time_launch(h->stream, e0, e1, [&] {
-        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, -4);
-      });
+      const double ty = time_y(-4);
       if (ty < by) { by = ty; best.y = -4; }
     }
   }
@@ -584,9 +585,7 @@ Tiles tune_tiles(etc_rve* h, const Geometry& g, R* t, const DctPlan<R>& p0, cons
   if (g.n1 > 1)
     for (int TI = 1; TI <= 32; TI *= 2) {
       if (TI > g.n0 || smem_y_bytes(g.n1, TI, eb) > smem_limit()) break;
-      const double ty = time_launch(h->stream, e0, e1, [&] {
-        return launch_dct_y<R>(g, p1, h->st, t, 0, 0, h->stream, TI);
-      });
+      const double ty = time_y(TI);
       if (ty < by) { by = ty; best.y = TI; }
     }
   return best;
