@@ -108,6 +108,11 @@ def test_fixed_point_dynamic_range_per_line(tiles, monkeypatch):
     u = rng.standard_normal(shape)
     u[1, :, :5] *= 1e-12  # a line with a wide range inside it
     u *= scales[:, None, None]
+    # exact zeros and subnormals inside rows and columns of normal range (the
+    # conversions' short path for such lines, against their full path)
+    u[1, :, 7:9] = 0.0
+    u[1, 20:22, :] = 0.0
+    u[1, 3, 10], u[1, 30, 40], u[3, 5, 6], u[3, 6, 6] = 5e-324, -2.2e-310, 1e-320, -0.0
     ref = O.dct_forward(O.dct_forward(u, 2), 1)
     out = torch.empty(shape, dtype=torch.float64, device="cuda")
     B.etc_dct_planes(rve.h, 2, 0, dev(u), out)
