@@ -461,7 +461,7 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
                                               double* __restrict__ r,
                                               const double* __restrict__ rin,
                                               double* __restrict__ t, double* partials, int par,
-                                              double rtol2) {
+                                              double rtol2, int pf) {
   using F = FxFast<N>;
   using fxp::cx;
   using fxp::i64;
@@ -477,6 +477,18 @@ __device__ __forceinline__ void fx_fwd_x_body(const Blk& b, Geometry g, DctTable
   const long long nrows = (long long)g.n1 * g.n2;
   const long long row0 = (long long)b.x * L;
   const double alpha = (MODE == 1) ? st->alpha[par] : 0.0;
+  if (MODE == 1 && pf > 0 && threadIdx.x == 0) {
+    // the rows of the block pf blocks ahead go to L2 while this block computes
+    const long long pr = row0 + (long long)pf * L;
+    if (pr < nrows) {
+      const unsigned int bytes = (unsigned int)(min((long long)L, nrows - pr) * N * 8);
+      const long long c = pr * N;
+      l2_prefetch(r + c, bytes);
+      l2_prefetch(q + c, bytes);
+      l2_prefetch(x + c, bytes);
+      l2_prefetch(w + c, bytes);
+    }
+  }
   double acc = 0.0;
   constexpr int NP = L * M;  // element pairs of the block
   // pairs per thread whose loads are in flight together (4: 1.95 -> 1.80 ms at
@@ -611,8 +623,8 @@ __global__ void __launch_bounds__(NT)
     k_fx_fwd_x(Geometry g, DctTables<double> tb, PcgState* st, double* __restrict__ x,
                const double* __restrict__ w, const double* __restrict__ q,
                double* __restrict__ r, const double* __restrict__ rin, double* __restrict__ t,
-               double* partials, int par, double rtol2) {
-  fx_fwd_x_body<N, MODE, NT>(hw_blk(), g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+               double* partials, int par, double rtol2, int pf) {
+  fx_fwd_x_body<N, MODE, NT>(hw_blk(), g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, pf);
 }
 
 // ---------------------------------------------------------------- axis 0, backward
@@ -798,7 +810,7 @@ __global__ void __launch_bounds__(NT)
   queue_loop(q, slot, nb, [&](int sv, unsigned int l) {
     const BatchSolve& a = bs[sv];
     fx_fwd_x_body<N, 1, NT>(item_blk(l, nb, 1, 1), g, tb, a.st, a.x, a.w, a.q, a.r, nullptr,
-                            a.t64, a.partials, par, 0.0);
+                            a.t64, a.partials, par, 0.0, 0);
   });
 }
 template <int N, int INV>
@@ -834,12 +846,19 @@ cudaError_t fx_fwd_x_nt(const Geometry& g, const DctTables<double>& tb, PcgState
   const long long nrows = (long long)g.n1 * g.n2;
   const unsigned int nb = (unsigned int)((nrows + L - 1) / L);
   const size_t sm = fx_x_smem<N, NT>();
+  // PCG update: the block's x, w, r, q rows about 3 MB ahead go to L2
+  // (512^3: 1.77 -> 1.73 ms at 3 MB; 9 MB and more ahead slower than none),
+  // when the grid is more than two waves
+  static const int resident = resident_blocks(k_fx_fwd_x<N, 1, NT>, NT, sm);
+  const int pf = resident > 0 && (long long)nb > 2LL * resident
+                     ? max(1, (int)((3u << 20) / (4u * L * N * 8u)))
+                     : 0;
   if (mode == 0)
-    k_fx_fwd_x<N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+    k_fx_fwd_x<N, 0, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, pf);
   else if (mode == 1)
-    k_fx_fwd_x<N, 1, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+    k_fx_fwd_x<N, 1, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, pf);
   else
-    k_fx_fwd_x<N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2);
+    k_fx_fwd_x<N, 2, NT><<<nb, NT, sm, s>>>(g, tb, st, x, w, q, r, rin, t, partials, par, rtol2, pf);
   return cudaGetLastError();
 }
 template <int N>
