@@ -294,6 +294,15 @@ etc_status etc_loading_dims(const etc_rve* rve, int dir, int* dims3);
 /* q = A w: the TPFA operator of Eq. (scaled bilinear forms) for direction dir. */
 etc_status etc_apply_operator(etc_rve* rve, int dir, const double* w, double* q);
 
+/* q = A w by the double-float operator of the mixed path (ETC_PREC_MIXED): w
+ * is FP32 (n0*n1*n2 floats, the search direction's storage there), q is
+ * returned as the FP64 value of each double-float pair (hi + lo, exact), and,
+ * if wq is not NULL, *wq = w.q as that kernel's reduction forms it (the
+ * denominator of alpha in Algorithm 1).  It runs the kernel a mixed solve of
+ * dir runs (the bulk-tensor form where n0 is a multiple of 4).  Uses the
+ * handle's work buffers; synchronises the handle's stream. */
+etc_status etc_apply_operator_df(etc_rve* rve, int dir, const float* w, double* q, double* wq);
+
 /* z = A_ref^{-1} r by Algorithm 3 with the kref that the next solve of dir uses;
  * precision = ETC_PREC_FP64, or one of the mixed forms (FP32 transforms and
  * solves: the kernels of the flexible PCG's initial apply, including the

@@ -23,7 +23,8 @@ ETC_INIT_ZERO, ETC_INIT_LINEAR = 0, 1
 EXPORTED = (
     "etc_default_opts", "etc_create_rve", "etc_destroy_rve", "etc_set_reference_params",
     "etc_solve_direction", "etc_get_solution", "etc_effective_tensor", "etc_loading_dims",
-    "etc_apply_operator", "etc_apply_preconditioner", "etc_dct_planes", "etc_status_string",
+    "etc_apply_operator", "etc_apply_operator_df", "etc_apply_preconditioner", "etc_dct_planes",
+    "etc_status_string",
     "etc_last_error", "etc_profile_iteration", "etc_transform_tiles", "etc_kernel_launches",
     "etc_apply_reference_inverse_static", "etc_convert_check", "etc_gradient",
     "etc_batch_create", "etc_batch_run", "etc_batch_destroy", "etc_effective_tensor_batch",
@@ -82,6 +83,7 @@ def load_library(path: str | None = None):
         "etc_effective_tensor": ([vp, POINTER(EtcOpts), dp, POINTER(EtcInfo)], c_int),
         "etc_loading_dims": ([vp, c_int, ip], c_int),
         "etc_apply_operator": ([vp, c_int, vp, vp], c_int),
+        "etc_apply_operator_df": ([vp, c_int, vp, vp, POINTER(c_double)], c_int),
         "etc_apply_preconditioner": ([vp, c_int, c_int, vp, vp], c_int),
         "etc_dct_planes": ([vp, c_int, c_int, vp, vp], c_int),
         "etc_status_string": ([c_int], ctypes.c_char_p),
@@ -202,6 +204,13 @@ def etc_loading_dims(h, direction):
 
 def etc_apply_operator(h, direction, w, q):
     return _check(load_library().etc_apply_operator(h, direction, _ptr(w), _ptr(q)), h)
+
+
+def etc_apply_operator_df(h, direction, w, q):
+    """q = A w by the mixed path's double-float operator (w FP32, q FP64); returns w.q."""
+    wq = c_double()
+    _check(load_library().etc_apply_operator_df(h, direction, _ptr(w), _ptr(q), byref(wq)), h)
+    return wq.value
 
 
 def etc_apply_preconditioner(h, direction, precision, r, z):

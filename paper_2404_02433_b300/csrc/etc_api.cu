@@ -1595,6 +1595,36 @@ etc_status etc_apply_operator(etc_rve* h, int dir, const double* w, double* q) {
   return ETC_OK;
 }
 
+etc_status etc_apply_operator_df(etc_rve* h, int dir, const float* w, double* q, double* wq) {
+  if (!h || !w || !q) return ETC_EINVAL;
+  etc_status s = check_dir(h, dir);
+  if (s != ETC_OK) return s;
+  s = setup_faces(h, dir);
+  if (s != ETC_OK) return s;
+  const Geometry g = geom_of(h, dir);
+  // the kernel's bulk-tensor map reads the handle's guarded FP32 direction
+  CK(cudaMemcpyAsync(h->wf, w, (size_t)g.n * sizeof(float), cudaMemcpyDeviceToDevice,
+                     h->stream));
+  CK(launch_state_reset(h->st, 1, h->stream));  // rho = 0: alpha is not used here
+  const int mode = wq ? 1 : 0;
+  if (h->frame_dir >= 0 && h->mv_tma[h->frame_dir])
+    CK(launch_matvec_df_tma(g, h->mv_maps[h->frame_dir], h->st, h->wf, df(h->q), h->Tdf[2],
+                            h->Bdf, h->partials, 0, mode, h->stream, h->tma_tx_extra));
+  else
+    CK(launch_matvec_df(g, h->st, h->wf, df(h->q), h->Tdf[0], h->Tdf[1], h->Tdf[2], h->Bdf,
+                        h->partials, 0, mode, h->stream));
+  // pairs to FP64 in place (no pending x step after the reset), then out
+  CK(launch_finish_x(g, h->st, h->q, nullptr, h->wf, 1, h->stream));
+  CK(cudaMemcpyAsync(q, h->q, (size_t)g.n * sizeof(double), cudaMemcpyDeviceToDevice,
+                     h->stream));
+  if (wq)
+    CK(cudaMemcpyAsync(&h->st_host->dq, &h->st->dq, sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (wq) *wq = h->st_host->dq;
+  return ETC_OK;
+}
+
 etc_status etc_apply_preconditioner(etc_rve* h, int dir, int prec, const double* r, double* z) {
   if (!h || !r || !z) return ETC_EINVAL;
   etc_status s = check_dir(h, dir);

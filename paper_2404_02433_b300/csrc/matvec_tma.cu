@@ -17,7 +17,7 @@
 //                                   16-byte aligned)
 // Copies that reach outside the box are filled with zeros by the hardware,
 // which are exactly the Neumann faces (T = 0) and harmless finite neighbours.
-// The block is warp-specialised: 4 consumer warps (two tile rows each) and one
+// The block is warp-specialised: 4 consumer warps (two adjacent tile rows each) and one
 // producer warp.  Each stage has a "full" mbarrier (completed by the copies'
 // transaction bytes) and an "empty" one (one arrival per consumer warp).  The
 // producer issues plane k into its stage once the consumers have released the
@@ -45,7 +45,7 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr int kConsumers = 4;                     // warps
-constexpr int kRowsPerWarp = 2;                   // tile rows r and r + kConsumers
+constexpr int kRowsPerWarp = 2;                   // adjacent tile rows 2w and 2w + 1
 constexpr int kTileY = kConsumers * kRowsPerWarp; // 8
 constexpr int kThreads = (kConsumers + 1) * 32;   // + one producer warp
 // box extents (elements of 8 bytes)
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     int oT0[kRowsPerWarp], oT1[kRowsPerWarp], oT2[kRowsPerWarp], oW[kRowsPerWarp];
 #pragma unroll
     for (int h = 0; h < kRowsPerWarp; ++h) {
-      const int r = warp + h * kConsumers, j = j0 + r;
+      const int r = kRowsPerWarp * warp + h, j = j0 + r;
       own[h] = i < g.n0 && j < g.n1;
       sidx[h] = (long long)j * g.n0 + i;
       // flux through the face below plane k0: T2[k0] (w_{k0-1} - w_{k0})
@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 6)
       const unsigned char* sg = smem + sc * kStageBytes;
       const float* sWn = reinterpret_cast<const float*>(smem + sn * kStageBytes + kOffW);
 #pragma unroll
+      float yp = 0.f, ype = 0.f;  // flux through the face between this warp's rows
       for (int h = 0; h < kRowsPerWarp; ++h) {
         if (!own[h]) continue;
         const float2* sT0 = reinterpret_cast<const float2*>(sg) + oT0[h];
@@ -212,9 +213,18 @@ __global__ void __launch_bounds__(kThreads, 6)
         flux_f(sT0[0], wc, sW[-1], sv, ev);
         flux_f(sT0[1], wc, sW[1], p, pe);
         acc_(p, pe, sv, ev);
-        flux_f(sT1[0], wc, sW[-kWX], p, pe);
+        // the minus y face of the second row is the plus y face of the first,
+        // whose flux (exact differences, so exactly negated) is reused
+        if (h == 0) {
+          flux_f(sT1[0], wc, sW[-kWX], p, pe);
+        } else {
+          p = -yp;
+          pe = -ype;
+        }
         acc_(p, pe, sv, ev);
         flux_f(sT1[kT1X], wc, sW[kWX], p, pe);
+        yp = p;
+        ype = pe;
         acc_(p, pe, sv, ev);
         acc_(-fz[h], -fze[h], sv, ev);
         flux_f(sT2[0], wc, wp, fz[h], fze[h]);

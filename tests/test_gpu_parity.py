@@ -62,6 +62,32 @@ def test_operator_matches_oracle(shape, direction):
     assert relmax(host(q), O.apply_operator(f, w)) < 1e-12
 
 
+# The mixed path's double-float operator (FP32 search direction, faces as
+# double-float pairs, the face-difference form summed by Sum2): both kernels,
+# the bulk-tensor one (n0 a multiple of 4 in the loading frame) and the plain
+# one, against the oracle's FP64 operator on the same FP32 w; and w.q, the
+# denominator of alpha, as the kernel reduces it.
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 10, 30), (11, 13, 17), (5, 7, 1),
+                                   (8, 64, 96), (40, 36, 48)])
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_double_float_operator_matches_oracle(shape, direction):
+    rng = np.random.default_rng(hash((shape, direction, "df")) % 2**32)
+    kx, ky, kz = (rng.uniform(0.1, 10.0, shape) for _ in range(3))
+    lengths = (1.0, 1.3, 0.7)
+    rve = make(kx, ky, kz, lengths)
+    f, fshape = oracle_faces(kx, ky, kz, lengths, direction)
+    w = rng.standard_normal(fshape).astype(np.float32)
+    w64 = w.astype(np.float64)
+    q = torch.empty(fshape, dtype=torch.float64, device="cuda")
+    wq = B.etc_apply_operator_df(rve.h, direction, torch.from_numpy(w).cuda(), q)
+    qo = O.apply_operator(f, w64)
+    # faces rounded to 48-bit pairs, exact differences, Sum2: a few units of 2^-47
+    assert relmax(host(q), qo) < 1e-12, (shape, direction)
+    wqo = float(np.dot(w64.ravel(), qo.ravel()))
+    assert wqo > 0 and abs(wq - wqo) <= 1e-11 * wqo, (wq, wqo)
+    rve.close()
+
+
 @pytest.mark.parametrize("shape", SHAPES + [(8, 64, 96), (4, 160, 192), (3, 200, 50),
                                    (2, 1024, 32), (2, 96, 384)])
 def test_dct_planes_match_oracle(shape):
