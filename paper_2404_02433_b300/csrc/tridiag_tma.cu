@@ -15,6 +15,12 @@
 // (bounded) for the chunk in use, a block barrier hands it to every thread and
 // frees the stage of the previous chunk.  Copies beyond the plane (the last
 // block) or below n2 (the last chunk) are zero-filled.
+// Two shapes of the ring, chosen per launch: 4 stages with 6 blocks per SM,
+// or 3 stages with 8 blocks per SM (at most 64 registers).  The launcher takes
+// the one that runs the grid in fewer waves of resident blocks, and on a tie
+// the deeper ring: measured at 512^3 (2048 blocks) 0.428 -> 0.403 ms with 3
+// stages; at 128^3..256^3 (under one wave either way) 4 stages were 3-5 %
+// faster.  Both shapes do the same arithmetic, so their results are identical.
 // Row strides of the maps are plane * 4 bytes: plane must be a multiple of 4.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -30,13 +36,13 @@ namespace {
 constexpr int kTriCols = 128;                            // columns per block
 constexpr int kTriBox = kTriCols * kTriChunk * 4;        // bytes of one r^ (or r_old) box
 constexpr int kTriStageBytes = 2 * kTriBox;              // r^ then r_old
-constexpr int kTriStages = 4;
-constexpr int kTriSmem = kTriStages * kTriStageBytes + 128 + 128;  // + barriers, + alignment
+// dynamic shared memory of a ring of `stages` stages, + barriers, + alignment
+constexpr int tri_smem(int stages) { return stages * kTriStageBytes + 128 + 128; }
 
 }  // namespace
 
-template <int MODE>
-__global__ void __launch_bounds__(kTriCols, 6)
+template <int MODE, int STAGES, int MINB>
+__global__ void __launch_bounds__(kTriCols, MINB)
     k_tridiag_tma(const __grid_constant__ CUtensorMap min_, const __grid_constant__ CUtensorMap mold,
                   Geometry g, PcgState* st, float* __restrict__ out, float2* __restrict__ ck,
                   const double* __restrict__ lam0, const double* __restrict__ lam1,
@@ -48,7 +54,7 @@ __global__ void __launch_bounds__(kTriCols, 6)
   if (st->done) return;
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   unsigned long long* bars =
-      reinterpret_cast<unsigned long long*>(smem + kTriStages * kTriStageBytes);
+      reinterpret_cast<unsigned long long*>(smem + STAGES * kTriStageBytes);
   const int n2 = g.n2;
   const int nch = (n2 + kTriChunk - 1) / kTriChunk;
   const int nuse = 2 * nch;  // chunk uses: forward 0..nch-1, backward nch-1..0
@@ -56,7 +62,7 @@ __global__ void __launch_bounds__(kTriCols, 6)
   // use u: its chunk and whether it is a backward use
   auto chunk_of = [&](int u) { return u < nch ? u : 2 * nch - 1 - u; };
   auto issue = [&](int u) {
-    const int sidx = u % kTriStages;
+    const int sidx = u % STAGES;
     unsigned char* sg = smem + sidx * kTriStageBytes;
     unsigned long long* b = bars + sidx;
     const int kb = chunk_of(u) * kTriChunk;
@@ -68,9 +74,9 @@ __global__ void __launch_bounds__(kTriCols, 6)
   if (threadIdx.x == 0) {
     failed = 0;
     tri_coef(kd, coef);
-    for (int sidx = 0; sidx < kTriStages; ++sidx) mbar_init(bars + sidx, 1);
+    for (int sidx = 0; sidx < STAGES; ++sidx) mbar_init(bars + sidx, 1);
     mbar_init_fence();
-    for (int u = 0; u < nuse && u < kTriStages - 1; ++u) issue(u);
+    for (int u = 0; u < nuse && u < STAGES - 1; ++u) issue(u);
   }
   __syncthreads();
   const long long s = s0 + threadIdx.x;
@@ -82,13 +88,13 @@ __global__ void __launch_bounds__(kTriCols, 6)
   float2 cp = make_float2(0.f, 0.f);  // checkpoint of the backward chunk in use
   int u = 0;
   for (; u < nuse; ++u) {
-    const int sidx = u % kTriStages;
-    if (threadIdx.x == 0 && !mbar_wait(bars + sidx, (unsigned int)((u / kTriStages) & 1)))
+    const int sidx = u % STAGES;
+    if (threadIdx.x == 0 && !mbar_wait(bars + sidx, (unsigned int)((u / STAGES) & 1)))
       failed = 1;
     __syncthreads();
     if (failed) break;
-    // every thread is past use u-1: its stage takes use u + kTriStages - 1
-    if (threadIdx.x == 0 && u + kTriStages - 1 < nuse) issue(u + kTriStages - 1);
+    // every thread is past use u-1: its stage takes use u + STAGES - 1
+    if (threadIdx.x == 0 && u + STAGES - 1 < nuse) issue(u + STAGES - 1);
     const float* sr = reinterpret_cast<const float*>(smem + sidx * kTriStageBytes) + threadIdx.x;
     const int ch = chunk_of(u);
     const int kb = ch * kTriChunk;
@@ -133,8 +139,8 @@ __global__ void __launch_bounds__(kTriCols, 6)
   if (failed) {
     if (threadIdx.x == 0) {
       // drain this block's copies still in flight (bounded), then report
-      for (int uu = u; uu < nuse && uu < u + kTriStages - 1; ++uu)
-        (void)mbar_wait(bars + uu % kTriStages, (unsigned int)((uu / kTriStages) & 1));
+      for (int uu = u; uu < nuse && uu < u + STAGES - 1; ++uu)
+        (void)mbar_wait(bars + uu % STAGES, (unsigned int)((uu / STAGES) & 1));
       st->status = kECUDA;
       st->done = 1;
     }
@@ -157,12 +163,25 @@ bool tridiag_tma_map(const Geometry& g, const float* buf, CUtensorMap* m) {
   return tma_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, buf, dim, stride, box);
 }
 
+namespace {
+
+// the two ring shapes: 4 stages and 6 blocks per SM, 3 stages and 8
+template <int MODE> constexpr auto kDeep = k_tridiag_tma<MODE, 4, 6>;
+template <int MODE> constexpr auto kWide = k_tridiag_tma<MODE, 3, 8>;
+
+template <typename K>
+cudaError_t set_smem(K k, int stages) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem(stages));
+}
+
+}  // namespace
+
 cudaError_t set_tridiag_tma_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_tridiag_tma<2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kTriSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tridiag_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kTriSmem);
+  cudaError_t e = set_smem(kDeep<2>, 4);
+  if (e == cudaSuccess) e = set_smem(kDeep<3>, 4);
+  if (e == cudaSuccess) e = set_smem(kWide<2>, 3);
+  if (e == cudaSuccess) e = set_smem(kWide<3>, 3);
+  return e;
 }
 
 cudaError_t launch_tridiag_tma(const Geometry& g, const CUtensorMap& min_,
@@ -171,12 +190,27 @@ cudaError_t launch_tridiag_tma(const Geometry& g, const CUtensorMap& min_,
                                double* partials, int mode, cudaStream_t s) {
   const unsigned int nb = (unsigned int)((g.plane + kTriCols - 1) / kTriCols);
   const double w4 = 4.0 / ((double)g.n0 * g.n1);
-  if (mode == 2)
-    k_tridiag_tma<2><<<nb, kTriCols, kTriSmem, s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd,
-                                                    w4, partials);
-  else
-    k_tridiag_tma<3><<<nb, kTriCols, kTriSmem, s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd,
-                                                    w4, partials);
+  // waves of resident blocks each shape needs for this grid (the shape's
+  // residency is the same for both modes)
+  static const int res_deep = resident_blocks(kDeep<2>, kTriCols, tri_smem(4));
+  static const int res_wide = resident_blocks(kWide<2>, kTriCols, tri_smem(3));
+  const long long waves_deep = res_deep > 0 ? (nb + res_deep - 1) / res_deep : 1;
+  const long long waves_wide = res_wide > 0 ? (nb + res_wide - 1) / res_wide : waves_deep;
+  if (waves_wide < waves_deep) {
+    if (mode == 2)
+      kWide<2><<<nb, kTriCols, tri_smem(3), s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd, w4,
+                                                 partials);
+    else
+      kWide<3><<<nb, kTriCols, tri_smem(3), s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd, w4,
+                                                 partials);
+  } else {
+    if (mode == 2)
+      kDeep<2><<<nb, kTriCols, tri_smem(4), s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd, w4,
+                                                 partials);
+    else
+      kDeep<3><<<nb, kTriCols, tri_smem(4), s>>>(min_, mold, g, st, out, ck, lam0, lam1, kd, w4,
+                                                 partials);
+  }
   count_launch();
   return cudaGetLastError();
 }
