@@ -1330,23 +1330,43 @@ cudaError_t launch_init(const Geometry& g, const double* Bin, const double* Bout
 }
 
 unsigned int matvec_blocks(const Geometry& g) { return grid_for(g.n, 256, 148 * 16); }
-// 32 x 8 (i, j) tiles; planes per block chosen so that there are at most
-// about 4736 blocks (32 per SM), but every tile column gets a block.
-// Planes per thread: enough blocks for 32 warps on each of the 148 SMs, but
-// at least 8 planes (a thread's first plane costs three w loads and one extra
-// face flux, which short marches do not amortise; measured 2.7x faster at
-// 128^3 than 2 planes), and 16 where that still leaves two waves of blocks.
+// 32 x 8 (i, j) tiles, each tile column split into chunks of kc planes (a
+// block's first plane costs three extra w loads and one extra face flux, which
+// short chunks do not amortise).  Three regimes, from sweeps of the chunk count
+// of the bulk-tensor kernel (6 resident blocks per SM) at 64^3 .. 512^3:
+//  * 8-plane chunks still fit in one wave of resident blocks (64^3, 96^3):
+//    kc = 8, the most blocks;
+//  * the tiles fit in one wave with chunks of at most 48 planes (128^3 ..
+//    192^3): one wave, chunks of at least 16 planes (128^3 34.0 -> 30.6 us,
+//    160^3 48.9 -> 45.4, 192^3 66.2 -> 63.1 against 8/16-plane chunks);
+//  * otherwise about 32 blocks per SM, chunks of at least 20 planes (256^3
+//    129.4 -> 123 us against 16; 512^3 keeps 128-plane chunks, within 1 % of
+//    every count from 3 to 8 chunks per column).
 dim3 matvec_df_grid(const Geometry& g, int* kchunk) {
-  const long long bx = (g.n0 + 31) / 32, by = (g.n1 + 7) / 8;
-  long long nz = 4736 / (bx * by);
-  if (nz < 1) nz = 1;
-  if (nz > g.n2) nz = g.n2;
-  long long kc = (g.n2 + nz - 1) / nz;
-  if (kc < 8) kc = 8;
-  if (kc < 16 && bx * by * ((g.n2 + 15) / 16) >= 2 * 4 * 148) kc = 16;
+  static const long long sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      (void)cudaGetLastError();
+      return 148LL;
+    }
+    return (long long)n;
+  }();
+  const long long bx = (g.n0 + 31) / 32, by = (g.n1 + 7) / 8, tiles = bx * by;
+  const long long wave = 6 * sms;  // resident blocks of the bulk-tensor kernel
+  const long long per = wave / tiles;  // chunks per tile column in one wave
+  long long kc;
+  if (tiles * ((g.n2 + 7) / 8) <= wave) {
+    kc = 8;
+  } else if (per >= 1 && (g.n2 + per - 1) / per <= 48) {
+    kc = std::max<long long>(16, (g.n2 + per - 1) / per);
+  } else {
+    const long long nz = std::max<long long>(1, 32 * sms / tiles);
+    kc = std::max<long long>(20, (g.n2 + nz - 1) / nz);
+  }
   if (kc > g.n2) kc = g.n2;
   *kchunk = (int)kc;
-  nz = (g.n2 + kc - 1) / kc;
+  const long long nz = (g.n2 + kc - 1) / kc;
   return dim3((unsigned int)bx, (unsigned int)by, (unsigned int)nz);
 }
 unsigned int matvec_df_blocks(const Geometry& g) {
