@@ -220,6 +220,32 @@ def test_preconditioner_long_loading_axis(shape, ku):
     assert relmax(host(z), zo) < 2e-5
 
 
+@pytest.mark.parametrize("shape", [
+    (1, 40, 36),    # one plane: the middle row alone
+    (2, 40, 36),    # one chunk, no bottom chain
+    (9, 24, 20),    # two chunks, the second partial
+    (17, 12, 16),   # three chunks: one more on top than below
+    (24, 8, 12),    # three full chunks
+    (33, 8, 8),     # five chunks, the last one plane
+    (65, 4, 8),
+    (9, 320, 512),  # 1280 blocks of columns: the one-ended kernels
+])
+def test_fp32_tridiagonal_forms_match_oracle(shape):
+    # Sec. 3.2 solves along the loading axis in FP32: grids that fit in one wave
+    # run the two-ended elimination (middle plane m, back-substitution outward),
+    # larger ones the one-ended sweeps; both against the oracle's Algorithm 3
+    rng = np.random.default_rng(17 + sum(shape))
+    kx, ky, kz = (rng.uniform(0.2, 5.0, shape) for _ in range(3))
+    rve = make(kx, ky, kz)
+    for ku in ([0.7, 1.9, 3.1, 0.4, 2.2], [1e-4, 3e-4, 3.0, 0.4, 2.2]):
+        rve.set_reference(2, B.ETC_REF_USER, ku)
+        r = rng.standard_normal(shape)
+        zo = O.apply_reference_inverse(r, ku)
+        z = torch.empty(shape, dtype=torch.float64, device="cuda")
+        B.etc_apply_preconditioner(rve.h, 2, B.ETC_PREC_MIXED, dev(r), z)
+        assert relmax(host(z), zo) < 2e-5, ku
+
+
 # ------------------------------------------------------------------ end to end
 def test_config_32_spheres_direction_x():
     # 32^3 two-phase random spheres (radius 3-5, fraction 0.3, 1:10), rtol 1e-10, load x
