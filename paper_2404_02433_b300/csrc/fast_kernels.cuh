@@ -192,20 +192,45 @@ __device__ __forceinline__ void fast_y_body(const Blk& b, Geometry g,
     // every input j needs X_j, X_{n-j}, X_{m-j}, X_{m+j}: stage the tile's
     // columns once (real view of the buffer, row-major over the C columns)
     R* sr = reinterpret_cast<R*>(smraw);
+    if constexpr (sizeof(R) == 4 && Q <= 16) {
+      // the thread loads rows j = tau + P s and j + m (P Q = m): X_j and
+      // X_{m+j} stay in its registers, and the staged tile supplies only
+      // X_{n-j} and X_{m-j} (half the shared-memory reads; this pass is
+      // bound by the L1/shared-memory pipe)
+      R xa[Q], xb[Q];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {  // rows tau + P s, s < 2Q, in two halves
-      R xs[Q];
+      for (int s = 0; s < Q; ++s) {
+        xa[s] = ok ? col[(tau + P * s) * n0] : (R)0;
+        xb[s] = ok ? col[(tau + P * s + M) * n0] : (R)0;
+      }
 #pragma unroll
-      for (int s = 0; s < Q; ++s) xs[s] = ok ? col[(tau + P * (s + h * Q)) * n0] : (R)0;
+      for (int s = 0; s < Q; ++s) {
+        sr[(tau + P * s) * C + c] = xa[s];
+        sr[(tau + P * s + M) * C + c] = xb[s];
+      }
+      __syncthreads();
 #pragma unroll
-      for (int s = 0; s < Q; ++s) sr[(tau + P * (s + h * Q)) * C + c] = xs[s];
-    }
-    __syncthreads();
+      for (int s = 0; s < Q; ++s) {
+        const int j = tau + P * s;
+        v[s] = inv_pre<R>(tb.ipre, j, M, xa[s], j ? sr[(N - j) * C + c] : (R)0,
+                          sr[(M - j) * C + c], xb[s]);
+      }
+    } else {
 #pragma unroll
-    for (int s = 0; s < Q; ++s) {
-      const int j = tau + P * s;
-      v[s] = inv_pre<R>(tb.ipre, j, M, sr[j * C + c], j ? sr[(N - j) * C + c] : (R)0,
-                        sr[(M - j) * C + c], sr[(M + j) * C + c]);
+      for (int h = 0; h < 2; ++h) {  // rows tau + P s, s < 2Q, in two halves
+        R xs[Q];
+#pragma unroll
+        for (int s = 0; s < Q; ++s) xs[s] = ok ? col[(tau + P * (s + h * Q)) * n0] : (R)0;
+#pragma unroll
+        for (int s = 0; s < Q; ++s) sr[(tau + P * (s + h * Q)) * C + c] = xs[s];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < Q; ++s) {
+        const int j = tau + P * s;
+        v[s] = inv_pre<R>(tb.ipre, j, M, sr[j * C + c], j ? sr[(N - j) * C + c] : (R)0,
+                          sr[(M - j) * C + c], sr[(M + j) * C + c]);
+      }
     }
     __syncthreads();  // the staged tile is read before the transpose reuses the buffer
   }
