@@ -3,7 +3,8 @@
 python -m paper_2404_02433_b300.profile_case --n 512 --precision fp64 --dir 2
 
 Builds the seeded random-sphere RVE (radius 8-20 voxels, fraction 0.25,
-inclusions 1000, seed 2001) at n^3, then runs one solve to relative residual
+inclusions 1000, seed 2001) on an n^3 grid (or an nz x ny x nx grid with
+--shape nz,ny,nx), then runs one solve to relative residual
 1e-8 through the C ABI and prints kappa_eff and the iteration count.  With
 --warm a two-iteration solve runs first (it fills the tile autotuner's cache)
 and only the measured solve lies inside cudaProfilerStart/Stop, so
@@ -28,6 +29,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--shape", type=str, default=None, help="nz,ny,nx instead of n^3")
     ap.add_argument("--dir", type=int, default=2)
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f64"], default="fp64")
     ap.add_argument("--contrast", type=float, default=1000.0)
@@ -35,7 +37,8 @@ def main():
     ap.add_argument("--warm", action="store_true")
     args = ap.parse_args()
     BUILD.build()
-    mask, _ = M.random_spheres((args.n,) * 3, (8.0, 20.0), 0.25, 2001, 0.0, 1.0)
+    shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else (args.n,) * 3
+    mask, _ = M.random_spheres(shape, (8.0, 20.0), 0.25, 2001, 0.0, 1.0)
     k = torch.from_numpy(np.ascontiguousarray(1.0 + (args.contrast - 1.0) * mask)).cuda()
     rve = B.RVE(k)
     del k
@@ -49,7 +52,7 @@ def main():
     torch.cuda.synchronize()
     if args.warm:
         torch.cuda.profiler.stop()
-    print(f"n={args.n} dir={args.dir} {args.precision}: kappa_eff={kap:.10f} "
+    print(f"shape={shape} dir={args.dir} {args.precision}: kappa_eff={kap:.10f} "
           f"iters={info['iters']} relres={info['relres']:.3e} "
           f"solve_ms={info['t_solve_ms']:.1f}")
     rve.close()
